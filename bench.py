@@ -1,0 +1,406 @@
+#!/usr/bin/env python
+"""Benchmark of the diagonal-budgeted Trotterization hot path on GB300.
+
+One bench step = the whole hot path over one synthetic instance: factor
+build from the Pauli terms (host planning + FP64 GPU build), the n_steps x G
+factor applications of the evolution, and the FP64 overlap/norm reduction.
+
+Metric: amplitude-updates/s = sum over the step of n_steps * G * N * R (one
+update = one output amplitude of one factor application to one state).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload heis16|maxcut24|tfim10]
+                  [--impl ours|reference] [--no-cpu-baseline] [--no-c128]
+
+Under torchrun (N > 1) every rank evolves its own replica of the instance
+(the path has no exchange step: replicas only) and rank 0 prints one JSON line
+with value = updates of all ranks / slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "amplitude-updates/s"
+L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="heis16", choices=["heis16", "maxcut24", "tfim10"])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-c128", action="store_true")
+    ap.add_argument("--method", type=int, default=0)
+    ap.add_argument("--tile-bits", type=int, default=0)
+    ap.add_argument("--rhs-block", type=int, default=0)
+    ap.add_argument("--graph", type=int, default=0)
+    return ap.parse_args()
+
+
+def make_job(name, dtype=None):
+    from paper_2606_16959_gb300 import workloads as W
+    if name == "heis16":
+        job = W.heis16(dtype or "c64")
+        desc = "Heisenberg XXX periodic chain n=16, J_i~U[0.5,1.5] (seed 1002), Gaussian state, t=1, 100 steps, budget 8"
+    elif name == "maxcut24":
+        job = W.maxcut24()
+        desc = ("weighted MaxCut random 3-regular n=24 (seed 1003) + 0.5 sum X, 16 states (|+> and Gaussians), "
+                "t=2, 50 steps, budget 4")
+    else:
+        job = W.tfim10()
+        desc = "TFIM open chain n=10, J=h=1, |0..0>, t=1, 10 steps, budget 4"
+    if dtype:
+        job.dtype = dtype
+    return job, desc
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi SM clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 7:
+                    continue
+                try:
+                    sm.append(float(parts[0]))
+                    mx.append(float(parts[1]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[3:7]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(local)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, world):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def algorithmic_bytes(f, job, n_rhs):
+    """Per factor application: s * S_g (factor read once for all states) + 2 s N R
+    (state read and write); summed over the n_steps x G applications."""
+    s = 8 if f.dtype == "c64" else 16
+    N = 1 << f.n_qubits
+    per_step = 0
+    for g in range(f.n_factors):
+        _, _, offs, _ = f.factor(g, values=False)
+        S = int(np.sum(N - np.abs(offs)))
+        per_step += s * S + 2 * s * N * n_rhs
+    return per_step * job.n_steps
+
+
+def time_ours(job, args, world, dtype, rank):
+    """Device-timed steps with inputs resident in HBM.  Returns dict."""
+    import torch
+    from paper_2606_16959_gb300 import hs
+    dev = torch.device("cuda", torch.cuda.current_device())
+    tdt = torch.complex64 if dtype == "c64" else torch.complex128
+    psi0 = torch.from_numpy(np.ascontiguousarray(job.psi0)).to(dev, tdt)
+    if psi0.dim() == 1:
+        psi0 = psi0.unsqueeze(0)
+    R, N = psi0.shape
+    work = torch.empty_like(psi0)
+    out4 = torch.zeros(4, dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    opts = dict(method=args.method, tile_bits=args.tile_bits, rhs_block=args.rhs_block, use_graph=bool(args.graph))
+    E = torch.cuda.Event
+
+    def step(keep):
+        work.copy_(psi0)
+        f = hs.hs_build_factors(job.ham.labels, job.ham.coeffs, job.t, job.n_steps, job.budget, dtype)
+        e0, e1 = E(enable_timing=True), E(enable_timing=True)
+        e0.record()
+        hs.hs_evolve_ex(f, work, job.n_steps, **opts)
+        e1.record()
+        hs.hs_inner_device(psi0[0], work[0], out4)
+        keep.append(f)
+        return e0, e1
+
+    keep = []
+    for _ in range(args.warmup):
+        step(keep)
+    torch.cuda.synchronize()
+    f0 = keep[0]
+    n_sweeps, n_plain, tb, rb = hs.hs_evolve_plan(f0, R, job.n_steps, **opts)
+    alg = algorithmic_bytes(f0, job, R)
+    for f in keep:
+        f.close()
+    keep = []
+    step_ms, evolve_ms = [], []
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    barrier(world)
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+    for _ in range(args.steps):
+        flush.zero_()
+        s0, s1 = E(enable_timing=True), E(enable_timing=True)
+        s0.record()
+        e0, e1 = step(keep)
+        s1.record()
+        torch.cuda.synchronize()
+        step_ms.append(s0.elapsed_time(s1))
+        evolve_ms.append(e0.elapsed_time(e1))
+        keep[-1].close()
+    clocks = sampler.stop() if sampler else None
+    barrier(world)
+    fid = out4.cpu().numpy()
+    G = f0.n_factors
+    units = job.n_steps * G * N * R
+    total_ms = max_over_ranks(sum(step_ms), world)
+    launches_per_step = 2 + n_sweeps + n_plain + 2
+    return dict(units=units, G=G, R=R, N=N, step_ms=step_ms, evolve_ms=evolve_ms, total_ms=total_ms,
+                n_sweeps=n_sweeps, n_plain=n_plain, tile_bits=tb, rhs_block=rb, alg_bytes=alg,
+                launches=launches_per_step * args.steps, clocks=clocks, overlap=fid)
+
+
+def time_e2e(job, args, dtype):
+    """Same metric through the public API with pinned host buffers: H2D of the
+    initial states, build, evolve, norm reduction, D2H of the final states."""
+    import torch
+    from paper_2606_16959_gb300 import hs
+    dev = torch.device("cuda", torch.cuda.current_device())
+    tdt = torch.complex64 if dtype == "c64" else torch.complex128
+    host_in = torch.from_numpy(np.ascontiguousarray(job.psi0)).to(tdt)
+    if host_in.dim() == 1:
+        host_in = host_in.unsqueeze(0)
+    host_in = host_in.pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    work = torch.empty(host_in.shape, dtype=tdt, device=dev)
+    out4 = torch.zeros(4, dtype=torch.float64, device=dev)
+    out4_h = torch.zeros(4, dtype=torch.float64).pin_memory()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    opts = dict(method=args.method, tile_bits=args.tile_bits, rhs_block=args.rhs_block, use_graph=bool(args.graph))
+
+    def step():
+        work.copy_(host_in, non_blocking=True)
+        f = hs.hs_build_factors(job.ham.labels, job.ham.coeffs, job.t, job.n_steps, job.budget, dtype)
+        hs.hs_evolve_ex(f, work, job.n_steps, **opts)
+        hs.hs_inner_device(work[0], work[0], out4)
+        host_out.copy_(work, non_blocking=True)
+        out4_h.copy_(out4, non_blocking=True)
+        return f
+
+    fs = [step() for _ in range(max(1, args.warmup))]
+    torch.cuda.synchronize()
+    for f in fs:
+        f.close()
+    times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record()
+        f = step()
+        s1.record()
+        torch.cuda.synchronize()
+        times.append(s0.elapsed_time(s1))
+        f.close()
+    m = len(job.ham.labels)
+    term_bytes = 28 * m + 256  # masks, coefficients and group tables uploaded by the build
+    return dict(ms=statistics.mean(times), h2d=int(host_in.numel() * host_in.element_size()) + term_bytes,
+                d2h=int(host_out.numel() * host_out.element_size()) + 32)
+
+
+def oracle_sample(job, G, budget_s=15.0):
+    """Time the FP64 oracle (single-threaded C) on a bounded sample of the same
+    workload: whole Trotter steps of state 0, as many as fit ~budget_s."""
+    import oracle
+    x, z, n = oracle.parse_terms(job.ham.labels)
+    psi = np.asarray(job.psi0)
+    psi = psi[0] if psi.ndim == 2 else psi
+    N = 1 << n
+    dt = job.t / job.n_steps
+    t0 = time.perf_counter()
+    oracle.evolve_direct(x, z, job.ham.coeffs, dt, 1, psi)
+    t1 = time.perf_counter() - t0
+    k = int(max(1, min(job.n_steps, budget_s // max(t1, 1e-9))))
+    if k > 1:
+        t0 = time.perf_counter()
+        oracle.evolve_direct(x, z, job.ham.coeffs, dt * k, k, psi)
+        t1 = time.perf_counter() - t0
+    else:
+        k = 1
+    units = k * G * N
+    R = psi.shape[0] if np.asarray(job.psi0).ndim == 2 else 1
+    R = np.asarray(job.psi0).shape[0] if np.asarray(job.psi0).ndim == 2 else 1
+    return dict(value=units / t1, seconds=t1, steps=k,
+                sample=f"{k} of {job.n_steps} Trotter steps of state 0 (of {R}), direct term-by-term FP64 "
+                       f"evolution, single thread; units counted as steps x G={G} factors x N={N}")
+
+
+def config_of(args, job, desc, res=None):
+    c = {"workload": args.workload, "description": desc, "n_qubits": job.ham.n_qubits, "n_terms": len(job.ham.labels),
+         "n_steps": job.n_steps, "diag_budget": job.budget, "n_rhs": int(np.asarray(job.psi0).shape[0]) if np.asarray(job.psi0).ndim == 2 else 1,
+         "t": job.t, "l2": "flushed (512 MiB write) before every timed step"}
+    if res:
+        c.update({"n_factors": res["G"], "tile_bits": res["tile_bits"], "rhs_block": res["rhs_block"],
+                  "sweep_launches_per_step": res["n_sweeps"], "plain_launches_per_step": res["n_plain"]})
+    return c
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    job, desc = make_job(args.workload)
+    from paper_2606_16959_gb300 import hs
+    x, z, n = __import__("oracle").parse_terms(job.ham.labels)
+    G = len(hs.hs_plan_factors(x, z, n, job.budget)[0])
+    per_step_budget = max(1.0, 150.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        oracle_sample(job, G, per_step_budget)
+    vals, secs = [], []
+    for _ in range(args.steps):
+        r = oracle_sample(job, G, per_step_budget)
+        vals.append(r["value"])
+        secs.append(r["seconds"])
+    v = len(vals) / sum(1.0 / x for x in vals)
+    line = {"metric": METRIC, "value": v, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000 * statistics.mean(secs), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic", "impl": "reference",
+            "config": config_of(args, job, desc),
+            "cpu_baseline": {"value": v, "unit": METRIC, "cores": 1, "kind": "oracle", "sample": r["sample"]},
+            "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_setup(args)
+    from paper_2606_16959_gb300 import hs
+    hs.lib()
+    job, desc = make_job(args.workload)
+    dtype = job.dtype
+    res = time_ours(job, args, world, dtype, rank)
+    K = args.steps
+    value = res["units"] * K * world / (res["total_ms"] / 1000.0)
+    ms = res["total_ms"] / K
+    e2e = time_e2e(job, args, dtype)
+    hbm, peak_kind = peaks()
+    launches_evolve = res["n_sweeps"] + res["n_plain"]
+    avg_launch_s = statistics.mean(res["evolve_ms"]) / 1000.0 / max(1, launches_evolve)
+    per_launch_bytes = res["alg_bytes"] / max(1, launches_evolve)
+    achieved = per_launch_bytes / avg_launch_s / 1e9
+    line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": K, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": dtype, "data": "synthetic", "config": config_of(args, job, desc, res),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                         "traffic": None, "peak_source": peak_kind,
+                         "kernel": "sweep_kernel" if res["n_sweeps"] else "apply_plain_kernel",
+                         "algorithmic_bytes_per_launch": per_launch_bytes,
+                         "avg_launch_us": avg_launch_s * 1e6},
+            "e2e": {"value": res["units"] / (e2e["ms"] / 1000.0), "unit": METRIC,
+                    "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"]},
+            "gpu_launches": res["launches"], "clocks": res["clocks"],
+            "evolve_ms_per_step": statistics.mean(res["evolve_ms"])}
+    if args.workload == "heis16" and not args.no_c128 and world >= 1:
+        r2 = time_ours(make_job(args.workload, "c128")[0], args, world, "c128", rank)
+        line["c128"] = {"value": r2["units"] * K * world / (r2["total_ms"] / 1000.0),
+                        "ms_per_step": r2["total_ms"] / K, "evolve_ms_per_step": statistics.mean(r2["evolve_ms"])}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = oracle_sample(job, res["G"])
+        line["cpu_baseline"] = {"value": cb["value"], "unit": METRIC, "cores": 1, "kind": "oracle",
+                                "sample": cb["sample"]}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

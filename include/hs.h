@@ -1,0 +1,181 @@
+/*
+ * hs.h -- C ABI of libhs: diagonal-budgeted Trotterization on one GB300 GPU.
+ *
+ * The library builds the per-step Trotter factors of a Pauli-sum Hamiltonian
+ * (Eq. 3, Eq. 4) grouped under a diagonal budget (Sec. 3.1, Eq. 5), stores each
+ * factor in the compact diagonal layout of Eq. 6 / Tab. 1 (an offset list plus
+ * dense complex diagonals of length N - |d|), and applies the factors to
+ * 2^n-amplitude state vectors for many steps (the evolution loop of Alg. 3,
+ * with the diagonal-times-vector product of Alg. 1 as the unit of work).
+ *
+ * Conventions used by every entry point:
+ *   - Pauli labels are strings over {I,X,Y,Z}, all of length n_qubits; the
+ *     rightmost character acts on qubit 0, which is bit 0 of the basis index.
+ *     A term's masks are x (X or Y present) and z (Z or Y present); its action
+ *     is P|b> = i^popcount(x&z) (-1)^popcount(z&b) |b xor x>.
+ *   - Coefficients are real (H is Hermitian).  theta_j = c_j * (t / n_steps);
+ *     term j's rotation is R_j = cos(theta_j) I - i sin(theta_j) P_j, and term 0
+ *     acts first, within a factor and within a step.
+ *   - Grouping: terms are taken in input order; a term joins the open factor
+ *     iff the factor is empty, or the factor's structural offset count after
+ *     adding it stays <= diag_budget, or adding it leaves the offset set
+ *     unchanged.  A single term above the budget still forms its own factor.
+ *   - Offsets are d = col - row; a factor's offsets are listed 0 first, then by
+ *     |d| ascending, negative before positive (Tab. 1 gives [0, -3, 3]).
+ *     Element i of diagonal d holds entry (row, col) with i = min(row, col).
+ *   - State vectors are caller-owned DEVICE buffers of interleaved complex
+ *     numbers (float2 for HS_C64, double2 for HS_C128), n_rhs states of 2^n
+ *     amplitudes each, rhs-major and contiguous, 16-byte aligned.
+ *   - cuda_stream is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Unless stated otherwise a call only enqueues work on it.
+ *   - Every entry point returns HS_OK (0) or a negative code; on failure
+ *     hs_last_error() returns a message (thread-local), no output object is
+ *     created, and a call rejected before any launch leaves caller buffers
+ *     untouched.
+ *   - The library never frees caller memory.  hs_factors objects are owned
+ *     by the library (device-resident, immutable after the build) and freed
+ *     only by hs_free_factors.
+ */
+#ifndef HS_H
+#define HS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  HS_OK = 0,
+  HS_EINVAL = -1,   /* bad argument: label, length, n_qubits, t, steps, budget, coefficient */
+  HS_ENOMEM = -2,   /* device allocation failed */
+  HS_ECUDA = -3,    /* a CUDA runtime call or kernel launch failed */
+  HS_ETIMEOUT = -4, /* a bounded device-side wait ran out */
+  HS_EDTYPE = -5    /* dtype mismatch between arguments */
+};
+
+typedef enum { HS_C64 = 1, HS_C128 = 2 } hs_dtype;
+
+#define HS_MAX_QUBITS 30
+
+/* Opaque factor set: G factors for one (H, t, n_steps, diag_budget, dtype). */
+typedef struct hs_factors hs_factors;
+
+/* Build the per-step factors of H = sum_j coeffs[j] P_j for time step
+ * t / n_steps (Eq. 4) under diag_budget (Eq. 5 read as a cap on each factor's
+ * diagonal count), in the compact layout of Eq. 6.
+ *   pauli_terms : n_terms NUL-terminated labels (see conventions); host memory.
+ *   coeffs      : n_terms finite real coefficients; host memory.
+ *   t > 0 and finite; n_steps >= 1; diag_budget >= 1.
+ *   dtype       : storage precision of the factor values.  Values are always
+ *                 computed in FP64 on the GPU (cos/sin of the angles and the
+ *                 group products) and rounded once to FP32 for HS_C64.
+ *   out         : receives the new object; set to NULL on failure.
+ * The grouping and offsets are planned on the host; the values are computed
+ * by kernels enqueued on cuda_stream.  Errors: HS_EINVAL (invalid label,
+ * labels of different lengths, n_qubits outside 1..HS_MAX_QUBITS, non-finite
+ * or non-positive t, n_steps < 1, diag_budget < 1, non-finite coefficient,
+ * a factor with more than 4096 diagonals or an x-mask set above 64 elements),
+ * HS_ENOMEM, HS_ECUDA. */
+int hs_build_factors(const char* const* pauli_terms, const double* coeffs, size_t n_terms, double t,
+                     int n_steps, int diag_budget, hs_dtype dtype, void* cuda_stream, hs_factors** out);
+
+/* Same as hs_build_factors with pre-parsed terms: x[j], z[j] are the flip and
+ * phase masks of term j (bits >= n_qubits must be zero). */
+int hs_build_factors_masks(const uint64_t* x, const uint64_t* z, const double* coeffs, size_t n_terms,
+                           int n_qubits, double t, int n_steps, int diag_budget, hs_dtype dtype,
+                           void* cuda_stream, hs_factors** out);
+
+/* Structural dry run on the host only (no GPU call): the grouping, each
+ * factor's offsets in canonical order and the device bytes of the padded
+ * factor values -- what the diagonal-set estimation paragraph (Sec. 3.2)
+ * computes before any numeric work so that storage is allocated once.
+ * Same grouping rule and limits as hs_build_factors (coefficients are not
+ * needed).  *n_factors and *n_offsets are always set on success; the arrays
+ * (group_first/group_last/n_diags: capacity_factors entries, offsets:
+ * capacity_offsets entries) are filled only if they are non-NULL and large
+ * enough, otherwise left untouched.  value_bytes may be NULL.
+ * Errors: HS_EINVAL, HS_EDTYPE. */
+int hs_plan_factors(const uint64_t* x, const uint64_t* z, size_t n_terms, int n_qubits, int diag_budget,
+                    hs_dtype dtype, int* n_factors, int* n_offsets, int* group_first, int* group_last, int* n_diags,
+                    int64_t* offsets, int64_t* value_bytes, int capacity_factors, int capacity_offsets);
+
+/* Evolve psi in place by n_steps Trotter steps: for each step, apply the
+ * factors F_0, ..., F_{G-1} in order (Alg. 3's loop, x <- U x, with U the
+ * ordered product of the grouped factors).  psi: device buffer of n_rhs
+ * states (see conventions), dtype equal to the factors'.  n_steps >= 0
+ * (0 is a no-op), n_rhs >= 1.  Work is enqueued on cuda_stream; the call may
+ * allocate a temporary device buffer of one state set when a factor cannot be
+ * applied tile-locally, and frees it stream-ordered.  Errors: HS_EINVAL,
+ * HS_ENOMEM, HS_ECUDA. */
+int hs_evolve(const hs_factors* f, void* psi, int n_rhs, int n_steps, void* cuda_stream);
+
+/* Evolution method selector for hs_evolve_ex. */
+typedef enum {
+  HS_METHOD_AUTO = 0,  /* fused tile sweeps where possible (same as hs_evolve) */
+  HS_METHOD_PLAIN = 1, /* one row-parallel diagonal-times-vector launch per factor application */
+  HS_METHOD_FUSED = 2  /* tile sweeps; factors that do not fit a tile fall back to PLAIN */
+} hs_method;
+
+typedef struct {
+  hs_method method;
+  int tile_bits;  /* log2 amplitudes per tile for FUSED; 0 = library choice */
+  int rhs_block;  /* states per tile for FUSED; 0 = library choice */
+  int use_graph;  /* 1: replay the launch sequence as a cached CUDA graph; 0: direct launches */
+} hs_evolve_opts;
+
+/* hs_evolve with an explicit method and tiling (opts may be NULL = AUTO). */
+int hs_evolve_ex(const hs_factors* f, void* psi, int n_rhs, int n_steps, const hs_evolve_opts* opts,
+                 void* cuda_stream);
+
+/* Launch plan of hs_evolve_ex for these arguments, computed on the host
+ * without launching anything: the number of fused tile-sweep launches, of
+ * plain one-factor launches, and the tile_bits / rhs_block that would be
+ * used.  Output pointers may be NULL.  Errors: HS_EINVAL. */
+int hs_evolve_plan(const hs_factors* f, int n_rhs, int n_steps, const hs_evolve_opts* opts, int* n_sweeps,
+                   int* n_plain, int* tile_bits, int* rhs_block);
+
+/* y = F_g x for one factor (Alg. 1: the sum over diagonals of the shifted
+ * element-wise products), out of place.  x and y are device buffers of n_rhs
+ * states of the factors' dtype and must not overlap.  Errors: HS_EINVAL. */
+int hs_apply_factor(const hs_factors* f, int g, const void* x, void* y, int n_rhs, void* cuda_stream);
+
+/* State fidelity (evaluation section, Metrics): |<a|b>|^2 / (|a|^2 |b|^2),
+ * accumulated in FP64 whatever the storage dtype.  a, b: device buffers of one
+ * state each (2^n_qubits amplitudes).  fid, norm_a2, norm_b2: host outputs;
+ * norm pointers may be NULL.  Synchronises cuda_stream.  Errors: HS_EINVAL,
+ * HS_ECUDA. */
+int hs_fidelity(const void* a, const void* b, int n_qubits, hs_dtype dtype, void* cuda_stream, double* fid,
+                double* norm_a2, double* norm_b2);
+
+/* <a|b> = sum conj(a_i) b_i and |a|^2, |b|^2 in FP64, written to a DEVICE
+ * buffer out[4] = {re, im, |a|^2, |b|^2} without synchronising (usable inside
+ * stream capture).  Errors: HS_EINVAL, HS_ECUDA. */
+int hs_inner_device(const void* a, const void* b, int n_qubits, hs_dtype dtype, double* out_device,
+                    void* cuda_stream);
+
+/* Introspection.  hs_factors_info: number of factors, qubits, steps the
+ * object was built for, dtype, and total device bytes of factor values. */
+int hs_factors_info(const hs_factors* f, int* n_factors, int* n_qubits, int* n_steps, hs_dtype* dtype,
+                    int64_t* value_bytes);
+
+/* Factor g's term range [term_first, term_last), diagonal count, offsets in
+ * canonical order and values as the Eq. 6 view: FP64 interleaved complex,
+ * diagonal after diagonal, N - |d| entries each, no padding (2 * S_g doubles,
+ * S_g = sum_k (N - |d_k|)).  offsets / values may be NULL to skip them.
+ * Copies from the device; synchronises with the device. */
+int hs_factor_get(const hs_factors* f, int g, int* term_first, int* term_last, int* n_diags, int64_t* offsets,
+                  double* values);
+
+/* Free a factor set (NULL is a no-op).  Synchronises the device first. */
+void hs_free_factors(hs_factors* f);
+
+/* Message for the last failing call on this thread ("" if none). */
+const char* hs_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HS_H */

@@ -1,0 +1,459 @@
+// C ABI of libhs (declared in include/hs.h).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "hs_internal.h"
+
+namespace hs {
+size_t inner_scratch_bytes();
+cudaError_t launch_inner_scratch(const void* a, const void* b, int64_t N, hs_dtype dt, double* d_out4, void* scratch,
+                                 cudaStream_t s);
+}  // namespace hs
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(e == cudaErrorMemoryAllocation ? HS_ENOMEM : HS_ECUDA,
+              std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
+}
+
+bool valid_dtype(hs_dtype d) { return d == HS_C64 || d == HS_C128; }
+
+// Minimum number of contiguous low bits in a tile, so that every warp access
+// along a diagonal or the state covers whole 128-byte lines.
+int min_low_bits(hs_dtype dt) { return dt == HS_C64 ? 4 : 3; }
+
+void release(hs_factors* f) {
+  if (!f) return;
+  {
+    std::lock_guard<std::mutex> lk(f->graph_mu);
+    for (auto& kv : f->graphs) cudaGraphExecDestroy(kv.second);
+    f->graphs.clear();
+  }
+  cudaFree(f->d_vals);
+  cudaFree(f->d_offs);
+  cudaFree(f->d_rowbase);
+  cudaFree(f->d_fac_D);
+  cudaFree(f->d_fac_diag0);
+  delete f;
+}
+
+// Enqueue the launches of one evolution on stream s.
+int enqueue_evolve(const hs_factors* f, void* psi, int n_rhs, int n_steps, hs_method method, int tile_bits,
+                   int rhs_block, void* scratch, cudaStream_t s) {
+  const hs::Plan& p = f->plan;
+  const bool fused = method != HS_METHOD_PLAIN;
+  std::vector<hs::Sweep> sw = hs::plan_sweeps(p, n_steps, tile_bits, min_low_bits(f->dtype), fused);
+  void* cur = psi;
+  void* other = scratch;
+  const uint64_t all = (1ull << p.n_qubits) - 1;
+  for (const hs::Sweep& w : sw) {
+    cudaError_t e;
+    if (w.fused) {
+      hs::SweepLaunch L;
+      L.src = cur;
+      L.dst = cur;
+      L.n_rhs = n_rhs;
+      L.rhs_block = rhs_block;
+      L.tile_bits = std::min(tile_bits, p.n_qubits);
+      L.local = hs::runs_of(w.local_mask, p.n_qubits);
+      L.rest = hs::runs_of(~uint64_t(w.local_mask) & all, p.n_qubits);
+      L.n_factors = int(w.factors.size());
+      for (int i = 0; i < L.n_factors; ++i) L.factors[i] = w.factors[i];
+      e = hs::launch_sweep(f, L, s);
+    } else {
+      if (!other) return fail(HS_EINVAL, "internal: plain application without scratch");
+      e = hs::launch_apply_plain(f, w.factors[0], cur, other, n_rhs, s);
+      std::swap(cur, other);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "launch");
+  }
+  if (cur != psi) {
+    cudaError_t e = cudaMemcpyAsync(psi, cur, size_t(n_rhs) * size_t(p.N) * hs::elem_bytes(f->dtype),
+                                    cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
+  }
+  return HS_OK;
+}
+
+bool needs_scratch(const hs_factors* f, int n_steps, hs_method method, int tile_bits) {
+  if (method == HS_METHOD_PLAIN) return n_steps > 0;
+  for (const hs::Group& g : f->plan.groups)
+    if (__builtin_popcountll(g.span | ((1ull << std::min(min_low_bits(f->dtype), f->plan.n_qubits)) - 1)) >
+        std::min(tile_bits, f->plan.n_qubits))
+      return n_steps > 0;
+  return false;
+}
+
+int pick_rhs_block(hs_dtype dt, int n_rhs) {
+  int rb = 1;
+  const int cap = dt == HS_C64 ? 16 : 8;
+  while (rb * 2 <= n_rhs && rb * 2 <= cap) rb *= 2;
+  return rb;
+}
+
+int pick_tile_bits(const hs_factors* f, int rhs_block) {
+  const int n = f->plan.n_qubits;
+  int t = hs::max_tile_bits(f->dtype, rhs_block);
+  // keep at least ~2 CTAs per SM when the state allows it
+  int cap = n - 9;
+  if (cap < min_low_bits(f->dtype) + 4) cap = min_low_bits(f->dtype) + 4;
+  if (t > cap) t = cap;
+  if (t > n) t = n;
+  return t;
+}
+
+}  // namespace
+
+bool hs_factors::GraphKey::operator<(const GraphKey& o) const {
+  return std::tie(psi, n_rhs, n_steps, method, tile_bits, rhs_block, stream) <
+         std::tie(o.psi, o.n_rhs, o.n_steps, o.method, o.tile_bits, o.rhs_block, o.stream);
+}
+
+extern "C" {
+
+const char* hs_last_error(void) { return g_err.c_str(); }
+
+int hs_build_factors_masks(const uint64_t* x, const uint64_t* z, const double* coeffs, size_t n_terms, int n_qubits,
+                           double t, int n_steps, int diag_budget, hs_dtype dtype, void* cuda_stream,
+                           hs_factors** out) {
+  if (!out) return fail(HS_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!x || !z || !coeffs) return fail(HS_EINVAL, "null term arrays");
+  if (!valid_dtype(dtype)) return fail(HS_EDTYPE, "dtype must be HS_C64 or HS_C128");
+  if (!(std::isfinite(t) && t > 0)) return fail(HS_EINVAL, "t must be finite and > 0");
+  if (n_steps < 1) return fail(HS_EINVAL, "n_steps must be >= 1");
+  if (diag_budget < 1) return fail(HS_EINVAL, "diag_budget must be >= 1");
+  std::unique_ptr<hs_factors> f(new hs_factors());
+  std::string err;
+  int rc = hs::make_plan(x, z, coeffs, n_terms, n_qubits, diag_budget, dtype, f->plan, &err);
+  if (rc != HS_OK) return fail(rc, err);
+  f->dtype = dtype;
+  f->n_steps = n_steps;
+  f->t = t;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+  cudaError_t e = cudaGetDevice(&f->device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+
+  const hs::Plan& p = f->plan;
+  const int G = int(p.groups.size());
+  const int nd = int(p.offs.size());
+  const size_t vbytes = size_t(p.total_elems) * hs::elem_bytes(dtype);
+  hs_factors* fp = f.get();
+  auto guard = [&](cudaError_t e2, const char* what) -> int { return e2 == cudaSuccess ? HS_OK : cuda_fail(e2, what); };
+  if ((rc = guard(cudaMalloc(&fp->d_vals, vbytes), "cudaMalloc(values)"))) { release(f.release()); return rc; }
+  if ((rc = guard(cudaMalloc(&fp->d_offs, nd * sizeof(int64_t)), "cudaMalloc")) ||
+      (rc = guard(cudaMalloc(&fp->d_rowbase, nd * sizeof(int64_t)), "cudaMalloc")) ||
+      (rc = guard(cudaMalloc(&fp->d_fac_D, G * sizeof(int)), "cudaMalloc")) ||
+      (rc = guard(cudaMalloc(&fp->d_fac_diag0, G * sizeof(int)), "cudaMalloc"))) {
+    release(f.release());
+    return rc;
+  }
+  // Term and group tables for the build, packed in one temporary buffer.
+  const size_t m = n_terms;
+  std::vector<int> fD(G), fd0(G), gfirst(G), glast(G), xdim(G), pivot(G * hs::kMaxXDim, 0);
+  std::vector<uint64_t> basis(G * hs::kMaxXDim, 0);
+  for (int g = 0; g < G; ++g) {
+    const hs::Group& gr = p.groups[g];
+    fD[g] = gr.D;
+    fd0[g] = gr.diag0;
+    gfirst[g] = gr.first;
+    glast[g] = gr.last;
+    xdim[g] = gr.xdim;
+    for (int i = 0; i < gr.xdim; ++i) {
+      basis[g * hs::kMaxXDim + i] = gr.basis[i];
+      pivot[g * hs::kMaxXDim + i] = gr.pivot[i];
+    }
+  }
+  std::vector<unsigned char> blob;
+  auto put = [&](const void* src, size_t bytes) {
+    size_t off = (blob.size() + 15) / 16 * 16;
+    blob.resize(off + bytes);
+    if (bytes) std::memcpy(blob.data() + off, src, bytes);
+    return off;
+  };
+  size_t o_x = put(p.x.data(), m * 8), o_z = put(p.z.data(), m * 8), o_c = put(p.coeff.data(), m * 8);
+  size_t o_cx = put(p.term_cx.data(), m * 4), o_gf = put(gfirst.data(), G * 4), o_gl = put(glast.data(), G * 4);
+  size_t o_b = put(basis.data(), basis.size() * 8), o_xd = put(xdim.data(), G * 4), o_pv = put(pivot.data(), pivot.size() * 4);
+  size_t o_cs = put(nullptr, 0);
+  blob.resize(o_cs + m * 16);
+  unsigned char* d_blob = nullptr;
+  if ((rc = guard(cudaMallocAsync((void**)&d_blob, blob.size(), s), "cudaMallocAsync"))) { release(f.release()); return rc; }
+  if ((rc = guard(cudaMemcpyAsync(d_blob, blob.data(), o_cs, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync")) ||
+      (rc = guard(cudaMemcpyAsync(fp->d_offs, p.offs.data(), nd * 8, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync")) ||
+      (rc = guard(cudaMemcpyAsync(fp->d_rowbase, p.rowbase.data(), nd * 8, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync")) ||
+      (rc = guard(cudaMemcpyAsync(fp->d_fac_D, fD.data(), G * 4, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync")) ||
+      (rc = guard(cudaMemcpyAsync(fp->d_fac_diag0, fd0.data(), G * 4, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync"))) {
+    cudaFreeAsync(d_blob, s);
+    cudaStreamSynchronize(s);
+    release(f.release());
+    return rc;
+  }
+  const double dt = t / double(n_steps);
+  double* d_cs = reinterpret_cast<double*>(d_blob + o_cs);
+  e = hs::launch_sincos(reinterpret_cast<const double*>(d_blob + o_c), dt, d_cs, int(m), s);
+  if (e == cudaSuccess)
+    e = hs::launch_build(fp, d_cs, reinterpret_cast<const uint64_t*>(d_blob + o_x),
+                         reinterpret_cast<const uint64_t*>(d_blob + o_z), reinterpret_cast<const uint32_t*>(d_blob + o_cx),
+                         reinterpret_cast<const int*>(d_blob + o_gf), reinterpret_cast<const int*>(d_blob + o_gl),
+                         reinterpret_cast<const uint64_t*>(d_blob + o_b), reinterpret_cast<const int*>(d_blob + o_xd),
+                         reinterpret_cast<const int*>(d_blob + o_pv), s);
+  cudaError_t e2 = cudaFreeAsync(d_blob, s);
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    cudaStreamSynchronize(s);
+    release(f.release());
+    return cuda_fail(e != cudaSuccess ? e : e2, "factor build launch");
+  }
+  *out = f.release();
+  return HS_OK;
+}
+
+int hs_build_factors(const char* const* pauli_terms, const double* coeffs, size_t n_terms, double t, int n_steps,
+                     int diag_budget, hs_dtype dtype, void* cuda_stream, hs_factors** out) {
+  if (!out) return fail(HS_EINVAL, "out is NULL");
+  *out = nullptr;
+  std::vector<uint64_t> x, z;
+  int nq = 0;
+  std::string err;
+  int rc = hs::parse_labels(pauli_terms, n_terms, x, z, nq, &err);
+  if (rc != HS_OK) return fail(rc, err);
+  return hs_build_factors_masks(x.data(), z.data(), coeffs, n_terms, nq, t, n_steps, diag_budget, dtype, cuda_stream,
+                                out);
+}
+
+int hs_plan_factors(const uint64_t* x, const uint64_t* z, size_t n_terms, int n_qubits, int diag_budget,
+                    hs_dtype dtype, int* n_factors, int* n_offsets, int* group_first, int* group_last, int* n_diags,
+                    int64_t* offsets, int64_t* value_bytes, int capacity_factors, int capacity_offsets) {
+  if (!x || !z || !n_factors || !n_offsets) return fail(HS_EINVAL, "null argument");
+  if (!valid_dtype(dtype)) return fail(HS_EDTYPE, "dtype must be HS_C64 or HS_C128");
+  hs::Plan p;
+  std::string err;
+  int rc = hs::make_plan(x, z, nullptr, n_terms, n_qubits, diag_budget, dtype, p, &err);
+  if (rc != HS_OK) return fail(rc, err);
+  const int G = int(p.groups.size());
+  *n_factors = G;
+  *n_offsets = int(p.offs.size());
+  if (value_bytes) *value_bytes = p.total_elems * int64_t(hs::elem_bytes(dtype));
+  if (group_first && group_last && n_diags && capacity_factors >= G)
+    for (int g = 0; g < G; ++g) {
+      group_first[g] = p.groups[g].first;
+      group_last[g] = p.groups[g].last;
+      n_diags[g] = p.groups[g].D;
+    }
+  if (offsets && capacity_offsets >= int(p.offs.size()))
+    for (size_t k = 0; k < p.offs.size(); ++k) offsets[k] = p.offs[k];
+  return HS_OK;
+}
+
+// Resolve evolve options: method, tile bits, rhs block.
+int resolve_opts(const hs_factors* f, int n_rhs, const hs_evolve_opts* opts, hs_evolve_opts& o, int& tb, int& rb) {
+  o = hs_evolve_opts{HS_METHOD_AUTO, 0, 0, 0};
+  if (opts) o = *opts;
+  if (o.method != HS_METHOD_AUTO && o.method != HS_METHOD_PLAIN && o.method != HS_METHOD_FUSED)
+    return fail(HS_EINVAL, "unknown method");
+  rb = o.rhs_block > 0 ? o.rhs_block : pick_rhs_block(f->dtype, n_rhs);
+  if (rb != 1 && rb != 2 && rb != 4 && rb != 8 && !(rb == 16 && f->dtype == HS_C64))
+    return fail(HS_EINVAL, "rhs_block must be 1, 2, 4, 8 (or 16 for complex64)");
+  tb = o.tile_bits > 0 ? o.tile_bits : pick_tile_bits(f, rb);
+  if (tb > f->plan.n_qubits) tb = f->plan.n_qubits;
+  if (tb > hs::max_tile_bits(f->dtype, rb))
+    return fail(HS_EINVAL, "tile_bits exceeds the shared-memory tile for this rhs_block");
+  if (tb < 1) return fail(HS_EINVAL, "tile_bits must be >= 1");
+  return HS_OK;
+}
+
+int hs_evolve_plan(const hs_factors* f, int n_rhs, int n_steps, const hs_evolve_opts* opts, int* n_sweeps,
+                   int* n_plain, int* tile_bits, int* rhs_block) {
+  if (!f) return fail(HS_EINVAL, "factors is NULL");
+  if (n_rhs < 1 || n_steps < 0) return fail(HS_EINVAL, "n_rhs must be >= 1 and n_steps >= 0");
+  hs_evolve_opts o;
+  int tb = 0, rb = 0;
+  int rc = resolve_opts(f, n_rhs, opts, o, tb, rb);
+  if (rc != HS_OK) return rc;
+  std::vector<hs::Sweep> sw = hs::plan_sweeps(f->plan, n_steps, tb, min_low_bits(f->dtype), o.method != HS_METHOD_PLAIN);
+  int ns = 0, np = 0;
+  for (const hs::Sweep& w : sw) (w.fused ? ns : np) += 1;
+  if (n_sweeps) *n_sweeps = ns;
+  if (n_plain) *n_plain = np;
+  if (tile_bits) *tile_bits = tb;
+  if (rhs_block) *rhs_block = rb;
+  return HS_OK;
+}
+
+int hs_evolve_ex(const hs_factors* f, void* psi, int n_rhs, int n_steps, const hs_evolve_opts* opts,
+                 void* cuda_stream) {
+  if (!f) return fail(HS_EINVAL, "factors is NULL");
+  if (!psi) return fail(HS_EINVAL, "psi is NULL");
+  if (n_rhs < 1) return fail(HS_EINVAL, "n_rhs must be >= 1");
+  if (n_steps < 0) return fail(HS_EINVAL, "n_steps must be >= 0");
+  if (reinterpret_cast<uintptr_t>(psi) % 16) return fail(HS_EINVAL, "psi must be 16-byte aligned");
+  hs_evolve_opts o;
+  int tb = 0, rb = 0;
+  int rc0 = resolve_opts(f, n_rhs, opts, o, tb, rb);
+  if (rc0 != HS_OK) return rc0;
+  if (n_steps == 0) return HS_OK;
+  {
+    cudaError_t e = hs::prepare_kernels();
+    if (e != cudaSuccess) return cuda_fail(e, "kernel attributes");
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+  const size_t state_bytes = size_t(n_rhs) * size_t(f->plan.N) * hs::elem_bytes(f->dtype);
+  const bool scratch_needed = needs_scratch(f, n_steps, o.method, tb);
+
+  if (o.use_graph) {
+    hs_factors::GraphKey key{psi, n_rhs, n_steps, int(o.method), tb, rb, nullptr};
+    cudaGraphExec_t exec = nullptr;
+    {
+      std::lock_guard<std::mutex> lk(f->graph_mu);
+      auto it = f->graphs.find(key);
+      if (it != f->graphs.end()) exec = it->second;
+    }
+    if (!exec) {
+      if (scratch_needed) return fail(HS_EINVAL, "use_graph needs a schedule without plain fallbacks");
+      cudaStream_t cs;
+      cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
+      e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) { cudaStreamDestroy(cs); return cuda_fail(e, "cudaStreamBeginCapture"); }
+      int rc = enqueue_evolve(f, psi, n_rhs, n_steps, o.method, tb, rb, nullptr, cs);
+      cudaGraph_t graph = nullptr;
+      e = cudaStreamEndCapture(cs, &graph);
+      cudaStreamDestroy(cs);
+      if (rc != HS_OK) { if (graph) cudaGraphDestroy(graph); return rc; }
+      if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+      e = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+      std::lock_guard<std::mutex> lk(f->graph_mu);
+      f->graphs[key] = exec;
+    }
+    cudaError_t e = cudaGraphLaunch(exec, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+    return HS_OK;
+  }
+
+  void* scratch = nullptr;
+  if (scratch_needed) {
+    cudaError_t e = cudaMallocAsync(&scratch, state_bytes, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(scratch state)");
+  }
+  int rc = enqueue_evolve(f, psi, n_rhs, n_steps, o.method, tb, rb, scratch, s);
+  if (scratch) cudaFreeAsync(scratch, s);
+  return rc;
+}
+
+int hs_evolve(const hs_factors* f, void* psi, int n_rhs, int n_steps, void* cuda_stream) {
+  return hs_evolve_ex(f, psi, n_rhs, n_steps, nullptr, cuda_stream);
+}
+
+int hs_apply_factor(const hs_factors* f, int g, const void* x, void* y, int n_rhs, void* cuda_stream) {
+  if (!f) return fail(HS_EINVAL, "factors is NULL");
+  if (g < 0 || g >= int(f->plan.groups.size())) return fail(HS_EINVAL, "factor index out of range");
+  if (!x || !y || x == y) return fail(HS_EINVAL, "x and y must be distinct non-NULL buffers");
+  if (n_rhs < 1) return fail(HS_EINVAL, "n_rhs must be >= 1");
+  cudaError_t e = hs::launch_apply_plain(f, g, x, y, n_rhs, reinterpret_cast<cudaStream_t>(cuda_stream));
+  return e == cudaSuccess ? HS_OK : cuda_fail(e, "apply launch");
+}
+
+int hs_inner_device(const void* a, const void* b, int n_qubits, hs_dtype dtype, double* out_device, void* cuda_stream) {
+  if (!a || !b || !out_device) return fail(HS_EINVAL, "null buffer");
+  if (!valid_dtype(dtype)) return fail(HS_EDTYPE, "dtype must be HS_C64 or HS_C128");
+  if (n_qubits < 1 || n_qubits > HS_MAX_QUBITS) return fail(HS_EINVAL, "n_qubits out of range");
+  cudaError_t e = hs::launch_inner(a, b, int64_t(1) << n_qubits, dtype, out_device,
+                                   reinterpret_cast<cudaStream_t>(cuda_stream));
+  return e == cudaSuccess ? HS_OK : cuda_fail(e, "inner product launch");
+}
+
+int hs_fidelity(const void* a, const void* b, int n_qubits, hs_dtype dtype, void* cuda_stream, double* fid,
+                double* norm_a2, double* norm_b2) {
+  if (!fid) return fail(HS_EINVAL, "fid is NULL");
+  if (!a || !b) return fail(HS_EINVAL, "null buffer");
+  if (!valid_dtype(dtype)) return fail(HS_EDTYPE, "dtype must be HS_C64 or HS_C128");
+  if (n_qubits < 1 || n_qubits > HS_MAX_QUBITS) return fail(HS_EINVAL, "n_qubits out of range");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+  double* d_out = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&d_out, 4 * sizeof(double), s);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync");
+  e = hs::launch_inner(a, b, int64_t(1) << n_qubits, dtype, d_out, s);
+  double h[4] = {0, 0, 0, 0};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, d_out, sizeof(h), cudaMemcpyDeviceToHost, s);
+  cudaFreeAsync(d_out, s);
+  cudaError_t e2 = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "fidelity");
+  if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamSynchronize");
+  const double den = h[2] * h[3];
+  *fid = den > 0 ? (h[0] * h[0] + h[1] * h[1]) / den : 0.0;
+  if (norm_a2) *norm_a2 = h[2];
+  if (norm_b2) *norm_b2 = h[3];
+  return HS_OK;
+}
+
+int hs_factors_info(const hs_factors* f, int* n_factors, int* n_qubits, int* n_steps, hs_dtype* dtype,
+                    int64_t* value_bytes) {
+  if (!f) return fail(HS_EINVAL, "factors is NULL");
+  if (n_factors) *n_factors = int(f->plan.groups.size());
+  if (n_qubits) *n_qubits = f->plan.n_qubits;
+  if (n_steps) *n_steps = f->n_steps;
+  if (dtype) *dtype = f->dtype;
+  if (value_bytes) *value_bytes = f->plan.total_elems * int64_t(hs::elem_bytes(f->dtype));
+  return HS_OK;
+}
+
+int hs_factor_get(const hs_factors* f, int g, int* term_first, int* term_last, int* n_diags, int64_t* offsets,
+                  double* values) {
+  if (!f) return fail(HS_EINVAL, "factors is NULL");
+  if (g < 0 || g >= int(f->plan.groups.size())) return fail(HS_EINVAL, "factor index out of range");
+  const hs::Group& G = f->plan.groups[g];
+  if (term_first) *term_first = G.first;
+  if (term_last) *term_last = G.last;
+  if (n_diags) *n_diags = G.D;
+  if (offsets)
+    for (int k = 0; k < G.D; ++k) offsets[k] = f->plan.offs[G.diag0 + k];
+  if (values) {
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+    const int64_t N = f->plan.N;
+    const size_t es = hs::elem_bytes(f->dtype);
+    int64_t out = 0;
+    for (int k = 0; k < G.D; ++k) {
+      const int64_t d = f->plan.offs[G.diag0 + k];
+      const int64_t len = N - (d < 0 ? -d : d);
+      std::vector<unsigned char> buf(size_t(len) * es);
+      e = cudaMemcpy(buf.data(), static_cast<const unsigned char*>(f->d_vals) + size_t(f->plan.dstart[G.diag0 + k]) * es,
+                     buf.size(), cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy");
+      for (int64_t i = 0; i < len; ++i, ++out) {
+        if (f->dtype == HS_C64) {
+          float v[2];
+          std::memcpy(v, buf.data() + size_t(i) * 8, 8);
+          values[2 * out] = v[0];
+          values[2 * out + 1] = v[1];
+        } else {
+          std::memcpy(values + 2 * out, buf.data() + size_t(i) * 16, 16);
+        }
+      }
+    }
+  }
+  return HS_OK;
+}
+
+void hs_free_factors(hs_factors* f) {
+  if (!f) return;
+  cudaDeviceSynchronize();
+  release(f);
+}
+
+}  // extern "C"

@@ -1,0 +1,172 @@
+// Factor construction on the GPU in FP64 (Eq. 4 factors, Eq. 6 layout).
+//
+// Each factor is F_g = R_last ... R_first with R_j = cos(theta_j) I -
+// i sin(theta_j) P_j.  One thread computes one ROW r of F_g: the row is the
+// conjugate of F_g^dagger e_r, and F_g^dagger e_r = R_first^dagger ... R_last^dagger e_r
+// is a vector supported on r xor X, where X (the group's x-mask space) has
+// 2^xdim elements.  It is kept as 2^xdim FP64 complex slots indexed by GF(2)
+// coordinates in the group's reduced echelon basis.  The thread then writes
+// row r's entry on every structural diagonal of the factor (zero where
+// r xor (r+d) is not in X), so writes are coalesced along each diagonal and
+// no separate clearing pass is needed.  Values are rounded once to float2
+// for complex64 storage.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "hs_internal.h"
+
+namespace hs {
+namespace {
+
+struct BuildArgs {
+  void* vals;
+  const int64_t* offs;
+  const int64_t* rowbase;
+  const int* fac_D;
+  const int* fac_diag0;
+  const double* cs;  // (cos, sin) per term
+  const uint64_t* x;
+  const uint64_t* z;
+  const uint32_t* cx;
+  const int* gfirst;
+  const int* glast;
+  const uint64_t* basis;  // kMaxXDim per group
+  const int* xdim;
+  const int* pivot;       // kMaxXDim per group
+  int64_t N;
+};
+
+__device__ __forceinline__ double2 mul_ipow(double2 v, int k) {
+  switch (k & 3) {
+    case 0: return v;
+    case 1: return make_double2(-v.y, v.x);
+    case 2: return make_double2(-v.x, -v.y);
+    default: return make_double2(v.y, -v.x);
+  }
+}
+
+__device__ __forceinline__ void store_val(void* vals, int64_t idx, double2 v, bool c64) {
+  if (c64)
+    reinterpret_cast<float2*>(vals)[idx] = make_float2(__double2float_rn(v.x), __double2float_rn(v.y));
+  else
+    reinterpret_cast<double2*>(vals)[idx] = v;
+}
+
+template <int MAXS>
+__global__ void __launch_bounds__(256) build_kernel(BuildArgs a, bool c64) {
+  const int g = blockIdx.y;
+  const int xd = a.xdim[g];
+  const int S = 1 << xd;
+  uint64_t bas[kMaxXDim];
+  int piv[kMaxXDim];
+#pragma unroll
+  for (int i = 0; i < kMaxXDim; ++i) {
+    bas[i] = (i < xd) ? a.basis[g * kMaxXDim + i] : 0;
+    piv[i] = (i < xd) ? a.pivot[g * kMaxXDim + i] : 0;
+  }
+  const int first = a.gfirst[g], last = a.glast[g];
+  const int D = a.fac_D[g], d0 = a.fac_diag0[g];
+
+  for (int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; r < a.N; r += int64_t(gridDim.x) * blockDim.x) {
+    double2 w[MAXS], nw[MAXS];
+    uint64_t u[MAXS];
+#pragma unroll
+    for (int s = 0; s < MAXS; ++s) {
+      w[s] = make_double2(s == 0 ? 1.0 : 0.0, 0.0);
+      uint64_t m = 0;
+#pragma unroll
+      for (int i = 0; i < kMaxXDim; ++i)
+        if (i < xd && ((s >> i) & 1)) m ^= bas[i];
+      u[s] = m;
+    }
+    // Apply R_j^dagger = cos I + i sin P_j for j = last-1 .. first.
+    for (int j = last - 1; j >= first; --j) {
+      const double c = a.cs[2 * j], sn = a.cs[2 * j + 1];
+      const uint64_t xj = a.x[j], zj = a.z[j];
+      const int y = __popcll(xj & zj);
+      const uint32_t cxj = a.cx[j];
+#pragma unroll
+      for (int s = 0; s < MAXS; ++s) {
+        if (s < S) {
+          const int src = s ^ int(cxj);
+          // P_j maps slot src (basis state r ^ u[src]) to slot s with phase
+          // i^y (-1)^popcount(z & (r ^ u[src])); times i sin.
+          const int par = __popcll(zj & (uint64_t(r) ^ u[src])) & 1;
+          double2 p = mul_ipow(w[src], y + 1 + 2 * par);
+          nw[s] = make_double2(fma(c, w[s].x, sn * p.x), fma(c, w[s].y, sn * p.y));
+        }
+      }
+#pragma unroll
+      for (int s = 0; s < MAXS; ++s)
+        if (s < S) w[s] = nw[s];
+    }
+    // Row r of F: F[r, c] = conj(w[coord(r ^ c)]) when r ^ c lies in X.
+    for (int k = 0; k < D; ++k) {
+      const int64_t d = a.offs[d0 + k];
+      const int64_t col = r + d;
+      if (col < 0 || col >= a.N) continue;
+      const uint64_t uu = uint64_t(r) ^ uint64_t(col);
+      int cc = 0;
+      uint64_t rec = 0;
+#pragma unroll
+      for (int i = 0; i < kMaxXDim; ++i)
+        if (i < xd && ((uu >> piv[i]) & 1ull)) {
+          cc |= 1 << i;
+          rec ^= bas[i];
+        }
+      double2 v = make_double2(0.0, 0.0);
+      if (rec == uu) {
+#pragma unroll
+        for (int s = 0; s < MAXS; ++s)
+          if (s == cc) v = make_double2(w[s].x, -w[s].y);
+      }
+      store_val(a.vals, a.rowbase[d0 + k] + r, v, c64);
+    }
+  }
+}
+
+__global__ void sincos_kernel(const double* coeff, double dt, double* cs, int n) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) {
+    const double theta = coeff[j] * dt;
+    double s, c;
+    sincos(theta, &s, &c);
+    cs[2 * j] = c;
+    cs[2 * j + 1] = s;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_sincos(const double* d_coeff, double dt, double* d_cs, int n, cudaStream_t s) {
+  sincos_kernel<<<(n + 127) / 128, 128, 0, s>>>(d_coeff, dt, d_cs, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_build(const hs_factors* f, const double* d_cs, const uint64_t* d_x, const uint64_t* d_z,
+                         const uint32_t* d_cx, const int* d_gfirst, const int* d_glast, const uint64_t* d_basis,
+                         const int* d_xdim, const int* d_pivot, cudaStream_t s) {
+  const Plan& p = f->plan;
+  int maxdim = 0;
+  for (const Group& g : p.groups) maxdim = g.xdim > maxdim ? g.xdim : maxdim;
+  BuildArgs a{f->d_vals, f->d_offs, f->d_rowbase, f->d_fac_D, f->d_fac_diag0, d_cs, d_x, d_z, d_cx,
+              d_gfirst, d_glast, d_basis, d_xdim, d_pivot, p.N};
+  const bool c64 = f->dtype == HS_C64;
+  const int threads = 256;
+  int64_t blocks_x = (p.N + threads - 1) / threads;
+  if (blocks_x > 4096) blocks_x = 4096;
+  dim3 grid(unsigned(blocks_x), unsigned(p.groups.size()));
+  switch (maxdim) {
+    case 0: build_kernel<1><<<grid, threads, 0, s>>>(a, c64); break;
+    case 1: build_kernel<2><<<grid, threads, 0, s>>>(a, c64); break;
+    case 2: build_kernel<4><<<grid, threads, 0, s>>>(a, c64); break;
+    case 3: build_kernel<8><<<grid, threads, 0, s>>>(a, c64); break;
+    case 4: build_kernel<16><<<grid, threads, 0, s>>>(a, c64); break;
+    case 5: build_kernel<32><<<grid, threads, 0, s>>>(a, c64); break;
+    default: build_kernel<64><<<grid, threads, 0, s>>>(a, c64); break;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace hs

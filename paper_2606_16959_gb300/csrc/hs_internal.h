@@ -1,0 +1,130 @@
+// Internal declarations shared by the translation units of libhs.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/hs.h"
+
+namespace hs {
+
+constexpr int kMaxDiags = 4096;     // diagonals per factor
+constexpr int kMaxXDim = 6;         // log2 of the x-mask set size per factor
+constexpr int kMaxRuns = 6;         // contiguous bit runs describing a tile's local bits
+constexpr int kMaxSweepFactors = 64;
+
+// Storage alignment of each diagonal's row-indexed base, in elements (32 bytes).
+inline int64_t align_elems(hs_dtype dt) { return dt == HS_C64 ? 4 : 2; }
+inline size_t elem_bytes(hs_dtype dt) { return dt == HS_C64 ? 8 : 16; }
+
+// One grouped factor (a contiguous range of terms).
+struct Group {
+  int first = 0, last = 0;   // term range [first, last)
+  int D = 0;                 // number of diagonals
+  int diag0 = 0;             // index of its first diagonal in the global diagonal arrays
+  int64_t S = 0;             // stored elements without padding (sum of N - |d|)
+  uint64_t span = 0;         // OR of the x masks: the qubits the factor flips
+  int xdim = 0;              // dimension of the x-mask space over GF(2)
+  uint64_t basis[kMaxXDim];  // reduced echelon basis of the x-mask space
+  int pivot[kMaxXDim];       // pivot bit of each basis vector
+};
+
+// Result of planning a factor set on the host.
+struct Plan {
+  int n_qubits = 0;
+  int64_t N = 0;
+  std::vector<uint64_t> x, z;
+  std::vector<double> coeff;
+  std::vector<Group> groups;
+  std::vector<int64_t> offs;      // all diagonals, factor after factor, canonical order
+  std::vector<int64_t> dstart;    // element index (padded storage) of element 0 of each diagonal
+  std::vector<int64_t> rowbase;   // value(row r) of diagonal k sits at element rowbase[k] + r
+  std::vector<uint32_t> term_cx;  // per term: coordinates of its x mask in its factor's basis
+  int64_t total_elems = 0;        // padded storage size in elements
+};
+
+// Parse labels into masks.  Returns HS_OK or HS_EINVAL (message in *err).
+int parse_labels(const char* const* labels, size_t n, std::vector<uint64_t>& x, std::vector<uint64_t>& z,
+                 int& n_qubits, std::string* err);
+
+// Group, order offsets and lay out storage.  Returns HS_OK or HS_EINVAL.
+int make_plan(const uint64_t* x, const uint64_t* z, const double* coeff, size_t n, int n_qubits, int budget,
+              hs_dtype dt, Plan& plan, std::string* err);
+
+// A tile partition: `local` bits (held by one CTA) and the rest (enumerated by the grid).
+struct Runs {
+  int n = 0;
+  int8_t pos[kMaxRuns + 2];
+  int8_t len[kMaxRuns + 2];
+};
+
+// One launch of the evolution schedule.
+struct Sweep {
+  bool fused = true;         // tile sweep (true) or plain diagonal-times-vector (false)
+  uint32_t local_mask = 0;   // fused: bits held by a tile
+  std::vector<int> factors;  // fused: factor ids in order; plain: exactly one
+};
+
+// Plan the launches for n_steps steps with tiles of tile_bits local bits.
+std::vector<Sweep> plan_sweeps(const Plan& p, int n_steps, int tile_bits, int min_low_bits, bool fused);
+
+// Decompose a bit mask into runs of consecutive set bits (low to high).
+Runs runs_of(uint64_t mask, int n_bits);
+
+}  // namespace hs
+
+// Opaque object behind the C ABI.
+struct hs_factors {
+  hs::Plan plan;
+  hs_dtype dtype = HS_C64;
+  int n_steps = 0;
+  double t = 0.0;
+  int device = 0;
+  void* d_vals = nullptr;        // padded factor values (float2 / double2)
+  int64_t* d_offs = nullptr;     // per diagonal offset
+  int64_t* d_rowbase = nullptr;  // per diagonal row-indexed base
+  int* d_fac_D = nullptr;        // per factor diagonal count
+  int* d_fac_diag0 = nullptr;    // per factor first diagonal index
+  // cached CUDA graphs of evolve launch sequences
+  struct GraphKey {
+    void* psi;
+    int n_rhs, n_steps, method, tile_bits, rhs_block;
+    cudaStream_t stream;
+    bool operator<(const GraphKey& o) const;
+  };
+  mutable std::mutex graph_mu;
+  mutable std::map<GraphKey, cudaGraphExec_t> graphs;
+};
+
+namespace hs {
+
+// Kernel launchers (defined in the .cu files).
+cudaError_t launch_build(const hs_factors* f, const double* d_theta_cs, const uint64_t* d_x, const uint64_t* d_z,
+                         const uint32_t* d_cx, const int* d_group_first, const int* d_group_last,
+                         const uint64_t* d_basis, const int* d_xdim, const int* d_pivot, cudaStream_t s);
+cudaError_t launch_sincos(const double* d_coeff, double dt, double* d_theta_cs, int n, cudaStream_t s);
+
+cudaError_t launch_apply_plain(const hs_factors* f, int g, const void* x, void* y, int n_rhs, cudaStream_t s);
+
+struct SweepLaunch {
+  const void* src;
+  void* dst;
+  int n_rhs;
+  int rhs_block;
+  int tile_bits;
+  Runs local, rest;
+  int n_factors;
+  int factors[kMaxSweepFactors];
+};
+cudaError_t launch_sweep(const hs_factors* f, const SweepLaunch& L, cudaStream_t s);
+int max_tile_bits(hs_dtype dt, int rhs_block);
+cudaError_t prepare_kernels();
+
+cudaError_t launch_inner(const void* a, const void* b, int64_t N, hs_dtype dt, double* d_out4, cudaStream_t s);
+
+}  // namespace hs

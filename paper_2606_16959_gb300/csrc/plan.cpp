@@ -1,0 +1,266 @@
+// Host-side structural planning: label parsing, budgeted grouping, the
+// structural offset sets of each factor (the "structural dry run" of the
+// diagonal-set estimation paragraph, Sec. 3.2), canonical diagonal order
+// (Tab. 1), the padded storage layout (Eq. 6 with alignment padding only),
+// and the tile-sweep schedule used by the fused evolution.
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <string>
+#include <vector>
+
+#include "hs_internal.h"
+
+namespace hs {
+
+namespace {
+
+// All signed sums sum_{k in u} +-2^k, appended to out (2^popcount(u) values).
+void append_offsets(uint64_t u, std::vector<int64_t>& out) {
+  size_t base = out.size();
+  out.push_back(0);
+  for (int k = 0; k < 63; ++k) {
+    if (!((u >> k) & 1ull)) continue;
+    size_t cur = out.size();
+    for (size_t i = base; i < cur; ++i) {
+      int64_t o = out[i];
+      out[i] = o + (int64_t(1) << k);
+      out.push_back(o - (int64_t(1) << k));
+    }
+  }
+}
+
+bool canonical_less(int64_t a, int64_t b) {
+  int64_t aa = a < 0 ? -a : a, bb = b < 0 ? -b : b;
+  return aa != bb ? aa < bb : a < b;
+}
+
+// Open group state: GF(2) basis of the x-mask space (reduced echelon form),
+// the list of its elements, and the sorted set of structural offsets.
+struct OpenGroup {
+  std::vector<uint64_t> basis;
+  std::vector<int> pivot;
+  std::vector<uint64_t> elems{0};
+  std::vector<int64_t> offs{0};  // sorted ascending, unique
+
+  uint64_t reduce(uint64_t v) const {
+    for (size_t i = 0; i < basis.size(); ++i)
+      if ((v >> pivot[i]) & 1ull) v ^= basis[i];
+    return v;
+  }
+  // Offsets of the enlarged set when v (already reduced, nonzero) joins.
+  std::vector<int64_t> offsets_with(uint64_t v) const {
+    std::vector<int64_t> add;
+    for (uint64_t u : elems) append_offsets(u ^ v, add);
+    std::vector<int64_t> merged;
+    merged.reserve(offs.size() + add.size());
+    std::sort(add.begin(), add.end());
+    std::set_union(offs.begin(), offs.end(), add.begin(), add.end(), std::back_inserter(merged));
+    merged.erase(std::unique(merged.begin(), merged.end()), merged.end());
+    return merged;
+  }
+  void admit(uint64_t v, std::vector<int64_t>&& new_offs) {
+    int p = 63 - __builtin_clzll(v);
+    for (size_t i = 0; i < basis.size(); ++i)
+      if ((basis[i] >> p) & 1ull) basis[i] ^= v;
+    basis.push_back(v);
+    pivot.push_back(p);
+    size_t n = elems.size();
+    for (size_t i = 0; i < n; ++i) elems.push_back(elems[i] ^ v);
+    offs = std::move(new_offs);
+  }
+};
+
+}  // namespace
+
+int parse_labels(const char* const* labels, size_t n, std::vector<uint64_t>& x, std::vector<uint64_t>& z,
+                 int& n_qubits, std::string* err) {
+  if (n == 0 || labels == nullptr) {
+    *err = "no terms";
+    return HS_EINVAL;
+  }
+  x.assign(n, 0);
+  z.assign(n, 0);
+  n_qubits = -1;
+  for (size_t j = 0; j < n; ++j) {
+    const char* s = labels[j];
+    if (!s) {
+      *err = "null label at term " + std::to_string(j);
+      return HS_EINVAL;
+    }
+    int len = 0;
+    while (s[len]) ++len;
+    if (n_qubits < 0) n_qubits = len;
+    if (len != n_qubits) {
+      *err = "label " + std::to_string(j) + " has length " + std::to_string(len) + ", expected " +
+             std::to_string(n_qubits);
+      return HS_EINVAL;
+    }
+    if (len < 1 || len > HS_MAX_QUBITS) {
+      *err = "label length must be 1.." + std::to_string(HS_MAX_QUBITS);
+      return HS_EINVAL;
+    }
+    for (int p = 0; p < len; ++p) {
+      uint64_t bit = 1ull << (len - 1 - p);
+      switch (s[p]) {
+        case 'I': break;
+        case 'X': x[j] |= bit; break;
+        case 'Z': z[j] |= bit; break;
+        case 'Y': x[j] |= bit; z[j] |= bit; break;
+        default:
+          *err = std::string("invalid Pauli character '") + s[p] + "' in label " + std::to_string(j);
+          return HS_EINVAL;
+      }
+    }
+  }
+  return HS_OK;
+}
+
+int make_plan(const uint64_t* x, const uint64_t* z, const double* coeff, size_t n, int n_qubits, int budget,
+              hs_dtype dt, Plan& plan, std::string* err) {
+  if (n == 0) { *err = "no terms"; return HS_EINVAL; }
+  if (n_qubits < 1 || n_qubits > HS_MAX_QUBITS) {
+    *err = "n_qubits must be 1.." + std::to_string(HS_MAX_QUBITS);
+    return HS_EINVAL;
+  }
+  if (budget < 1) { *err = "diag_budget must be >= 1"; return HS_EINVAL; }
+  const uint64_t N = 1ull << n_qubits;
+  for (size_t j = 0; j < n; ++j) {
+    if ((x[j] | z[j]) >= N) { *err = "mask of term " + std::to_string(j) + " exceeds n_qubits"; return HS_EINVAL; }
+    if (coeff && !std::isfinite(coeff[j])) { *err = "non-finite coefficient at term " + std::to_string(j); return HS_EINVAL; }
+    if (__builtin_popcountll(x[j]) > 12) {
+      *err = "term " + std::to_string(j) + " flips more than 12 qubits (over 4096 diagonals)";
+      return HS_EINVAL;
+    }
+  }
+  plan = Plan();
+  plan.n_qubits = n_qubits;
+  plan.N = int64_t(N);
+  plan.x.assign(x, x + n);
+  plan.z.assign(z, z + n);
+  if (coeff) plan.coeff.assign(coeff, coeff + n);
+  else plan.coeff.assign(n, 0.0);
+  plan.term_cx.assign(n, 0);
+
+  // Next-fit grouping in input order.
+  std::vector<std::pair<int, OpenGroup>> closed;
+  OpenGroup g;
+  int first = 0;
+  for (size_t j = 0; j < n; ++j) {
+    uint64_t v = g.reduce(x[j]);
+    if (v == 0) continue;  // x_j already in the set: offsets unchanged, always admitted
+    std::vector<int64_t> nxt = g.offsets_with(v);
+    bool empty = (int(j) == first);
+    if (empty || int64_t(nxt.size()) <= budget || nxt == g.offs) {
+      g.admit(v, std::move(nxt));
+    } else {
+      closed.emplace_back(first, std::move(g));
+      g = OpenGroup();
+      first = int(j);
+      uint64_t v2 = g.reduce(x[j]);
+      if (v2) g.admit(v2, g.offsets_with(v2));
+    }
+    if (int(g.basis.size()) > kMaxXDim || int(g.offs.size()) > kMaxDiags) {
+      *err = "factor starting at term " + std::to_string(first) + " exceeds the implementation limits (" +
+             std::to_string(kMaxDiags) + " diagonals, x-mask set of 2^" + std::to_string(kMaxXDim) + ")";
+      return HS_EINVAL;
+    }
+  }
+  closed.emplace_back(first, std::move(g));
+
+  // Canonical order, padded layout, bases.
+  const int64_t A = align_elems(dt);
+  int64_t cursor = 0;
+  for (size_t gi = 0; gi < closed.size(); ++gi) {
+    OpenGroup& og = closed[gi].second;
+    Group G;
+    G.first = closed[gi].first;
+    G.last = (gi + 1 < closed.size()) ? closed[gi + 1].first : int(n);
+    std::vector<int64_t> o = og.offs;
+    std::sort(o.begin(), o.end(), canonical_less);
+    G.D = int(o.size());
+    G.diag0 = int(plan.offs.size());
+    G.xdim = int(og.basis.size());
+    for (int i = 0; i < G.xdim; ++i) {
+      G.basis[i] = og.basis[i];
+      G.pivot[i] = og.pivot[i];
+      G.span |= og.basis[i];
+    }
+    for (int64_t d : o) {
+      int64_t len = plan.N - (d < 0 ? -d : d);
+      int64_t pad = d < 0 ? ((-d) % A) : 0;  // makes rowbase = start + pad + d a multiple of A
+      int64_t start = cursor + pad;
+      plan.offs.push_back(d);
+      plan.dstart.push_back(start);
+      plan.rowbase.push_back(start + (d < 0 ? d : 0));
+      G.S += len;
+      cursor = (start + len + A - 1) / A * A;
+    }
+    for (int j = G.first; j < G.last; ++j) {
+      uint32_t c = 0;
+      for (int i = 0; i < G.xdim; ++i)
+        if ((x[j] >> G.pivot[i]) & 1ull) c |= 1u << i;
+      plan.term_cx[j] = c;
+    }
+    plan.groups.push_back(G);
+  }
+  plan.total_elems = cursor;
+  return HS_OK;
+}
+
+Runs runs_of(uint64_t mask, int n_bits) {
+  Runs r;
+  int b = 0;
+  while (b < n_bits) {
+    if (!((mask >> b) & 1ull)) { ++b; continue; }
+    int s = b;
+    while (b < n_bits && ((mask >> b) & 1ull)) ++b;
+    r.pos[r.n] = int8_t(s);
+    r.len[r.n] = int8_t(b - s);
+    ++r.n;
+  }
+  return r;
+}
+
+std::vector<Sweep> plan_sweeps(const Plan& p, int n_steps, int tile_bits, int min_low_bits, bool fused) {
+  std::vector<Sweep> out;
+  const int n = p.n_qubits;
+  const uint64_t all = (n >= 64) ? ~0ull : ((1ull << n) - 1);
+  const uint64_t low = (min_low_bits >= 64) ? ~0ull : ((1ull << std::min(min_low_bits, n)) - 1);
+  tile_bits = std::min(tile_bits, n);
+  auto close = [&](Sweep& s, uint64_t used) {
+    uint64_t L = used | low;
+    for (int b = 0; b < n && __builtin_popcountll(L) < tile_bits; ++b) L |= 1ull << b;
+    s.local_mask = uint32_t(L & all);
+    out.push_back(std::move(s));
+    s = Sweep();
+  };
+  Sweep cur;
+  uint64_t used = 0;
+  for (int st = 0; st < n_steps; ++st) {
+    for (int g = 0; g < int(p.groups.size()); ++g) {
+      uint64_t span = p.groups[g].span;
+      bool fits_alone = fused && __builtin_popcountll(span | low) <= tile_bits;
+      if (!fits_alone) {
+        if (!cur.factors.empty()) close(cur, used);
+        used = 0;
+        Sweep pl;
+        pl.fused = false;
+        pl.factors.push_back(g);
+        out.push_back(std::move(pl));
+        continue;
+      }
+      if (!cur.factors.empty() &&
+          (__builtin_popcountll(used | span | low) > tile_bits || int(cur.factors.size()) >= kMaxSweepFactors)) {
+        close(cur, used);
+        used = 0;
+      }
+      cur.factors.push_back(g);
+      used |= span;
+    }
+  }
+  if (!cur.factors.empty()) close(cur, used);
+  return out;
+}
+
+}  // namespace hs

@@ -1,0 +1,277 @@
+"""Thin Python binding of libhs (include/hs.h): same names, argument marshalling only.
+
+Every computation runs in the CUDA library; PyTorch supplies device memory
+(state tensors) and streams.  There is no CPU fallback: if the compiled
+library is missing, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence, Tuple
+
+import numpy as np
+
+HS_OK, HS_EINVAL, HS_ENOMEM, HS_ECUDA, HS_ETIMEOUT, HS_EDTYPE = 0, -1, -2, -3, -4, -5
+HS_C64, HS_C128 = 1, 2
+HS_METHOD_AUTO, HS_METHOD_PLAIN, HS_METHOD_FUSED = 0, 1, 2
+HS_MAX_QUBITS = 30
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libhs.so")
+
+# Every symbol declared in include/hs.h.
+EXPORTS = (
+    "hs_build_factors", "hs_build_factors_masks", "hs_evolve", "hs_evolve_ex", "hs_apply_factor",
+    "hs_fidelity", "hs_inner_device", "hs_factors_info", "hs_factor_get", "hs_free_factors", "hs_last_error",
+    "hs_plan_factors", "hs_evolve_plan",
+)
+
+
+class HSError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libhs error {code}: {msg}")
+        self.code = code
+
+
+class EvolveOpts(ctypes.Structure):
+    _fields_ = [("method", ctypes.c_int), ("tile_bits", ctypes.c_int), ("rhs_block", ctypes.c_int),
+                ("use_graph", ctypes.c_int)]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libhs.so (built by __graft_entry__.build()); raises if it is absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libhs.so not found at {LIB_PATH}: build the CUDA library first "
+                               "(python -c 'import __graft_entry__ as g; g.build()')")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i, d, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+        L.hs_build_factors.argtypes = [ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(d), sz, d, i, i, i, vp,
+                                       ctypes.POINTER(vp)]
+        L.hs_build_factors_masks.argtypes = [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
+                                             ctypes.POINTER(d), sz, i, d, i, i, i, vp, ctypes.POINTER(vp)]
+        L.hs_evolve.argtypes = [vp, vp, i, i, vp]
+        L.hs_evolve_ex.argtypes = [vp, vp, i, i, ctypes.POINTER(EvolveOpts), vp]
+        L.hs_apply_factor.argtypes = [vp, i, vp, vp, i, vp]
+        L.hs_fidelity.argtypes = [vp, vp, i, i, vp, ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(d)]
+        L.hs_inner_device.argtypes = [vp, vp, i, i, vp, vp]
+        L.hs_factors_info.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i),
+                                      ctypes.POINTER(ctypes.c_int64)]
+        L.hs_factor_get.argtypes = [vp, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i),
+                                    ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(d)]
+        ip, i64p = ctypes.POINTER(i), ctypes.POINTER(ctypes.c_int64)
+        L.hs_plan_factors.argtypes = [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64), sz, i, i, i,
+                                      ip, ip, ip, ip, ip, i64p, i64p, i, i]
+        L.hs_evolve_plan.argtypes = [vp, i, i, ctypes.POINTER(EvolveOpts), ip, ip, ip, ip]
+        L.hs_free_factors.argtypes = [vp]
+        L.hs_free_factors.restype = None
+        L.hs_last_error.restype = ctypes.c_char_p
+        for name in EXPORTS:
+            if name not in ("hs_free_factors", "hs_last_error"):
+                getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != HS_OK:
+        raise HSError(rc, lib().hs_last_error().decode(errors="replace"))
+
+
+def _dtype_code(dtype) -> int:
+    import torch
+    if dtype in ("c64", torch.complex64, HS_C64):
+        return HS_C64
+    if dtype in ("c128", torch.complex128, HS_C128):
+        return HS_C128
+    raise ValueError(f"unsupported dtype {dtype!r}")
+
+
+def _stream(stream) -> int:
+    import torch
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+def _state_args(psi):
+    """(pointer, n_rhs, n_qubits, dtype code) of a CUDA state tensor (N,) or (R, N)."""
+    import torch
+    if not isinstance(psi, torch.Tensor) or not psi.is_cuda:
+        raise TypeError("state must be a CUDA tensor")
+    if not psi.is_contiguous():
+        raise ValueError("state must be contiguous")
+    N = psi.shape[-1]
+    n = int(N).bit_length() - 1
+    if N != 1 << n:
+        raise ValueError("state length must be a power of two")
+    n_rhs = 1 if psi.dim() == 1 else int(np.prod(psi.shape[:-1]))
+    return psi.data_ptr(), n_rhs, n, _dtype_code(psi.dtype)
+
+
+class Factors:
+    """Owner of an hs_factors handle (freed on close or garbage collection)."""
+
+    def __init__(self, handle: int):
+        self.handle = ctypes.c_void_p(handle)
+        nf, nq, ns, dt = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        vb = ctypes.c_int64()
+        _check(lib().hs_factors_info(self.handle, ctypes.byref(nf), ctypes.byref(nq), ctypes.byref(ns),
+                                     ctypes.byref(dt), ctypes.byref(vb)))
+        self.n_factors, self.n_qubits, self.n_steps, self.dtype_code = nf.value, nq.value, ns.value, dt.value
+        self.value_bytes = vb.value
+
+    @property
+    def dtype(self) -> str:
+        return "c64" if self.dtype_code == HS_C64 else "c128"
+
+    def factor(self, g: int, values: bool = True):
+        """(term_first, term_last, offsets, values) of factor g; values as complex128 (the Eq. 6 view)."""
+        tf, tl, nd = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(lib().hs_factor_get(self.handle, g, ctypes.byref(tf), ctypes.byref(tl), ctypes.byref(nd), None, None))
+        offs = np.zeros(nd.value, dtype=np.int64)
+        N = 1 << self.n_qubits
+        _check(lib().hs_factor_get(self.handle, g, None, None, None,
+                                   offs.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), None))
+        vals = None
+        if values:
+            S = int(np.sum(N - np.abs(offs)))
+            buf = np.zeros(2 * S, dtype=np.float64)
+            _check(lib().hs_factor_get(self.handle, g, None, None, None, None,
+                                       buf.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+            vals = buf.view(np.complex128)
+        return tf.value, tl.value, offs, vals
+
+    def close(self):
+        if self.handle and self.handle.value:
+            if _lib is not None:
+                _lib.hs_free_factors(self.handle)
+            self.handle = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def hs_build_factors(labels: Sequence[str], coeffs, t: float, n_steps: int, diag_budget: int, dtype="c64",
+                     stream=None) -> Factors:
+    arr = (ctypes.c_char_p * len(labels))(*[l.encode() for l in labels])
+    c = np.ascontiguousarray(np.asarray(coeffs, dtype=np.float64))
+    if c.size != len(labels):
+        raise ValueError("one coefficient per label")
+    out = ctypes.c_void_p()
+    _check(lib().hs_build_factors(arr, c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(labels), float(t),
+                                  int(n_steps), int(diag_budget), _dtype_code(dtype), _stream(stream),
+                                  ctypes.byref(out)))
+    return Factors(out.value)
+
+
+def hs_build_factors_masks(x, z, coeffs, n_qubits: int, t: float, n_steps: int, diag_budget: int, dtype="c64",
+                           stream=None) -> Factors:
+    xa = np.ascontiguousarray(np.asarray(x, dtype=np.uint64))
+    za = np.ascontiguousarray(np.asarray(z, dtype=np.uint64))
+    c = np.ascontiguousarray(np.asarray(coeffs, dtype=np.float64))
+    if not (xa.size == za.size == c.size):
+        raise ValueError("x, z and coeffs differ in length")
+    out = ctypes.c_void_p()
+    _check(lib().hs_build_factors_masks(xa.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                        za.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                        c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), xa.size, int(n_qubits),
+                                        float(t), int(n_steps), int(diag_budget), _dtype_code(dtype), _stream(stream),
+                                        ctypes.byref(out)))
+    return Factors(out.value)
+
+
+def _check_state(f: Factors, psi):
+    ptr, n_rhs, n, code = _state_args(psi)
+    if n != f.n_qubits:
+        raise ValueError(f"state has {n} qubits, factors {f.n_qubits}")
+    if code != f.dtype_code:
+        raise HSError(HS_EDTYPE, "state dtype differs from the factors' dtype")
+    return ptr, n_rhs
+
+
+def hs_evolve(f: Factors, psi, n_steps: int, stream=None) -> None:
+    ptr, n_rhs = _check_state(f, psi)
+    _check(lib().hs_evolve(f.handle, ptr, n_rhs, int(n_steps), _stream(stream)))
+
+
+def hs_evolve_ex(f: Factors, psi, n_steps: int, method: int = HS_METHOD_AUTO, tile_bits: int = 0,
+                 rhs_block: int = 0, use_graph: bool = False, stream=None) -> None:
+    ptr, n_rhs = _check_state(f, psi)
+    o = EvolveOpts(int(method), int(tile_bits), int(rhs_block), int(bool(use_graph)))
+    _check(lib().hs_evolve_ex(f.handle, ptr, n_rhs, int(n_steps), ctypes.byref(o), _stream(stream)))
+
+
+def hs_evolve_plan(f: Factors, n_rhs: int, n_steps: int, method: int = HS_METHOD_AUTO, tile_bits: int = 0,
+                   rhs_block: int = 0, use_graph: bool = False):
+    """(n_sweep_launches, n_plain_launches, tile_bits, rhs_block) hs_evolve_ex would use."""
+    o = EvolveOpts(int(method), int(tile_bits), int(rhs_block), int(bool(use_graph)))
+    a, b, c, d = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().hs_evolve_plan(f.handle, int(n_rhs), int(n_steps), ctypes.byref(o), ctypes.byref(a), ctypes.byref(b),
+                                ctypes.byref(c), ctypes.byref(d)))
+    return a.value, b.value, c.value, d.value
+
+
+def hs_apply_factor(f: Factors, g: int, x, y, stream=None) -> None:
+    px, n_rhs = _check_state(f, x)
+    py, n_rhs2 = _check_state(f, y)
+    if n_rhs != n_rhs2:
+        raise ValueError("x and y differ in shape")
+    _check(lib().hs_apply_factor(f.handle, int(g), px, py, n_rhs, _stream(stream)))
+
+
+def hs_fidelity(a, b, stream=None) -> Tuple[float, float, float]:
+    """(|<a|b>|^2 / (|a|^2 |b|^2), |a|^2, |b|^2) for two single-state CUDA tensors."""
+    pa, ra, na, ca = _state_args(a)
+    pb, rb, nb, cb = _state_args(b)
+    if (ra, na, ca) != (1, nb, cb) or rb != 1:
+        raise ValueError("fidelity takes two single states of equal size and dtype")
+    fid, n1, n2 = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(lib().hs_fidelity(pa, pb, na, ca, _stream(stream), ctypes.byref(fid), ctypes.byref(n1), ctypes.byref(n2)))
+    return fid.value, n1.value, n2.value
+
+
+def hs_inner_device(a, b, out, stream=None) -> None:
+    """out (CUDA float64 tensor of 4) <- (Re<a|b>, Im<a|b>, |a|^2, |b|^2), no synchronisation."""
+    pa, ra, na, ca = _state_args(a)
+    pb, rb, nb, cb = _state_args(b)
+    if (ra, na, ca) != (1, nb, cb) or rb != 1:
+        raise ValueError("inner product takes two single states of equal size and dtype")
+    _check(lib().hs_inner_device(pa, pb, na, ca, out.data_ptr(), _stream(stream)))
+
+
+def hs_plan_factors(x, z, n_qubits: int, diag_budget: int, dtype="c64"):
+    """Structural dry run on the host (no GPU): list of (term_first, term_last, offsets)
+    per factor and the device bytes the factor values will take."""
+    xa = np.ascontiguousarray(np.asarray(x, dtype=np.uint64))
+    za = np.ascontiguousarray(np.asarray(z, dtype=np.uint64))
+    code = HS_C64 if dtype in ("c64", HS_C64) else HS_C128
+    nf, no = ctypes.c_int(), ctypes.c_int()
+    vb = ctypes.c_int64()
+    ip = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    _check(lib().hs_plan_factors(xa.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                 za.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), xa.size, int(n_qubits),
+                                 int(diag_budget), code, ctypes.byref(nf), ctypes.byref(no), None, None, None, None,
+                                 ctypes.byref(vb), 0, 0))
+    gf = np.zeros(nf.value, dtype=np.int32)
+    gl = np.zeros(nf.value, dtype=np.int32)
+    nd = np.zeros(nf.value, dtype=np.int32)
+    offs = np.zeros(no.value, dtype=np.int64)
+    _check(lib().hs_plan_factors(xa.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                 za.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), xa.size, int(n_qubits),
+                                 int(diag_budget), code, ctypes.byref(nf), ctypes.byref(no), ip(gf), ip(gl), ip(nd),
+                                 offs.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), ctypes.byref(vb), nf.value,
+                                 no.value))
+    out, k = [], 0
+    for g in range(nf.value):
+        out.append((int(gf[g]), int(gl[g]), [int(o) for o in offs[k:k + nd[g]]]))
+        k += int(nd[g])
+    return out, int(vb.value)

@@ -1,0 +1,80 @@
+"""CPU-only checks of the C ABI: the library loads, exports every symbol that
+include/hs.h declares, and its host-side planner (the structural dry run)
+groups terms and orders offsets bit-exactly like the oracle."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from conftest import ROOT
+from paper_2606_16959_gb300 import hs, workloads as W
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "hs.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:int|void|const char\*)\s+(hs_\w+)\s*\(", src, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2606_16959_gb300 import _build
+    _build.build()
+    return hs.lib()
+
+
+def test_exports_every_declared_symbol(lib):
+    decl = declared_symbols()
+    assert len(decl) >= 10
+    for name in decl:
+        assert hasattr(lib, name), name
+    assert sorted(hs.EXPORTS) == decl
+
+
+def test_plan_rejects_bad_input(lib):
+    with pytest.raises(hs.HSError) as e:
+        hs.hs_plan_factors([1], [0], 0, 4)
+    assert e.value.code == hs.HS_EINVAL
+    with pytest.raises(hs.HSError):
+        hs.hs_plan_factors([1], [0], 4, 0)
+    with pytest.raises(hs.HSError):
+        hs.hs_plan_factors([1 << 5], [0], 4, 4)  # mask beyond n_qubits
+    with pytest.raises(hs.HSError):
+        hs.hs_plan_factors([(1 << 13) - 1], [0], 13, 4)  # 13 flipped qubits: over 4096 diagonals
+
+
+def _compare(oracle, x, z, n, budget):
+    got, vbytes = hs.hs_plan_factors(x, z, n, budget)
+    want = oracle.group_terms(x, budget)
+    assert [(g[0], g[1]) for g in got] == [(g.first, g.last) for g in want]
+    for g, w in zip(got, want):
+        assert g[2] == w.offsets
+    N = 1 << n
+    S = sum(N - abs(d) for g in got for d in g[2])
+    assert S * 8 <= vbytes <= (S + 4 * sum(len(g[2]) for g in got)) * 8
+
+
+def test_plan_matches_oracle_families(oracle, lib):
+    for ham, budgets in [(W.tfim_chain(10, 1, 1), (1, 3, 4, 8)), (W.heisenberg_chain(16, np.ones(16)), (4, 5, 8, 16)),
+                         (W.maxcut_3regular(24, 1003), (1, 4, 9)), (W.tsp_onehot(4, 5), (1,)),
+                         (W.tfim_chain(20, 1, 1, periodic=True), (4, 7, 16))]:
+        x, z, n = oracle.parse_terms(ham.labels)
+        for b in budgets:
+            _compare(oracle, x, z, n, b)
+
+
+def test_plan_matches_oracle_random(oracle, lib):
+    rng = np.random.default_rng(77)
+    for trial in range(200):
+        n = int(rng.integers(1, 12))
+        m = int(rng.integers(1, 14))
+        labels = ["".join(rng.choice(list("IXYZ"), p=[0.55, 0.15, 0.15, 0.15], size=n)) for _ in range(m)]
+        x, z, _ = oracle.parse_terms(labels)
+        _compare(oracle, x, z, n, int(rng.integers(1, 24)))
+
+
+def test_batch_and_serve_generators_plan(oracle, lib):
+    for job in W.batch256(n_jobs=24, n_hi=14):
+        x, z, n = oracle.parse_terms(job.ham.labels)
+        _compare(oracle, x, z, n, job.budget)
