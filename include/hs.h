@@ -155,6 +155,24 @@ int hs_fidelity(const void* a, const void* b, int n_qubits, hs_dtype dtype, void
 int hs_inner_device(const void* a, const void* b, int n_qubits, hs_dtype dtype, double* out_device,
                     void* cuda_stream);
 
+/* Batched <a_i|b_i>, |a_i|^2, |b_i|^2 (FP64, i = 0 .. n_states-1) that
+ * allocates no device memory.  The paper has no counterpart of this call.
+ * It exists for callers that cannot allocate: a serving loop that keeps all
+ * device memory reserved for resident states and factors, or an application
+ * whose device memory belongs to its own allocator.  a, b: device buffers of
+ * n_states states each (rhs-major, 2^n_qubits amplitudes per state).
+ * out_device: DEVICE buffer of 4 * n_states doubles, written as
+ * {re, im, |a_i|^2, |b_i|^2} per state; the values equal hs_inner_device's
+ * for each pair.  Scratch is a static per-device array of 4864 partial sums
+ * (152 KiB, held by every GPU that loads the library until exit): a call
+ * needs n_states * min(ceil(2^n_qubits / 256), 608) of them and is rejected
+ * with HS_EINVAL above that (at least 8 states of any size per call).  The
+ * first call on a device looks up the array's device address (make it before
+ * any stream capture); calls that overlap on the GPU race on the array.
+ * Does not synchronise.  Errors: HS_EINVAL, HS_EDTYPE, HS_ECUDA. */
+int hs_inner_batch_noalloc(const void* a, const void* b, int n_qubits, int n_states, hs_dtype dtype,
+                           double* out_device, void* cuda_stream);
+
 /* Introspection.  hs_factors_info: number of factors, qubits, steps the
  * object was built for, dtype, and total device bytes of factor values. */
 int hs_factors_info(const hs_factors* f, int* n_factors, int* n_qubits, int* n_steps, hs_dtype* dtype,

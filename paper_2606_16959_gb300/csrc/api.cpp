@@ -118,6 +118,10 @@ int pick_tile_bits(const hs_factors* f, int rhs_block) {
 
 }  // namespace
 
+namespace hs {
+int report_error(int code, const std::string& msg) { return fail(code, msg); }
+}  // namespace hs
+
 bool hs_factors::GraphKey::operator<(const GraphKey& o) const {
   return std::tie(psi, n_rhs, n_steps, method, tile_bits, rhs_block, stream) <
          std::tie(o.psi, o.n_rhs, o.n_steps, o.method, o.tile_bits, o.rhs_block, o.stream);

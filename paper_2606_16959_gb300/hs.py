@@ -24,7 +24,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libhs.so")
 EXPORTS = (
     "hs_build_factors", "hs_build_factors_masks", "hs_evolve", "hs_evolve_ex", "hs_apply_factor",
     "hs_fidelity", "hs_inner_device", "hs_factors_info", "hs_factor_get", "hs_free_factors", "hs_last_error",
-    "hs_plan_factors", "hs_evolve_plan",
+    "hs_plan_factors", "hs_evolve_plan", "hs_inner_batch_noalloc",
 )
 
 
@@ -68,6 +68,7 @@ def lib() -> ctypes.CDLL:
         L.hs_plan_factors.argtypes = [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64), sz, i, i, i,
                                       ip, ip, ip, ip, ip, i64p, i64p, i, i]
         L.hs_evolve_plan.argtypes = [vp, i, i, ctypes.POINTER(EvolveOpts), ip, ip, ip, ip]
+        L.hs_inner_batch_noalloc.argtypes = [vp, vp, i, i, i, vp, vp]
         L.hs_free_factors.argtypes = [vp]
         L.hs_free_factors.restype = None
         L.hs_last_error.restype = ctypes.c_char_p
@@ -275,3 +276,15 @@ def hs_plan_factors(x, z, n_qubits: int, diag_budget: int, dtype="c64"):
         out.append((int(gf[g]), int(gl[g]), [int(o) for o in offs[k:k + nd[g]]]))
         k += int(nd[g])
     return out, int(vb.value)
+
+
+def hs_inner_batch_noalloc(a, b, out, stream=None) -> None:
+    """out (CUDA float64 tensor (R, 4)) <- per state pair (Re<a_i|b_i>, Im<a_i|b_i>, |a_i|^2, |b_i|^2),
+    computed without any device allocation (static scratch; see include/hs.h)."""
+    pa, ra, na, ca = _state_args(a)
+    pb, rb, nb, cb = _state_args(b)
+    if (ra, na, ca) != (rb, nb, cb):
+        raise ValueError("a and b differ in shape or dtype")
+    if out.numel() < 4 * ra or not out.is_cuda or not out.is_contiguous():
+        raise ValueError("out must be a contiguous CUDA float64 tensor of 4 * n_states elements")
+    _check(lib().hs_inner_batch_noalloc(pa, pb, na, ra, ca, out.data_ptr(), _stream(stream)))
