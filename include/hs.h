@@ -123,6 +123,8 @@ typedef struct {
   int tile_bits;  /* log2 amplitudes per tile for FUSED; 0 = library choice */
   int rhs_block;  /* states per tile for FUSED; 0 = library choice */
   int use_graph;  /* 1: replay the launch sequence as a cached CUDA graph; 0: direct launches */
+  int low_bits;   /* FUSED: contiguous low bits every tile keeps (coalescing run of 2^low_bits
+                     amplitudes); 0 = library choice (64-byte runs) */
 } hs_evolve_opts;
 
 /* hs_evolve with an explicit method and tiling (opts may be NULL = AUTO). */

@@ -32,9 +32,9 @@ int cuda_fail(cudaError_t e, const char* what) {
 
 bool valid_dtype(hs_dtype d) { return d == HS_C64 || d == HS_C128; }
 
-// Minimum number of contiguous low bits in a tile, so that every warp access
-// along a diagonal or the state covers whole 128-byte lines.
-int min_low_bits(hs_dtype dt) { return dt == HS_C64 ? 4 : 3; }
+// Default number of contiguous low bits in a tile: every access along a
+// diagonal or the state then covers whole 64-byte runs.
+int min_low_bits(hs_dtype dt) { return dt == HS_C64 ? 3 : 2; }
 
 void release(hs_factors* f) {
   if (!f) return;
@@ -53,10 +53,10 @@ void release(hs_factors* f) {
 
 // Enqueue the launches of one evolution on stream s.
 int enqueue_evolve(const hs_factors* f, void* psi, int n_rhs, int n_steps, hs_method method, int tile_bits,
-                   int rhs_block, void* scratch, cudaStream_t s) {
+                   int rhs_block, int low_bits, void* scratch, cudaStream_t s) {
   const hs::Plan& p = f->plan;
   const bool fused = method != HS_METHOD_PLAIN;
-  std::vector<hs::Sweep> sw = hs::plan_sweeps(p, n_steps, tile_bits, min_low_bits(f->dtype), fused);
+  std::vector<hs::Sweep> sw = hs::plan_sweeps(p, n_steps, tile_bits, low_bits, fused);
   void* cur = psi;
   void* other = scratch;
   const uint64_t all = (1ull << p.n_qubits) - 1;
@@ -73,6 +73,8 @@ int enqueue_evolve(const hs_factors* f, void* psi, int n_rhs, int n_steps, hs_me
       L.rest = hs::runs_of(~uint64_t(w.local_mask) & all, p.n_qubits);
       L.n_factors = int(w.factors.size());
       for (int i = 0; i < L.n_factors; ++i) L.factors[i] = w.factors[i];
+      L.smem_budget = hs::kSweepSmemDefault;
+      L.pdl = true;
       e = hs::launch_sweep(f, L, s);
     } else {
       if (!other) return fail(HS_EINVAL, "internal: plain application without scratch");
@@ -89,13 +91,22 @@ int enqueue_evolve(const hs_factors* f, void* psi, int n_rhs, int n_steps, hs_me
   return HS_OK;
 }
 
-bool needs_scratch(const hs_factors* f, int n_steps, hs_method method, int tile_bits) {
+bool needs_scratch(const hs_factors* f, int n_steps, hs_method method, int tile_bits, int low_bits) {
   if (method == HS_METHOD_PLAIN) return n_steps > 0;
   for (const hs::Group& g : f->plan.groups)
-    if (__builtin_popcountll(g.span | ((1ull << std::min(min_low_bits(f->dtype), f->plan.n_qubits)) - 1)) >
-        std::min(tile_bits, f->plan.n_qubits))
+    if (g.D > hs::kMaxFusedDiags ||
+        __builtin_popcountll(g.span | ((1ull << std::min(low_bits, f->plan.n_qubits)) - 1)) >
+            std::min(tile_bits, f->plan.n_qubits))
       return n_steps > 0;
   return false;
+}
+
+// Largest diagonal count among the factors a sweep may hold.
+int fused_dmax(const hs_factors* f) {
+  int d = 1;
+  for (const hs::Group& g : f->plan.groups)
+    if (g.D <= hs::kMaxFusedDiags && g.D > d) d = g.D;
+  return d;
 }
 
 int pick_rhs_block(hs_dtype dt, int n_rhs) {
@@ -107,7 +118,7 @@ int pick_rhs_block(hs_dtype dt, int n_rhs) {
 
 int pick_tile_bits(const hs_factors* f, int rhs_block) {
   const int n = f->plan.n_qubits;
-  int t = hs::max_tile_bits(f->dtype, rhs_block);
+  int t = hs::max_tile_bits(f->dtype, rhs_block, fused_dmax(f), hs::kSweepSmemDefault);
   // keep at least ~2 CTAs per SM when the state allows it
   int cap = n - 9;
   if (cap < min_low_bits(f->dtype) + 4) cap = min_low_bits(f->dtype) + 4;
@@ -262,10 +273,12 @@ int hs_plan_factors(const uint64_t* x, const uint64_t* z, size_t n_terms, int n_
   return HS_OK;
 }
 
-// Resolve evolve options: method, tile bits, rhs block.
+// Resolve evolve options: method, tile bits, rhs block, low bits.
 int resolve_opts(const hs_factors* f, int n_rhs, const hs_evolve_opts* opts, hs_evolve_opts& o, int& tb, int& rb) {
-  o = hs_evolve_opts{HS_METHOD_AUTO, 0, 0, 0};
+  o = hs_evolve_opts{HS_METHOD_AUTO, 0, 0, 0, 0};
   if (opts) o = *opts;
+  if (o.low_bits <= 0) o.low_bits = min_low_bits(f->dtype);
+  if (o.low_bits < (f->dtype == HS_C64 ? 1 : 0) || o.low_bits > 12) return fail(HS_EINVAL, "low_bits out of range");
   if (o.method != HS_METHOD_AUTO && o.method != HS_METHOD_PLAIN && o.method != HS_METHOD_FUSED)
     return fail(HS_EINVAL, "unknown method");
   rb = o.rhs_block > 0 ? o.rhs_block : pick_rhs_block(f->dtype, n_rhs);
@@ -273,7 +286,7 @@ int resolve_opts(const hs_factors* f, int n_rhs, const hs_evolve_opts* opts, hs_
     return fail(HS_EINVAL, "rhs_block must be 1, 2, 4, 8 (or 16 for complex64)");
   tb = o.tile_bits > 0 ? o.tile_bits : pick_tile_bits(f, rb);
   if (tb > f->plan.n_qubits) tb = f->plan.n_qubits;
-  if (tb > hs::max_tile_bits(f->dtype, rb))
+  if (o.method != HS_METHOD_PLAIN && tb > hs::max_tile_bits(f->dtype, rb, fused_dmax(f), hs::kSweepSmemDefault))
     return fail(HS_EINVAL, "tile_bits exceeds the shared-memory tile for this rhs_block");
   if (tb < 1) return fail(HS_EINVAL, "tile_bits must be >= 1");
   return HS_OK;
@@ -287,7 +300,7 @@ int hs_evolve_plan(const hs_factors* f, int n_rhs, int n_steps, const hs_evolve_
   int tb = 0, rb = 0;
   int rc = resolve_opts(f, n_rhs, opts, o, tb, rb);
   if (rc != HS_OK) return rc;
-  std::vector<hs::Sweep> sw = hs::plan_sweeps(f->plan, n_steps, tb, min_low_bits(f->dtype), o.method != HS_METHOD_PLAIN);
+  std::vector<hs::Sweep> sw = hs::plan_sweeps(f->plan, n_steps, tb, o.low_bits, o.method != HS_METHOD_PLAIN);
   int ns = 0, np = 0;
   for (const hs::Sweep& w : sw) (w.fused ? ns : np) += 1;
   if (n_sweeps) *n_sweeps = ns;
@@ -315,10 +328,10 @@ int hs_evolve_ex(const hs_factors* f, void* psi, int n_rhs, int n_steps, const h
   }
   cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
   const size_t state_bytes = size_t(n_rhs) * size_t(f->plan.N) * hs::elem_bytes(f->dtype);
-  const bool scratch_needed = needs_scratch(f, n_steps, o.method, tb);
+  const bool scratch_needed = needs_scratch(f, n_steps, o.method, tb, o.low_bits);
 
   if (o.use_graph) {
-    hs_factors::GraphKey key{psi, n_rhs, n_steps, int(o.method), tb, rb, nullptr};
+    hs_factors::GraphKey key{psi, n_rhs, n_steps, int(o.method), tb, rb * 64 + o.low_bits, nullptr};
     cudaGraphExec_t exec = nullptr;
     {
       std::lock_guard<std::mutex> lk(f->graph_mu);
@@ -332,7 +345,7 @@ int hs_evolve_ex(const hs_factors* f, void* psi, int n_rhs, int n_steps, const h
       if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
       e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
       if (e != cudaSuccess) { cudaStreamDestroy(cs); return cuda_fail(e, "cudaStreamBeginCapture"); }
-      int rc = enqueue_evolve(f, psi, n_rhs, n_steps, o.method, tb, rb, nullptr, cs);
+      int rc = enqueue_evolve(f, psi, n_rhs, n_steps, o.method, tb, rb, o.low_bits, nullptr, cs);
       cudaGraph_t graph = nullptr;
       e = cudaStreamEndCapture(cs, &graph);
       cudaStreamDestroy(cs);
@@ -354,7 +367,7 @@ int hs_evolve_ex(const hs_factors* f, void* psi, int n_rhs, int n_steps, const h
     cudaError_t e = cudaMallocAsync(&scratch, state_bytes, s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(scratch state)");
   }
-  int rc = enqueue_evolve(f, psi, n_rhs, n_steps, o.method, tb, rb, scratch, s);
+  int rc = enqueue_evolve(f, psi, n_rhs, n_steps, o.method, tb, rb, o.low_bits, scratch, s);
   if (scratch) cudaFreeAsync(scratch, s);
   return rc;
 }

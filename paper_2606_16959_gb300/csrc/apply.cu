@@ -10,16 +10,23 @@
 //  * apply_plain: one launch per factor application, out of place, one thread
 //    per row, factor values read once per launch and reused for every state
 //    of a multi-RHS block.
-//  * sweep: a CTA holds a TILE of 2^T amplitudes in shared memory -- the
-//    amplitudes whose bits outside a "local" bit set L are fixed by the CTA
-//    index -- and applies a run of consecutive factors whose flip masks lie
-//    inside L.  For such a factor every structural nonzero of row r sits in a
-//    column r xor u with u spanned by L, i.e. inside the same tile; a stored
-//    value on a column outside the tile is an exact zero written by the build,
-//    so the column is read at its in-tile image (the bits of r + d_k selected
-//    by L), which is always a valid shared-memory address and contributes 0.
-//    The tile is read from and written to global memory once per sweep
-//    instead of once per factor.
+//  * sweep: a CTA holds a TILE of 2^T amplitudes (for rhs_block states) in
+//    shared memory -- the amplitudes whose bits outside a "local" bit set L are
+//    fixed by the CTA index -- and applies a run of consecutive factors whose
+//    flip masks lie inside L.  For such a factor every structural nonzero of
+//    row r sits in a column r xor u with u spanned by L, i.e. inside the same
+//    tile; a stored value on a column outside the tile is an exact zero written
+//    by the build, so the column is read at its in-tile image (the bits of
+//    r + d_k selected by L), which is always a valid shared-memory address and
+//    contributes 0.  The tile is read from and written to global memory once
+//    per sweep instead of once per factor.
+//
+//    Factor values do not depend on the state, so they are staged into a ring
+//    of shared-memory stages with cp.async several factors ahead of their use,
+//    and the kernel is launched with programmatic dependent launch: the next
+//    sweep's CTAs start, stage their first factors while the previous sweep is
+//    still finishing, and only then wait (griddepcontrol.wait) before they read
+//    the state.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -88,9 +95,16 @@ struct SweepArgs {
   int rhs_block;
   int tile_bits;
   int n_tiles_log2;
+  int n_stages;      // factor stages in the shared-memory ring
+  int stage_diags;   // diagonals per stage (max D over the sweep's factors)
+  int n_meta;        // diagonals listed in the shared-memory metadata table
   Runs local, rest;
   int n_factors;
-  int factors[kMaxSweepFactors];
+  // Per factor of the sweep: first diagonal in the global diagonal arrays,
+  // diagonal count, and position of its first diagonal in the metadata table.
+  int fdiag0[kMaxSweepFactors];
+  int16_t fD[kMaxSweepFactors];
+  int16_t fmeta[kMaxSweepFactors];
 };
 
 // Scatter the low bits of v into the positions of the runs.
@@ -121,29 +135,90 @@ __device__ __forceinline__ uint32_t extract(uint32_t c, const Runs& R) {
   return out;
 }
 
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const uint32_t s = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// Wait until at most n of the most recently committed groups are pending.
+__device__ __forceinline__ void cp_async_wait(int n) {
+  switch (n) {
+    case 0: asm volatile("cp.async.wait_group 0;\n" ::: "memory"); break;
+    case 1: asm volatile("cp.async.wait_group 1;\n" ::: "memory"); break;
+    case 2: asm volatile("cp.async.wait_group 2;\n" ::: "memory"); break;
+    case 3: asm volatile("cp.async.wait_group 3;\n" ::: "memory"); break;
+    case 4: asm volatile("cp.async.wait_group 4;\n" ::: "memory"); break;
+    case 5: asm volatile("cp.async.wait_group 5;\n" ::: "memory"); break;
+    case 6: asm volatile("cp.async.wait_group 6;\n" ::: "memory"); break;
+    default: asm volatile("cp.async.wait_group 7;\n" ::: "memory"); break;
+  }
+}
+// Programmatic dependent launch controls (no-ops when launched without the attribute).
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void grid_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+
 template <typename R, int NT, int MAXROWS, int RB>
 __global__ void __launch_bounds__(NT) sweep_kernel(const __grid_constant__ SweepArgs a) {
   using T2 = typename C2<R>::T;
+  constexpr int V = 16 / sizeof(T2);  // elements per 16-byte chunk
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T2* tile = reinterpret_cast<T2*>(smem_raw);
+  const uint32_t TS = 1u << a.tile_bits;
+  // Shared memory: [diagonal metadata (offset, rowbase)][tile][factor stages]
+  longlong2* meta = reinterpret_cast<longlong2*>(smem_raw);
+  T2* tile = reinterpret_cast<T2*>(smem_raw + size_t(a.n_meta) * sizeof(longlong2));
+  T2* stages = tile + size_t(a.rhs_block) * TS;
+  const size_t stage_elems = size_t(a.stage_diags) * TS;
   // src and dst may be the same buffer (in-place sweep): every CTA reads its
   // own tile completely before it writes it back, and tiles are disjoint.
   const T2* src = reinterpret_cast<const T2*>(a.src);
   T2* dst = reinterpret_cast<T2*>(a.dst);
   const T2* __restrict__ vals = reinterpret_cast<const T2*>(a.vals);
 
-  const uint32_t TS = 1u << a.tile_bits;
   const uint32_t tile_id = blockIdx.x & ((1u << a.n_tiles_log2) - 1u);
   const int rhs0 = int(blockIdx.x >> a.n_tiles_log2) * a.rhs_block;
   const int nrb = min(a.rhs_block, a.n_rhs - rhs0);
   const uint32_t base = deposit(tile_id, a.rest);
+  const uint32_t n_chunks = TS / V;
 
-  // Load the tile.
-  for (uint32_t l = threadIdx.x; l < TS; l += NT) {
-    const int64_t g = int64_t(deposit(l, a.local) | base);
-    for (int q = 0; q < nrb; ++q) tile[q * TS + l] = src[int64_t(rhs0 + q) * a.N + g];
+  // Diagonal metadata of every factor of the sweep, loaded in parallel once.
+  for (int i = 0; i < a.n_factors; ++i)
+    for (int k = threadIdx.x; k < a.fD[i]; k += NT)
+      meta[a.fmeta[i] + k] = make_longlong2(a.offs[a.fdiag0[i] + k], a.rowbase[a.fdiag0[i] + k]);
+  __syncthreads();
+
+  // Stage the tile rows of factor fi's diagonals (16-byte chunks; a chunk is
+  // skipped when none of its rows has an element on that diagonal).
+  auto issue_factor = [&](int fi, int stage) {
+    const int D = a.fD[fi];
+    const longlong2* m = meta + a.fmeta[fi];
+    T2* st = stages + size_t(stage) * stage_elems;
+    for (int k = 0; k < D; ++k) {
+      const longlong2 dk = m[k];
+      const T2* vk = vals + dk.y;
+      for (uint32_t j = threadIdx.x; j < n_chunks; j += NT) {
+        const uint32_t l = j * V;
+        const int64_t r = int64_t(deposit(l, a.local) | base);
+        if (r + (V - 1) + dk.x >= 0 && r + dk.x < a.N) cp_async16(st + size_t(k) * TS + l, vk + r);
+      }
+    }
+  };
+
+  const int S = a.n_stages;
+  for (int s = 0; s < S; ++s) {
+    if (s < a.n_factors) issue_factor(s, s);
+    cp_async_commit();
   }
-  // Rows of this thread: local indices threadIdx.x + i * NT below TS.
+  // The state written by the previous launch is visible only after this.
+  grid_dependency_wait();
+  for (int q = 0; q < nrb; ++q) {
+    const T2* sq = src + int64_t(rhs0 + q) * a.N;
+    for (uint32_t j = threadIdx.x; j < n_chunks; j += NT) {
+      const uint32_t l = j * V;
+      cp_async16(tile + size_t(q) * TS + l, sq + (deposit(l, a.local) | base));
+    }
+  }
+  cp_async_commit();
+
   uint32_t myrow[MAXROWS];
   bool valid[MAXROWS];
 #pragma unroll
@@ -152,28 +227,29 @@ __global__ void __launch_bounds__(NT) sweep_kernel(const __grid_constant__ Sweep
     valid[i] = l < TS;
     myrow[i] = valid[i] ? (deposit(l, a.local) | base) : 0u;
   }
-  __syncthreads();
 
   for (int fi = 0; fi < a.n_factors; ++fi) {
-    const int f = a.factors[fi];
-    const int D = a.fac_D[f], d0 = a.fac_diag0[f];
+    cp_async_wait(fi == 0 ? 0 : S - 1);
+    __syncthreads();
+    const int D = a.fD[fi];
+    const longlong2* m = meta + a.fmeta[fi];
+    const T2* st = stages + size_t(fi % S) * stage_elems;
     T2 acc[MAXROWS][RB];
 #pragma unroll
     for (int i = 0; i < MAXROWS; ++i)
 #pragma unroll
       for (int q = 0; q < RB; ++q) acc[i][q] = T2{0, 0};
     for (int k = 0; k < D; ++k) {
-      const int64_t d = a.offs[d0 + k];
-      const int64_t rb = a.rowbase[d0 + k];
+      const int64_t d = m[k].x;
 #pragma unroll
       for (int i = 0; i < MAXROWS; ++i) {
         const int64_t c = int64_t(myrow[i]) + d;
         if (valid[i] && c >= 0 && c < a.N) {
-          const T2 v = vals[rb + myrow[i]];
+          const T2 v = st[size_t(k) * TS + threadIdx.x + i * NT];
           const uint32_t lc = extract(uint32_t(c), a.local);
 #pragma unroll
           for (int q = 0; q < RB; ++q)
-            if (q < nrb) cfma(acc[i][q], v, tile[q * TS + lc]);
+            if (q < nrb) cfma(acc[i][q], v, tile[size_t(q) * TS + lc]);
         }
       }
     }
@@ -183,15 +259,23 @@ __global__ void __launch_bounds__(NT) sweep_kernel(const __grid_constant__ Sweep
       if (valid[i])
 #pragma unroll
         for (int q = 0; q < RB; ++q)
-          if (q < nrb) tile[q * TS + threadIdx.x + i * NT] = acc[i][q];
-    __syncthreads();
+          if (q < nrb) tile[size_t(q) * TS + threadIdx.x + i * NT] = acc[i][q];
+    // Refill the stage just consumed (every thread is past the barrier above).
+    if (fi + S < a.n_factors) issue_factor(fi + S, fi % S);
+    cp_async_commit();
   }
+  __syncthreads();
 
   // Store the tile.
-  for (uint32_t l = threadIdx.x; l < TS; l += NT) {
-    const int64_t g = int64_t(deposit(l, a.local) | base);
-    for (int q = 0; q < nrb; ++q) dst[int64_t(rhs0 + q) * a.N + g] = tile[q * TS + l];
+  for (int q = 0; q < nrb; ++q) {
+    T2* dq = dst + int64_t(rhs0 + q) * a.N;
+    for (uint32_t j = threadIdx.x; j < n_chunks; j += NT) {
+      const uint32_t l = j * V;
+      *reinterpret_cast<uint4*>(dq + (deposit(l, a.local) | base)) =
+          *reinterpret_cast<const uint4*>(tile + size_t(q) * TS + l);
+    }
   }
+  grid_launch_dependents();
 }
 
 constexpr int kSweepThreads = 256;
@@ -208,14 +292,21 @@ constexpr auto sweep_fn() {
 }
 
 template <typename R, int RB>
-cudaError_t launch_sweep_t(const SweepArgs& a, int n_blocks, size_t smem, cudaStream_t s) {
-  sweep_fn<R, RB>()<<<n_blocks, kSweepThreads, smem, s>>>(a);
-  return cudaGetLastError();
+cudaError_t launch_sweep_t(const SweepArgs& a, int n_blocks, size_t smem, bool pdl, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(unsigned(n_blocks), 1u, 1u);
+  cfg.blockDim = dim3(unsigned(kSweepThreads), 1u, 1u);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, sweep_fn<R, RB>(), a);
 }
 
 }  // namespace
-
-constexpr size_t kSweepSmemBudget = 96 * 1024;
 
 // Raise the dynamic shared-memory limit of every sweep instantiation once per
 // device (before any launch or stream capture).
@@ -227,7 +318,7 @@ cudaError_t prepare_kernels() {
   if (e != cudaSuccess) return e;
   std::lock_guard<std::mutex> lk(mu);
   if (dev < 64 && done[dev]) return cudaSuccess;
-  const int b = int(kSweepSmemBudget);
+  const int b = int(kSweepSmemMax);
   const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
   cudaError_t r = cudaSuccess;
   auto set = [&](const void* fn) { if (r == cudaSuccess) r = cudaFuncSetAttribute(fn, A, b); };
@@ -244,12 +335,21 @@ cudaError_t prepare_kernels() {
   return r;
 }
 
-int max_tile_bits(hs_dtype dt, int rhs_block) {
-  // Largest T with rhs_block * 2^T * elem <= budget and 2^T <= threads * rows per thread.
+size_t sweep_smem_bytes(hs_dtype dt, int rhs_block, int tile_bits, int stage_diags, int n_stages) {
+  return (size_t(rhs_block) + size_t(stage_diags) * n_stages) * (size_t(1) << tile_bits) * elem_bytes(dt);
+}
+
+// Metadata table of a sweep: one (offset, rowbase) pair per listed diagonal.
+static size_t meta_bytes(int n_meta) { return size_t(n_meta) * 16; }
+
+int max_rows_per_thread(hs_dtype dt, int rhs_block) { return max_rows(dt, rhs_block); }
+
+int max_tile_bits(hs_dtype dt, int rhs_block, int stage_diags, size_t budget) {
+  // Largest T whose tile plus two factor stages fit the budget, with at most
+  // max_rows rows per thread.
   const int rows = max_rows(dt, rhs_block);
   int t = 0;
-  while ((size_t(rhs_block) << (t + 1)) * elem_bytes(dt) <= kSweepSmemBudget &&
-         (1 << (t + 1)) <= kSweepThreads * rows)
+  while (sweep_smem_bytes(dt, rhs_block, t + 1, stage_diags, 2) <= budget && (1 << (t + 1)) <= kSweepThreads * rows)
     ++t;
   return t;
 }
@@ -296,18 +396,38 @@ cudaError_t launch_sweep(const hs_factors* f, const SweepLaunch& L, cudaStream_t
   a.local = L.local;
   a.rest = L.rest;
   a.n_factors = L.n_factors;
-  for (int i = 0; i < L.n_factors; ++i) a.factors[i] = L.factors[i];
+  int dmax = 1, n_meta = 0;
+  for (int i = 0; i < L.n_factors; ++i) {
+    const Group& G = p.groups[L.factors[i]];
+    a.fdiag0[i] = G.diag0;
+    a.fD[i] = int16_t(G.D);
+    a.fmeta[i] = int16_t(n_meta);
+    n_meta += G.D;
+    dmax = G.D > dmax ? G.D : dmax;
+  }
+  if (n_meta > 32767) return cudaErrorInvalidValue;
+  a.n_meta = n_meta;
+  a.stage_diags = dmax;
+  // As many stages (<= 8, <= n_factors) as the shared-memory budget allows.
+  int S = 1;
+  while (S < 8 && S < L.n_factors &&
+         meta_bytes(n_meta) + sweep_smem_bytes(f->dtype, L.rhs_block, L.tile_bits, dmax, S + 1) <= L.smem_budget)
+    ++S;
+  a.n_stages = S;
+  const size_t smem = meta_bytes(n_meta) + sweep_smem_bytes(f->dtype, L.rhs_block, L.tile_bits, dmax, S);
+  if (smem > kSweepSmemMax || L.tile_bits > p.n_qubits) return cudaErrorInvalidValue;
+  const int rows = max_rows(f->dtype, L.rhs_block);
+  if ((1 << L.tile_bits) > kSweepThreads * rows) return cudaErrorInvalidValue;
+  if (L.tile_bits < (f->dtype == HS_C64 ? 1 : 0)) return cudaErrorInvalidValue;
   const int n_rhs_blocks = (L.n_rhs + L.rhs_block - 1) / L.rhs_block;
   const int n_blocks = (1 << a.n_tiles_log2) * n_rhs_blocks;
-  const size_t smem = (size_t(L.rhs_block) << L.tile_bits) * elem_bytes(f->dtype);
-  if (L.tile_bits > max_tile_bits(f->dtype, L.rhs_block) || L.tile_bits > p.n_qubits) return cudaErrorInvalidValue;
   const bool c64 = f->dtype == HS_C64;
   switch (L.rhs_block) {
-    case 1: return c64 ? launch_sweep_t<float, 1>(a, n_blocks, smem, s) : launch_sweep_t<double, 1>(a, n_blocks, smem, s);
-    case 2: return c64 ? launch_sweep_t<float, 2>(a, n_blocks, smem, s) : launch_sweep_t<double, 2>(a, n_blocks, smem, s);
-    case 4: return c64 ? launch_sweep_t<float, 4>(a, n_blocks, smem, s) : launch_sweep_t<double, 4>(a, n_blocks, smem, s);
-    case 8: return c64 ? launch_sweep_t<float, 8>(a, n_blocks, smem, s) : launch_sweep_t<double, 8>(a, n_blocks, smem, s);
-    case 16: return c64 ? launch_sweep_t<float, 16>(a, n_blocks, smem, s) : cudaErrorInvalidValue;
+    case 1: return c64 ? launch_sweep_t<float, 1>(a, n_blocks, smem, L.pdl, s) : launch_sweep_t<double, 1>(a, n_blocks, smem, L.pdl, s);
+    case 2: return c64 ? launch_sweep_t<float, 2>(a, n_blocks, smem, L.pdl, s) : launch_sweep_t<double, 2>(a, n_blocks, smem, L.pdl, s);
+    case 4: return c64 ? launch_sweep_t<float, 4>(a, n_blocks, smem, L.pdl, s) : launch_sweep_t<double, 4>(a, n_blocks, smem, L.pdl, s);
+    case 8: return c64 ? launch_sweep_t<float, 8>(a, n_blocks, smem, L.pdl, s) : launch_sweep_t<double, 8>(a, n_blocks, smem, L.pdl, s);
+    case 16: return c64 ? launch_sweep_t<float, 16>(a, n_blocks, smem, L.pdl, s) : cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
   }
 }

@@ -17,6 +17,9 @@ constexpr int kMaxDiags = 4096;     // diagonals per factor
 constexpr int kMaxXDim = 6;         // log2 of the x-mask set size per factor
 constexpr int kMaxRuns = 6;         // contiguous bit runs describing a tile's local bits
 constexpr int kMaxSweepFactors = 64;
+constexpr int kMaxFusedDiags = 32;                 // factors with more diagonals use the plain kernel
+constexpr size_t kSweepSmemMax = 227 * 1024;       // opt-in shared memory per CTA
+constexpr size_t kSweepSmemDefault = 112 * 1024;   // two sweep CTAs per SM
 
 // Storage alignment of each diagonal's row-indexed base, in elements (32 bytes).
 inline int64_t align_elems(hs_dtype dt) { return dt == HS_C64 ? 4 : 2; }
@@ -71,7 +74,10 @@ struct Sweep {
 };
 
 // Plan the launches for n_steps steps with tiles of tile_bits local bits.
-std::vector<Sweep> plan_sweeps(const Plan& p, int n_steps, int tile_bits, int min_low_bits, bool fused);
+// Factors with more than max_fused_diags diagonals, or whose flip span does not
+// fit a tile, get plain launches.
+std::vector<Sweep> plan_sweeps(const Plan& p, int n_steps, int tile_bits, int min_low_bits, bool fused,
+                               int max_fused_diags = kMaxFusedDiags);
 
 // Decompose a bit mask into runs of consecutive set bits (low to high).
 Runs runs_of(uint64_t mask, int n_bits);
@@ -120,9 +126,13 @@ struct SweepLaunch {
   Runs local, rest;
   int n_factors;
   int factors[kMaxSweepFactors];
+  size_t smem_budget;  // shared memory the launch may use (sets the number of factor stages)
+  bool pdl;            // launch with programmatic dependent launch
 };
 cudaError_t launch_sweep(const hs_factors* f, const SweepLaunch& L, cudaStream_t s);
-int max_tile_bits(hs_dtype dt, int rhs_block);
+size_t sweep_smem_bytes(hs_dtype dt, int rhs_block, int tile_bits, int stage_diags, int n_stages);
+int max_tile_bits(hs_dtype dt, int rhs_block, int stage_diags, size_t budget);
+int max_rows_per_thread(hs_dtype dt, int rhs_block);
 cudaError_t prepare_kernels();
 
 cudaError_t launch_inner(const void* a, const void* b, int64_t N, hs_dtype dt, double* d_out4, cudaStream_t s);

@@ -204,7 +204,9 @@ int make_plan(const uint64_t* x, const uint64_t* z, const double* coeff, size_t 
     }
     plan.groups.push_back(G);
   }
-  plan.total_elems = cursor;
+  // One extra aligned block: a 16-byte staging copy that straddles the end of
+  // the last diagonal stays inside the allocation.
+  plan.total_elems = cursor + A;
   return HS_OK;
 }
 
@@ -222,7 +224,8 @@ Runs runs_of(uint64_t mask, int n_bits) {
   return r;
 }
 
-std::vector<Sweep> plan_sweeps(const Plan& p, int n_steps, int tile_bits, int min_low_bits, bool fused) {
+std::vector<Sweep> plan_sweeps(const Plan& p, int n_steps, int tile_bits, int min_low_bits, bool fused,
+                               int max_fused_diags) {
   std::vector<Sweep> out;
   const int n = p.n_qubits;
   const uint64_t all = (n >= 64) ? ~0ull : ((1ull << n) - 1);
@@ -240,7 +243,7 @@ std::vector<Sweep> plan_sweeps(const Plan& p, int n_steps, int tile_bits, int mi
   for (int st = 0; st < n_steps; ++st) {
     for (int g = 0; g < int(p.groups.size()); ++g) {
       uint64_t span = p.groups[g].span;
-      bool fits_alone = fused && __builtin_popcountll(span | low) <= tile_bits;
+      bool fits_alone = fused && p.groups[g].D <= max_fused_diags && __builtin_popcountll(span | low) <= tile_bits;
       if (!fits_alone) {
         if (!cur.factors.empty()) close(cur, used);
         used = 0;

@@ -36,7 +36,7 @@ class HSError(RuntimeError):
 
 class EvolveOpts(ctypes.Structure):
     _fields_ = [("method", ctypes.c_int), ("tile_bits", ctypes.c_int), ("rhs_block", ctypes.c_int),
-                ("use_graph", ctypes.c_int)]
+                ("use_graph", ctypes.c_int), ("low_bits", ctypes.c_int)]
 
 
 _lib = None
@@ -205,16 +205,16 @@ def hs_evolve(f: Factors, psi, n_steps: int, stream=None) -> None:
 
 
 def hs_evolve_ex(f: Factors, psi, n_steps: int, method: int = HS_METHOD_AUTO, tile_bits: int = 0,
-                 rhs_block: int = 0, use_graph: bool = False, stream=None) -> None:
+                 rhs_block: int = 0, use_graph: bool = False, low_bits: int = 0, stream=None) -> None:
     ptr, n_rhs = _check_state(f, psi)
-    o = EvolveOpts(int(method), int(tile_bits), int(rhs_block), int(bool(use_graph)))
+    o = EvolveOpts(int(method), int(tile_bits), int(rhs_block), int(bool(use_graph)), int(low_bits))
     _check(lib().hs_evolve_ex(f.handle, ptr, n_rhs, int(n_steps), ctypes.byref(o), _stream(stream)))
 
 
 def hs_evolve_plan(f: Factors, n_rhs: int, n_steps: int, method: int = HS_METHOD_AUTO, tile_bits: int = 0,
-                   rhs_block: int = 0, use_graph: bool = False):
+                   rhs_block: int = 0, use_graph: bool = False, low_bits: int = 0):
     """(n_sweep_launches, n_plain_launches, tile_bits, rhs_block) hs_evolve_ex would use."""
-    o = EvolveOpts(int(method), int(tile_bits), int(rhs_block), int(bool(use_graph)))
+    o = EvolveOpts(int(method), int(tile_bits), int(rhs_block), int(bool(use_graph)), int(low_bits))
     a, b, c, d = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     _check(lib().hs_evolve_plan(f.handle, int(n_rhs), int(n_steps), ctypes.byref(o), ctypes.byref(a), ctypes.byref(b),
                                 ctypes.byref(c), ctypes.byref(d)))

@@ -52,7 +52,7 @@ def _compare(oracle, x, z, n, budget):
         assert g[2] == w.offsets
     N = 1 << n
     S = sum(N - abs(d) for g in got for d in g[2])
-    assert S * 8 <= vbytes <= (S + 4 * sum(len(g[2]) for g in got)) * 8
+    assert S * 8 <= vbytes <= (S + 4 * sum(len(g[2]) for g in got) + 4) * 8
 
 
 def test_plan_matches_oracle_families(oracle, lib):

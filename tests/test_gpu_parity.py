@@ -196,7 +196,7 @@ def test_small_tiles_and_plain_fallback(dt):
     coeffs = rng.uniform(-1, 1, len(labels))
     psi0 = np.stack([W.gaussian_state(n, rng) for _ in range(3)])
     want = oracle_evolve(labels, coeffs, 1.1, 4, psi0)
-    for tb, rb in ((8, 1), (8, 2), (9, 4), (11, 1)):
+    for tb, rb in ((5, 1), (6, 2), (7, 1), (8, 4)):
         got = gpu_evolve(labels, coeffs, 1.1, 4, 4, dt, psi0, method=hs.HS_METHOD_FUSED, tile_bits=tb, rhs_block=rb)
         check_state(got, want, dt)
 
