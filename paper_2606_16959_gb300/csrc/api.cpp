@@ -52,11 +52,9 @@ void release(hs_factors* f) {
 }
 
 // Enqueue the launches of one evolution on stream s.
-int enqueue_evolve(const hs_factors* f, void* psi, int n_rhs, int n_steps, hs_method method, int tile_bits,
-                   int rhs_block, int low_bits, void* scratch, cudaStream_t s) {
+int enqueue_evolve(const hs_factors* f, const std::vector<hs::Sweep>& sw, void* psi, int n_rhs, int tile_bits,
+                   int rhs_block, void* scratch, cudaStream_t s) {
   const hs::Plan& p = f->plan;
-  const bool fused = method != HS_METHOD_PLAIN;
-  std::vector<hs::Sweep> sw = hs::plan_sweeps(p, n_steps, tile_bits, low_bits, fused);
   void* cur = psi;
   void* other = scratch;
   const uint64_t all = (1ull << p.n_qubits) - 1;
@@ -69,7 +67,7 @@ int enqueue_evolve(const hs_factors* f, void* psi, int n_rhs, int n_steps, hs_me
       L.n_rhs = n_rhs;
       L.rhs_block = rhs_block;
       L.tile_bits = std::min(tile_bits, p.n_qubits);
-      L.local = hs::runs_of(w.local_mask, p.n_qubits);
+      L.local_mask = w.local_mask;
       L.rest = hs::runs_of(~uint64_t(w.local_mask) & all, p.n_qubits);
       L.n_factors = int(w.factors.size());
       for (int i = 0; i < L.n_factors; ++i) L.factors[i] = w.factors[i];
@@ -91,13 +89,9 @@ int enqueue_evolve(const hs_factors* f, void* psi, int n_rhs, int n_steps, hs_me
   return HS_OK;
 }
 
-bool needs_scratch(const hs_factors* f, int n_steps, hs_method method, int tile_bits, int low_bits) {
-  if (method == HS_METHOD_PLAIN) return n_steps > 0;
-  for (const hs::Group& g : f->plan.groups)
-    if (g.D > hs::kMaxFusedDiags ||
-        __builtin_popcountll(g.span | ((1ull << std::min(low_bits, f->plan.n_qubits)) - 1)) >
-            std::min(tile_bits, f->plan.n_qubits))
-      return n_steps > 0;
+bool has_plain(const std::vector<hs::Sweep>& sw) {
+  for (const hs::Sweep& w : sw)
+    if (!w.fused) return true;
   return false;
 }
 
@@ -328,7 +322,8 @@ int hs_evolve_ex(const hs_factors* f, void* psi, int n_rhs, int n_steps, const h
   }
   cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
   const size_t state_bytes = size_t(n_rhs) * size_t(f->plan.N) * hs::elem_bytes(f->dtype);
-  const bool scratch_needed = needs_scratch(f, n_steps, o.method, tb, o.low_bits);
+  const std::vector<hs::Sweep> sw = hs::plan_sweeps(f->plan, n_steps, tb, o.low_bits, o.method != HS_METHOD_PLAIN);
+  const bool scratch_needed = has_plain(sw);
 
   if (o.use_graph) {
     hs_factors::GraphKey key{psi, n_rhs, n_steps, int(o.method), tb, rb * 64 + o.low_bits, nullptr};
@@ -345,7 +340,7 @@ int hs_evolve_ex(const hs_factors* f, void* psi, int n_rhs, int n_steps, const h
       if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
       e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
       if (e != cudaSuccess) { cudaStreamDestroy(cs); return cuda_fail(e, "cudaStreamBeginCapture"); }
-      int rc = enqueue_evolve(f, psi, n_rhs, n_steps, o.method, tb, rb, o.low_bits, nullptr, cs);
+      int rc = enqueue_evolve(f, sw, psi, n_rhs, tb, rb, nullptr, cs);
       cudaGraph_t graph = nullptr;
       e = cudaStreamEndCapture(cs, &graph);
       cudaStreamDestroy(cs);
@@ -367,7 +362,7 @@ int hs_evolve_ex(const hs_factors* f, void* psi, int n_rhs, int n_steps, const h
     cudaError_t e = cudaMallocAsync(&scratch, state_bytes, s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(scratch state)");
   }
-  int rc = enqueue_evolve(f, psi, n_rhs, n_steps, o.method, tb, rb, o.low_bits, scratch, s);
+  int rc = enqueue_evolve(f, sw, psi, n_rhs, tb, rb, scratch, s);
   if (scratch) cudaFreeAsync(scratch, s);
   return rc;
 }

@@ -88,8 +88,6 @@ struct SweepArgs {
   const void* vals;
   const int64_t* offs;
   const int64_t* rowbase;
-  const int* fac_D;
-  const int* fac_diag0;
   int64_t N;
   int n_rhs;
   int rhs_block;
@@ -98,7 +96,11 @@ struct SweepArgs {
   int n_stages;      // factor stages in the shared-memory ring
   int stage_diags;   // diagonals per stage (max D over the sweep's factors)
   int n_meta;        // diagonals listed in the shared-memory metadata table
-  Runs local, rest;
+  // Local bits [0, a) U [h, h + w): local index of row r is
+  // (r & m0) | ((r >> sh) & m1), with m0 = 2^a - 1, m1 = (2^w - 1) << a, sh = h - a.
+  uint32_t m0, m1;
+  int sh;
+  Runs rest;         // the other bits, enumerated by the CTA index
   int n_factors;
   // Per factor of the sweep: first diagonal in the global diagonal arrays,
   // diagonal count, and position of its first diagonal in the metadata table.
@@ -108,36 +110,26 @@ struct SweepArgs {
 };
 
 // Scatter the low bits of v into the positions of the runs.
-__device__ __forceinline__ uint32_t deposit(uint32_t v, const Runs& R) {
+__device__ __forceinline__ uint32_t deposit_runs(uint32_t v, const Runs& R) {
   uint32_t out = 0;
   int q = 0;
-#pragma unroll
-  for (int i = 0; i < kMaxRuns + 2; ++i) {
-    if (i < R.n) {
-      out |= ((v >> q) & ((1u << R.len[i]) - 1u)) << R.pos[i];
-      q += R.len[i];
-    }
+  for (int i = 0; i < R.n; ++i) {
+    out |= ((v >> q) & ((1u << R.len[i]) - 1u)) << R.pos[i];
+    q += R.len[i];
   }
   return out;
 }
 
-// Gather the bits of c at the runs' positions into the low bits.
-__device__ __forceinline__ uint32_t extract(uint32_t c, const Runs& R) {
-  uint32_t out = 0;
-  int q = 0;
-#pragma unroll
-  for (int i = 0; i < kMaxRuns + 2; ++i) {
-    if (i < R.n) {
-      out |= ((c >> R.pos[i]) & ((1u << R.len[i]) - 1u)) << q;
-      q += R.len[i];
-    }
-  }
-  return out;
+__device__ __forceinline__ uint32_t local_of(uint32_t c, uint32_t m0, uint32_t m1, int sh) {
+  return (c & m0) | ((c >> sh) & m1);
+}
+__device__ __forceinline__ uint32_t global_of(uint32_t l, uint32_t m0, uint32_t m1, int sh) {
+  return (l & m0) | ((l & m1) << sh);
 }
 
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, uint32_t src_bytes) {
   const uint32_t s = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(src_bytes) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 // Wait until at most n of the most recently committed groups are pending.
@@ -157,17 +149,21 @@ __device__ __forceinline__ void cp_async_wait(int n) {
 __device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
 __device__ __forceinline__ void grid_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
 
-template <typename R, int NT, int MAXROWS, int RB>
-__global__ void __launch_bounds__(NT) sweep_kernel(const __grid_constant__ SweepArgs a) {
+// Block of TS / ROWS threads; thread t owns local rows t + i * blockDim.x.
+template <typename R, int ROWS, int RB>
+__global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ SweepArgs a) {
   using T2 = typename C2<R>::T;
   constexpr int V = 16 / sizeof(T2);  // elements per 16-byte chunk
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int NT = blockDim.x;
   const uint32_t TS = 1u << a.tile_bits;
+  const uint32_t m0 = a.m0, m1 = a.m1;
+  const int sh = a.sh;
   // Shared memory: [diagonal metadata (offset, rowbase)][tile][factor stages]
   longlong2* meta = reinterpret_cast<longlong2*>(smem_raw);
   T2* tile = reinterpret_cast<T2*>(smem_raw + size_t(a.n_meta) * sizeof(longlong2));
   T2* stages = tile + size_t(a.rhs_block) * TS;
-  const size_t stage_elems = size_t(a.stage_diags) * TS;
+  const uint32_t stage_elems = uint32_t(a.stage_diags) * TS;
   // src and dst may be the same buffer (in-place sweep): every CTA reads its
   // own tile completely before it writes it back, and tiles are disjoint.
   const T2* src = reinterpret_cast<const T2*>(a.src);
@@ -177,8 +173,9 @@ __global__ void __launch_bounds__(NT) sweep_kernel(const __grid_constant__ Sweep
   const uint32_t tile_id = blockIdx.x & ((1u << a.n_tiles_log2) - 1u);
   const int rhs0 = int(blockIdx.x >> a.n_tiles_log2) * a.rhs_block;
   const int nrb = min(a.rhs_block, a.n_rhs - rhs0);
-  const uint32_t base = deposit(tile_id, a.rest);
+  const uint32_t base = deposit_runs(tile_id, a.rest);
   const uint32_t n_chunks = TS / V;
+  const int N = int(a.N);  // N <= 2^30
 
   // Diagonal metadata of every factor of the sweep, loaded in parallel once.
   for (int i = 0; i < a.n_factors; ++i)
@@ -186,19 +183,34 @@ __global__ void __launch_bounds__(NT) sweep_kernel(const __grid_constant__ Sweep
       meta[a.fmeta[i] + k] = make_longlong2(a.offs[a.fdiag0[i] + k], a.rowbase[a.fdiag0[i] + k]);
   __syncthreads();
 
-  // Stage the tile rows of factor fi's diagonals (16-byte chunks; a chunk is
-  // skipped when none of its rows has an element on that diagonal).
+  // Stage the tile rows of factor fi's diagonals.  A row without an element on
+  // a diagonal (r + d outside [0, N)) gets the value 0, so the multiply loop
+  // needs no bounds test: its column is read at a valid in-tile index and
+  // contributes nothing.
   auto issue_factor = [&](int fi, int stage) {
     const int D = a.fD[fi];
     const longlong2* m = meta + a.fmeta[fi];
     T2* st = stages + size_t(stage) * stage_elems;
     for (int k = 0; k < D; ++k) {
-      const longlong2 dk = m[k];
-      const T2* vk = vals + dk.y;
+      const int d = int(m[k].x);
+      const T2* vk = vals + m[k].y;
       for (uint32_t j = threadIdx.x; j < n_chunks; j += NT) {
         const uint32_t l = j * V;
-        const int64_t r = int64_t(deposit(l, a.local) | base);
-        if (r + (V - 1) + dk.x >= 0 && r + dk.x < a.N) cp_async16(st + size_t(k) * TS + l, vk + r);
+        const int r = int(global_of(l, m0, m1, sh) | base);
+        T2* dst_s = st + size_t(k) * TS + l;
+        const bool first_ok = r + d >= 0 && r + d < N;
+        const bool last_ok = r + (V - 1) + d >= 0 && r + (V - 1) + d < N;
+        if (first_ok && last_ok) {
+          cp_async16(dst_s, vk + r, 16);
+        } else if (!first_ok && !last_ok) {
+          cp_async16(dst_s, vals, 0);  // zero fill, nothing read
+        } else {
+#pragma unroll
+          for (int e = 0; e < V; ++e) {
+            const bool ok = r + e + d >= 0 && r + e + d < N;
+            dst_s[e] = ok ? vk[r + e] : T2{0, 0};
+          }
+        }
       }
     }
   };
@@ -214,52 +226,43 @@ __global__ void __launch_bounds__(NT) sweep_kernel(const __grid_constant__ Sweep
     const T2* sq = src + int64_t(rhs0 + q) * a.N;
     for (uint32_t j = threadIdx.x; j < n_chunks; j += NT) {
       const uint32_t l = j * V;
-      cp_async16(tile + size_t(q) * TS + l, sq + (deposit(l, a.local) | base));
+      cp_async16(tile + size_t(q) * TS + l, sq + (global_of(l, m0, m1, sh) | base), 16);
     }
   }
   cp_async_commit();
 
-  uint32_t myrow[MAXROWS];
-  bool valid[MAXROWS];
+  uint32_t myrow[ROWS];
 #pragma unroll
-  for (int i = 0; i < MAXROWS; ++i) {
-    const uint32_t l = threadIdx.x + uint32_t(i) * NT;
-    valid[i] = l < TS;
-    myrow[i] = valid[i] ? (deposit(l, a.local) | base) : 0u;
-  }
+  for (int i = 0; i < ROWS; ++i) myrow[i] = global_of(threadIdx.x + uint32_t(i) * NT, m0, m1, sh) | base;
 
   for (int fi = 0; fi < a.n_factors; ++fi) {
     cp_async_wait(fi == 0 ? 0 : S - 1);
     __syncthreads();
     const int D = a.fD[fi];
     const longlong2* m = meta + a.fmeta[fi];
-    const T2* st = stages + size_t(fi % S) * stage_elems;
-    T2 acc[MAXROWS][RB];
+    const T2* st = stages + size_t(fi % S) * stage_elems + threadIdx.x;
+    T2 acc[ROWS][RB];
 #pragma unroll
-    for (int i = 0; i < MAXROWS; ++i)
+    for (int i = 0; i < ROWS; ++i)
 #pragma unroll
       for (int q = 0; q < RB; ++q) acc[i][q] = T2{0, 0};
     for (int k = 0; k < D; ++k) {
-      const int64_t d = m[k].x;
+      const int d = int(m[k].x);
 #pragma unroll
-      for (int i = 0; i < MAXROWS; ++i) {
-        const int64_t c = int64_t(myrow[i]) + d;
-        if (valid[i] && c >= 0 && c < a.N) {
-          const T2 v = st[size_t(k) * TS + threadIdx.x + i * NT];
-          const uint32_t lc = extract(uint32_t(c), a.local);
+      for (int i = 0; i < ROWS; ++i) {
+        const T2 v = st[k * TS + i * NT];
+        const uint32_t lc = local_of(uint32_t(int(myrow[i]) + d), m0, m1, sh);
 #pragma unroll
-          for (int q = 0; q < RB; ++q)
-            if (q < nrb) cfma(acc[i][q], v, tile[size_t(q) * TS + lc]);
-        }
+        for (int q = 0; q < RB; ++q)
+          if (q < nrb) cfma(acc[i][q], v, tile[q * TS + lc]);
       }
     }
     __syncthreads();
 #pragma unroll
-    for (int i = 0; i < MAXROWS; ++i)
-      if (valid[i])
+    for (int i = 0; i < ROWS; ++i)
 #pragma unroll
-        for (int q = 0; q < RB; ++q)
-          if (q < nrb) tile[size_t(q) * TS + threadIdx.x + i * NT] = acc[i][q];
+      for (int q = 0; q < RB; ++q)
+        if (q < nrb) tile[q * TS + threadIdx.x + i * NT] = acc[i][q];
     // Refill the stage just consumed (every thread is past the barrier above).
     if (fi + S < a.n_factors) issue_factor(fi + S, fi % S);
     cp_async_commit();
@@ -271,39 +274,35 @@ __global__ void __launch_bounds__(NT) sweep_kernel(const __grid_constant__ Sweep
     T2* dq = dst + int64_t(rhs0 + q) * a.N;
     for (uint32_t j = threadIdx.x; j < n_chunks; j += NT) {
       const uint32_t l = j * V;
-      *reinterpret_cast<uint4*>(dq + (deposit(l, a.local) | base)) =
+      *reinterpret_cast<uint4*>(dq + (global_of(l, m0, m1, sh) | base)) =
           *reinterpret_cast<const uint4*>(tile + size_t(q) * TS + l);
     }
   }
   grid_launch_dependents();
 }
 
-constexpr int kSweepThreads = 256;
+constexpr int kSweepMaxThreads = 256;
 
 // Accumulators per thread (rows x states) kept in registers: 16 complex for
 // complex64, 8 for complex128.
-template <typename R> constexpr int acc_budget() { return sizeof(R) == 4 ? 16 : 8; }
-constexpr int max_rows(hs_dtype dt, int rb) { return (dt == HS_C64 ? 16 : 8) / rb < 1 ? 1 : (dt == HS_C64 ? 16 : 8) / rb; }
+constexpr int acc_budget(hs_dtype dt) { return dt == HS_C64 ? 16 : 8; }
 
-template <typename R, int RB>
-constexpr auto sweep_fn() {
-  constexpr int MR = acc_budget<R>() / RB < 1 ? 1 : acc_budget<R>() / RB;
-  return sweep_kernel<R, kSweepThreads, MR, RB>;
-}
+using SweepFn = void (*)(SweepArgs);
 
-template <typename R, int RB>
-cudaError_t launch_sweep_t(const SweepArgs& a, int n_blocks, size_t smem, bool pdl, cudaStream_t s) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(unsigned(n_blocks), 1u, 1u);
-  cfg.blockDim = dim3(unsigned(kSweepThreads), 1u, 1u);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = pdl ? 1 : 0;
-  return cudaLaunchKernelEx(&cfg, sweep_fn<R, RB>(), a);
+// Instantiation for (precision, rows per thread, rhs block); nullptr if unsupported.
+template <typename R>
+SweepFn sweep_fn(int rows, int rb) {
+#define HS_SWEEP_CASE(RW, B) \
+  if (rows == RW && rb == B) return sweep_kernel<R, RW, B>;
+  HS_SWEEP_CASE(1, 1) HS_SWEEP_CASE(2, 1) HS_SWEEP_CASE(4, 1) HS_SWEEP_CASE(8, 1)
+  HS_SWEEP_CASE(1, 2) HS_SWEEP_CASE(2, 2) HS_SWEEP_CASE(4, 2)
+  HS_SWEEP_CASE(1, 4) HS_SWEEP_CASE(2, 4)
+  HS_SWEEP_CASE(1, 8)
+  if (sizeof(R) == 4) {
+    HS_SWEEP_CASE(16, 1) HS_SWEEP_CASE(8, 2) HS_SWEEP_CASE(4, 4) HS_SWEEP_CASE(2, 8) HS_SWEEP_CASE(1, 16)
+  }
+#undef HS_SWEEP_CASE
+  return nullptr;
 }
 
 }  // namespace
@@ -318,19 +317,15 @@ cudaError_t prepare_kernels() {
   if (e != cudaSuccess) return e;
   std::lock_guard<std::mutex> lk(mu);
   if (dev < 64 && done[dev]) return cudaSuccess;
-  const int b = int(kSweepSmemMax);
-  const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
   cudaError_t r = cudaSuccess;
-  auto set = [&](const void* fn) { if (r == cudaSuccess) r = cudaFuncSetAttribute(fn, A, b); };
-  set((const void*)sweep_fn<float, 1>());
-  set((const void*)sweep_fn<float, 2>());
-  set((const void*)sweep_fn<float, 4>());
-  set((const void*)sweep_fn<float, 8>());
-  set((const void*)sweep_fn<float, 16>());
-  set((const void*)sweep_fn<double, 1>());
-  set((const void*)sweep_fn<double, 2>());
-  set((const void*)sweep_fn<double, 4>());
-  set((const void*)sweep_fn<double, 8>());
+  for (int rows = 1; rows <= 16; rows *= 2)
+    for (int rb = 1; rb <= 16; rb *= 2) {
+      SweepFn f32 = sweep_fn<float>(rows, rb), f64 = sweep_fn<double>(rows, rb);
+      if (f32 && r == cudaSuccess)
+        r = cudaFuncSetAttribute((const void*)f32, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSweepSmemMax));
+      if (f64 && r == cudaSuccess)
+        r = cudaFuncSetAttribute((const void*)f64, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSweepSmemMax));
+    }
   if (r == cudaSuccess && dev < 64) done[dev] = true;
   return r;
 }
@@ -342,14 +337,18 @@ size_t sweep_smem_bytes(hs_dtype dt, int rhs_block, int tile_bits, int stage_dia
 // Metadata table of a sweep: one (offset, rowbase) pair per listed diagonal.
 static size_t meta_bytes(int n_meta) { return size_t(n_meta) * 16; }
 
-int max_rows_per_thread(hs_dtype dt, int rhs_block) { return max_rows(dt, rhs_block); }
+int max_rows_per_thread(hs_dtype dt, int rhs_block) {
+  const int r = acc_budget(dt) / rhs_block;
+  return r < 1 ? 1 : r;
+}
 
 int max_tile_bits(hs_dtype dt, int rhs_block, int stage_diags, size_t budget) {
   // Largest T whose tile plus two factor stages fit the budget, with at most
-  // max_rows rows per thread.
-  const int rows = max_rows(dt, rhs_block);
+  // max_rows_per_thread rows per thread at 256 threads.
+  const int rows = max_rows_per_thread(dt, rhs_block);
   int t = 0;
-  while (sweep_smem_bytes(dt, rhs_block, t + 1, stage_diags, 2) <= budget && (1 << (t + 1)) <= kSweepThreads * rows)
+  while (sweep_smem_bytes(dt, rhs_block, t + 1, stage_diags, 2) <= budget &&
+         (1 << (t + 1)) <= kSweepMaxThreads * rows)
     ++t;
   return t;
 }
@@ -386,14 +385,22 @@ cudaError_t launch_sweep(const hs_factors* f, const SweepLaunch& L, cudaStream_t
   a.vals = f->d_vals;
   a.offs = f->d_offs;
   a.rowbase = f->d_rowbase;
-  a.fac_D = f->d_fac_D;
-  a.fac_diag0 = f->d_fac_diag0;
   a.N = p.N;
   a.n_rhs = L.n_rhs;
   a.rhs_block = L.rhs_block;
   a.tile_bits = L.tile_bits;
   a.n_tiles_log2 = p.n_qubits - L.tile_bits;
-  a.local = L.local;
+  // Split the two-run local mask into [0, lo) and [h, h + w).
+  const uint32_t lm = L.local_mask;
+  int lo = 0;
+  while (lo < 32 && ((lm >> lo) & 1u)) ++lo;
+  const uint32_t hi = lo < 32 ? (lm & ~((1u << lo) - 1u)) : 0u;
+  const int w = __builtin_popcount(hi);
+  const int h = hi ? __builtin_ctz(hi) : lo;
+  if (lo + w != L.tile_bits || (hi && hi != (((1u << w) - 1u) << h))) return cudaErrorInvalidValue;
+  a.m0 = lo >= 32 ? 0xffffffffu : ((1u << lo) - 1u);
+  a.m1 = ((1u << w) - 1u) << lo;
+  a.sh = h - lo;
   a.rest = L.rest;
   a.n_factors = L.n_factors;
   int dmax = 1, n_meta = 0;
@@ -416,20 +423,25 @@ cudaError_t launch_sweep(const hs_factors* f, const SweepLaunch& L, cudaStream_t
   a.n_stages = S;
   const size_t smem = meta_bytes(n_meta) + sweep_smem_bytes(f->dtype, L.rhs_block, L.tile_bits, dmax, S);
   if (smem > kSweepSmemMax || L.tile_bits > p.n_qubits) return cudaErrorInvalidValue;
-  const int rows = max_rows(f->dtype, L.rhs_block);
-  if ((1 << L.tile_bits) > kSweepThreads * rows) return cudaErrorInvalidValue;
-  if (L.tile_bits < (f->dtype == HS_C64 ? 1 : 0)) return cudaErrorInvalidValue;
-  const int n_rhs_blocks = (L.n_rhs + L.rhs_block - 1) / L.rhs_block;
-  const int n_blocks = (1 << a.n_tiles_log2) * n_rhs_blocks;
+  const int TS = 1 << L.tile_bits;
+  const int rows = TS > kSweepMaxThreads ? TS / kSweepMaxThreads : 1;
+  const int threads = TS / rows;
   const bool c64 = f->dtype == HS_C64;
-  switch (L.rhs_block) {
-    case 1: return c64 ? launch_sweep_t<float, 1>(a, n_blocks, smem, L.pdl, s) : launch_sweep_t<double, 1>(a, n_blocks, smem, L.pdl, s);
-    case 2: return c64 ? launch_sweep_t<float, 2>(a, n_blocks, smem, L.pdl, s) : launch_sweep_t<double, 2>(a, n_blocks, smem, L.pdl, s);
-    case 4: return c64 ? launch_sweep_t<float, 4>(a, n_blocks, smem, L.pdl, s) : launch_sweep_t<double, 4>(a, n_blocks, smem, L.pdl, s);
-    case 8: return c64 ? launch_sweep_t<float, 8>(a, n_blocks, smem, L.pdl, s) : launch_sweep_t<double, 8>(a, n_blocks, smem, L.pdl, s);
-    case 16: return c64 ? launch_sweep_t<float, 16>(a, n_blocks, smem, L.pdl, s) : cudaErrorInvalidValue;
-    default: return cudaErrorInvalidValue;
-  }
+  if (TS < (c64 ? 2 : 1)) return cudaErrorInvalidValue;
+  SweepFn fn = c64 ? sweep_fn<float>(rows, L.rhs_block) : sweep_fn<double>(rows, L.rhs_block);
+  if (!fn) return cudaErrorInvalidValue;
+  const int n_rhs_blocks = (L.n_rhs + L.rhs_block - 1) / L.rhs_block;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(unsigned((1 << a.n_tiles_log2) * n_rhs_blocks), 1u, 1u);
+  cfg.blockDim = dim3(unsigned(threads), 1u, 1u);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = L.pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, fn, a);
 }
 
 }  // namespace hs

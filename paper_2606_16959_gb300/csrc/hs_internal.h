@@ -82,6 +82,11 @@ std::vector<Sweep> plan_sweeps(const Plan& p, int n_steps, int tile_bits, int mi
 // Decompose a bit mask into runs of consecutive set bits (low to high).
 Runs runs_of(uint64_t mask, int n_bits);
 
+// A tile's local bits [0, a) U [h, h + T - a) with a >= low_bits that cover
+// `used` (the window is placed at the lowest used bit above a, moved down to
+// fit below n); 0 if no such mask exists.  T >= n gives all n bits.
+uint64_t two_run_mask(uint64_t used, int n, int T, int low_bits);
+
 }  // namespace hs
 
 // Opaque object behind the C ABI.
@@ -123,7 +128,8 @@ struct SweepLaunch {
   int n_rhs;
   int rhs_block;
   int tile_bits;
-  Runs local, rest;
+  uint32_t local_mask;  // two-run local bit set (see two_run_mask)
+  Runs rest;            // the other bits
   int n_factors;
   int factors[kMaxSweepFactors];
   size_t smem_budget;  // shared memory the launch may use (sets the number of factor stages)

@@ -224,17 +224,31 @@ Runs runs_of(uint64_t mask, int n_bits) {
   return r;
 }
 
+uint64_t two_run_mask(uint64_t used, int n, int T, int low_bits) {
+  const uint64_t all = (n >= 64) ? ~0ull : ((1ull << n) - 1);
+  if (T >= n) return all;
+  for (int a = std::max(low_bits, 0); a <= T; ++a) {
+    const uint64_t lowm = (1ull << a) - 1;
+    const uint64_t hi = used & ~lowm;
+    const int w = T - a;
+    if (hi == 0) return (1ull << T) - 1;
+    if (w == 0) continue;
+    const int lo_b = __builtin_ctzll(hi), hi_b = 63 - __builtin_clzll(hi);
+    if (hi_b - lo_b + 1 > w) continue;
+    int h = lo_b;
+    if (h + w > n) h = n - w;
+    return lowm | (((1ull << w) - 1) << h);
+  }
+  return 0;
+}
+
 std::vector<Sweep> plan_sweeps(const Plan& p, int n_steps, int tile_bits, int min_low_bits, bool fused,
                                int max_fused_diags) {
   std::vector<Sweep> out;
   const int n = p.n_qubits;
-  const uint64_t all = (n >= 64) ? ~0ull : ((1ull << n) - 1);
-  const uint64_t low = (min_low_bits >= 64) ? ~0ull : ((1ull << std::min(min_low_bits, n)) - 1);
   tile_bits = std::min(tile_bits, n);
   auto close = [&](Sweep& s, uint64_t used) {
-    uint64_t L = used | low;
-    for (int b = 0; b < n && __builtin_popcountll(L) < tile_bits; ++b) L |= 1ull << b;
-    s.local_mask = uint32_t(L & all);
+    s.local_mask = uint32_t(two_run_mask(used, n, tile_bits, min_low_bits));
     out.push_back(std::move(s));
     s = Sweep();
   };
@@ -242,8 +256,9 @@ std::vector<Sweep> plan_sweeps(const Plan& p, int n_steps, int tile_bits, int mi
   uint64_t used = 0;
   for (int st = 0; st < n_steps; ++st) {
     for (int g = 0; g < int(p.groups.size()); ++g) {
-      uint64_t span = p.groups[g].span;
-      bool fits_alone = fused && p.groups[g].D <= max_fused_diags && __builtin_popcountll(span | low) <= tile_bits;
+      const uint64_t span = p.groups[g].span;
+      const bool fits_alone = fused && p.groups[g].D <= max_fused_diags && min_low_bits <= tile_bits &&
+                              two_run_mask(span, n, tile_bits, min_low_bits) != 0;
       if (!fits_alone) {
         if (!cur.factors.empty()) close(cur, used);
         used = 0;
@@ -253,8 +268,8 @@ std::vector<Sweep> plan_sweeps(const Plan& p, int n_steps, int tile_bits, int mi
         out.push_back(std::move(pl));
         continue;
       }
-      if (!cur.factors.empty() &&
-          (__builtin_popcountll(used | span | low) > tile_bits || int(cur.factors.size()) >= kMaxSweepFactors)) {
+      if (!cur.factors.empty() && (two_run_mask(used | span, n, tile_bits, min_low_bits) == 0 ||
+                                   int(cur.factors.size()) >= kMaxSweepFactors)) {
         close(cur, used);
         used = 0;
       }
