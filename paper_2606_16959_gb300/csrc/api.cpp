@@ -48,6 +48,9 @@ void release(hs_factors* f) {
   cudaFree(f->d_rowbase);
   cudaFree(f->d_fac_D);
   cudaFree(f->d_fac_diag0);
+  cudaFree(f->d_slot_u);
+  cudaFree(f->d_slot_tab);
+  cudaFree(f->d_tab_rb);
   delete f;
 }
 
@@ -95,11 +98,11 @@ bool has_plain(const std::vector<hs::Sweep>& sw) {
   return false;
 }
 
-// Largest diagonal count among the factors a sweep may hold.
+// Largest number of staged planes (slots) among the factors a sweep may hold.
 int fused_dmax(const hs_factors* f) {
   int d = 1;
   for (const hs::Group& g : f->plan.groups)
-    if (g.D <= hs::kMaxFusedDiags && g.D > d) d = g.D;
+    if (g.nslot > d) d = g.nslot;
   return d;
 }
 
@@ -167,7 +170,10 @@ int hs_build_factors_masks(const uint64_t* x, const uint64_t* z, const double* c
   if ((rc = guard(cudaMalloc(&fp->d_offs, nd * sizeof(int64_t)), "cudaMalloc")) ||
       (rc = guard(cudaMalloc(&fp->d_rowbase, nd * sizeof(int64_t)), "cudaMalloc")) ||
       (rc = guard(cudaMalloc(&fp->d_fac_D, G * sizeof(int)), "cudaMalloc")) ||
-      (rc = guard(cudaMalloc(&fp->d_fac_diag0, G * sizeof(int)), "cudaMalloc"))) {
+      (rc = guard(cudaMalloc(&fp->d_fac_diag0, G * sizeof(int)), "cudaMalloc")) ||
+      (rc = guard(cudaMalloc(&fp->d_slot_u, (p.slot_u.size() + 1) * sizeof(uint32_t)), "cudaMalloc")) ||
+      (rc = guard(cudaMalloc(&fp->d_slot_tab, p.slot_tab.size() * sizeof(int32_t)), "cudaMalloc")) ||
+      (rc = guard(cudaMalloc(&fp->d_tab_rb, (p.tab_rb.size() + 1) * sizeof(int64_t)), "cudaMalloc"))) {
     release(f.release());
     return rc;
   }
@@ -205,7 +211,13 @@ int hs_build_factors_masks(const uint64_t* x, const uint64_t* z, const double* c
       (rc = guard(cudaMemcpyAsync(fp->d_offs, p.offs.data(), nd * 8, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync")) ||
       (rc = guard(cudaMemcpyAsync(fp->d_rowbase, p.rowbase.data(), nd * 8, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync")) ||
       (rc = guard(cudaMemcpyAsync(fp->d_fac_D, fD.data(), G * 4, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync")) ||
-      (rc = guard(cudaMemcpyAsync(fp->d_fac_diag0, fd0.data(), G * 4, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync"))) {
+      (rc = guard(cudaMemcpyAsync(fp->d_fac_diag0, fd0.data(), G * 4, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync")) ||
+      (rc = guard(cudaMemcpyAsync(fp->d_slot_u, p.slot_u.data(), p.slot_u.size() * 4, cudaMemcpyHostToDevice, s),
+                  "cudaMemcpyAsync")) ||
+      (rc = guard(cudaMemcpyAsync(fp->d_slot_tab, p.slot_tab.data(), p.slot_tab.size() * 4, cudaMemcpyHostToDevice, s),
+                  "cudaMemcpyAsync")) ||
+      (rc = guard(cudaMemcpyAsync(fp->d_tab_rb, p.tab_rb.data(), p.tab_rb.size() * 8, cudaMemcpyHostToDevice, s),
+                  "cudaMemcpyAsync"))) {
     cudaFreeAsync(d_blob, s);
     cudaStreamSynchronize(s);
     release(f.release());

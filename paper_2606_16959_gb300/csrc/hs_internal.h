@@ -35,6 +35,13 @@ struct Group {
   int xdim = 0;              // dimension of the x-mask space over GF(2)
   uint64_t basis[kMaxXDim];  // reduced echelon basis of the x-mask space
   int pivot[kMaxXDim];       // pivot bit of each basis vector
+  // Slot tables (only for factors with at most kMaxFusedDiags diagonals):
+  // slot s is the x-mask u_s = XOR of basis[i] over the set bits i of s; row r's
+  // entry in column r ^ u_s lies on diagonal (r ^ u_s) - r, whose row-indexed
+  // base is tab_rb[slot_tab[slot0 + s] + p] with p the bits of r at the set
+  // bits of u_s (lowest bit of u_s -> bit 0 of p).
+  int slot0 = 0;             // first slot in the global slot arrays
+  int nslot = 0;             // 2^xdim, or 0 if the factor has no slot tables
 };
 
 // Result of planning a factor set on the host.
@@ -49,6 +56,9 @@ struct Plan {
   std::vector<int64_t> rowbase;   // value(row r) of diagonal k sits at element rowbase[k] + r
   std::vector<uint32_t> term_cx;  // per term: coordinates of its x mask in its factor's basis
   int64_t total_elems = 0;        // padded storage size in elements
+  std::vector<uint32_t> slot_u;   // per slot: its x-mask
+  std::vector<int32_t> slot_tab;  // per slot: first entry in tab_rb (one sentinel at the end)
+  std::vector<int64_t> tab_rb;    // per (slot, row pattern): row-indexed base of the diagonal
 };
 
 // Parse labels into masks.  Returns HS_OK or HS_EINVAL (message in *err).
@@ -101,6 +111,9 @@ struct hs_factors {
   int64_t* d_rowbase = nullptr;  // per diagonal row-indexed base
   int* d_fac_D = nullptr;        // per factor diagonal count
   int* d_fac_diag0 = nullptr;    // per factor first diagonal index
+  uint32_t* d_slot_u = nullptr;  // slot tables (see Group)
+  int32_t* d_slot_tab = nullptr;
+  int64_t* d_tab_rb = nullptr;
   // cached CUDA graphs of evolve launch sequences
   struct GraphKey {
     void* psi;

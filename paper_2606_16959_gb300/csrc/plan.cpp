@@ -196,6 +196,29 @@ int make_plan(const uint64_t* x, const uint64_t* z, const double* coeff, size_t 
       G.S += len;
       cursor = (start + len + A - 1) / A * A;
     }
+    // Slot tables of a factor that sweeps can hold.
+    if (G.D <= kMaxFusedDiags) {
+      G.slot0 = int(plan.slot_u.size());
+      G.nslot = 1 << G.xdim;
+      for (int sl = 0; sl < G.nslot; ++sl) {
+        uint64_t u = 0;
+        for (int i = 0; i < G.xdim; ++i)
+          if ((sl >> i) & 1) u ^= G.basis[i];
+        int bits[64], w = 0;
+        for (int b = 0; b < 63; ++b)
+          if ((u >> b) & 1ull) bits[w++] = b;
+        plan.slot_u.push_back(uint32_t(u));
+        plan.slot_tab.push_back(int32_t(plan.tab_rb.size()));
+        for (int pat = 0; pat < (1 << w); ++pat) {
+          int64_t d = 0;
+          for (int j = 0; j < w; ++j) d += ((pat >> j) & 1) ? -(int64_t(1) << bits[j]) : (int64_t(1) << bits[j]);
+          int k = 0;
+          while (k < G.D && plan.offs[G.diag0 + k] != d) ++k;
+          if (k == G.D) { *err = "internal: slot offset missing from the factor's diagonals"; return HS_EINVAL; }
+          plan.tab_rb.push_back(plan.rowbase[G.diag0 + k]);
+        }
+      }
+    }
     for (int j = G.first; j < G.last; ++j) {
       uint32_t c = 0;
       for (int i = 0; i < G.xdim; ++i)
@@ -207,6 +230,7 @@ int make_plan(const uint64_t* x, const uint64_t* z, const double* coeff, size_t 
   // One extra aligned block: a 16-byte staging copy that straddles the end of
   // the last diagonal stays inside the allocation.
   plan.total_elems = cursor + A;
+  plan.slot_tab.push_back(int32_t(plan.tab_rb.size()));
   return HS_OK;
 }
 
@@ -257,7 +281,8 @@ std::vector<Sweep> plan_sweeps(const Plan& p, int n_steps, int tile_bits, int mi
   for (int st = 0; st < n_steps; ++st) {
     for (int g = 0; g < int(p.groups.size()); ++g) {
       const uint64_t span = p.groups[g].span;
-      const bool fits_alone = fused && p.groups[g].D <= max_fused_diags && min_low_bits <= tile_bits &&
+      const bool fits_alone = fused && p.groups[g].D <= max_fused_diags && p.groups[g].nslot > 0 &&
+                              min_low_bits <= tile_bits &&
                               two_run_mask(span, n, tile_bits, min_low_bits) != 0;
       if (!fits_alone) {
         if (!cur.factors.empty()) close(cur, used);
