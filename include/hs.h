@@ -138,6 +138,57 @@ int hs_evolve_ex(const hs_factors* f, void* psi, int n_rhs, int n_steps, const h
 int hs_evolve_plan(const hs_factors* f, int n_rhs, int n_steps, const hs_evolve_opts* opts, int* n_sweeps,
                    int* n_plain, int* tile_bits, int* rhs_block);
 
+/* Measure candidate launch parameters for evolving these n_rhs states by
+ * n_steps steps (plain, and fused with several tile_bits / low_bits /
+ * rhs_block values) on a temporary copy of psi (psi itself is not modified),
+ * return the fastest in *best, and remember it for every factor set of the
+ * same shape (qubits, dtype, n_rhs, and each factor's flip span and slot
+ * count): later hs_evolve / hs_evolve_ex calls with default options use it.
+ * Allocates one temporary state set, synchronises cuda_stream; do not call
+ * during stream capture.  Errors: HS_EINVAL, HS_ENOMEM, HS_ECUDA. */
+int hs_autotune(const hs_factors* f, const void* psi, int n_rhs, int n_steps, void* cuda_stream,
+                hs_evolve_opts* best);
+
+/* ---- Batched evolution of many independent jobs (one graph launch) ---- */
+
+typedef struct hs_batch hs_batch;
+
+typedef struct {
+  const hs_factors* factors; /* the job's factor set */
+  void* psi;                 /* its states: device buffer of n_rhs states, the factors' dtype */
+  int n_rhs;                 /* >= 1 */
+  int n_steps;               /* >= 0 */
+} hs_batch_job;
+
+typedef struct {
+  int tile_bits; /* log2 amplitudes per tile, 8..11 (0 = 9); jobs with fewer qubits, or whose
+                    factors do not fit a tile, are evolved with their own launches */
+  int low_bits;  /* contiguous low bits of a tile (0 = library choice) */
+  int use_graph; /* 1 (default): capture the launch sequence once and replay it as a CUDA graph */
+} hs_batch_opts;
+
+/* Plan a batch: every job is scheduled exactly as hs_evolve_ex schedules it
+ * (same sweeps, same arithmetic, so results are bitwise those of evolving each
+ * job alone with the same tile_bits/low_bits and rhs_block 1), and launch k
+ * applies the k-th sweep of every job that has one.  All jobs must share one
+ * dtype.  The jobs' factor sets and state buffers must outlive the batch.
+ * Host planning plus small device tables (synchronous uploads).  Errors:
+ * HS_EINVAL, HS_EDTYPE, HS_ENOMEM, HS_ECUDA. */
+int hs_batch_create(const hs_batch_job* jobs, size_t n_jobs, const hs_batch_opts* opts, hs_batch** out);
+
+/* Evolve every job of the batch in place by its n_steps (enqueued on
+ * cuda_stream; with use_graph the first call captures the launch sequence).
+ * Launching twice evolves twice.  Errors: HS_EINVAL, HS_ECUDA. */
+int hs_batch_launch(hs_batch* b, void* cuda_stream);
+
+/* Number of launches (levels), CTAs over all levels, amplitude updates per
+ * launch of the batch (sum over jobs of n_steps * factors * 2^n * n_rhs), and
+ * jobs evolved with their own launches.  Pointers may be NULL. */
+int hs_batch_info(const hs_batch* b, int* n_levels, int64_t* n_ctas, int64_t* n_updates, int* n_separate);
+
+/* Free a batch (NULL is a no-op).  Synchronises the device first. */
+void hs_batch_free(hs_batch* b);
+
 /* y = F_g x for one factor (Alg. 1: the sum over diagonals of the shifted
  * element-wise products), out of place.  x and y are device buffers of n_rhs
  * states of the factors' dtype and must not overlap.  Errors: HS_EINVAL. */

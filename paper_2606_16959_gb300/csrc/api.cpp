@@ -33,8 +33,8 @@ int cuda_fail(cudaError_t e, const char* what) {
 bool valid_dtype(hs_dtype d) { return d == HS_C64 || d == HS_C128; }
 
 // Default number of contiguous low bits in a tile: every access along a
-// diagonal or the state then covers whole 64-byte runs.
-int min_low_bits(hs_dtype dt) { return dt == HS_C64 ? 3 : 2; }
+// diagonal or the state then covers whole 32-byte sectors.
+int min_low_bits(hs_dtype dt) { return dt == HS_C64 ? 2 : 1; }
 
 void release(hs_factors* f) {
   if (!f) return;
@@ -116,8 +116,8 @@ int pick_rhs_block(hs_dtype dt, int n_rhs) {
 int pick_tile_bits(const hs_factors* f, int rhs_block) {
   const int n = f->plan.n_qubits;
   int t = hs::max_tile_bits(f->dtype, rhs_block, fused_dmax(f), hs::kSweepSmemDefault);
-  // keep at least ~2 CTAs per SM when the state allows it
-  int cap = n - 9;
+  // keep at least ~128 tiles when the state allows it
+  int cap = n - 7;
   if (cap < min_low_bits(f->dtype) + 4) cap = min_low_bits(f->dtype) + 4;
   if (t > cap) t = cap;
   if (t > n) t = n;
@@ -283,6 +283,13 @@ int hs_plan_factors(const uint64_t* x, const uint64_t* z, size_t n_terms, int n_
 int resolve_opts(const hs_factors* f, int n_rhs, const hs_evolve_opts* opts, hs_evolve_opts& o, int& tb, int& rb) {
   o = hs_evolve_opts{HS_METHOD_AUTO, 0, 0, 0, 0};
   if (opts) o = *opts;
+  if (o.method == HS_METHOD_AUTO && o.tile_bits == 0 && o.rhs_block == 0 && o.low_bits == 0) {
+    hs_evolve_opts t;
+    if (hs::tuned_opts(f, n_rhs, &t)) {
+      t.use_graph = o.use_graph;
+      o = t;
+    }
+  }
   if (o.low_bits <= 0) o.low_bits = min_low_bits(f->dtype);
   if (o.low_bits < (f->dtype == HS_C64 ? 1 : 0) || o.low_bits > 12) return fail(HS_EINVAL, "low_bits out of range");
   if (o.method != HS_METHOD_AUTO && o.method != HS_METHOD_PLAIN && o.method != HS_METHOD_FUSED)
@@ -292,7 +299,7 @@ int resolve_opts(const hs_factors* f, int n_rhs, const hs_evolve_opts* opts, hs_
     return fail(HS_EINVAL, "rhs_block must be 1, 2, 4, 8 (or 16 for complex64)");
   tb = o.tile_bits > 0 ? o.tile_bits : pick_tile_bits(f, rb);
   if (tb > f->plan.n_qubits) tb = f->plan.n_qubits;
-  if (o.method != HS_METHOD_PLAIN && tb > hs::max_tile_bits(f->dtype, rb, fused_dmax(f), hs::kSweepSmemDefault))
+  if (o.method != HS_METHOD_PLAIN && tb > hs::max_tile_bits(f->dtype, rb, fused_dmax(f), hs::kSweepSmemMax))
     return fail(HS_EINVAL, "tile_bits exceeds the shared-memory tile for this rhs_block");
   if (tb < 1) return fail(HS_EINVAL, "tile_bits must be >= 1");
   return HS_OK;

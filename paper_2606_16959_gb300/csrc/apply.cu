@@ -33,21 +33,15 @@
 #include <mutex>
 
 #include "hs_internal.h"
+#include "sweep_core.cuh"
 
 namespace hs {
 namespace {
 
-template <typename R> struct C2;
-template <> struct C2<float> { using T = float2; };
-template <> struct C2<double> { using T = double2; };
-
-template <typename T2>
-__device__ __forceinline__ void cfma(T2& acc, const T2 v, const T2 x) {
-  acc.x = fma(v.x, x.x, acc.x);
-  acc.x = fma(-v.y, x.y, acc.x);
-  acc.y = fma(v.x, x.y, acc.y);
-  acc.y = fma(v.y, x.x, acc.y);
-}
+using sweep::C2;
+using sweep::cfma;
+using sweep::SweepArgs;
+using sweep::meta_bytes;
 
 // ---------------------------------------------------------------------------
 // Plain row-parallel diagonal-times-vector product.
@@ -79,252 +73,11 @@ __global__ void __launch_bounds__(256) apply_plain_kernel(const typename C2<R>::
   }
 }
 
-// ---------------------------------------------------------------------------
-// Fused tile sweep.
-// ---------------------------------------------------------------------------
-struct SweepArgs {
-  const void* src;
-  void* dst;
-  const void* vals;
-  const uint32_t* slot_u;
-  const int32_t* slot_tab;
-  const int64_t* tab_rb;
-  int64_t N;
-  int n_rhs;
-  int rhs_block;
-  int tile_bits;
-  int n_tiles_log2;
-  int n_stages;      // factor stages in the shared-memory ring
-  int stage_planes;  // planes per stage (max slot count over the sweep's factors)
-  int n_mslot;       // slots listed in the shared-memory slot table
-  int n_mtab;        // entries in the shared-memory row-base table
-  // Local bits [0, a) U [h, h + w): local index of row r is
-  // (r & m0) | ((r >> sh) & m1), with m0 = 2^a - 1, m1 = (2^w - 1) << a, sh = h - a.
-  uint32_t m0, m1;
-  int sh;
-  Runs rest;         // the other bits, enumerated by the CTA index
-  int n_factors;
-  // Per factor of the sweep: first global slot, slot count, position of its
-  // first slot in the shared slot table, first global / shared row-base table
-  // entry and the number of entries.
-  int fslot0[kMaxSweepFactors];
-  int ftab_g[kMaxSweepFactors];
-  int16_t fnslot[kMaxSweepFactors];
-  int16_t fmslot[kMaxSweepFactors];
-  int16_t ftab_s[kMaxSweepFactors];
-  int16_t ftab_n[kMaxSweepFactors];
-};
-
-struct SlotMeta {
-  uint32_t u;    // x-mask of the slot
-  uint32_t U;    // its local image (u lies inside the tile's local bits)
-  int32_t tab;   // first row-base table entry in shared memory
-  int32_t pad;
-};
-
-// Scatter the low bits of v into the positions of the runs.
-__device__ __forceinline__ uint32_t deposit_runs(uint32_t v, const Runs& R) {
-  uint32_t out = 0;
-  int q = 0;
-  for (int i = 0; i < R.n; ++i) {
-    out |= ((v >> q) & ((1u << R.len[i]) - 1u)) << R.pos[i];
-    q += R.len[i];
-  }
-  return out;
-}
-
-__device__ __forceinline__ uint32_t local_of(uint32_t c, uint32_t m0, uint32_t m1, int sh) {
-  return (c & m0) | ((c >> sh) & m1);
-}
-__device__ __forceinline__ uint32_t global_of(uint32_t l, uint32_t m0, uint32_t m1, int sh) {
-  return (l & m0) | ((l & m1) << sh);
-}
-// Bits of r at the set bits of u, packed (lowest set bit of u -> bit 0).
-__device__ __forceinline__ uint32_t pattern_of(uint32_t r, uint32_t u) {
-  uint32_t p = 0;
-  int j = 0;
-  for (uint32_t t = u; t; t &= t - 1u, ++j) p |= ((r >> (__ffs(t) - 1)) & 1u) << j;
-  return p;
-}
-
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const uint32_t s = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
-  const uint32_t s = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-// Wait until at most n of the most recently committed groups are pending.
-__device__ __forceinline__ void cp_async_wait(int n) {
-  switch (n) {
-    case 0: asm volatile("cp.async.wait_group 0;\n" ::: "memory"); break;
-    case 1: asm volatile("cp.async.wait_group 1;\n" ::: "memory"); break;
-    case 2: asm volatile("cp.async.wait_group 2;\n" ::: "memory"); break;
-    case 3: asm volatile("cp.async.wait_group 3;\n" ::: "memory"); break;
-    case 4: asm volatile("cp.async.wait_group 4;\n" ::: "memory"); break;
-    case 5: asm volatile("cp.async.wait_group 5;\n" ::: "memory"); break;
-    case 6: asm volatile("cp.async.wait_group 6;\n" ::: "memory"); break;
-    default: asm volatile("cp.async.wait_group 7;\n" ::: "memory"); break;
-  }
-}
-// Programmatic dependent launch controls (no-ops when launched without the attribute).
-__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
-__device__ __forceinline__ void grid_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
-
-// The factor loop of a sweep.  NRB = RB when the CTA's block of states is
-// full (no per-state guard), 0 for the last, partial block.
-template <typename T2, int ROWS, int RB, int NRB, typename Issue>
-__device__ __forceinline__ void sweep_body(const SweepArgs& a, T2* tile, const T2* stages, uint32_t stage_elems,
-                                           const SlotMeta* mslot, uint32_t TS, int NT, Issue& issue_factor) {
-  const int rhs0 = int(blockIdx.x >> a.n_tiles_log2) * a.rhs_block;
-  const int nrb = NRB ? NRB : min(a.rhs_block, a.n_rhs - rhs0);
-  const int S = a.n_stages;
-  for (int fi = 0; fi < a.n_factors; ++fi) {
-    cp_async_wait(fi == 0 ? 0 : S - 1);
-    __syncthreads();
-    const int ns = a.fnslot[fi];
-    const SlotMeta* ms = mslot + a.fmslot[fi];
-    const T2* st = stages + size_t(fi % S) * stage_elems + threadIdx.x;
-    T2 acc[ROWS][RB];
-#pragma unroll
-    for (int i = 0; i < ROWS; ++i)
-#pragma unroll
-      for (int q = 0; q < RB; ++q) acc[i][q] = T2{0, 0};
-#pragma unroll 2
-    for (int j = 0; j < ns; ++j) {
-      const uint32_t U = ms[j].U;
-#pragma unroll
-      for (int i = 0; i < ROWS; ++i) {
-        const T2 v = st[j * TS + i * NT];
-        const T2* xp = tile + ((threadIdx.x + uint32_t(i) * NT) ^ U);
-#pragma unroll
-        for (int q = 0; q < RB; ++q, xp += TS)
-          if (NRB || q < nrb) cfma(acc[i][q], v, *xp);
-      }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int i = 0; i < ROWS; ++i) {
-      T2* yp = tile + threadIdx.x + i * NT;
-#pragma unroll
-      for (int q = 0; q < RB; ++q, yp += TS)
-        if (NRB || q < nrb) *yp = acc[i][q];
-    }
-    // Refill the stage just consumed (every thread is past the barrier above).
-    if (fi + S < a.n_factors) issue_factor(fi + S, fi % S);
-    cp_async_commit();
-  }
-  __syncthreads();
-}
-
-// Block of TS / ROWS threads; thread t owns local rows t + i * blockDim.x.
-//
-// For a factor whose x-mask set X lies in the local bits, row r of the factor
-// has exactly one structural entry per u in X, in column r ^ u (always inside
-// [0, N) and inside the tile); every other stored value on that row is an
-// exact zero.  The sweep therefore stages, for every slot u and tile row, the
-// value of entry (r, r ^ u) -- element min(r, r ^ u) of diagonal (r ^ u) - r,
-// found through the slot's row-base table -- into plane u of the stage, and
-// the multiply is acc[l] += plane_u[l] * x[l ^ U] with U the local image of u.
-// The sum is the diagonal-times-vector product without its zero terms.
 template <typename R, int ROWS, int RB>
-__global__ void __launch_bounds__(512) sweep_kernel(const __grid_constant__ SweepArgs a) {
-  using T2 = typename C2<R>::T;
-  constexpr int V = 16 / sizeof(T2);  // elements per 16-byte chunk
+__global__ void __launch_bounds__(512) sweep_kernel(const __grid_constant__ sweep::SweepArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int NT = blockDim.x;
-  const uint32_t TS = 1u << a.tile_bits;
-  const uint32_t m0 = a.m0, m1 = a.m1;
-  const int sh = a.sh;
-  // Shared memory: [slot table][row-base table][tile][factor stages]
-  SlotMeta* mslot = reinterpret_cast<SlotMeta*>(smem_raw);
-  int64_t* mtab = reinterpret_cast<int64_t*>(mslot + a.n_mslot);
-  T2* tile = reinterpret_cast<T2*>(mtab + ((a.n_mtab + 1) & ~1));
-  T2* stages = tile + size_t(a.rhs_block) * TS;
-  const uint32_t stage_elems = uint32_t(a.stage_planes) * TS;
-  // src and dst may be the same buffer (in-place sweep): every CTA reads its
-  // own tile completely before it writes it back, and tiles are disjoint.
-  const T2* src = reinterpret_cast<const T2*>(a.src);
-  T2* dst = reinterpret_cast<T2*>(a.dst);
-  const T2* __restrict__ vals = reinterpret_cast<const T2*>(a.vals);
-
-  const uint32_t tile_id = blockIdx.x & ((1u << a.n_tiles_log2) - 1u);
-  const int rhs0 = int(blockIdx.x >> a.n_tiles_log2) * a.rhs_block;
-  const int nrb = min(a.rhs_block, a.n_rhs - rhs0);
-  const uint32_t base = deposit_runs(tile_id, a.rest);
-  const uint32_t n_chunks = TS / V;
-
-  // Slot and row-base tables of every factor of the sweep, loaded once.
-  for (int i = 0; i < a.n_factors; ++i) {
-    for (int j = threadIdx.x; j < a.fnslot[i]; j += NT) {
-      const uint32_t u = a.slot_u[a.fslot0[i] + j];
-      mslot[a.fmslot[i] + j] = SlotMeta{u, local_of(u, m0, m1, sh), a.ftab_s[i] + (a.slot_tab[a.fslot0[i] + j] - a.ftab_g[i]), 0};
-    }
-    for (int e = threadIdx.x; e < a.ftab_n[i]; e += NT) mtab[a.ftab_s[i] + e] = a.tab_rb[a.ftab_g[i] + e];
-  }
-  __syncthreads();
-
-  // Stage plane u of factor fi for the tile rows.
-  auto issue_factor = [&](int fi, int stage) {
-    const int ns = a.fnslot[fi];
-    T2* st = stages + size_t(stage) * stage_elems;
-    for (int j = 0; j < ns; ++j) {
-      const SlotMeta m = mslot[a.fmslot[fi] + j];
-      const int64_t* tab = mtab + m.tab;
-      T2* plane = st + size_t(j) * TS;
-      if (V == 1 || !(m.u & 1u)) {
-        for (uint32_t c = threadIdx.x; c < n_chunks; c += NT) {
-          const uint32_t l = c * V;
-          const uint32_t r = global_of(l, m0, m1, sh) | base;
-          cp_async16(plane + l, vals + tab[pattern_of(r, m.u)] + r);
-        }
-      } else {
-        // u flips bit 0: the two rows of a 16-byte chunk lie on different diagonals.
-        for (uint32_t c = threadIdx.x; c < n_chunks; c += NT) {
-          const uint32_t l = c * V;
-          const uint32_t r = global_of(l, m0, m1, sh) | base;
-          const uint32_t p0 = pattern_of(r, m.u);  // bit 0 of r is 0
-          cp_async8(plane + l, vals + tab[p0] + r);
-          cp_async8(plane + l + 1, vals + tab[p0 | 1u] + r + 1);
-        }
-      }
-    }
-  };
-
-  const int S = a.n_stages;
-  for (int s = 0; s < S; ++s) {
-    if (s < a.n_factors) issue_factor(s, s);
-    cp_async_commit();
-  }
-  // The state written by the previous launch is visible only after this.
-  grid_dependency_wait();
-  // Let the next sweep start its own prologue (tables and factor staging, which
-  // read no state) while this one computes; it waits for this grid to finish
-  // before it touches the state.
-  grid_launch_dependents();
-  for (uint32_t c = threadIdx.x; c < n_chunks; c += NT) {
-    const uint32_t l = c * V;
-    const T2* sp = src + int64_t(rhs0) * a.N + (global_of(l, m0, m1, sh) | base);
-    T2* tp = tile + l;
-    for (int q = 0; q < nrb; ++q, sp += a.N, tp += TS) cp_async16(tp, sp);
-  }
-  cp_async_commit();
-
-  if (nrb == RB)
-    sweep_body<T2, ROWS, RB, RB>(a, tile, stages, stage_elems, mslot, TS, NT, issue_factor);
-  else
-    sweep_body<T2, ROWS, RB, 0>(a, tile, stages, stage_elems, mslot, TS, NT, issue_factor);
-
-  // Store the tile.
-  for (uint32_t c = threadIdx.x; c < n_chunks; c += NT) {
-    const uint32_t l = c * V;
-    T2* dp = dst + int64_t(rhs0) * a.N + (global_of(l, m0, m1, sh) | base);
-    const T2* tp = tile + l;
-    for (int q = 0; q < nrb; ++q, dp += a.N, tp += TS)
-      *reinterpret_cast<uint4*>(dp) = *reinterpret_cast<const uint4*>(tp);
-  }
+  sweep::sweep_tile<R, ROWS, RB>(a, blockIdx.x & ((1u << a.n_tiles_log2) - 1u), int(blockIdx.x >> a.n_tiles_log2),
+                                 smem_raw);
 }
 
 constexpr int kSweepMaxThreads = 512;
@@ -380,8 +133,7 @@ size_t sweep_smem_bytes(hs_dtype dt, int rhs_block, int tile_bits, int stage_pla
   return (size_t(rhs_block) + size_t(stage_planes) * n_stages) * (size_t(1) << tile_bits) * elem_bytes(dt);
 }
 
-// Slot and row-base tables of a sweep in shared memory.
-static size_t meta_bytes(int n_mslot, int n_mtab) { return size_t(n_mslot) * 16 + size_t((n_mtab + 1) & ~1) * 8; }
+
 
 int max_rows_per_thread(hs_dtype dt, int rhs_block) {
   const int r = acc_budget(dt) / rhs_block;

@@ -1,0 +1,389 @@
+// Batched evolution of many independent jobs of uneven size.
+//
+// Every job (its own factor set, states and step count) is planned into its
+// sweep schedule exactly as hs_evolve_ex would plan it.  Launch k ("level k")
+// then applies the k-th sweep of every job that has one: its grid is the union
+// of those jobs' tiles, and each CTA finds its job by a binary search over the
+// level's prefix table, rebuilds the sweep's arguments in shared memory from
+// device tables, and runs the same tile code as the per-sweep kernel.  Levels
+// are chained with programmatic dependent launch and the whole launch sequence
+// is captured once into a CUDA graph, so a batch is one graph launch.  A job's
+// schedule is eventually periodic, so only its distinct sweeps are stored.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "hs_internal.h"
+#include "sweep_core.cuh"
+
+namespace hs {
+int report_error(int code, const std::string& msg);
+}
+
+namespace {
+
+using hs::sweep::SweepArgs;
+
+struct BJob {
+  void* psi;
+  const void* vals;
+  const uint32_t* slot_u;
+  const int32_t* slot_tab;
+  const int64_t* tab_rb;
+  int64_t N;
+  int n_qubits;
+  int n_rhs;
+};
+
+struct BFac {
+  int slot0, tab_g;
+  int16_t nslot, mslot, tab_s, tab_n;
+};
+
+struct BSweep {
+  int job;
+  int fac_off, n_factors;
+  int n_stages, stage_planes, n_mslot, n_mtab;
+  uint32_t m0, m1;
+  int sh;
+  hs::Runs rest;
+};
+
+struct LevelArgs {
+  const BJob* jobs;
+  const BSweep* sweeps;
+  const BFac* facs;
+  const int* lvl_sweep;   // per entry of the level: distinct-sweep id
+  const int* lvl_prefix;  // per entry: first CTA of the entry within the level
+  int off, count;         // the level's entries
+  int tile_bits;
+};
+
+constexpr int kBatchThreads = 256;
+constexpr size_t kArgsBytes = (sizeof(SweepArgs) + 15) / 16 * 16;
+
+template <typename R, int ROWS>
+__global__ void __launch_bounds__(kBatchThreads) batch_level_kernel(const __grid_constant__ LevelArgs p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  SweepArgs* sa = reinterpret_cast<SweepArgs*>(smem);
+  int* pref = reinterpret_cast<int*>(smem + kArgsBytes);
+  for (int i = threadIdx.x; i < p.count; i += blockDim.x) pref[i] = p.lvl_prefix[p.off + i];
+  __syncthreads();
+  // Entry of this CTA: the last one whose first CTA is <= blockIdx.x.
+  int lo = 0, hi = p.count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (pref[mid] <= int(blockIdx.x)) lo = mid; else hi = mid - 1;
+  }
+  const int local = int(blockIdx.x) - pref[lo];
+  const BSweep& bs = p.sweeps[p.lvl_sweep[p.off + lo]];
+  const BJob& bj = p.jobs[bs.job];
+  if (threadIdx.x == 0) {
+    sa->src = bj.psi;
+    sa->dst = bj.psi;
+    sa->vals = bj.vals;
+    sa->slot_u = bj.slot_u;
+    sa->slot_tab = bj.slot_tab;
+    sa->tab_rb = bj.tab_rb;
+    sa->N = bj.N;
+    sa->n_rhs = bj.n_rhs;
+    sa->rhs_block = 1;
+    sa->tile_bits = p.tile_bits;
+    sa->n_tiles_log2 = bj.n_qubits - p.tile_bits;
+    sa->n_stages = bs.n_stages;
+    sa->stage_planes = bs.stage_planes;
+    sa->n_mslot = bs.n_mslot;
+    sa->n_mtab = bs.n_mtab;
+    sa->m0 = bs.m0;
+    sa->m1 = bs.m1;
+    sa->sh = bs.sh;
+    sa->rest = bs.rest;
+    sa->n_factors = bs.n_factors;
+  }
+  for (int i = threadIdx.x; i < bs.n_factors; i += blockDim.x) {
+    const BFac fe = p.facs[bs.fac_off + i];
+    sa->fslot0[i] = fe.slot0;
+    sa->ftab_g[i] = fe.tab_g;
+    sa->fnslot[i] = fe.nslot;
+    sa->fmslot[i] = fe.mslot;
+    sa->ftab_s[i] = fe.tab_s;
+    sa->ftab_n[i] = fe.tab_n;
+  }
+  __syncthreads();
+  const int tl = bj.n_qubits - p.tile_bits;
+  hs::sweep::sweep_tile<R, ROWS, 1>(*sa, uint32_t(local) & ((1u << tl) - 1u), local >> tl,
+                                    smem + kArgsBytes + size_t((p.count + 3) & ~3) * sizeof(int));
+}
+
+using LevelFn = void (*)(LevelArgs);
+
+template <typename R>
+LevelFn level_fn(int rows) {
+  switch (rows) {
+    case 1: return batch_level_kernel<R, 1>;
+    case 2: return batch_level_kernel<R, 2>;
+    case 4: return batch_level_kernel<R, 4>;
+    case 8: return sizeof(R) == 4 ? batch_level_kernel<R, 8> : nullptr;
+    default: return nullptr;
+  }
+}
+
+}  // namespace
+
+struct hs_batch {
+  hs_dtype dtype = HS_C64;
+  int tile_bits = 0, low_bits = 0, rows = 1;
+  bool use_graph = true;
+  size_t smem = 0;
+  struct Sep {
+    const hs_factors* f;
+    void* psi;
+    int n_rhs, n_steps;
+  };
+  std::vector<Sep> separate;  // jobs evolved with their own launches
+  struct Level {
+    int off, count;
+    int64_t ctas;
+  };
+  std::vector<Level> levels;
+  int max_count = 0;
+  BJob* d_jobs = nullptr;
+  BSweep* d_sweeps = nullptr;
+  BFac* d_facs = nullptr;
+  int* d_lvl_sweep = nullptr;
+  int* d_lvl_prefix = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  int64_t updates = 0;
+  int64_t ctas = 0;
+  int64_t n_batched = 0;
+};
+
+namespace {
+
+void batch_release(hs_batch* b) {
+  if (!b) return;
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  cudaFree(b->d_jobs);
+  cudaFree(b->d_sweeps);
+  cudaFree(b->d_facs);
+  cudaFree(b->d_lvl_sweep);
+  cudaFree(b->d_lvl_prefix);
+  delete b;
+}
+
+template <typename T>
+cudaError_t upload(T** dptr, const std::vector<T>& v) {
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(dptr), std::max<size_t>(1, v.size()) * sizeof(T));
+  if (e != cudaSuccess || v.empty()) return e;
+  return cudaMemcpy(*dptr, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+int enqueue_batch(hs_batch* b, cudaStream_t s) {
+  for (const hs_batch::Sep& j : b->separate) {
+    hs_evolve_opts o{HS_METHOD_AUTO, 0, 0, 0, 0};
+    int rc = hs_evolve_ex(j.f, j.psi, j.n_rhs, j.n_steps, &o, s);
+    if (rc != HS_OK) return rc;
+  }
+  LevelFn fn = b->dtype == HS_C64 ? level_fn<float>(b->rows) : level_fn<double>(b->rows);
+  if (!fn) return hs::report_error(HS_EINVAL, "internal: no batch kernel for this tile size");
+  for (const hs_batch::Level& L : b->levels) {
+    LevelArgs a{b->d_jobs, b->d_sweeps, b->d_facs, b->d_lvl_sweep, b->d_lvl_prefix, L.off, L.count, b->tile_bits};
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(unsigned(L.ctas), 1u, 1u);
+    cfg.blockDim = dim3(unsigned(kBatchThreads), 1u, 1u);
+    cfg.dynamicSmemBytes = b->smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, fn, a);
+    if (e != cudaSuccess) return hs::report_error(HS_ECUDA, std::string("batch level launch: ") + cudaGetErrorString(e));
+  }
+  return HS_OK;
+}
+
+}  // namespace
+
+extern "C" int hs_batch_create(const hs_batch_job* jobs, size_t n_jobs, const hs_batch_opts* opts, hs_batch** out) {
+  if (!out) return hs::report_error(HS_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!jobs || n_jobs == 0) return hs::report_error(HS_EINVAL, "no jobs");
+  hs_batch_opts o{0, 0, 1};
+  if (opts) o = *opts;
+  std::unique_ptr<hs_batch> b(new hs_batch());
+  b->dtype = jobs[0].factors ? jobs[0].factors->dtype : HS_C64;
+  int min_n = 64;
+  for (size_t j = 0; j < n_jobs; ++j) {
+    const hs_batch_job& J = jobs[j];
+    if (!J.factors || !J.psi) return hs::report_error(HS_EINVAL, "job " + std::to_string(j) + ": null factors or psi");
+    if (J.factors->dtype != b->dtype) return hs::report_error(HS_EDTYPE, "jobs differ in dtype");
+    if (J.n_rhs < 1 || J.n_steps < 0) return hs::report_error(HS_EINVAL, "job " + std::to_string(j) + ": bad n_rhs/n_steps");
+    if (reinterpret_cast<uintptr_t>(J.psi) % 16) return hs::report_error(HS_EINVAL, "psi must be 16-byte aligned");
+    min_n = std::min(min_n, J.factors->plan.n_qubits);
+  }
+  const hs_dtype dt = b->dtype;
+  b->tile_bits = o.tile_bits > 0 ? o.tile_bits : 9;
+  b->low_bits = o.low_bits > 0 ? o.low_bits : (dt == HS_C64 ? 2 : 1);
+  b->use_graph = o.use_graph != 0;
+  if (b->tile_bits < 8 || b->tile_bits > 11) return hs::report_error(HS_EINVAL, "batch tile_bits must be 8..11");
+  b->rows = (1 << b->tile_bits) / kBatchThreads;
+  if ((dt == HS_C64 ? level_fn<float>(b->rows) : level_fn<double>(b->rows)) == nullptr)
+    return hs::report_error(HS_EINVAL, "batch tile_bits too large for complex128");
+  const int T = b->tile_bits;
+  const size_t budget = hs::kSweepSmemDefault;
+
+  std::vector<BJob> hjobs;
+  std::vector<BSweep> hsweeps;
+  std::vector<BFac> hfacs;
+  std::vector<std::vector<int>> job_levels;  // per batched job: distinct-sweep id of each level
+  std::vector<int64_t> job_ctas;
+  size_t need_smem = 0;
+  for (size_t j = 0; j < n_jobs; ++j) {
+    const hs_batch_job& J = jobs[j];
+    const hs::Plan& p = J.factors->plan;
+    b->updates += int64_t(J.n_steps) * int64_t(p.groups.size()) * p.N * J.n_rhs;
+    if (J.n_steps == 0) continue;
+    std::vector<hs::Sweep> sw = p.n_qubits >= T ? hs::plan_sweeps(p, J.n_steps, T, b->low_bits, true)
+                                                : std::vector<hs::Sweep>{};
+    bool ok = !sw.empty();
+    for (const hs::Sweep& w : sw) ok = ok && w.fused;
+    if (!ok) {
+      b->separate.push_back(hs_batch::Sep{J.factors, J.psi, J.n_rhs, J.n_steps});
+      continue;
+    }
+    const int jid = int(hjobs.size());
+    const hs_factors* f = J.factors;
+    hjobs.push_back(BJob{J.psi, f->d_vals, f->d_slot_u, f->d_slot_tab, f->d_tab_rb, p.N, p.n_qubits, J.n_rhs});
+    job_ctas.push_back((int64_t(1) << (p.n_qubits - T)) * J.n_rhs);
+    std::map<std::pair<uint32_t, std::vector<int>>, int> uniq;
+    std::vector<int> lv;
+    const uint64_t all = (1ull << p.n_qubits) - 1;
+    for (const hs::Sweep& w : sw) {
+      auto key = std::make_pair(w.local_mask, w.factors);
+      auto it = uniq.find(key);
+      if (it != uniq.end()) { lv.push_back(it->second); continue; }
+      BSweep bs{};
+      bs.job = jid;
+      bs.fac_off = int(hfacs.size());
+      bs.n_factors = int(w.factors.size());
+      const uint32_t lm = w.local_mask;
+      int lo = 0;
+      while (lo < 32 && ((lm >> lo) & 1u)) ++lo;
+      const uint32_t hi = lm & ~((1u << lo) - 1u);
+      const int wd = __builtin_popcount(hi);
+      const int h = hi ? __builtin_ctz(hi) : lo;
+      bs.m0 = (1u << lo) - 1u;
+      bs.m1 = ((1u << wd) - 1u) << lo;
+      bs.sh = h - lo;
+      bs.rest = hs::runs_of(~uint64_t(lm) & all, p.n_qubits);
+      int planes = 1, n_mslot = 0, n_mtab = 0;
+      for (int g : w.factors) {
+        const hs::Group& G = p.groups[g];
+        const int t0 = p.slot_tab[G.slot0], t1 = p.slot_tab[G.slot0 + G.nslot];
+        hfacs.push_back(BFac{G.slot0, t0, int16_t(G.nslot), int16_t(n_mslot), int16_t(n_mtab), int16_t(t1 - t0)});
+        n_mslot += G.nslot;
+        n_mtab += t1 - t0;
+        planes = std::max(planes, G.nslot);
+      }
+      bs.n_mslot = n_mslot;
+      bs.n_mtab = n_mtab;
+      bs.stage_planes = planes;
+      const size_t mb = hs::sweep::meta_bytes(n_mslot, n_mtab);
+      int S = 1;
+      while (S < 8 && S < bs.n_factors && mb + hs::sweep_smem_bytes(dt, 1, T, planes, S + 1) <= budget) ++S;
+      bs.n_stages = S;
+      need_smem = std::max(need_smem, mb + hs::sweep_smem_bytes(dt, 1, T, planes, S));
+      const int id = int(hsweeps.size());
+      hsweeps.push_back(bs);
+      uniq[key] = id;
+      lv.push_back(id);
+    }
+    job_levels.push_back(std::move(lv));
+  }
+  // Level tables.
+  std::vector<int> lvl_sweep, lvl_prefix;
+  size_t max_levels = 0;
+  for (const auto& lv : job_levels) max_levels = std::max(max_levels, lv.size());
+  for (size_t k = 0; k < max_levels; ++k) {
+    hs_batch::Level L{int(lvl_sweep.size()), 0, 0};
+    for (size_t j = 0; j < job_levels.size(); ++j) {
+      if (k >= job_levels[j].size()) continue;
+      lvl_sweep.push_back(job_levels[j][k]);
+      lvl_prefix.push_back(int(L.ctas));
+      L.ctas += job_ctas[j];
+      ++L.count;
+    }
+    if (L.ctas >= (int64_t(1) << 31)) return hs::report_error(HS_EINVAL, "batch level exceeds 2^31 CTAs");
+    b->max_count = std::max(b->max_count, L.count);
+    b->ctas += L.ctas;
+    b->levels.push_back(L);
+  }
+  b->n_batched = int64_t(hjobs.size());
+  b->smem = kArgsBytes + size_t((b->max_count + 3) & ~3) * sizeof(int) + need_smem;
+  if (b->smem > hs::kSweepSmemMax) return hs::report_error(HS_EINVAL, "batch needs more shared memory than a CTA has");
+  cudaError_t e;
+  if ((e = upload(&b->d_jobs, hjobs)) != cudaSuccess || (e = upload(&b->d_sweeps, hsweeps)) != cudaSuccess ||
+      (e = upload(&b->d_facs, hfacs)) != cudaSuccess || (e = upload(&b->d_lvl_sweep, lvl_sweep)) != cudaSuccess ||
+      (e = upload(&b->d_lvl_prefix, lvl_prefix)) != cudaSuccess) {
+    batch_release(b.release());
+    return hs::report_error(e == cudaErrorMemoryAllocation ? HS_ENOMEM : HS_ECUDA,
+                            std::string("batch tables: ") + cudaGetErrorString(e));
+  }
+  LevelFn fn = dt == HS_C64 ? level_fn<float>(b->rows) : level_fn<double>(b->rows);
+  e = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(hs::kSweepSmemMax));
+  if (e != cudaSuccess) {
+    batch_release(b.release());
+    return hs::report_error(HS_ECUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
+  }
+  *out = b.release();
+  return HS_OK;
+}
+
+extern "C" int hs_batch_launch(hs_batch* b, void* cuda_stream) {
+  if (!b) return hs::report_error(HS_EINVAL, "batch is NULL");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+  cudaError_t e = hs::prepare_kernels();
+  if (e != cudaSuccess) return hs::report_error(HS_ECUDA, std::string("kernel attributes: ") + cudaGetErrorString(e));
+  if (!b->use_graph) return enqueue_batch(b, s);
+  if (!b->graph) {
+    cudaStream_t cs;
+    e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return hs::report_error(HS_ECUDA, "cudaStreamCreate");
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) { cudaStreamDestroy(cs); return hs::report_error(HS_ECUDA, "cudaStreamBeginCapture"); }
+    int rc = enqueue_batch(b, cs);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(cs, &g);
+    cudaStreamDestroy(cs);
+    if (rc != HS_OK) { if (g) cudaGraphDestroy(g); return rc; }
+    if (e != cudaSuccess) return hs::report_error(HS_ECUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return hs::report_error(HS_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+  }
+  e = cudaGraphLaunch(b->graph, s);
+  return e == cudaSuccess ? HS_OK : hs::report_error(HS_ECUDA, std::string("cudaGraphLaunch: ") + cudaGetErrorString(e));
+}
+
+extern "C" int hs_batch_info(const hs_batch* b, int* n_levels, int64_t* n_ctas, int64_t* n_updates, int* n_separate) {
+  if (!b) return hs::report_error(HS_EINVAL, "batch is NULL");
+  if (n_levels) *n_levels = int(b->levels.size());
+  if (n_ctas) *n_ctas = b->ctas;
+  if (n_updates) *n_updates = b->updates;
+  if (n_separate) *n_separate = int(b->separate.size());
+  return HS_OK;
+}
+
+extern "C" void hs_batch_free(hs_batch* b) {
+  if (!b) return;
+  cudaDeviceSynchronize();
+  batch_release(b);
+}

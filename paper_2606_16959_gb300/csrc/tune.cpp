@@ -1,0 +1,109 @@
+// Autotuner for the evolution launch parameters (tile bits, contiguous low
+// bits, states per tile, plain vs fused), with a process-wide cache keyed by
+// the shape of the problem, so that factor sets built later for the same shape
+// (new instances of a family, serving requests) reuse the measured choice.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "hs_internal.h"
+
+namespace hs {
+int report_error(int code, const std::string& msg);
+
+namespace {
+std::mutex g_tune_mu;
+std::map<std::string, hs_evolve_opts> g_tune_cache;
+}  // namespace
+
+// Shape class: qubits, precision, number of states, and per factor its flip
+// span and slot count (which decide the sweep schedule and stage sizes).
+std::string shape_key(const hs_factors* f, int n_rhs) {
+  std::ostringstream k;
+  k << f->plan.n_qubits << ':' << int(f->dtype) << ':' << n_rhs;
+  for (const Group& g : f->plan.groups) k << ':' << std::hex << g.span << '/' << std::dec << g.nslot << '/' << g.D;
+  return k.str();
+}
+
+bool tuned_opts(const hs_factors* f, int n_rhs, hs_evolve_opts* out) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tune_cache.find(shape_key(f, n_rhs));
+  if (it == g_tune_cache.end()) return false;
+  *out = it->second;
+  return true;
+}
+
+void store_tuned(const hs_factors* f, int n_rhs, const hs_evolve_opts& o) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache[shape_key(f, n_rhs)] = o;
+}
+
+}  // namespace hs
+
+extern "C" int hs_autotune(const hs_factors* f, const void* psi, int n_rhs, int n_steps, void* cuda_stream,
+                           hs_evolve_opts* best) {
+  if (!f || !psi || !best) return hs::report_error(HS_EINVAL, "null argument");
+  if (n_rhs < 1 || n_steps < 1) return hs::report_error(HS_EINVAL, "n_rhs and n_steps must be >= 1");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+  const hs_dtype dt = f->dtype;
+  const size_t bytes = size_t(n_rhs) * size_t(f->plan.N) * hs::elem_bytes(dt);
+  void* work = nullptr;
+  cudaError_t e = cudaMallocAsync(&work, bytes, s);
+  if (e != cudaSuccess) return hs::report_error(e == cudaErrorMemoryAllocation ? HS_ENOMEM : HS_ECUDA,
+                                                std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
+  std::vector<hs_evolve_opts> cand;
+  cand.push_back(hs_evolve_opts{HS_METHOD_PLAIN, 0, 0, 0, 0});
+  int planes = 1;
+  for (const hs::Group& g : f->plan.groups) planes = std::max(planes, g.nslot);
+  const int cap = dt == HS_C64 ? 16 : 8;
+  int rb_max = 1;
+  while (rb_max * 2 <= n_rhs && rb_max * 2 <= cap) rb_max *= 2;
+  for (int rb : {rb_max, rb_max / 2}) {
+    if (rb < 1 || (rb != rb_max && rb_max < 4)) continue;
+    const int tmax = std::min(f->plan.n_qubits, hs::max_tile_bits(dt, rb, planes, hs::kSweepSmemDefault));
+    for (int tb = tmax; tb >= std::max(3, tmax - 4); --tb)
+      for (int lb : {1, 2, 3}) {
+        if (dt == HS_C128 && lb == 3) continue;
+        if (lb > tb) continue;
+        cand.push_back(hs_evolve_opts{HS_METHOD_FUSED, tb, rb, 0, lb});
+      }
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best_ms = 1e30f;
+  hs_evolve_opts best_o = cand[0];
+  int rc = HS_OK;
+  for (const hs_evolve_opts& o : cand) {
+    float t_min = 1e30f;
+    bool ok = true;
+    for (int rep = 0; rep < 2 && ok; ++rep) {
+      cudaMemcpyAsync(work, psi, bytes, cudaMemcpyDeviceToDevice, s);
+      cudaEventRecord(e0, s);
+      if (hs_evolve_ex(f, work, n_rhs, n_steps, &o, cuda_stream) != HS_OK) ok = false;
+      cudaEventRecord(e1, s);
+      if (cudaEventSynchronize(e1) != cudaSuccess) { ok = false; rc = HS_ECUDA; break; }
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      t_min = std::min(t_min, ms);
+    }
+    if (rc != HS_OK) break;
+    if (ok && t_min < best_ms) {
+      best_ms = t_min;
+      best_o = o;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFreeAsync(work, s);
+  cudaStreamSynchronize(s);
+  if (rc != HS_OK) return hs::report_error(rc, "autotune: a CUDA call failed");
+  hs::store_tuned(f, n_rhs, best_o);
+  *best = best_o;
+  return HS_OK;
+}

@@ -24,7 +24,8 @@ LIB_PATH = os.path.join(_HERE, "_build", "libhs.so")
 EXPORTS = (
     "hs_build_factors", "hs_build_factors_masks", "hs_evolve", "hs_evolve_ex", "hs_apply_factor",
     "hs_fidelity", "hs_inner_device", "hs_factors_info", "hs_factor_get", "hs_free_factors", "hs_last_error",
-    "hs_plan_factors", "hs_evolve_plan", "hs_inner_batch_noalloc",
+    "hs_plan_factors", "hs_evolve_plan", "hs_inner_batch_noalloc", "hs_autotune",
+    "hs_batch_create", "hs_batch_launch", "hs_batch_info", "hs_batch_free",
 )
 
 
@@ -32,6 +33,15 @@ class HSError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"libhs error {code}: {msg}")
         self.code = code
+
+
+class BatchJob(ctypes.Structure):
+    _fields_ = [("factors", ctypes.c_void_p), ("psi", ctypes.c_void_p), ("n_rhs", ctypes.c_int),
+                ("n_steps", ctypes.c_int)]
+
+
+class BatchOpts(ctypes.Structure):
+    _fields_ = [("tile_bits", ctypes.c_int), ("low_bits", ctypes.c_int), ("use_graph", ctypes.c_int)]
 
 
 class EvolveOpts(ctypes.Structure):
@@ -69,11 +79,17 @@ def lib() -> ctypes.CDLL:
                                       ip, ip, ip, ip, ip, i64p, i64p, i, i]
         L.hs_evolve_plan.argtypes = [vp, i, i, ctypes.POINTER(EvolveOpts), ip, ip, ip, ip]
         L.hs_inner_batch_noalloc.argtypes = [vp, vp, i, i, i, vp, vp]
+        L.hs_autotune.argtypes = [vp, vp, i, i, vp, ctypes.POINTER(EvolveOpts)]
+        L.hs_batch_create.argtypes = [ctypes.POINTER(BatchJob), sz, ctypes.POINTER(BatchOpts), ctypes.POINTER(vp)]
+        L.hs_batch_launch.argtypes = [vp, vp]
+        L.hs_batch_info.argtypes = [vp, ip, i64p, i64p, ip]
+        L.hs_batch_free.argtypes = [vp]
+        L.hs_batch_free.restype = None
         L.hs_free_factors.argtypes = [vp]
         L.hs_free_factors.restype = None
         L.hs_last_error.restype = ctypes.c_char_p
         for name in EXPORTS:
-            if name not in ("hs_free_factors", "hs_last_error"):
+            if name not in ("hs_free_factors", "hs_last_error", "hs_batch_free"):
                 getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -221,6 +237,15 @@ def hs_evolve_plan(f: Factors, n_rhs: int, n_steps: int, method: int = HS_METHOD
     return a.value, b.value, c.value, d.value
 
 
+def hs_autotune(f: Factors, psi, n_steps: int, stream=None) -> dict:
+    """Time candidate launch parameters on a copy of psi; the winner is used by later
+    default-option evolutions of the same shape.  Returns it as a dict."""
+    ptr, n_rhs = _check_state(f, psi)
+    o = EvolveOpts()
+    _check(lib().hs_autotune(f.handle, ptr, n_rhs, int(n_steps), _stream(stream), ctypes.byref(o)))
+    return dict(method=o.method, tile_bits=o.tile_bits, rhs_block=o.rhs_block, low_bits=o.low_bits)
+
+
 def hs_apply_factor(f: Factors, g: int, x, y, stream=None) -> None:
     px, n_rhs = _check_state(f, x)
     py, n_rhs2 = _check_state(f, y)
@@ -288,3 +313,45 @@ def hs_inner_batch_noalloc(a, b, out, stream=None) -> None:
     if out.numel() < 4 * ra or not out.is_cuda or not out.is_contiguous():
         raise ValueError("out must be a contiguous CUDA float64 tensor of 4 * n_states elements")
     _check(lib().hs_inner_batch_noalloc(pa, pb, na, ra, ca, out.data_ptr(), _stream(stream)))
+
+
+class Batch:
+    """Owner of an hs_batch handle; keeps its jobs' factor sets and states alive."""
+
+    def __init__(self, handle: int, keep):
+        self.handle = ctypes.c_void_p(handle)
+        self._keep = keep
+        nl, ns = ctypes.c_int(), ctypes.c_int()
+        nc, nu = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().hs_batch_info(self.handle, ctypes.byref(nl), ctypes.byref(nc), ctypes.byref(nu), ctypes.byref(ns)))
+        self.n_levels, self.n_ctas, self.n_updates, self.n_separate = nl.value, nc.value, nu.value, ns.value
+
+    def close(self):
+        if self.handle and self.handle.value:
+            if _lib is not None:
+                _lib.hs_batch_free(self.handle)
+            self.handle = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def hs_batch_create(jobs, tile_bits: int = 0, low_bits: int = 0, use_graph: bool = True) -> Batch:
+    """jobs: sequence of (Factors, state tensor, n_steps)."""
+    arr = (BatchJob * len(jobs))()
+    keep = []
+    for k, (f, psi, n_steps) in enumerate(jobs):
+        ptr, n_rhs = _check_state(f, psi)
+        arr[k] = BatchJob(f.handle.value, ptr, n_rhs, int(n_steps))
+        keep.append((f, psi))
+    o = BatchOpts(int(tile_bits), int(low_bits), int(bool(use_graph)))
+    out = ctypes.c_void_p()
+    _check(lib().hs_batch_create(arr, len(jobs), ctypes.byref(o), ctypes.byref(out)))
+    return Batch(out.value, keep)
+
+
+def hs_batch_launch(b: Batch, stream=None) -> None:
+    _check(lib().hs_batch_launch(b.handle, _stream(stream)))
