@@ -41,7 +41,9 @@ def parse_args():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default="heis16", choices=["heis16", "maxcut24", "tfim10"])
+    ap.add_argument("--workload", default="heis16", choices=["heis16", "maxcut24", "tfim10", "batch256"])
+    ap.add_argument("--autotune", type=int, default=1)
+    ap.add_argument("--batch-jobs", type=int, default=256)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-c128", action="store_true")
@@ -160,6 +162,57 @@ def max_over_ranks(v, world):
     return float(t.item())
 
 
+TUNE_CACHE = os.path.join(ROOT, "paper_2606_16959_gb300", "_build", "autotune_bench.json")
+PROFILE_SUMMARY = {"heis16": "sweep_kernel_heis16.md", "maxcut24": "sweep_kernel_maxcut24.md",
+                   "batch256": "batch_level_kernel_batch256.md"}
+KERNEL_SOURCES = ("apply.cu", "sweep_core.cuh", "batch.cu", "hs_internal.h", "plan.cpp", "api.cpp")
+
+
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2606_16959_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary, or None if there is none or the kernel sources changed since."""
+    path = os.path.join(ROOT, "profiles", PROFILE_SUMMARY.get(workload, "-"))
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    with open(path) as fh:
+        for line in fh:
+            if ":" in line and line.strip().startswith(("kernel_source_sha256", "dram_bytes_per_launch")):
+                k, v = line.strip().strip("`").split(":", 1)
+                vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernel_source_sha256") != kernel_source_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def load_tune_cache():
+    """Autotuner choices of earlier runs on this machine (so that a run under a
+    profiler replays the configuration measured without it)."""
+    try:
+        with open(TUNE_CACHE) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+def save_tune_cache(cache):
+    os.makedirs(os.path.dirname(TUNE_CACHE), exist_ok=True)
+    with open(TUNE_CACHE, "w") as fh:
+        json.dump(cache, fh)
+
+
 def algorithmic_bytes(f, job, n_rhs):
     """Per factor application: s * S_g (factor read once for all states) + 2 s N R
     (state read and write); summed over the n_steps x G applications."""
@@ -200,6 +253,21 @@ def time_ours(job, args, world, dtype, rank):
         keep.append(f)
         return e0, e1
 
+    tuned = None
+    if args.autotune and not any((args.method, args.tile_bits, args.rhs_block)):
+        key = f"{args.workload}:{dtype}:{torch.cuda.get_device_name()}"
+        cache = load_tune_cache()
+        if key in cache:
+            tuned = cache[key]
+        else:
+            ft = hs.hs_build_factors(job.ham.labels, job.ham.coeffs, job.t, job.n_steps, job.budget, dtype)
+            tuned = hs.hs_autotune(ft, psi0, min(job.n_steps, 10))
+            ft.close()
+            cache[key] = tuned
+            save_tune_cache(cache)
+        opts = dict(method=tuned["method"], tile_bits=tuned["tile_bits"], rhs_block=tuned["rhs_block"],
+                    low_bits=tuned["low_bits"], use_graph=bool(args.graph))
+    args.tuned_opts = opts
     keep = []
     for _ in range(args.warmup):
         step(keep)
@@ -235,7 +303,7 @@ def time_ours(job, args, world, dtype, rank):
     launches_per_step = 2 + n_sweeps + n_plain + 2
     return dict(units=units, G=G, R=R, N=N, step_ms=step_ms, evolve_ms=evolve_ms, total_ms=total_ms,
                 n_sweeps=n_sweeps, n_plain=n_plain, tile_bits=tb, rhs_block=rb, alg_bytes=alg,
-                launches=launches_per_step * args.steps, clocks=clocks, overlap=fid)
+                launches=launches_per_step * args.steps, clocks=clocks, overlap=fid, tuned=tuned)
 
 
 def time_e2e(job, args, dtype):
@@ -254,7 +322,8 @@ def time_e2e(job, args, dtype):
     out4 = torch.zeros(4, dtype=torch.float64, device=dev)
     out4_h = torch.zeros(4, dtype=torch.float64).pin_memory()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
-    opts = dict(method=args.method, tile_bits=args.tile_bits, rhs_block=args.rhs_block, use_graph=bool(args.graph))
+    opts = getattr(args, "tuned_opts", None) or dict(method=args.method, tile_bits=args.tile_bits,
+                                                     rhs_block=args.rhs_block, use_graph=bool(args.graph))
 
     def step():
         work.copy_(host_in, non_blocking=True)
@@ -284,6 +353,136 @@ def time_e2e(job, args, dtype):
     term_bytes = 28 * m + 256  # masks, coefficients and group tables uploaded by the build
     return dict(ms=statistics.mean(times), h2d=int(host_in.numel() * host_in.element_size()) + term_bytes,
                 d2h=int(host_out.numel() * host_out.element_size()) + 32)
+
+
+def batch_jobs(args, dtype="c64"):
+    from paper_2606_16959_gb300 import workloads as W
+    jobs = W.batch256(n_jobs=args.batch_jobs, dtype=dtype)
+    desc = (f"{len(jobs)} instances: TFIM open / Heisenberg periodic chains 50/50, n~U{{12..20}}, J~U[0.5,1.5], "
+            "h~U[0,2], steps~U{20..200}, budget~U{4..16}, Gaussian states, t=1 (seed 1004)")
+    return jobs, desc
+
+
+def time_batch(jobs, args, world, rank, dtype):
+    """Device-timed batch steps: build every job's factors, plan the batch, one
+    batched launch sequence, and each job's FP64 norm; states resident."""
+    import torch
+    from paper_2606_16959_gb300 import hs
+    dev = torch.device("cuda", torch.cuda.current_device())
+    tdt = torch.complex64 if dtype == "c64" else torch.complex128
+    sizes = [1 << j.ham.n_qubits for j in jobs]
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    host = np.concatenate([np.asarray(j.psi0).ravel() for j in jobs])
+    init = torch.from_numpy(host).to(dev, tdt)
+    work = torch.empty_like(init)
+    views = [work[int(offs[k]):int(offs[k + 1])] for k in range(len(jobs))]
+    outs = torch.zeros(len(jobs), 4, dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    E = torch.cuda.Event
+
+    def step():
+        work.copy_(init)
+        facs = [hs.hs_build_factors(j.ham.labels, j.ham.coeffs, j.t, j.n_steps, j.budget, dtype) for j in jobs]
+        b = hs.hs_batch_create([(f, v, j.n_steps) for f, v, j in zip(facs, views, jobs)], use_graph=False)
+        e0, e1 = E(enable_timing=True), E(enable_timing=True)
+        e0.record()
+        hs.hs_batch_launch(b)
+        e1.record()
+        for k, v in enumerate(views):
+            hs.hs_inner_device(v, v, outs[k])
+        return facs, b, e0, e1
+
+    for _ in range(args.warmup):
+        facs, b, _, _ = step()
+        torch.cuda.synchronize()
+        info = (b.n_levels, b.n_ctas, b.n_updates, b.n_separate)
+        alg = sum(algorithmic_bytes(f, j, 1) for f, j in zip(facs, jobs))
+        b.close()
+        for f in facs:
+            f.close()
+    step_ms, launch_ms = [], []
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    barrier(world)
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+    for _ in range(args.steps):
+        flush.zero_()
+        s0, s1 = E(enable_timing=True), E(enable_timing=True)
+        s0.record()
+        facs, b, e0, e1 = step()
+        s1.record()
+        torch.cuda.synchronize()
+        step_ms.append(s0.elapsed_time(s1))
+        launch_ms.append(e0.elapsed_time(e1))
+        b.close()
+        for f in facs:
+            f.close()
+    clocks = sampler.stop() if sampler else None
+    barrier(world)
+    norms = outs[:, 2].cpu().numpy()
+    total_ms = max_over_ranks(sum(step_ms), world)
+    return dict(units=info[2], levels=info[0], ctas=info[1], separate=info[3], step_ms=step_ms, launch_ms=launch_ms,
+                total_ms=total_ms, alg_bytes=alg, clocks=clocks, max_norm_drift=float(np.max(np.abs(norms - 1.0))),
+                launches=(2 * len(jobs) + info[0] + 2 * len(jobs)) * args.steps)
+
+
+def time_batch_e2e(jobs, args, dtype):
+    import torch
+    from paper_2606_16959_gb300 import hs
+    dev = torch.device("cuda", torch.cuda.current_device())
+    tdt = torch.complex64 if dtype == "c64" else torch.complex128
+    sizes = [1 << j.ham.n_qubits for j in jobs]
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    host_in = torch.from_numpy(np.concatenate([np.asarray(j.psi0).ravel() for j in jobs])).to(tdt).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    work = torch.empty(host_in.shape, dtype=tdt, device=dev)
+    views = [work[int(offs[k]):int(offs[k + 1])] for k in range(len(jobs))]
+    outs = torch.zeros(len(jobs), 4, dtype=torch.float64, device=dev)
+    outs_h = torch.zeros(len(jobs), 4, dtype=torch.float64).pin_memory()
+    times = []
+    for it in range(1 + args.steps):
+        torch.cuda.synchronize()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record()
+        work.copy_(host_in, non_blocking=True)
+        facs = [hs.hs_build_factors(j.ham.labels, j.ham.coeffs, j.t, j.n_steps, j.budget, dtype) for j in jobs]
+        b = hs.hs_batch_create([(f, v, j.n_steps) for f, v, j in zip(facs, views, jobs)], use_graph=False)
+        hs.hs_batch_launch(b)
+        for k, v in enumerate(views):
+            hs.hs_inner_device(v, v, outs[k])
+        host_out.copy_(work, non_blocking=True)
+        outs_h.copy_(outs, non_blocking=True)
+        s1.record()
+        torch.cuda.synchronize()
+        if it:
+            times.append(s0.elapsed_time(s1))
+        b.close()
+        for f in facs:
+            f.close()
+    m = sum(len(j.ham.labels) for j in jobs)
+    return dict(ms=statistics.mean(times), h2d=int(host_in.numel() * host_in.element_size()) + 28 * m + 256 * len(jobs),
+                d2h=int(host_out.numel() * host_out.element_size()) + 32 * len(jobs))
+
+
+def oracle_batch_sample(jobs, budget_s=15.0):
+    """FP64 oracle on the batch's jobs in order (whole jobs, single thread),
+    until about budget_s seconds of work."""
+    import oracle
+    done_units, t_total, n_done = 0, 0.0, 0
+    for j in jobs:
+        x, z, n = oracle.parse_terms(j.ham.labels)
+        G = len(oracle.group_terms(x, j.budget))
+        t0 = time.perf_counter()
+        oracle.evolve_direct(x, z, j.ham.coeffs, j.t, j.n_steps, j.psi0)
+        t_total += time.perf_counter() - t0
+        done_units += j.n_steps * G * (1 << n)
+        n_done += 1
+        if t_total >= budget_s:
+            break
+    return dict(value=done_units / t_total, seconds=t_total,
+                sample=f"the first {n_done} of {len(jobs)} instances, whole evolutions, direct term-by-term FP64, "
+                       "single thread; units counted as steps x G x N per instance")
 
 
 def oracle_sample(job, G, budget_s=15.0):
@@ -328,23 +527,31 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    job, desc = make_job(args.workload)
-    from paper_2606_16959_gb300 import hs
-    x, z, n = __import__("oracle").parse_terms(job.ham.labels)
-    G = len(hs.hs_plan_factors(x, z, n, job.budget)[0])
     per_step_budget = max(1.0, 150.0 / max(1, args.steps + args.warmup))
+    if args.workload == "batch256":
+        jobs, desc = batch_jobs(args)
+        job = jobs[0]
+        sample = lambda: oracle_batch_sample(jobs, per_step_budget)
+        cfg = {"workload": "batch256", "description": desc, "n_jobs": len(jobs)}
+    else:
+        job, desc = make_job(args.workload)
+        import oracle as _o
+        x, z, n = _o.parse_terms(job.ham.labels)
+        G = len(_o.group_terms(x, job.budget))
+        sample = lambda: oracle_sample(job, G, per_step_budget)
+        cfg = config_of(args, job, desc)
     for _ in range(args.warmup):
-        oracle_sample(job, G, per_step_budget)
+        sample()
     vals, secs = [], []
     for _ in range(args.steps):
-        r = oracle_sample(job, G, per_step_budget)
+        r = sample()
         vals.append(r["value"])
         secs.append(r["seconds"])
     v = len(vals) / sum(1.0 / x for x in vals)
     line = {"metric": METRIC, "value": v, "unit": METRIC, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000 * statistics.mean(secs), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic", "impl": "reference",
-            "config": config_of(args, job, desc),
+            "config": cfg,
             "cpu_baseline": {"value": v, "unit": METRIC, "cores": 1, "kind": "oracle", "sample": r["sample"]},
             "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -355,6 +562,8 @@ def run_ours(args):
     rank, world, local = dist_setup(args)
     from paper_2606_16959_gb300 import hs
     hs.lib()
+    if args.workload == "batch256":
+        return run_batch(args, rank, world)
     job, desc = make_job(args.workload)
     dtype = job.dtype
     res = time_ours(job, args, world, dtype, rank)
@@ -371,14 +580,14 @@ def run_ours(args):
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": dtype, "data": "synthetic", "config": config_of(args, job, desc, res),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                         "traffic": None, "peak_source": peak_kind,
+                         "traffic": profiled_traffic(args.workload), "peak_source": peak_kind,
                          "kernel": "sweep_kernel" if res["n_sweeps"] else "apply_plain_kernel",
                          "algorithmic_bytes_per_launch": per_launch_bytes,
                          "avg_launch_us": avg_launch_s * 1e6},
             "e2e": {"value": res["units"] / (e2e["ms"] / 1000.0), "unit": METRIC,
                     "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"]},
             "gpu_launches": res["launches"], "clocks": res["clocks"],
-            "evolve_ms_per_step": statistics.mean(res["evolve_ms"])}
+            "evolve_ms_per_step": statistics.mean(res["evolve_ms"]), "autotuned": res["tuned"]}
     if args.workload == "heis16" and not args.no_c128 and world >= 1:
         r2 = time_ours(make_job(args.workload, "c128")[0], args, world, "c128", rank)
         line["c128"] = {"value": r2["units"] * K * world / (r2["total_ms"] / 1000.0),
@@ -387,6 +596,42 @@ def run_ours(args):
         cb = oracle_sample(job, res["G"])
         line["cpu_baseline"] = {"value": cb["value"], "unit": METRIC, "cores": 1, "kind": "oracle",
                                 "sample": cb["sample"]}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_batch(args, rank, world):
+    import torch
+    jobs, desc = batch_jobs(args)
+    dtype = "c64"
+    res = time_batch(jobs, args, world, rank, dtype)
+    K = args.steps
+    value = res["units"] * K * world / (res["total_ms"] / 1000.0)
+    e2e = time_batch_e2e(jobs, args, dtype)
+    hbm, peak_kind = peaks()
+    launch_s = statistics.mean(res["launch_ms"]) / 1000.0
+    per_launch_bytes = res["alg_bytes"] / max(1, res["levels"])
+    achieved = res["alg_bytes"] / launch_s / 1e9
+    cfg = {"workload": "batch256", "description": desc, "n_jobs": len(jobs), "levels_per_step": res["levels"],
+           "ctas_per_step": res["ctas"], "separate_jobs": res["separate"], "tile_bits": 9,
+           "l2": "flushed (512 MiB write) before every timed step"}
+    line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": K, "warmup": args.warmup,
+            "ms_per_step": res["total_ms"] / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": dtype, "data": "synthetic", "config": cfg,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                         "traffic": profiled_traffic("batch256"), "peak_source": peak_kind, "kernel": "batch_level_kernel",
+                         "algorithmic_bytes_per_launch": per_launch_bytes,
+                         "avg_launch_us": launch_s * 1e6 / max(1, res["levels"])},
+            "e2e": {"value": res["units"] / (e2e["ms"] / 1000.0), "unit": METRIC,
+                    "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"]},
+            "gpu_launches": res["launches"], "clocks": res["clocks"],
+            "batch_launch_ms_per_step": statistics.mean(res["launch_ms"]), "max_norm_drift": res["max_norm_drift"]}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = oracle_batch_sample(jobs)
+        line["cpu_baseline"] = {"value": cb["value"], "unit": METRIC, "cores": 1, "kind": "oracle", "sample": cb["sample"]}
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
