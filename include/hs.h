@@ -73,7 +73,8 @@ typedef struct hs_factors hs_factors;
  *                 group products) and rounded once to FP32 for HS_C64.
  *   out         : receives the new object; set to NULL on failure.
  * The grouping and offsets are planned on the host; the values are computed
- * by kernels enqueued on cuda_stream.  Errors: HS_EINVAL (invalid label,
+ * by kernels enqueued on cuda_stream, into device memory allocated in stream
+ * order on cuda_stream (use the factors on that stream, or after it).  Errors: HS_EINVAL (invalid label,
  * labels of different lengths, n_qubits outside 1..HS_MAX_QUBITS, non-finite
  * or non-positive t, n_steps < 1, diag_budget < 1, non-finite coefficient,
  * a factor with more than 4096 diagonals or an x-mask set above 64 elements),
@@ -167,13 +168,13 @@ typedef struct {
   int use_graph; /* 1 (default): capture the launch sequence once and replay it as a CUDA graph */
 } hs_batch_opts;
 
-/* Plan a batch: every job is scheduled exactly as hs_evolve_ex schedules it
+/* Plan a batch (host only; device tables are uploaded on the first launch's
+ * stream): every job is scheduled exactly as hs_evolve_ex schedules it
  * (same sweeps, same arithmetic, so results are bitwise those of evolving each
  * job alone with the same tile_bits/low_bits and rhs_block 1), and launch k
  * applies the k-th sweep of every job that has one.  All jobs must share one
  * dtype.  The jobs' factor sets and state buffers must outlive the batch.
- * Host planning plus small device tables (synchronous uploads).  Errors:
- * HS_EINVAL, HS_EDTYPE, HS_ENOMEM, HS_ECUDA. */
+ * Errors: HS_EINVAL, HS_EDTYPE. */
 int hs_batch_create(const hs_batch_job* jobs, size_t n_jobs, const hs_batch_opts* opts, hs_batch** out);
 
 /* Evolve every job of the batch in place by its n_steps (enqueued on
@@ -188,6 +189,11 @@ int hs_batch_info(const hs_batch* b, int* n_levels, int64_t* n_ctas, int64_t* n_
 
 /* Free a batch (NULL is a no-op).  Synchronises the device first. */
 void hs_batch_free(hs_batch* b);
+
+/* Free a batch in stream order without synchronising (its tables return to the
+ * pool after the work already enqueued on cuda_stream); every launch of b must
+ * be ordered before that.  Always HS_OK. */
+int hs_batch_free_async(hs_batch* b, void* cuda_stream);
 
 /* y = F_g x for one factor (Alg. 1: the sum over diagonals of the shifted
  * element-wise products), out of place.  x and y are device buffers of n_rhs
@@ -241,6 +247,12 @@ int hs_factor_get(const hs_factors* f, int g, int* term_first, int* term_last, i
 
 /* Free a factor set (NULL is a no-op).  Synchronises the device first. */
 void hs_free_factors(hs_factors* f);
+
+/* Free a factor set in stream order without synchronising: its device memory
+ * returns to the stream-ordered pool once the work already enqueued on
+ * cuda_stream completes.  All work that uses f must be enqueued on cuda_stream
+ * or ordered before it.  Always HS_OK. */
+int hs_free_factors_async(hs_factors* f, void* cuda_stream);
 
 /* Message for the last failing call on this thread ("" if none). */
 const char* hs_last_error(void);

@@ -36,21 +36,18 @@ bool valid_dtype(hs_dtype d) { return d == HS_C64 || d == HS_C128; }
 // diagonal or the state then covers whole 32-byte sectors.
 int min_low_bits(hs_dtype dt) { return dt == HS_C64 ? 2 : 1; }
 
-void release(hs_factors* f) {
+// Free a factor set's device memory in stream order on s (stream-ordered
+// allocations) and delete the object.
+void release(hs_factors* f, cudaStream_t s) {
   if (!f) return;
   {
     std::lock_guard<std::mutex> lk(f->graph_mu);
     for (auto& kv : f->graphs) cudaGraphExecDestroy(kv.second);
     f->graphs.clear();
   }
-  cudaFree(f->d_vals);
-  cudaFree(f->d_offs);
-  cudaFree(f->d_rowbase);
-  cudaFree(f->d_fac_D);
-  cudaFree(f->d_fac_diag0);
-  cudaFree(f->d_slot_u);
-  cudaFree(f->d_slot_tab);
-  cudaFree(f->d_tab_rb);
+  void* bufs[] = {f->d_vals, f->d_offs, f->d_rowbase, f->d_fac_D, f->d_fac_diag0, f->d_slot_u, f->d_slot_tab, f->d_tab_rb};
+  for (void* b : bufs)
+    if (b) cudaFreeAsync(b, s);
   delete f;
 }
 
@@ -166,15 +163,18 @@ int hs_build_factors_masks(const uint64_t* x, const uint64_t* z, const double* c
   const size_t vbytes = size_t(p.total_elems) * hs::elem_bytes(dtype);
   hs_factors* fp = f.get();
   auto guard = [&](cudaError_t e2, const char* what) -> int { return e2 == cudaSuccess ? HS_OK : cuda_fail(e2, what); };
-  if ((rc = guard(cudaMalloc(&fp->d_vals, vbytes), "cudaMalloc(values)"))) { release(f.release()); return rc; }
-  if ((rc = guard(cudaMalloc(&fp->d_offs, nd * sizeof(int64_t)), "cudaMalloc")) ||
-      (rc = guard(cudaMalloc(&fp->d_rowbase, nd * sizeof(int64_t)), "cudaMalloc")) ||
-      (rc = guard(cudaMalloc(&fp->d_fac_D, G * sizeof(int)), "cudaMalloc")) ||
-      (rc = guard(cudaMalloc(&fp->d_fac_diag0, G * sizeof(int)), "cudaMalloc")) ||
-      (rc = guard(cudaMalloc(&fp->d_slot_u, (p.slot_u.size() + 1) * sizeof(uint32_t)), "cudaMalloc")) ||
-      (rc = guard(cudaMalloc(&fp->d_slot_tab, p.slot_tab.size() * sizeof(int32_t)), "cudaMalloc")) ||
-      (rc = guard(cudaMalloc(&fp->d_tab_rb, (p.tab_rb.size() + 1) * sizeof(int64_t)), "cudaMalloc"))) {
-    release(f.release());
+  // Stream-ordered allocations: building, using and freeing a factor set
+  // never synchronises the device.
+  auto mal = [&](void** ptr, size_t bytes) { return cudaMallocAsync(ptr, bytes, s); };
+  if ((rc = guard(mal(&fp->d_vals, vbytes), "cudaMallocAsync(values)"))) { release(f.release(), s); return rc; }
+  if ((rc = guard(mal((void**)&fp->d_offs, nd * sizeof(int64_t)), "cudaMallocAsync")) ||
+      (rc = guard(mal((void**)&fp->d_rowbase, nd * sizeof(int64_t)), "cudaMallocAsync")) ||
+      (rc = guard(mal((void**)&fp->d_fac_D, G * sizeof(int)), "cudaMallocAsync")) ||
+      (rc = guard(mal((void**)&fp->d_fac_diag0, G * sizeof(int)), "cudaMallocAsync")) ||
+      (rc = guard(mal((void**)&fp->d_slot_u, (p.slot_u.size() + 1) * sizeof(uint32_t)), "cudaMallocAsync")) ||
+      (rc = guard(mal((void**)&fp->d_slot_tab, p.slot_tab.size() * sizeof(int32_t)), "cudaMallocAsync")) ||
+      (rc = guard(mal((void**)&fp->d_tab_rb, (p.tab_rb.size() + 1) * sizeof(int64_t)), "cudaMallocAsync"))) {
+    release(f.release(), s);
     return rc;
   }
   // Term and group tables for the build, packed in one temporary buffer.
@@ -206,7 +206,7 @@ int hs_build_factors_masks(const uint64_t* x, const uint64_t* z, const double* c
   size_t o_cs = put(nullptr, 0);
   blob.resize(o_cs + m * 16);
   unsigned char* d_blob = nullptr;
-  if ((rc = guard(cudaMallocAsync((void**)&d_blob, blob.size(), s), "cudaMallocAsync"))) { release(f.release()); return rc; }
+  if ((rc = guard(cudaMallocAsync((void**)&d_blob, blob.size(), s), "cudaMallocAsync"))) { release(f.release(), s); return rc; }
   if ((rc = guard(cudaMemcpyAsync(d_blob, blob.data(), o_cs, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync")) ||
       (rc = guard(cudaMemcpyAsync(fp->d_offs, p.offs.data(), nd * 8, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync")) ||
       (rc = guard(cudaMemcpyAsync(fp->d_rowbase, p.rowbase.data(), nd * 8, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync")) ||
@@ -220,7 +220,7 @@ int hs_build_factors_masks(const uint64_t* x, const uint64_t* z, const double* c
                   "cudaMemcpyAsync"))) {
     cudaFreeAsync(d_blob, s);
     cudaStreamSynchronize(s);
-    release(f.release());
+    release(f.release(), s);
     return rc;
   }
   const double dt = t / double(n_steps);
@@ -235,7 +235,7 @@ int hs_build_factors_masks(const uint64_t* x, const uint64_t* z, const double* c
   cudaError_t e2 = cudaFreeAsync(d_blob, s);
   if (e != cudaSuccess || e2 != cudaSuccess) {
     cudaStreamSynchronize(s);
-    release(f.release());
+    release(f.release(), s);
     return cuda_fail(e != cudaSuccess ? e : e2, "factor build launch");
   }
   *out = f.release();
@@ -484,7 +484,14 @@ int hs_factor_get(const hs_factors* f, int g, int* term_first, int* term_last, i
 void hs_free_factors(hs_factors* f) {
   if (!f) return;
   cudaDeviceSynchronize();
-  release(f);
+  release(f, nullptr);
+  cudaDeviceSynchronize();
+}
+
+int hs_free_factors_async(hs_factors* f, void* cuda_stream) {
+  if (!f) return HS_OK;
+  release(f, reinterpret_cast<cudaStream_t>(cuda_stream));
+  return HS_OK;
 }
 
 }  // extern "C"

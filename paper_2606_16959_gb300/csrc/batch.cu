@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <memory>
 #include <string>
 #include <tuple>
@@ -158,6 +159,12 @@ struct hs_batch {
   BFac* d_facs = nullptr;
   int* d_lvl_sweep = nullptr;
   int* d_lvl_prefix = nullptr;
+  bool uploaded = false;
+  // host copies of the device tables (uploaded on the first launch's stream)
+  std::vector<BJob> hjobs;
+  std::vector<BSweep> hsweeps;
+  std::vector<BFac> hfacs;
+  std::vector<int> hlvl_sweep, hlvl_prefix;
   cudaGraphExec_t graph = nullptr;
   int64_t updates = 0;
   int64_t ctas = 0;
@@ -166,22 +173,33 @@ struct hs_batch {
 
 namespace {
 
-void batch_release(hs_batch* b) {
+void batch_release(hs_batch* b, cudaStream_t s) {
   if (!b) return;
   if (b->graph) cudaGraphExecDestroy(b->graph);
-  cudaFree(b->d_jobs);
-  cudaFree(b->d_sweeps);
-  cudaFree(b->d_facs);
-  cudaFree(b->d_lvl_sweep);
-  cudaFree(b->d_lvl_prefix);
+  void* bufs[] = {b->d_jobs, b->d_sweeps, b->d_facs, b->d_lvl_sweep, b->d_lvl_prefix};
+  for (void* p : bufs)
+    if (p) cudaFreeAsync(p, s);
   delete b;
 }
 
 template <typename T>
-cudaError_t upload(T** dptr, const std::vector<T>& v) {
-  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(dptr), std::max<size_t>(1, v.size()) * sizeof(T));
+cudaError_t upload(T** dptr, const std::vector<T>& v, cudaStream_t s) {
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(dptr), std::max<size_t>(1, v.size()) * sizeof(T), s);
   if (e != cudaSuccess || v.empty()) return e;
-  return cudaMemcpy(*dptr, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+  return cudaMemcpyAsync(*dptr, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s);
+}
+
+// Upload the tables in stream order on s (once).
+int upload_tables(hs_batch* b, cudaStream_t s) {
+  if (b->uploaded) return HS_OK;
+  cudaError_t e;
+  if ((e = upload(&b->d_jobs, b->hjobs, s)) != cudaSuccess || (e = upload(&b->d_sweeps, b->hsweeps, s)) != cudaSuccess ||
+      (e = upload(&b->d_facs, b->hfacs, s)) != cudaSuccess || (e = upload(&b->d_lvl_sweep, b->hlvl_sweep, s)) != cudaSuccess ||
+      (e = upload(&b->d_lvl_prefix, b->hlvl_prefix, s)) != cudaSuccess)
+    return hs::report_error(e == cudaErrorMemoryAllocation ? HS_ENOMEM : HS_ECUDA,
+                            std::string("batch tables: ") + cudaGetErrorString(e));
+  b->uploaded = true;
+  return HS_OK;
 }
 
 int enqueue_batch(hs_batch* b, cudaStream_t s) {
@@ -329,20 +347,11 @@ extern "C" int hs_batch_create(const hs_batch_job* jobs, size_t n_jobs, const hs
   b->n_batched = int64_t(hjobs.size());
   b->smem = kArgsBytes + size_t((b->max_count + 3) & ~3) * sizeof(int) + need_smem;
   if (b->smem > hs::kSweepSmemMax) return hs::report_error(HS_EINVAL, "batch needs more shared memory than a CTA has");
-  cudaError_t e;
-  if ((e = upload(&b->d_jobs, hjobs)) != cudaSuccess || (e = upload(&b->d_sweeps, hsweeps)) != cudaSuccess ||
-      (e = upload(&b->d_facs, hfacs)) != cudaSuccess || (e = upload(&b->d_lvl_sweep, lvl_sweep)) != cudaSuccess ||
-      (e = upload(&b->d_lvl_prefix, lvl_prefix)) != cudaSuccess) {
-    batch_release(b.release());
-    return hs::report_error(e == cudaErrorMemoryAllocation ? HS_ENOMEM : HS_ECUDA,
-                            std::string("batch tables: ") + cudaGetErrorString(e));
-  }
-  LevelFn fn = dt == HS_C64 ? level_fn<float>(b->rows) : level_fn<double>(b->rows);
-  e = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(hs::kSweepSmemMax));
-  if (e != cudaSuccess) {
-    batch_release(b.release());
-    return hs::report_error(HS_ECUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
-  }
+  b->hjobs = std::move(hjobs);
+  b->hsweeps = std::move(hsweeps);
+  b->hfacs = std::move(hfacs);
+  b->hlvl_sweep = std::move(lvl_sweep);
+  b->hlvl_prefix = std::move(lvl_prefix);
   *out = b.release();
   return HS_OK;
 }
@@ -352,6 +361,24 @@ extern "C" int hs_batch_launch(hs_batch* b, void* cuda_stream) {
   cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
   cudaError_t e = hs::prepare_kernels();
   if (e != cudaSuccess) return hs::report_error(HS_ECUDA, std::string("kernel attributes: ") + cudaGetErrorString(e));
+  static std::mutex attr_mu;
+  static bool attr_done[2][9] = {};
+  {
+    std::lock_guard<std::mutex> lk(attr_mu);
+    bool& done = attr_done[b->dtype == HS_C64 ? 0 : 1][b->rows];
+    if (!done) {
+      LevelFn fn = b->dtype == HS_C64 ? level_fn<float>(b->rows) : level_fn<double>(b->rows);
+      e = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(hs::kSweepSmemMax));
+      if (e != cudaSuccess) return hs::report_error(HS_ECUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
+      done = true;
+    }
+  }
+  if (!b->uploaded) {
+    int rc = upload_tables(b, s);
+    if (rc != HS_OK) return rc;
+    // A captured graph may later be launched on another stream.
+    if (b->use_graph && cudaStreamSynchronize(s) != cudaSuccess) return hs::report_error(HS_ECUDA, "table upload");
+  }
   if (!b->use_graph) return enqueue_batch(b, s);
   if (!b->graph) {
     cudaStream_t cs;
@@ -385,5 +412,11 @@ extern "C" int hs_batch_info(const hs_batch* b, int* n_levels, int64_t* n_ctas, 
 extern "C" void hs_batch_free(hs_batch* b) {
   if (!b) return;
   cudaDeviceSynchronize();
-  batch_release(b);
+  batch_release(b, nullptr);
+  cudaDeviceSynchronize();
+}
+
+extern "C" int hs_batch_free_async(hs_batch* b, void* cuda_stream) {
+  if (b) batch_release(b, reinterpret_cast<cudaStream_t>(cuda_stream));
+  return HS_OK;
 }

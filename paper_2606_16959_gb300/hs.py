@@ -25,7 +25,8 @@ EXPORTS = (
     "hs_build_factors", "hs_build_factors_masks", "hs_evolve", "hs_evolve_ex", "hs_apply_factor",
     "hs_fidelity", "hs_inner_device", "hs_factors_info", "hs_factor_get", "hs_free_factors", "hs_last_error",
     "hs_plan_factors", "hs_evolve_plan", "hs_inner_batch_noalloc", "hs_autotune",
-    "hs_batch_create", "hs_batch_launch", "hs_batch_info", "hs_batch_free",
+    "hs_batch_create", "hs_batch_launch", "hs_batch_info", "hs_batch_free", "hs_free_factors_async",
+    "hs_batch_free_async",
 )
 
 
@@ -84,6 +85,8 @@ def lib() -> ctypes.CDLL:
         L.hs_batch_launch.argtypes = [vp, vp]
         L.hs_batch_info.argtypes = [vp, ip, i64p, i64p, ip]
         L.hs_batch_free.argtypes = [vp]
+        L.hs_free_factors_async.argtypes = [vp, vp]
+        L.hs_batch_free_async.argtypes = [vp, vp]
         L.hs_batch_free.restype = None
         L.hs_free_factors.argtypes = [vp]
         L.hs_free_factors.restype = None
@@ -164,10 +167,14 @@ class Factors:
             vals = buf.view(np.complex128)
         return tf.value, tl.value, offs, vals
 
-    def close(self):
+    def close(self, stream=None):
+        """Free the factor set; with a stream, in stream order without synchronising."""
         if self.handle and self.handle.value:
             if _lib is not None:
-                _lib.hs_free_factors(self.handle)
+                if stream is None:
+                    _lib.hs_free_factors(self.handle)
+                else:
+                    _lib.hs_free_factors_async(self.handle, _stream(stream))
             self.handle = ctypes.c_void_p(0)
 
     def __del__(self):
@@ -326,10 +333,14 @@ class Batch:
         _check(lib().hs_batch_info(self.handle, ctypes.byref(nl), ctypes.byref(nc), ctypes.byref(nu), ctypes.byref(ns)))
         self.n_levels, self.n_ctas, self.n_updates, self.n_separate = nl.value, nc.value, nu.value, ns.value
 
-    def close(self):
+    def close(self, stream=None):
+        """Free the batch; with a stream, in stream order without synchronising."""
         if self.handle and self.handle.value:
             if _lib is not None:
-                _lib.hs_batch_free(self.handle)
+                if stream is None:
+                    _lib.hs_batch_free(self.handle)
+                else:
+                    _lib.hs_batch_free_async(self.handle, _stream(stream))
             self.handle = ctypes.c_void_p(0)
 
     def __del__(self):

@@ -1,0 +1,218 @@
+"""Continuous-batching request loop for evolution jobs on one GPU.
+
+Requests (a Hamiltonian, a time, a step count, an initial state) arrive over
+time.  The loop admits waiting requests while in-flight slots and an HBM budget
+allow (each request is charged its factor bytes from the structural dry run,
+hs_plan_factors, plus its state bytes), builds their factors and launches them
+as one batch (hs_batch_*) on the next of several CUDA streams, so that groups
+admitted while earlier groups still run overlap on the device.  Factors and
+states stay on the device; memory is returned in stream order when a group
+finishes.  Completion times come from CUDA events measured against a start
+event, so latency = GPU completion time - arrival time.
+
+All computation runs in libhs; this module only schedules.  shard_jobs splits
+a request stream across ranks (independent jobs, no data exchange).
+"""
+from __future__ import annotations
+
+import collections
+import time
+from dataclasses import dataclass, field
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+from . import hs
+
+
+@dataclass
+class Request:
+    labels: List[str]
+    coeffs: np.ndarray
+    n_qubits: int
+    t: float
+    n_steps: int
+    budget: int
+    arrival: float = 0.0                 # seconds after the start of the run
+    psi0: Optional[np.ndarray] = None    # initial state (host); None: seeded Gaussian made on the device
+    seed: int = 0
+    rid: int = -1
+    # filled by the server
+    admitted: Optional[float] = None
+    done: Optional[float] = None
+    updates: int = 0
+    norm2: Optional[float] = None
+    result: Optional[np.ndarray] = None
+
+
+def requests_from_jobs(jobs) -> List[Request]:
+    """Requests from workloads.Job objects (arrival times included)."""
+    out = []
+    for k, j in enumerate(jobs):
+        out.append(Request(list(j.ham.labels), np.asarray(j.ham.coeffs), j.ham.n_qubits, j.t, j.n_steps, j.budget,
+                           arrival=j.arrival, psi0=None, seed=k, rid=k))
+    return out
+
+
+def shard_jobs(items: Sequence, rank: int, world: int) -> list:
+    """Round-robin share of independent jobs for one rank (no collective needed)."""
+    if world < 1 or not 0 <= rank < world:
+        raise ValueError("bad rank/world")
+    return [x for k, x in enumerate(items) if k % world == rank]
+
+
+@dataclass
+class _Group:
+    reqs: list
+    factors: list
+    states: list
+    batch: object
+    stream: object
+    event: object
+    bytes: int
+    out: object = None
+    host: list = field(default_factory=list)
+
+
+class Server:
+    def __init__(self, dtype: str = "c64", hbm_bytes: Optional[int] = None, max_inflight: int = 64,
+                 max_group: int = 32, n_streams: int = 4, tile_bits: int = 0, keep_results: bool = False):
+        import torch
+        self.torch = torch
+        self.dtype = dtype
+        self.tdt = torch.complex64 if dtype == "c64" else torch.complex128
+        self.esize = 8 if dtype == "c64" else 16
+        free, _ = torch.cuda.mem_get_info()
+        self.budget = int(hbm_bytes) if hbm_bytes else int(free * 0.8)
+        self.max_inflight = max_inflight
+        self.max_group = max_group
+        self.streams = [torch.cuda.Stream() for _ in range(n_streams)]
+        self.tile_bits = tile_bits
+        self.keep_results = keep_results
+        self.used = 0
+        self.peak_used = 0
+        self._next_stream = 0
+
+    def _masks(self, r: Request):
+        x = np.zeros(len(r.labels), dtype=np.uint64)
+        z = np.zeros(len(r.labels), dtype=np.uint64)
+        n = r.n_qubits
+        for j, lab in enumerate(r.labels):
+            xv = zv = 0
+            for p, ch in enumerate(lab):
+                q = n - 1 - p
+                if ch in "XY":
+                    xv |= 1 << q
+                if ch in "ZY":
+                    zv |= 1 << q
+            x[j], z[j] = xv, zv
+        return x, z
+
+    def _bytes(self, r: Request) -> int:
+        """Device bytes a request holds while in flight: its factor values (structural
+        dry run), its state, and a margin for tables."""
+        x, z = self._masks(r)
+        _, vbytes = hs.hs_plan_factors(x, z, r.n_qubits, r.budget, self.dtype)
+        return int(vbytes) + (1 << r.n_qubits) * self.esize + (1 << 20)
+
+    def _launch(self, group: List[Request], t0_event):
+        torch = self.torch
+        s = self.streams[self._next_stream % len(self.streams)]
+        self._next_stream += 1
+        states, facs = [], []
+        with torch.cuda.stream(s):
+            for r in group:
+                if r.psi0 is not None:
+                    st = torch.from_numpy(np.ascontiguousarray(r.psi0)).to("cuda", self.tdt, non_blocking=True)
+                else:
+                    g = torch.Generator(device="cuda")
+                    g.manual_seed(int(r.seed))
+                    re = torch.randn(1 << r.n_qubits, generator=g, device="cuda", dtype=torch.float32)
+                    im = torch.randn(1 << r.n_qubits, generator=g, device="cuda", dtype=torch.float32)
+                    st = torch.complex(re, im).to(self.tdt)
+                    st /= torch.linalg.vector_norm(st)
+                states.append(st)
+                facs.append(hs.hs_build_factors(r.labels, r.coeffs, r.t, r.n_steps, r.budget, self.dtype, stream=s))
+                r.updates = r.n_steps * facs[-1].n_factors * (1 << r.n_qubits)
+            b = hs.hs_batch_create([(f, st, r.n_steps) for f, st, r in zip(facs, states, group)],
+                                   tile_bits=self.tile_bits, use_graph=False)
+            hs.hs_batch_launch(b, stream=s)
+            out = torch.zeros(len(group), 4, dtype=torch.float64, device="cuda")
+            for k, st in enumerate(states):
+                hs.hs_inner_device(st, st, out[k], stream=s)
+            host = []
+            if self.keep_results:
+                host = [st.to("cpu", non_blocking=True) for st in states]
+            ev = torch.cuda.Event(enable_timing=True)
+            ev.record(s)
+        return _Group(group, facs, states, b, s, ev, 0, out, host)
+
+    def run(self, requests: Sequence[Request], realtime: bool = True, poll_s: float = 5e-5):
+        """Serve the requests (sorted by arrival).  realtime: wait for arrival times;
+        otherwise every request is available at once.  Returns a stats dict."""
+        torch = self.torch
+        pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
+        waiting: collections.deque = collections.deque()
+        inflight: List[_Group] = []
+        n_inflight = 0
+        t0_event = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        t0_event.record()
+        t0 = time.perf_counter()
+        while pending or waiting or inflight:
+            now = time.perf_counter() - t0
+            while pending and (not realtime or pending[0].arrival <= now):
+                waiting.append(pending.popleft())
+            # retire finished groups
+            keep = []
+            for g in inflight:
+                if g.event.query():
+                    t_done = t0_event.elapsed_time(g.event) / 1000.0
+                    norms = g.out[:, 2].cpu().numpy()
+                    for k, r in enumerate(g.reqs):
+                        r.done = t_done
+                        r.norm2 = float(norms[k])
+                        if self.keep_results:
+                            r.result = g.host[k].numpy()
+                    g.batch.close(stream=g.stream)
+                    for f in g.factors:
+                        f.close(stream=g.stream)
+                    self.used -= g.bytes
+                    n_inflight -= len(g.reqs)
+                else:
+                    keep.append(g)
+            inflight = keep
+            # admit
+            group, gbytes = [], 0
+            while waiting and n_inflight + len(group) < self.max_inflight and len(group) < self.max_group:
+                r = waiting[0]
+                need = self._bytes(r)
+                if self.used + gbytes + need > self.budget:
+                    if not inflight and not group and self.used == 0:
+                        raise RuntimeError(f"request {r.rid} needs {need} bytes, above the HBM budget")
+                    break
+                waiting.popleft()
+                r.admitted = time.perf_counter() - t0
+                group.append(r)
+                gbytes += need
+            if group:
+                g = self._launch(group, t0_event)
+                g.bytes = gbytes
+                self.used += gbytes
+                self.peak_used = max(self.peak_used, self.used)
+                n_inflight += len(group)
+                inflight.append(g)
+                continue
+            # nothing to admit: wait a little (for an arrival or a completion)
+            wait = poll_s
+            if pending and not waiting and not inflight:
+                wait = min(1e-3, max(0.0, pending[0].arrival - (time.perf_counter() - t0)))
+            time.sleep(wait)
+        torch.cuda.synchronize()
+        lat = np.array([r.done - r.arrival for r in requests])
+        t_first = min(r.arrival for r in requests)
+        t_last = max(r.done for r in requests)
+        updates = sum(r.updates for r in requests)
+        return dict(n=len(requests), p50_ms=float(np.percentile(lat, 50) * 1e3), p99_ms=float(np.percentile(lat, 99) * 1e3),
+                    mean_ms=float(lat.mean() * 1e3), makespan_s=t_last - t_first, updates=updates,
+                    throughput=updates / max(t_last - t_first, 1e-9), peak_bytes=self.peak_used)
