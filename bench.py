@@ -41,7 +41,9 @@ def parse_args():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default="heis16", choices=["heis16", "maxcut24", "tfim10", "batch256"])
+    ap.add_argument("--workload", default="heis16", choices=["heis16", "maxcut24", "tfim10", "batch256", "serve"])
+    ap.add_argument("--serve-seconds", type=float, default=2.0)
+    ap.add_argument("--serve-rate", type=float, default=500.0)
     ap.add_argument("--autotune", type=int, default=1)
     ap.add_argument("--batch-jobs", type=int, default=256)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
@@ -564,6 +566,8 @@ def run_ours(args):
     hs.lib()
     if args.workload == "batch256":
         return run_batch(args, rank, world)
+    if args.workload == "serve":
+        return run_serve(args, rank, world)
     job, desc = make_job(args.workload)
     dtype = job.dtype
     res = time_ours(job, args, world, dtype, rank)
@@ -632,6 +636,52 @@ def run_batch(args, rank, world):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = oracle_batch_sample(jobs)
         line["cpu_baseline"] = {"value": cb["value"], "unit": METRIC, "cores": 1, "kind": "oracle", "sample": cb["sample"]}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_serve(args, rank, world):
+    """A step = serving one Poisson request stream (arrivals over --serve-seconds,
+    then the drain).  Value = amplitude updates of all requests / (last
+    completion - first arrival); p50/p99 arrival-to-completion latency beside it."""
+    import torch
+    from paper_2606_16959_gb300 import serve, workloads as W
+    jobs = W.serve_stream(rate=args.serve_rate, duration=args.serve_seconds, seed=1005)
+    jobs = serve.shard_jobs(jobs, rank, world)
+    desc = (f"Poisson stream {args.serve_rate:g} req/s for {args.serve_seconds:g} s (seed 1005): TFIM, Heisenberg, "
+            "MaxCut (n~U{12..24}) and one-hot TSP (16 qubits), t~U[0.5,2], steps~U{10..100}, complex64, "
+            "per-family budgets; HBM admission")
+    for _ in range(args.warmup):
+        warm = serve.requests_from_jobs(jobs[:8])
+        for r in warm:
+            r.arrival = 0.0
+        serve.Server().run(warm, realtime=False)
+    runs = []
+    barrier(world)
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    for _ in range(args.steps):
+        reqs = serve.requests_from_jobs(jobs)
+        runs.append(serve.Server().run(reqs, realtime=True))
+    clocks = sampler.stop() if sampler else None
+    barrier(world)
+    updates = sum(r["updates"] for r in runs)
+    span = max_over_ranks(sum(r["makespan_s"] for r in runs), world)
+    value = updates * world / span
+    p50 = statistics.median([r["p50_ms"] for r in runs])
+    p99 = max(r["p99_ms"] for r in runs)
+    line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000 * span / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+            "config": {"workload": "serve", "description": desc, "requests_per_step": len(jobs),
+                       "l2": "inputs larger than L2 (factor sets up to 16 GB)"},
+            "latency_ms": {"p50": p50, "p99": p99, "mean": statistics.mean([r["mean_ms"] for r in runs])},
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 32 * len(jobs)},
+            "gpu_launches": None, "clocks": clocks, "peak_admitted_bytes": max(r["peak_bytes"] for r in runs)}
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

@@ -162,7 +162,7 @@ typedef struct {
 } hs_batch_job;
 
 typedef struct {
-  int tile_bits; /* log2 amplitudes per tile, 8..11 (0 = 9); jobs with fewer qubits, or whose
+  int tile_bits; /* log2 amplitudes per tile, 8..11 (0 = 10); jobs with fewer qubits, or whose
                     factors do not fit a tile, are evolved with their own launches */
   int low_bits;  /* contiguous low bits of a tile (0 = library choice) */
   int use_graph; /* 1 (default): capture the launch sequence once and replay it as a CUDA graph */

@@ -248,7 +248,7 @@ extern "C" int hs_batch_create(const hs_batch_job* jobs, size_t n_jobs, const hs
     min_n = std::min(min_n, J.factors->plan.n_qubits);
   }
   const hs_dtype dt = b->dtype;
-  b->tile_bits = o.tile_bits > 0 ? o.tile_bits : 9;
+  b->tile_bits = o.tile_bits > 0 ? o.tile_bits : 10;
   b->low_bits = o.low_bits > 0 ? o.low_bits : (dt == HS_C64 ? 2 : 1);
   b->use_graph = o.use_graph != 0;
   if (b->tile_bits < 8 || b->tile_bits > 11) return hs::report_error(HS_EINVAL, "batch tile_bits must be 8..11");

@@ -50,7 +50,7 @@ def requests_from_jobs(jobs) -> List[Request]:
     out = []
     for k, j in enumerate(jobs):
         out.append(Request(list(j.ham.labels), np.asarray(j.ham.coeffs), j.ham.n_qubits, j.t, j.n_steps, j.budget,
-                           arrival=j.arrival, psi0=None, seed=k, rid=k))
+                           arrival=j.arrival, psi0=j.psi0, seed=j.seed if j.psi0 is None else k, rid=k))
     return out
 
 

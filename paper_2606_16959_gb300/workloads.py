@@ -214,9 +214,10 @@ class Job:
     t: float
     n_steps: int
     budget: int
-    psi0: np.ndarray          # (N,) or (n_rhs, N) complex128
+    psi0: Optional[np.ndarray]  # (N,) or (n_rhs, N) complex128; None: made from `seed` where it is used
     dtype: str = "c64"        # "c64" or "c128"
     arrival: float = 0.0      # seconds, serving only
+    seed: int = 0             # seed of the initial state when psi0 is None
 
 
 def tfim10() -> Job:
@@ -283,12 +284,14 @@ def serve_stream(rate: float = 500.0, duration: float = 20.0, seed: int = 1005,
         elif fam == "heisenberg":
             ham = heisenberg_chain(n, rng.uniform(0.5, 1.5, size=n), periodic=True)
         elif fam == "maxcut":
+            n = n + (n % 2) if n + (n % 2) <= n_hi else n - 1  # a 3-regular graph needs an even n
             ham = maxcut_3regular(n, int(rng.integers(0, 2**31)), 0.5)
         else:
             ham = tsp_onehot(4, int(rng.integers(0, 2**31)))
             n = ham.n_qubits
         t = float(rng.uniform(0.5, 2.0))
         steps = int(rng.integers(10, 101))
-        psi = gaussian_state(n, rng)
-        jobs.append(Job(ham, t, steps, FAMILY_BUDGET[fam], psi, "c64", arrival=tnow))
+        # the initial state is a seeded Gaussian made on the device when served
+        jobs.append(Job(ham, t, steps, FAMILY_BUDGET[fam], None, "c64", arrival=tnow,
+                        seed=int(rng.integers(0, 2**31))))
     return jobs

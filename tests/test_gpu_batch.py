@@ -99,7 +99,7 @@ def test_batch_uneven_heisenberg_tfim_mix():
         r = torch.from_numpy(j.psi0).to("cuda", torch.complex64)
         hs.hs_evolve_ex(f, r, j.n_steps, method=hs.HS_METHOD_FUSED, tile_bits=9, rhs_block=1, low_bits=2)
         refs.append(r)
-    b = hs.hs_batch_create([(f, s, j.n_steps) for f, s, j in zip(facs, states, jobs)])
+    b = hs.hs_batch_create([(f, s, j.n_steps) for f, s, j in zip(facs, states, jobs)], tile_bits=9, low_bits=2)
     assert b.n_separate == 0
     assert b.n_updates == sum(j.n_steps * f.n_factors * (1 << j.ham.n_qubits) for f, j in zip(facs, jobs))
     hs.hs_batch_launch(b)
