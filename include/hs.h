@@ -125,7 +125,9 @@ typedef struct {
   int rhs_block;  /* states per tile for FUSED; 0 = library choice */
   int use_graph;  /* 1: replay the launch sequence as a cached CUDA graph; 0: direct launches */
   int low_bits;   /* FUSED: contiguous low bits every tile keeps (coalescing run of 2^low_bits
-                     amplitudes); 0 = library choice (64-byte runs) */
+                     amplitudes); 0 = library choice (32-byte runs) */
+  int max_fuse;   /* FUSED: most factor applications one sweep launch applies (step-fusion
+                     depth, 1..64); 0 = 64 */
 } hs_evolve_opts;
 
 /* hs_evolve with an explicit method and tiling (opts may be NULL = AUTO). */

@@ -45,9 +45,8 @@ void release(hs_factors* f, cudaStream_t s) {
     for (auto& kv : f->graphs) cudaGraphExecDestroy(kv.second);
     f->graphs.clear();
   }
-  void* bufs[] = {f->d_vals, f->d_offs, f->d_rowbase, f->d_fac_D, f->d_fac_diag0, f->d_slot_u, f->d_slot_tab, f->d_tab_rb};
-  for (void* b : bufs)
-    if (b) cudaFreeAsync(b, s);
+  if (f->d_vals) cudaFreeAsync(f->d_vals, s);
+  if (f->d_tables) cudaFreeAsync(f->d_tables, s);
   delete f;
 }
 
@@ -163,21 +162,14 @@ int hs_build_factors_masks(const uint64_t* x, const uint64_t* z, const double* c
   const size_t vbytes = size_t(p.total_elems) * hs::elem_bytes(dtype);
   hs_factors* fp = f.get();
   auto guard = [&](cudaError_t e2, const char* what) -> int { return e2 == cudaSuccess ? HS_OK : cuda_fail(e2, what); };
-  // Stream-ordered allocations: building, using and freeing a factor set
-  // never synchronises the device.
-  auto mal = [&](void** ptr, size_t bytes) { return cudaMallocAsync(ptr, bytes, s); };
-  if ((rc = guard(mal(&fp->d_vals, vbytes), "cudaMallocAsync(values)"))) { release(f.release(), s); return rc; }
-  if ((rc = guard(mal((void**)&fp->d_offs, nd * sizeof(int64_t)), "cudaMallocAsync")) ||
-      (rc = guard(mal((void**)&fp->d_rowbase, nd * sizeof(int64_t)), "cudaMallocAsync")) ||
-      (rc = guard(mal((void**)&fp->d_fac_D, G * sizeof(int)), "cudaMallocAsync")) ||
-      (rc = guard(mal((void**)&fp->d_fac_diag0, G * sizeof(int)), "cudaMallocAsync")) ||
-      (rc = guard(mal((void**)&fp->d_slot_u, (p.slot_u.size() + 1) * sizeof(uint32_t)), "cudaMallocAsync")) ||
-      (rc = guard(mal((void**)&fp->d_slot_tab, p.slot_tab.size() * sizeof(int32_t)), "cudaMallocAsync")) ||
-      (rc = guard(mal((void**)&fp->d_tab_rb, (p.tab_rb.size() + 1) * sizeof(int64_t)), "cudaMallocAsync"))) {
+  // Stream-ordered allocations (building, using and freeing a factor set never
+  // synchronises the device): one for the values and one for every table --
+  // the persistent per-diagonal / per-factor / slot tables and the build-only
+  // term tables -- filled by a single host-to-device copy.
+  if ((rc = guard(cudaMallocAsync(&fp->d_vals, vbytes, s), "cudaMallocAsync(values)"))) {
     release(f.release(), s);
     return rc;
   }
-  // Term and group tables for the build, packed in one temporary buffer.
   const size_t m = n_terms;
   std::vector<int> fD(G), fd0(G), gfirst(G), glast(G), xdim(G), pivot(G * hs::kMaxXDim, 0);
   std::vector<uint64_t> basis(G * hs::kMaxXDim, 0);
@@ -196,29 +188,33 @@ int hs_build_factors_masks(const uint64_t* x, const uint64_t* z, const double* c
   std::vector<unsigned char> blob;
   auto put = [&](const void* src, size_t bytes) {
     size_t off = (blob.size() + 15) / 16 * 16;
-    blob.resize(off + bytes);
-    if (bytes) std::memcpy(blob.data() + off, src, bytes);
+    blob.resize(off + std::max<size_t>(bytes, 16));
+    if (src && bytes) std::memcpy(blob.data() + off, src, bytes);
     return off;
   };
-  size_t o_x = put(p.x.data(), m * 8), o_z = put(p.z.data(), m * 8), o_c = put(p.coeff.data(), m * 8);
-  size_t o_cx = put(p.term_cx.data(), m * 4), o_gf = put(gfirst.data(), G * 4), o_gl = put(glast.data(), G * 4);
-  size_t o_b = put(basis.data(), basis.size() * 8), o_xd = put(xdim.data(), G * 4), o_pv = put(pivot.data(), pivot.size() * 4);
-  size_t o_cs = put(nullptr, 0);
-  blob.resize(o_cs + m * 16);
+  const size_t o_offs = put(p.offs.data(), nd * 8), o_rb = put(p.rowbase.data(), nd * 8);
+  const size_t o_fD = put(fD.data(), G * 4), o_fd0 = put(fd0.data(), G * 4);
+  const size_t o_su = put(p.slot_u.data(), p.slot_u.size() * 4), o_st = put(p.slot_tab.data(), p.slot_tab.size() * 4);
+  const size_t o_tab = put(p.tab_rb.data(), p.tab_rb.size() * 8);
+  const size_t o_x = put(p.x.data(), m * 8), o_z = put(p.z.data(), m * 8), o_c = put(p.coeff.data(), m * 8);
+  const size_t o_cx = put(p.term_cx.data(), m * 4), o_gf = put(gfirst.data(), G * 4), o_gl = put(glast.data(), G * 4);
+  const size_t o_b = put(basis.data(), basis.size() * 8), o_xd = put(xdim.data(), G * 4);
+  const size_t o_pv = put(pivot.data(), pivot.size() * 4);
+  const size_t o_cs = put(nullptr, m * 16);  // (cos, sin) per term, written on the device
   unsigned char* d_blob = nullptr;
-  if ((rc = guard(cudaMallocAsync((void**)&d_blob, blob.size(), s), "cudaMallocAsync"))) { release(f.release(), s); return rc; }
-  if ((rc = guard(cudaMemcpyAsync(d_blob, blob.data(), o_cs, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync")) ||
-      (rc = guard(cudaMemcpyAsync(fp->d_offs, p.offs.data(), nd * 8, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync")) ||
-      (rc = guard(cudaMemcpyAsync(fp->d_rowbase, p.rowbase.data(), nd * 8, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync")) ||
-      (rc = guard(cudaMemcpyAsync(fp->d_fac_D, fD.data(), G * 4, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync")) ||
-      (rc = guard(cudaMemcpyAsync(fp->d_fac_diag0, fd0.data(), G * 4, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync")) ||
-      (rc = guard(cudaMemcpyAsync(fp->d_slot_u, p.slot_u.data(), p.slot_u.size() * 4, cudaMemcpyHostToDevice, s),
-                  "cudaMemcpyAsync")) ||
-      (rc = guard(cudaMemcpyAsync(fp->d_slot_tab, p.slot_tab.data(), p.slot_tab.size() * 4, cudaMemcpyHostToDevice, s),
-                  "cudaMemcpyAsync")) ||
-      (rc = guard(cudaMemcpyAsync(fp->d_tab_rb, p.tab_rb.data(), p.tab_rb.size() * 8, cudaMemcpyHostToDevice, s),
-                  "cudaMemcpyAsync"))) {
-    cudaFreeAsync(d_blob, s);
+  if ((rc = guard(cudaMallocAsync((void**)&d_blob, blob.size(), s), "cudaMallocAsync(tables)"))) {
+    release(f.release(), s);
+    return rc;
+  }
+  fp->d_tables = d_blob;
+  fp->d_offs = reinterpret_cast<int64_t*>(d_blob + o_offs);
+  fp->d_rowbase = reinterpret_cast<int64_t*>(d_blob + o_rb);
+  fp->d_fac_D = reinterpret_cast<int*>(d_blob + o_fD);
+  fp->d_fac_diag0 = reinterpret_cast<int*>(d_blob + o_fd0);
+  fp->d_slot_u = reinterpret_cast<uint32_t*>(d_blob + o_su);
+  fp->d_slot_tab = reinterpret_cast<int32_t*>(d_blob + o_st);
+  fp->d_tab_rb = reinterpret_cast<int64_t*>(d_blob + o_tab);
+  if ((rc = guard(cudaMemcpyAsync(d_blob, blob.data(), o_cs, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync"))) {
     cudaStreamSynchronize(s);
     release(f.release(), s);
     return rc;
@@ -232,11 +228,10 @@ int hs_build_factors_masks(const uint64_t* x, const uint64_t* z, const double* c
                          reinterpret_cast<const int*>(d_blob + o_gf), reinterpret_cast<const int*>(d_blob + o_gl),
                          reinterpret_cast<const uint64_t*>(d_blob + o_b), reinterpret_cast<const int*>(d_blob + o_xd),
                          reinterpret_cast<const int*>(d_blob + o_pv), s);
-  cudaError_t e2 = cudaFreeAsync(d_blob, s);
-  if (e != cudaSuccess || e2 != cudaSuccess) {
+  if (e != cudaSuccess) {
     cudaStreamSynchronize(s);
     release(f.release(), s);
-    return cuda_fail(e != cudaSuccess ? e : e2, "factor build launch");
+    return cuda_fail(e, "factor build launch");
   }
   *out = f.release();
   return HS_OK;
@@ -281,9 +276,9 @@ int hs_plan_factors(const uint64_t* x, const uint64_t* z, size_t n_terms, int n_
 
 // Resolve evolve options: method, tile bits, rhs block, low bits.
 int resolve_opts(const hs_factors* f, int n_rhs, const hs_evolve_opts* opts, hs_evolve_opts& o, int& tb, int& rb) {
-  o = hs_evolve_opts{HS_METHOD_AUTO, 0, 0, 0, 0};
+  o = hs_evolve_opts{HS_METHOD_AUTO, 0, 0, 0, 0, 0};
   if (opts) o = *opts;
-  if (o.method == HS_METHOD_AUTO && o.tile_bits == 0 && o.rhs_block == 0 && o.low_bits == 0) {
+  if (o.method == HS_METHOD_AUTO && o.tile_bits == 0 && o.rhs_block == 0 && o.low_bits == 0 && o.max_fuse == 0) {
     hs_evolve_opts t;
     if (hs::tuned_opts(f, n_rhs, &t)) {
       t.use_graph = o.use_graph;
@@ -291,6 +286,7 @@ int resolve_opts(const hs_factors* f, int n_rhs, const hs_evolve_opts* opts, hs_
     }
   }
   if (o.low_bits <= 0) o.low_bits = min_low_bits(f->dtype);
+  if (o.max_fuse <= 0 || o.max_fuse > hs::kMaxSweepFactors) o.max_fuse = hs::kMaxSweepFactors;
   if (o.low_bits < (f->dtype == HS_C64 ? 1 : 0) || o.low_bits > 12) return fail(HS_EINVAL, "low_bits out of range");
   if (o.method != HS_METHOD_AUTO && o.method != HS_METHOD_PLAIN && o.method != HS_METHOD_FUSED)
     return fail(HS_EINVAL, "unknown method");
@@ -313,7 +309,8 @@ int hs_evolve_plan(const hs_factors* f, int n_rhs, int n_steps, const hs_evolve_
   int tb = 0, rb = 0;
   int rc = resolve_opts(f, n_rhs, opts, o, tb, rb);
   if (rc != HS_OK) return rc;
-  std::vector<hs::Sweep> sw = hs::plan_sweeps(f->plan, n_steps, tb, o.low_bits, o.method != HS_METHOD_PLAIN);
+  std::vector<hs::Sweep> sw = hs::plan_sweeps(f->plan, n_steps, tb, o.low_bits, o.method != HS_METHOD_PLAIN,
+                                              hs::kMaxFusedDiags, o.max_fuse);
   int ns = 0, np = 0;
   for (const hs::Sweep& w : sw) (w.fused ? ns : np) += 1;
   if (n_sweeps) *n_sweeps = ns;
@@ -341,11 +338,12 @@ int hs_evolve_ex(const hs_factors* f, void* psi, int n_rhs, int n_steps, const h
   }
   cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
   const size_t state_bytes = size_t(n_rhs) * size_t(f->plan.N) * hs::elem_bytes(f->dtype);
-  const std::vector<hs::Sweep> sw = hs::plan_sweeps(f->plan, n_steps, tb, o.low_bits, o.method != HS_METHOD_PLAIN);
+  const std::vector<hs::Sweep> sw = hs::plan_sweeps(f->plan, n_steps, tb, o.low_bits, o.method != HS_METHOD_PLAIN,
+                                                    hs::kMaxFusedDiags, o.max_fuse);
   const bool scratch_needed = has_plain(sw);
 
   if (o.use_graph) {
-    hs_factors::GraphKey key{psi, n_rhs, n_steps, int(o.method), tb, rb * 64 + o.low_bits, nullptr};
+    hs_factors::GraphKey key{psi, n_rhs, n_steps, int(o.method) * 128 + o.max_fuse, tb, rb * 64 + o.low_bits, nullptr};
     cudaGraphExec_t exec = nullptr;
     {
       std::lock_guard<std::mutex> lk(f->graph_mu);

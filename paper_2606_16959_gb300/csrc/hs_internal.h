@@ -87,7 +87,7 @@ struct Sweep {
 // Factors with more than max_fused_diags diagonals, or whose flip span does not
 // fit a tile, get plain launches.
 std::vector<Sweep> plan_sweeps(const Plan& p, int n_steps, int tile_bits, int min_low_bits, bool fused,
-                               int max_fused_diags = kMaxFusedDiags);
+                               int max_fused_diags = kMaxFusedDiags, int max_fuse = kMaxSweepFactors);
 
 // Decompose a bit mask into runs of consecutive set bits (low to high).
 Runs runs_of(uint64_t mask, int n_bits);
@@ -107,6 +107,7 @@ struct hs_factors {
   double t = 0.0;
   int device = 0;
   void* d_vals = nullptr;        // padded factor values (float2 / double2)
+  void* d_tables = nullptr;      // one allocation holding every table below (and the build inputs)
   int64_t* d_offs = nullptr;     // per diagonal offset
   int64_t* d_rowbase = nullptr;  // per diagonal row-indexed base
   int* d_fac_D = nullptr;        // per factor diagonal count

@@ -267,7 +267,8 @@ uint64_t two_run_mask(uint64_t used, int n, int T, int low_bits) {
 }
 
 std::vector<Sweep> plan_sweeps(const Plan& p, int n_steps, int tile_bits, int min_low_bits, bool fused,
-                               int max_fused_diags) {
+                               int max_fused_diags, int max_fuse) {
+  if (max_fuse < 1 || max_fuse > kMaxSweepFactors) max_fuse = kMaxSweepFactors;
   std::vector<Sweep> out;
   const int n = p.n_qubits;
   tile_bits = std::min(tile_bits, n);
@@ -294,7 +295,7 @@ std::vector<Sweep> plan_sweeps(const Plan& p, int n_steps, int tile_bits, int mi
         continue;
       }
       if (!cur.factors.empty() && (two_run_mask(used | span, n, tile_bits, min_low_bits) == 0 ||
-                                   int(cur.factors.size()) >= kMaxSweepFactors)) {
+                                   int(cur.factors.size()) >= max_fuse)) {
         close(cur, used);
         used = 0;
       }

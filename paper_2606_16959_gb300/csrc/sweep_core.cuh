@@ -63,7 +63,7 @@ struct SlotMeta {
   uint32_t u;    // x-mask of the slot
   uint32_t U;    // its local image (u lies inside the tile's local bits)
   int32_t tab;   // first row-base table entry in shared memory
-  int32_t pad;
+  int32_t pos;   // plane position in the stage ring (factors staged by the prologue)
 };
 
 // Scatter the low bits of v into the positions of the runs.
@@ -91,15 +91,17 @@ __device__ __forceinline__ uint32_t pattern_of(uint32_t r, uint32_t u) {
   return p;
 }
 
+// The copies carry no memory clobber: shared memory they write is read only
+// after cp.async.wait_group and a barrier, which do.
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   const uint32_t s = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
 }
 __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
   const uint32_t s = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem));
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n"); }
 // Wait until at most n of the most recently committed groups are pending.
 __device__ __forceinline__ void cp_async_wait(int n) {
   switch (n) {
@@ -123,12 +125,13 @@ template <typename T2, int ROWS, int RB, int NRB, typename Issue>
 __device__ __forceinline__ void sweep_body(const SweepArgs& a, int nrb, T2* tile, const T2* stages, uint32_t stage_elems,
                                            const SlotMeta* mslot, uint32_t TS, int NT, Issue& issue_factor) {
   const int S = a.n_stages;
+  int stage = 0;  // fi % S
   for (int fi = 0; fi < a.n_factors; ++fi) {
     cp_async_wait(fi == 0 ? 0 : S - 1);
     __syncthreads();
     const int ns = a.fnslot[fi];
     const SlotMeta* ms = mslot + a.fmslot[fi];
-    const T2* st = stages + size_t(fi % S) * stage_elems + threadIdx.x;
+    const T2* st = stages + size_t(stage) * stage_elems + threadIdx.x;
     T2 acc[ROWS][RB];
 #pragma unroll
     for (int i = 0; i < ROWS; ++i)
@@ -155,8 +158,9 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a, int nrb, T2* tile
         if (NRB || q < nrb) *yp = acc[i][q];
     }
     // Refill the stage just consumed (every thread is past the barrier above).
-    if (fi + S < a.n_factors) issue_factor(fi + S, fi % S);
+    if (fi + S < a.n_factors) issue_factor(fi + S, stage);
     cp_async_commit();
+    stage = (stage + 1 == S) ? 0 : stage + 1;
   }
   __syncthreads();
 }
@@ -196,48 +200,64 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, uint32_t tile_id,
   const uint32_t base = deposit_runs(tile_id, a.rest);
   const uint32_t n_chunks = TS / V;
 
-  // Slot and row-base tables of every factor of the sweep, loaded once.
-  for (int i = 0; i < a.n_factors; ++i) {
-    for (int j = threadIdx.x; j < a.fnslot[i]; j += NT) {
-      const uint32_t u = a.slot_u[a.fslot0[i] + j];
-      mslot[a.fmslot[i] + j] = SlotMeta{u, local_of(u, m0, m1, sh), a.ftab_s[i] + (a.slot_tab[a.fslot0[i] + j] - a.ftab_g[i]), 0};
+  // Slot and row-base tables of every factor of the sweep, loaded once: each
+  // thread takes table entries t, t + NT, ... and finds the factor that owns
+  // an entry by binary search, so all global loads are independent.
+  for (int t = threadIdx.x; t < a.n_mslot; t += NT) {
+    int lo = 0, hi = a.n_factors - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (a.fmslot[mid] <= t) lo = mid; else hi = mid - 1;
     }
-    for (int e = threadIdx.x; e < a.ftab_n[i]; e += NT) mtab[a.ftab_s[i] + e] = a.tab_rb[a.ftab_g[i] + e];
+    const int gs = a.fslot0[lo] + (t - a.fmslot[lo]);
+    const uint32_t u = a.slot_u[gs];
+    mslot[t] = SlotMeta{u, local_of(u, m0, m1, sh), a.ftab_s[lo] + (a.slot_tab[gs] - a.ftab_g[lo]),
+                        lo * a.stage_planes + (t - a.fmslot[lo])};
+  }
+  for (int e = threadIdx.x; e < a.n_mtab; e += NT) {
+    int lo = 0, hi = a.n_factors - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (a.ftab_s[mid] <= e) lo = mid; else hi = mid - 1;
+    }
+    mtab[e] = a.tab_rb[a.ftab_g[lo] + (e - a.ftab_s[lo])];
   }
   __syncthreads();
 
-  // Stage plane u of factor fi for the tile rows.
-  auto issue_factor = [&](int fi, int stage) {
-    const int ns = a.fnslot[fi];
-    T2* st = stages + size_t(stage) * stage_elems;
-    for (int j = 0; j < ns; ++j) {
-      const SlotMeta m = mslot[a.fmslot[fi] + j];
+  // Stage slots [p0, p1) of the slot table for the tile rows: plane u of a
+  // factor receives, for every tile row r, the value of entry (r, r ^ u).  The
+  // items (slot, 16-byte chunk) are independent, so one flat loop keeps many
+  // copies in flight.  stage < 0: the prologue, whose planes sit at the
+  // positions recorded in the slot table; otherwise the planes of one factor go
+  // to that stage.
+  const int chunk_log2 = a.tile_bits - (V == 2 ? 1 : 0);
+  auto issue_slots = [&](int p0, int p1, int stage) {
+    const int items = (p1 - p0) << chunk_log2;
+#pragma unroll 4
+    for (int k = threadIdx.x; k < items; k += NT) {
+      const int p = p0 + (k >> chunk_log2);
+      const uint32_t c = uint32_t(k) & (n_chunks - 1u);
+      const SlotMeta m = mslot[p];
+      const int pos = stage < 0 ? m.pos : stage * a.stage_planes + (p - p0);
+      T2* dst_s = stages + size_t(pos) * TS + c * V;
+      const uint32_t r = global_of(c * V, m0, m1, sh) | base;
       const int64_t* tab = mtab + m.tab;
-      T2* plane = st + size_t(j) * TS;
+      const uint32_t pat = pattern_of(r, m.u);
       if (V == 1 || !(m.u & 1u)) {
-        for (uint32_t c = threadIdx.x; c < n_chunks; c += NT) {
-          const uint32_t l = c * V;
-          const uint32_t r = global_of(l, m0, m1, sh) | base;
-          cp_async16(plane + l, vals + tab[pattern_of(r, m.u)] + r);
-        }
+        cp_async16(dst_s, vals + tab[pat] + r);
       } else {
         // u flips bit 0: the two rows of a 16-byte chunk lie on different diagonals.
-        for (uint32_t c = threadIdx.x; c < n_chunks; c += NT) {
-          const uint32_t l = c * V;
-          const uint32_t r = global_of(l, m0, m1, sh) | base;
-          const uint32_t p0 = pattern_of(r, m.u);  // bit 0 of r is 0
-          cp_async8(plane + l, vals + tab[p0] + r);
-          cp_async8(plane + l + 1, vals + tab[p0 | 1u] + r + 1);
-        }
+        cp_async8(dst_s, vals + tab[pat] + r);
+        cp_async8(dst_s + 1, vals + tab[pat | 1u] + r + 1);
       }
     }
   };
+  auto issue_factor = [&](int fi, int stage) { issue_slots(a.fmslot[fi], a.fmslot[fi] + a.fnslot[fi], stage); };
 
+  // Prologue: the first S factors, as one copy group.
   const int S = a.n_stages;
-  for (int s = 0; s < S; ++s) {
-    if (s < a.n_factors) issue_factor(s, s);
-    cp_async_commit();
-  }
+  issue_slots(0, S < a.n_factors ? a.fmslot[S] : a.n_mslot, -1);
+  cp_async_commit();
   // The state written by the previous launch is visible only after this.
   grid_dependency_wait();
   // Let the next sweep start its own prologue (tables and factor staging, which
