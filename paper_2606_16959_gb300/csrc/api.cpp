@@ -3,6 +3,8 @@
 
 #include <cmath>
 #include <cstring>
+#include <list>
+#include <unordered_map>
 #include <memory>
 #include <string>
 #include <tuple>
@@ -120,6 +122,142 @@ int pick_tile_bits(const hs_factors* f, int rhs_block) {
   return t;
 }
 
+// Plans depend only on the flip masks, the qubit count, the budget and the
+// dtype (not on coefficients or the time step), so rebuilding a factor set for
+// the same structure reuses the planned grouping, layout and slot tables.
+struct PlanCache {
+  std::mutex mu;
+  std::list<std::string> lru;
+  std::unordered_map<std::string, std::pair<hs::Plan, std::list<std::string>::iterator>> map;
+  static constexpr size_t kCap = 64;
+};
+PlanCache& plan_cache() {
+  static PlanCache c;
+  return c;
+}
+std::string plan_key(const uint64_t* x, size_t n, int n_qubits, int budget, hs_dtype dt) {
+  std::string k(reinterpret_cast<const char*>(x), n * sizeof(uint64_t));
+  k.append(reinterpret_cast<const char*>(&n_qubits), sizeof(int));
+  k.append(reinterpret_cast<const char*>(&budget), sizeof(int));
+  const int d = int(dt);
+  k.append(reinterpret_cast<const char*>(&d), sizeof(int));
+  return k;
+}
+int cached_plan(const uint64_t* x, const uint64_t* z, const double* coeff, size_t n, int n_qubits, int budget,
+                hs_dtype dt, hs::Plan& plan, std::string* err) {
+  const std::string key = plan_key(x, n, n_qubits, budget, dt);
+  PlanCache& c = plan_cache();
+  {
+    std::lock_guard<std::mutex> lk(c.mu);
+    auto it = c.map.find(key);
+    if (it != c.map.end()) {
+      c.lru.splice(c.lru.begin(), c.lru, it->second.second);
+      plan = it->second.first;
+    } else {
+      plan = hs::Plan();
+    }
+  }
+  if (plan.n_qubits == 0) {
+    int rc = hs::make_plan(x, z, coeff, n, n_qubits, budget, dt, plan, err);
+    if (rc != HS_OK) return rc;
+    std::lock_guard<std::mutex> lk(c.mu);
+    if (c.map.find(key) == c.map.end()) {
+      c.lru.push_front(key);
+      c.map.emplace(key, std::make_pair(plan, c.lru.begin()));
+      if (c.lru.size() > PlanCache::kCap) {
+        c.map.erase(c.lru.back());
+        c.lru.pop_back();
+      }
+    }
+    return HS_OK;
+  }
+  // Same structure: take this call's phase masks and coefficients.
+  for (size_t j = 0; j < n; ++j) {
+    if (coeff && !std::isfinite(coeff[j])) { *err = "non-finite coefficient at term " + std::to_string(j); return HS_EINVAL; }
+    if (z[j] >= (1ull << n_qubits)) { *err = "mask of term " + std::to_string(j) + " exceeds n_qubits"; return HS_EINVAL; }
+  }
+  plan.z.assign(z, z + n);
+  plan.coeff.assign(coeff, coeff + n);
+  return HS_OK;
+}
+
+}  // namespace
+
+namespace hs {
+// The library's stream-ordered memory pool on the current device: memory freed
+// by hs_free_factors_async / hs_batch_free_async stays in the pool (release
+// threshold unlimited) so that the next factor build reuses it without mapping
+// new memory.  Falls back to the device's default pool if creation fails.
+cudaMemPool_t library_pool() {
+  static std::mutex mu;
+  static cudaMemPool_t pools[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!pools[dev]) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t p = nullptr;
+    if (cudaMemPoolCreate(&p, &props) != cudaSuccess) {
+      cudaGetLastError();
+      if (cudaDeviceGetDefaultMemPool(&p, dev) != cudaSuccess) return nullptr;
+    }
+    uint64_t thr = ~0ull;
+    cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &thr);
+    pools[dev] = p;
+  }
+  return pools[dev];
+}
+
+cudaError_t pool_malloc(void** ptr, size_t bytes, cudaStream_t s) {
+  cudaMemPool_t p = library_pool();
+  if (!p) return cudaMallocAsync(ptr, bytes, s);
+  return cudaMallocFromPoolAsync(ptr, bytes, p, s);
+}
+}  // namespace hs
+
+namespace {
+
+// Pinned host staging for table uploads: a small ring of buffers, each reused
+// only after the copy that last read it has completed.
+struct Staging {
+  void* buf = nullptr;
+  size_t cap = 0;
+  cudaEvent_t ev = nullptr;
+};
+int stage_upload(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+  static std::mutex mu;
+  static Staging ring[8];
+  static int next = 0;
+  std::lock_guard<std::mutex> lk(mu);
+  Staging& st = ring[next];
+  next = (next + 1) % 8;
+  if (st.ev) cudaEventSynchronize(st.ev);
+  if (st.cap < bytes) {
+    if (st.buf) cudaFreeHost(st.buf);
+    st.buf = nullptr;
+    st.cap = 0;
+    size_t cap = std::max<size_t>(bytes, 64 << 10);
+    if (cudaHostAlloc(&st.buf, cap, cudaHostAllocDefault) != cudaSuccess) {
+      st.buf = nullptr;
+      cudaGetLastError();
+      return int(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s));  // pageable fallback
+    }
+    st.cap = cap;
+  }
+  if (!st.ev && cudaEventCreateWithFlags(&st.ev, cudaEventDisableTiming) != cudaSuccess) {
+    st.ev = nullptr;
+    return int(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s));
+  }
+  std::memcpy(st.buf, src, bytes);
+  cudaError_t e = cudaMemcpyAsync(dst, st.buf, bytes, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaEventRecord(st.ev, s);
+  return int(e);
+}
+
 }  // namespace
 
 namespace hs {
@@ -147,7 +285,7 @@ int hs_build_factors_masks(const uint64_t* x, const uint64_t* z, const double* c
   if (diag_budget < 1) return fail(HS_EINVAL, "diag_budget must be >= 1");
   std::unique_ptr<hs_factors> f(new hs_factors());
   std::string err;
-  int rc = hs::make_plan(x, z, coeffs, n_terms, n_qubits, diag_budget, dtype, f->plan, &err);
+  int rc = cached_plan(x, z, coeffs, n_terms, n_qubits, diag_budget, dtype, f->plan, &err);
   if (rc != HS_OK) return fail(rc, err);
   f->dtype = dtype;
   f->n_steps = n_steps;
@@ -166,7 +304,7 @@ int hs_build_factors_masks(const uint64_t* x, const uint64_t* z, const double* c
   // synchronises the device): one for the values and one for every table --
   // the persistent per-diagonal / per-factor / slot tables and the build-only
   // term tables -- filled by a single host-to-device copy.
-  if ((rc = guard(cudaMallocAsync(&fp->d_vals, vbytes, s), "cudaMallocAsync(values)"))) {
+  if ((rc = guard(hs::pool_malloc(&fp->d_vals, vbytes, s), "cudaMallocAsync(values)"))) {
     release(f.release(), s);
     return rc;
   }
@@ -202,7 +340,7 @@ int hs_build_factors_masks(const uint64_t* x, const uint64_t* z, const double* c
   const size_t o_pv = put(pivot.data(), pivot.size() * 4);
   const size_t o_cs = put(nullptr, m * 16);  // (cos, sin) per term, written on the device
   unsigned char* d_blob = nullptr;
-  if ((rc = guard(cudaMallocAsync((void**)&d_blob, blob.size(), s), "cudaMallocAsync(tables)"))) {
+  if ((rc = guard(hs::pool_malloc((void**)&d_blob, blob.size(), s), "cudaMallocAsync(tables)"))) {
     release(f.release(), s);
     return rc;
   }
@@ -214,7 +352,7 @@ int hs_build_factors_masks(const uint64_t* x, const uint64_t* z, const double* c
   fp->d_slot_u = reinterpret_cast<uint32_t*>(d_blob + o_su);
   fp->d_slot_tab = reinterpret_cast<int32_t*>(d_blob + o_st);
   fp->d_tab_rb = reinterpret_cast<int64_t*>(d_blob + o_tab);
-  if ((rc = guard(cudaMemcpyAsync(d_blob, blob.data(), o_cs, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync"))) {
+  if ((rc = guard(cudaError_t(stage_upload(d_blob, blob.data(), o_cs, s)), "table upload"))) {
     cudaStreamSynchronize(s);
     release(f.release(), s);
     return rc;
@@ -376,7 +514,7 @@ int hs_evolve_ex(const hs_factors* f, void* psi, int n_rhs, int n_steps, const h
 
   void* scratch = nullptr;
   if (scratch_needed) {
-    cudaError_t e = cudaMallocAsync(&scratch, state_bytes, s);
+    cudaError_t e = hs::pool_malloc(&scratch, state_bytes, s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(scratch state)");
   }
   int rc = enqueue_evolve(f, sw, psi, n_rhs, tb, rb, scratch, s);
@@ -414,7 +552,7 @@ int hs_fidelity(const void* a, const void* b, int n_qubits, hs_dtype dtype, void
   if (n_qubits < 1 || n_qubits > HS_MAX_QUBITS) return fail(HS_EINVAL, "n_qubits out of range");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
   double* d_out = nullptr;
-  cudaError_t e = cudaMallocAsync((void**)&d_out, 4 * sizeof(double), s);
+  cudaError_t e = hs::pool_malloc((void**)&d_out, 4 * sizeof(double), s);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync");
   e = hs::launch_inner(a, b, int64_t(1) << n_qubits, dtype, d_out, s);
   double h[4] = {0, 0, 0, 0};

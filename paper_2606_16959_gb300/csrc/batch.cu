@@ -184,7 +184,7 @@ void batch_release(hs_batch* b, cudaStream_t s) {
 
 template <typename T>
 cudaError_t upload(T** dptr, const std::vector<T>& v, cudaStream_t s) {
-  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(dptr), std::max<size_t>(1, v.size()) * sizeof(T), s);
+  cudaError_t e = hs::pool_malloc(reinterpret_cast<void**>(dptr), std::max<size_t>(1, v.size()) * sizeof(T), s);
   if (e != cudaSuccess || v.empty()) return e;
   return cudaMemcpyAsync(*dptr, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s);
 }

@@ -157,6 +157,9 @@ cudaError_t prepare_kernels();
 
 cudaError_t launch_inner(const void* a, const void* b, int64_t N, hs_dtype dt, double* d_out4, cudaStream_t s);
 
+// Stream-ordered allocation from the library's memory pool (api.cpp).
+cudaError_t pool_malloc(void** ptr, size_t bytes, cudaStream_t s);
+
 // Autotuner cache (tune.cpp).
 bool tuned_opts(const hs_factors* f, int n_rhs, hs_evolve_opts* out);
 

@@ -101,7 +101,7 @@ cudaError_t launch_inner_scratch(const void* a, const void* b, int64_t N, hs_dty
 
 cudaError_t launch_inner(const void* a, const void* b, int64_t N, hs_dtype dt, double* d_out4, cudaStream_t s) {
   void* scratch = nullptr;
-  cudaError_t e = cudaMallocAsync(&scratch, inner_scratch_bytes(), s);
+  cudaError_t e = pool_malloc(&scratch, inner_scratch_bytes(), s);
   if (e != cudaSuccess) return e;
   e = launch_inner_scratch(a, b, N, dt, d_out4, scratch, s);
   cudaError_t e2 = cudaFreeAsync(scratch, s);

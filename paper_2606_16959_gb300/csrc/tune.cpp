@@ -53,7 +53,7 @@ extern "C" int hs_autotune(const hs_factors* f, const void* psi, int n_rhs, int 
   const hs_dtype dt = f->dtype;
   const size_t bytes = size_t(n_rhs) * size_t(f->plan.N) * hs::elem_bytes(dt);
   void* work = nullptr;
-  cudaError_t e = cudaMallocAsync(&work, bytes, s);
+  cudaError_t e = hs::pool_malloc(&work, bytes, s);
   if (e != cudaSuccess) return hs::report_error(e == cudaErrorMemoryAllocation ? HS_ENOMEM : HS_ECUDA,
                                                 std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
   std::vector<hs_evolve_opts> cand;
