@@ -315,9 +315,11 @@ def dia_from_dense(M, offsets=None, tol: float = 0.0):
     return list(offsets), st, vals
 
 
-def hamiltonian_structure(x, z, coeffs, n_qubits: int, tol: float = 0.0):
-    """Numeric diagonal count and nonzero count of H = sum c_j P_j (zeros dropped),
-    the two structural columns of Tab. 3."""
+def ham_diagonals(x, z, coeffs, n_qubits: int) -> dict:
+    """Every diagonal of H = sum_j c_j P_j that some term touches, as
+    {offset d: values indexed by min(row, col)} (Eq. 6 element index).  Entry
+    (row b xor x_j, col b) of P_j is i^{y_j} (-1)^{popcount(z_j & b)}; terms are
+    accumulated in input order, so cancelling terms leave exact zeros."""
     N = 1 << n_qubits
     b = np.arange(N, dtype=np.uint64)
     diags = {}
@@ -337,6 +339,13 @@ def hamiltonian_structure(x, z, coeffs, n_qubits: int, tol: float = 0.0):
             arr = diags.setdefault(int(d), np.zeros(N - abs(int(d)), dtype=np.complex128))
             idx = np.minimum(row[sel], col[sel])
             np.add.at(arr, idx, c * phase[sel])
+    return diags
+
+
+def hamiltonian_structure(x, z, coeffs, n_qubits: int, tol: float = 0.0):
+    """Numeric diagonal count and nonzero count of H = sum c_j P_j (zeros dropped),
+    the two structural columns of Tab. 3."""
+    diags = ham_diagonals(x, z, coeffs, n_qubits)
     nz = {d: int(np.count_nonzero(np.abs(v) > tol)) for d, v in diags.items()}
     kept = [d for d, k in nz.items() if k > 0]
     return len(kept), sum(nz.values())
