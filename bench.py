@@ -53,12 +53,18 @@ def parse_args():
     ap.add_argument("--tile-bits", type=int, default=0)
     ap.add_argument("--rhs-block", type=int, default=0)
     ap.add_argument("--graph", type=int, default=0)
+    ap.add_argument("--qubits", type=int, default=0,
+                    help="maxcut24 only: a smaller instance of the same family (profiling cases)")
     return ap.parse_args()
 
 
-def make_job(name, dtype=None):
+def make_job(name, dtype=None, qubits=0):
     from paper_2606_16959_gb300 import workloads as W
-    if name == "heis16":
+    if name == "maxcut24" and qubits:
+        job = W.maxcut24(n=qubits)
+        desc = (f"weighted MaxCut random 3-regular n={qubits} (seed 1003) + 0.5 sum X, 16 states (|+> and Gaussians), "
+                "t=2, 50 steps, budget 4")
+    elif name == "heis16":
         job = W.heis16(dtype or "c64")
         desc = "Heisenberg XXX periodic chain n=16, J_i~U[0.5,1.5] (seed 1002), Gaussian state, t=1, 100 steps, budget 8"
     elif name == "maxcut24":
@@ -199,6 +205,16 @@ def profiled_traffic(workload):
         return None
 
 
+def dram_fields(traffic, launch_s, peak):
+    """DRAM bytes actually moved per launch (ncu) over the live launch time: the
+    roofline figure that a fused sweep, which keeps the state on chip across
+    several factors, cannot beat by construction."""
+    if traffic is None:
+        return {}
+    a = traffic / launch_s / 1e9
+    return {"dram_achieved": a, "dram_frac": a / peak}
+
+
 def load_tune_cache():
     """Autotuner choices of earlier runs on this machine (so that a run under a
     profiler replays the configuration measured without it)."""
@@ -257,7 +273,7 @@ def time_ours(job, args, world, dtype, rank):
 
     tuned = None
     if args.autotune and not any((args.method, args.tile_bits, args.rhs_block)):
-        key = f"{args.workload}:{dtype}:{torch.cuda.get_device_name()}"
+        key = f"{args.workload}:{job.ham.n_qubits}:{dtype}:{torch.cuda.get_device_name()}"
         cache = load_tune_cache()
         if key in cache:
             tuned = cache[key]
@@ -568,7 +584,7 @@ def run_ours(args):
         return run_batch(args, rank, world)
     if args.workload == "serve":
         return run_serve(args, rank, world)
-    job, desc = make_job(args.workload)
+    job, desc = make_job(args.workload, qubits=args.qubits)
     dtype = job.dtype
     res = time_ours(job, args, world, dtype, rank)
     K = args.steps
@@ -580,14 +596,15 @@ def run_ours(args):
     avg_launch_s = statistics.mean(res["evolve_ms"]) / 1000.0 / max(1, launches_evolve)
     per_launch_bytes = res["alg_bytes"] / max(1, launches_evolve)
     achieved = per_launch_bytes / avg_launch_s / 1e9
+    traffic = profiled_traffic(args.workload) if not args.qubits else None
     line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": K, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": dtype, "data": "synthetic", "config": config_of(args, job, desc, res),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                         "traffic": profiled_traffic(args.workload), "peak_source": peak_kind,
+                         "traffic": traffic, "peak_source": peak_kind,
                          "kernel": "sweep_kernel" if res["n_sweeps"] else "apply_plain_kernel",
                          "algorithmic_bytes_per_launch": per_launch_bytes,
-                         "avg_launch_us": avg_launch_s * 1e6},
+                         "avg_launch_us": avg_launch_s * 1e6, **dram_fields(traffic, avg_launch_s, hbm)},
             "e2e": {"value": res["units"] / (e2e["ms"] / 1000.0), "unit": METRIC,
                     "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"]},
             "gpu_launches": res["launches"], "clocks": res["clocks"],
@@ -619,6 +636,7 @@ def run_batch(args, rank, world):
     launch_s = statistics.mean(res["launch_ms"]) / 1000.0
     per_launch_bytes = res["alg_bytes"] / max(1, res["levels"])
     achieved = res["alg_bytes"] / launch_s / 1e9
+    traffic = profiled_traffic("batch256") if args.batch_jobs == 256 else None
     cfg = {"workload": "batch256", "description": desc, "n_jobs": len(jobs), "levels_per_step": res["levels"],
            "ctas_per_step": res["ctas"], "separate_jobs": res["separate"], "tile_bits": 9,
            "l2": "flushed (512 MiB write) before every timed step"}
@@ -626,9 +644,10 @@ def run_batch(args, rank, world):
             "ms_per_step": res["total_ms"] / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": dtype, "data": "synthetic", "config": cfg,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                         "traffic": profiled_traffic("batch256"), "peak_source": peak_kind, "kernel": "batch_level_kernel",
+                         "traffic": traffic, "peak_source": peak_kind, "kernel": "batch_level_kernel",
                          "algorithmic_bytes_per_launch": per_launch_bytes,
-                         "avg_launch_us": launch_s * 1e6 / max(1, res["levels"])},
+                         "avg_launch_us": launch_s * 1e6 / max(1, res["levels"]),
+                         **dram_fields(traffic, launch_s / max(1, res["levels"]), hbm)},
             "e2e": {"value": res["units"] / (e2e["ms"] / 1000.0), "unit": METRIC,
                     "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"]},
             "gpu_launches": res["launches"], "clocks": res["clocks"],
@@ -681,7 +700,7 @@ def run_serve(args, rank, world):
                        "l2": "inputs larger than L2 (factor sets up to 16 GB)"},
             "latency_ms": {"p50": p50, "p99": p99, "mean": statistics.mean([r["mean_ms"] for r in runs])},
             "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 32 * len(jobs)},
-            "gpu_launches": None, "clocks": clocks, "peak_admitted_bytes": max(r["peak_bytes"] for r in runs)}
+            "gpu_launches": sum(r["launches"] for r in runs), "clocks": clocks, "peak_admitted_bytes": max(r["peak_bytes"] for r in runs)}
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

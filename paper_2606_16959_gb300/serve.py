@@ -91,6 +91,7 @@ class Server:
         self.keep_results = keep_results
         self.used = 0
         self.peak_used = 0
+        self.launches = 0  # libhs kernel launches enqueued (build, batch levels, reductions)
         self._next_stream = 0
 
     def _masks(self, r: Request):
@@ -137,6 +138,7 @@ class Server:
             b = hs.hs_batch_create([(f, st, r.n_steps) for f, st, r in zip(facs, states, group)],
                                    tile_bits=self.tile_bits, use_graph=False)
             hs.hs_batch_launch(b, stream=s)
+            self.launches += 4 * len(group) + b.n_levels
             out = torch.zeros(len(group), 4, dtype=torch.float64, device="cuda")
             for k, st in enumerate(states):
                 hs.hs_inner_device(st, st, out[k], stream=s)
@@ -215,4 +217,5 @@ class Server:
         updates = sum(r.updates for r in requests)
         return dict(n=len(requests), p50_ms=float(np.percentile(lat, 50) * 1e3), p99_ms=float(np.percentile(lat, 99) * 1e3),
                     mean_ms=float(lat.mean() * 1e3), makespan_s=t_last - t_first, updates=updates,
-                    throughput=updates / max(t_last - t_first, 1e-9), peak_bytes=self.peak_used)
+                    throughput=updates / max(t_last - t_first, 1e-9), peak_bytes=self.peak_used,
+                    launches=self.launches)
