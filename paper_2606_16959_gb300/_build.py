@@ -11,7 +11,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 SO = os.path.join(OUT_DIR, "libhs.so")
 ROOT = os.path.dirname(HERE)
-HEADERS = ([os.path.join(ROOT, "include", "hs.h")] + glob.glob(os.path.join(CSRC, "*.h"))
+HEADERS = (glob.glob(os.path.join(ROOT, "include", "*.h")) + glob.glob(os.path.join(CSRC, "*.h"))
            + glob.glob(os.path.join(CSRC, "*.cuh")))
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

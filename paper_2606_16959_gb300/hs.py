@@ -20,13 +20,15 @@ HS_MAX_QUBITS = 30
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libhs.so")
 
-# Every symbol declared in include/hs.h.
+# Every symbol declared in include/hs.h and include/hs_dia.h.
 EXPORTS = (
     "hs_build_factors", "hs_build_factors_masks", "hs_evolve", "hs_evolve_ex", "hs_apply_factor",
     "hs_fidelity", "hs_inner_device", "hs_factors_info", "hs_factor_get", "hs_free_factors", "hs_last_error",
     "hs_plan_factors", "hs_evolve_plan", "hs_inner_batch_noalloc", "hs_autotune",
     "hs_batch_create", "hs_batch_launch", "hs_batch_info", "hs_batch_free", "hs_free_factors_async",
     "hs_batch_free_async",
+    "hs_dia_from_terms", "hs_dia_from_masks", "hs_dia_create", "hs_spgemm", "hs_spme", "hs_estimate_timesteps",
+    "hs_spmv", "hs_dia_evolve", "hs_dia_convert", "hs_dia_info", "hs_dia_get", "hs_dia_free",
 )
 
 
@@ -91,8 +93,23 @@ def lib() -> ctypes.CDLL:
         L.hs_free_factors.argtypes = [vp]
         L.hs_free_factors.restype = None
         L.hs_last_error.restype = ctypes.c_char_p
+        dp = ctypes.POINTER(d)
+        L.hs_dia_from_terms.argtypes = [ctypes.POINTER(ctypes.c_char_p), dp, sz, vp, ctypes.POINTER(vp)]
+        L.hs_dia_from_masks.argtypes = [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64), dp, sz, i,
+                                        vp, ctypes.POINTER(vp)]
+        L.hs_dia_create.argtypes = [i, i64p, sz, dp, i, vp, ctypes.POINTER(vp)]
+        L.hs_spgemm.argtypes = [vp, vp, vp, ctypes.POINTER(vp), dp]
+        L.hs_spme.argtypes = [vp, d, d, i, vp, ctypes.POINTER(vp), ip, ip]
+        L.hs_estimate_timesteps.argtypes = [vp, d, i, d, i, i, vp, ip]
+        L.hs_spmv.argtypes = [vp, vp, vp, i, vp]
+        L.hs_dia_evolve.argtypes = [vp, vp, i, i, vp]
+        L.hs_dia_convert.argtypes = [vp, i, vp, ctypes.POINTER(vp)]
+        L.hs_dia_info.argtypes = [vp, ip, ip, i64p, ip]
+        L.hs_dia_get.argtypes = [vp, i64p, dp]
+        L.hs_dia_free.argtypes = [vp]
+        L.hs_dia_free.restype = None
         for name in EXPORTS:
-            if name not in ("hs_free_factors", "hs_last_error", "hs_batch_free"):
+            if name not in ("hs_free_factors", "hs_last_error", "hs_batch_free", "hs_dia_free"):
                 getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -368,3 +385,138 @@ def hs_batch_create(jobs, tile_bits: int = 0, low_bits: int = 0, use_graph: bool
 
 def hs_batch_launch(b: Batch, stream=None) -> None:
     _check(lib().hs_batch_launch(b.handle, _stream(stream)))
+
+
+# ---------------------------------------------------------------------------
+# Single-factor Taylor mode (include/hs_dia.h): Alg. 2, Alg. 3, Eq. 5
+# ---------------------------------------------------------------------------
+
+class Dia:
+    """Owner of an hs_dia handle: a device-resident matrix in the compact
+    diagonal layout (freed on close or garbage collection)."""
+
+    def __init__(self, handle: int):
+        self.handle = ctypes.c_void_p(handle)
+        nq, nd, dt = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        nnz = ctypes.c_int64()
+        _check(lib().hs_dia_info(self.handle, ctypes.byref(nq), ctypes.byref(nd), ctypes.byref(nnz),
+                                 ctypes.byref(dt)))
+        self.n_qubits, self.n_diags, self.nnz = nq.value, nd.value, nnz.value
+        self.dtype = "c64" if dt.value == HS_C64 else "c128"
+
+    @property
+    def N(self) -> int:
+        return 1 << self.n_qubits
+
+    def offsets(self) -> np.ndarray:
+        out = np.zeros(self.n_diags, dtype=np.int64)
+        _check(lib().hs_dia_get(self.handle, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), None))
+        return out
+
+    def get(self):
+        """(offsets, {offset: complex128 values}) copied to the host (Eq. 6 order)."""
+        offs = self.offsets()
+        total = int(sum(self.N - abs(int(d)) for d in offs))
+        vals = np.zeros(2 * total, dtype=np.float64)
+        _check(lib().hs_dia_get(self.handle, None, vals.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        c = vals.view(np.complex128)
+        out, pos = {}, 0
+        for d in offs:
+            L = self.N - abs(int(d))
+            out[int(d)] = c[pos:pos + L].copy()
+            pos += L
+        return offs, out
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            lib().hs_dia_free(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _new_dia(fn, *args) -> Dia:
+    out = ctypes.c_void_p()
+    _check(fn(*args, ctypes.byref(out)))
+    return Dia(out.value)
+
+
+def hs_dia_from_terms(labels: Sequence[str], coeffs, stream=None) -> Dia:
+    """H = sum_j c_j P_j in the compact layout (FP64, zero diagonals dropped)."""
+    arr = (ctypes.c_char_p * len(labels))(*[l.encode() for l in labels])
+    c = np.ascontiguousarray(np.asarray(coeffs, dtype=np.float64))
+    return _new_dia(lib().hs_dia_from_terms, arr, c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(labels),
+                    _stream(stream))
+
+
+def hs_dia_from_masks(x, z, coeffs, n_qubits: int, stream=None) -> Dia:
+    x = np.ascontiguousarray(np.asarray(x, dtype=np.uint64))
+    z = np.ascontiguousarray(np.asarray(z, dtype=np.uint64))
+    c = np.ascontiguousarray(np.asarray(coeffs, dtype=np.float64))
+    return _new_dia(lib().hs_dia_from_masks, x.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                    z.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                    len(c), int(n_qubits), _stream(stream))
+
+
+def hs_dia_create(n_qubits: int, diags: dict, dtype="c128", stream=None) -> Dia:
+    """A matrix from host diagonals {offset: complex values of length N - |offset|}."""
+    offs = np.ascontiguousarray(np.asarray(list(diags.keys()), dtype=np.int64))
+    vals = np.concatenate([np.asarray(diags[int(d)], dtype=np.complex128) for d in offs]) if len(offs) else \
+        np.zeros(0, dtype=np.complex128)
+    vals = np.ascontiguousarray(vals).view(np.float64)
+    return _new_dia(lib().hs_dia_create, int(n_qubits), offs.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                    len(offs), vals.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _dtype_code(dtype),
+                    _stream(stream))
+
+
+def hs_spgemm(a: Dia, b: Dia, stream=None) -> Tuple[Dia, float]:
+    """(A B, ||A B||_F)."""
+    out, fro = ctypes.c_void_p(), ctypes.c_double()
+    _check(lib().hs_spgemm(a.handle, b.handle, _stream(stream), ctypes.byref(out), ctypes.byref(fro)))
+    return Dia(out.value), fro.value
+
+
+def hs_spme(a: Dia, t: float, tol: float = 1e-6, max_iter: int = 100, stream=None) -> Tuple[Dia, int, bool]:
+    """(exp(-i t A), Taylor terms used, converged)."""
+    out, k, ok = ctypes.c_void_p(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().hs_spme(a.handle, float(t), float(tol), int(max_iter), _stream(stream), ctypes.byref(out),
+                         ctypes.byref(k), ctypes.byref(ok)))
+    return Dia(out.value), k.value, bool(ok.value)
+
+
+def hs_estimate_timesteps(a: Dia, t: float, diag_budget: int, tol: float = 1e-6, max_iter: int = 100,
+                          max_steps: int = 1 << 20, stream=None) -> int:
+    r = ctypes.c_int()
+    _check(lib().hs_estimate_timesteps(a.handle, float(t), int(diag_budget), float(tol), int(max_iter),
+                                       int(max_steps), _stream(stream), ctypes.byref(r)))
+    return r.value
+
+
+def _dia_state(a: Dia, psi):
+    ptr, n_rhs, n, dt = _state_args(psi)
+    if n != a.n_qubits:
+        raise ValueError("state size does not match the matrix")
+    if dt != _dtype_code(a.dtype):
+        raise ValueError("state dtype does not match the matrix")
+    return ptr, n_rhs
+
+
+def hs_spmv(a: Dia, x, y, stream=None) -> None:
+    px, n_rhs = _dia_state(a, x)
+    py, n_rhs_y = _dia_state(a, y)
+    if n_rhs != n_rhs_y:
+        raise ValueError("x and y hold different numbers of states")
+    _check(lib().hs_spmv(a.handle, px, py, n_rhs, _stream(stream)))
+
+
+def hs_dia_evolve(u: Dia, psi, n_steps: int, stream=None) -> None:
+    p, n_rhs = _dia_state(u, psi)
+    _check(lib().hs_dia_evolve(u.handle, p, n_rhs, int(n_steps), _stream(stream)))
+
+
+def hs_dia_convert(a: Dia, dtype, stream=None) -> Dia:
+    return _new_dia(lib().hs_dia_convert, a.handle, _dtype_code(dtype), _stream(stream))

@@ -1,5 +1,5 @@
 """CPU-only checks of the C ABI: the library loads, exports every symbol that
-include/hs.h declares, and its host-side planner (the structural dry run)
+include/*.h declares, and its host-side planner (the structural dry run)
 groups terms and orders offsets bit-exactly like the oracle."""
 import os
 import re
@@ -12,9 +12,15 @@ from paper_2606_16959_gb300 import hs, workloads as W
 
 
 def declared_symbols():
-    src = open(os.path.join(ROOT, "include", "hs.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"^\s*(?:int|void|const char\*)\s+(hs_\w+)\s*\(", src, flags=re.M)))
+    """Every entry point declared in include/*.h."""
+    names = set()
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not h.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", h)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names |= set(re.findall(r"^\s*(?:int|void|const char\*)\s+(hs_\w+)\s*\(", src, flags=re.M))
+    return sorted(names)
 
 
 @pytest.fixture(scope="module")
