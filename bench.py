@@ -41,7 +41,8 @@ def parse_args():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default="heis16", choices=["heis16", "maxcut24", "tfim10", "batch256", "serve"])
+    ap.add_argument("--workload", default="heis16",
+                    choices=["heis16", "maxcut24", "tfim10", "batch256", "serve", "taylor16"])
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--serve-rate", type=float, default=500.0)
     ap.add_argument("--autotune", type=int, default=1)
@@ -584,6 +585,8 @@ def run_ours(args):
         return run_batch(args, rank, world)
     if args.workload == "serve":
         return run_serve(args, rank, world)
+    if args.workload == "taylor16":
+        return run_taylor(args, rank, world)
     job, desc = make_job(args.workload, qubits=args.qubits)
     dtype = job.dtype
     res = time_ours(job, args, world, dtype, rank)
@@ -655,6 +658,131 @@ def run_batch(args, rank, world):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = oracle_batch_sample(jobs)
         line["cpu_baseline"] = {"value": cb["value"], "unit": METRIC, "cores": 1, "kind": "oracle", "sample": cb["sample"]}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+TAYLOR_DESC = ("single-factor Taylor mode (Alg. 3): TFIM open chain n={n}, J=1, h=0.1, Gaussian state, t=1, "
+               "diagonal budget {b}; H to the compact layout, budgeted step search, SpME (FP64), complex64 SpMV "
+               "evolution, FP64 norm")
+
+
+def taylor_job(args):
+    from paper_2606_16959_gb300 import workloads as W
+    n = args.qubits or 16
+    job = W.taylor_tfim(n=n)
+    return job, TAYLOR_DESC.format(n=n, b=job.budget)
+
+
+def time_taylor(job, args, world, rank):
+    """Device-timed Alg. 3 steps: every step rebuilds H, searches r, builds U and
+    evolves r SpMVs; the SpMV evolution is also timed on its own."""
+    import torch
+    from paper_2606_16959_gb300 import hs
+    dev = torch.device("cuda", torch.cuda.current_device())
+    psi0 = torch.from_numpy(np.ascontiguousarray(job.psi0)).to(dev, torch.complex64)
+    work = torch.empty_like(psi0)
+    out4 = torch.zeros(4, dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    E = torch.cuda.Event
+    info = {}
+
+    def step():
+        work.copy_(psi0)
+        H = hs.hs_dia_from_terms(job.ham.labels, job.ham.coeffs)
+        r = hs.hs_estimate_timesteps(H, job.t, job.budget)
+        U, K, ok = hs.hs_spme(H, job.t / r)
+        Uc = hs.hs_dia_convert(U, "c64")
+        e0, e1 = E(enable_timing=True), E(enable_timing=True)
+        e0.record()
+        hs.hs_dia_evolve(Uc, work, r)
+        e1.record()
+        hs.hs_inner_device(work, work, out4)
+        info.update(r=r, K=K, converged=ok, D=U.n_diags, H_diags=H.n_diags,
+                    S=int(sum(Uc.N - abs(int(d)) for d in Uc.offsets())))
+        return (H, U, Uc), e0, e1
+
+    for _ in range(args.warmup):
+        keep, _, _ = step()
+        torch.cuda.synchronize()
+    step_ms, evolve_ms = [], []
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    barrier(world)
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+    for _ in range(args.steps):
+        flush.zero_()
+        s0, s1 = E(enable_timing=True), E(enable_timing=True)
+        s0.record()
+        keep, e0, e1 = step()
+        s1.record()
+        torch.cuda.synchronize()
+        step_ms.append(s0.elapsed_time(s1))
+        evolve_ms.append(e0.elapsed_time(e1))
+    clocks = sampler.stop() if sampler else None
+    barrier(world)
+    N = 1 << job.ham.n_qubits
+    return dict(units=info["r"] * N, step_ms=step_ms, evolve_ms=evolve_ms,
+                total_ms=max_over_ranks(sum(step_ms), world), clocks=clocks, info=info,
+                norm2=float(out4[2].item()), N=N)
+
+
+def oracle_taylor_sample(budget_s=15.0):
+    """The oracle's whole Alg. 3 pipeline (H in the compact layout, step search,
+    Taylor exponential, r SpMVs) on the 10-qubit instance of the same family at
+    the same diagonal-budget fraction of 2N-1, repeated for ~budget_s seconds."""
+    import oracle as _o
+    from oracle import taylor as OT
+    from paper_2606_16959_gb300 import workloads as W
+    n = 10
+    job = W.taylor_tfim(n=n, budget=256)
+    x, z, _ = _o.parse_terms(job.ham.labels)
+    units, t_total, reps = 0, 0.0, 0
+    while t_total < budget_s or reps == 0:
+        t0 = time.perf_counter()
+        A = OT.ham_dia(x, z, job.ham.coeffs, n)
+        r = OT.estimate_timesteps(A, job.t, job.budget)
+        U, _, _ = OT.expm_taylor(A, job.t / r)
+        OT.evolve(U, job.psi0, r)
+        t_total += time.perf_counter() - t0
+        units += r * (1 << n)
+        reps += 1
+    return dict(value=units / t_total, seconds=t_total,
+                sample=f"{reps} run(s) of the oracle's whole Alg. 3 pipeline on the {n}-qubit TFIM chain "
+                       f"(h=0.1, budget {job.budget} of 2N-1={2 * (1 << n) - 1}, r={r}), FP64 numpy, "
+                       "single thread; units r x N")
+
+
+def run_taylor(args, rank, world):
+    import torch
+    job, desc = taylor_job(args)
+    res = time_taylor(job, args, world, rank)
+    K = args.steps
+    info = res["info"]
+    value = res["units"] * K * world / (res["total_ms"] / 1000.0)
+    hbm, peak_kind = peaks()
+    launch_s = statistics.mean(res["evolve_ms"]) / 1000.0 / max(1, info["r"])
+    per_launch = 8 * info["S"] + 2 * 8 * res["N"]
+    achieved = per_launch / launch_s / 1e9
+    cfg = {"workload": "taylor16", "description": desc, "n_qubits": job.ham.n_qubits, "n_terms": len(job.ham.labels),
+           "diag_budget": job.budget, "t": job.t, "n_rhs": 1, "H_diags": info["H_diags"], "n_steps": info["r"],
+           "U_diags": info["D"], "taylor_terms": info["K"], "l2": "flushed (512 MiB write) before every timed step"}
+    line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": K, "warmup": args.warmup,
+            "ms_per_step": res["total_ms"] / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "c64", "data": "synthetic", "config": cfg,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                         "traffic": None, "peak_source": peak_kind, "kernel": "spmv_kernel",
+                         "algorithmic_bytes_per_launch": per_launch, "avg_launch_us": launch_s * 1e6},
+            "e2e": None, "gpu_launches": None, "clocks": res["clocks"],
+            "evolve_ms_per_step": statistics.mean(res["evolve_ms"]), "final_norm2": res["norm2"]}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = oracle_taylor_sample()
+        line["cpu_baseline"] = {"value": cb["value"], "unit": METRIC, "cores": 1, "kind": "oracle",
+                                "sample": cb["sample"]}
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

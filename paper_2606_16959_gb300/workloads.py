@@ -234,6 +234,15 @@ def heis16(dtype: str = "c128", n: int = 16, seed: int = 1002, n_steps: int = 10
     return Job(heisenberg_chain(n, J, periodic=True), 1.0, n_steps, 8, psi, dtype)
 
 
+def taylor_tfim(n: int = 16, h: float = 0.1, budget: int = 1024, seed: int = 1006, dtype: str = "c64") -> Job:
+    """Single-factor Taylor-mode workload shaped like the largest TFIM row of
+    the benchmark table (open chain, n=16, small transverse field h=0.1): J=1,
+    Gaussian state, t=1, diagonal budget `budget` for the propagator; the step
+    count is chosen by the budget search, so n_steps is 0 here."""
+    rng = np.random.default_rng(seed)
+    return Job(tfim_chain(n, 1.0, h, periodic=False), 1.0, 0, budget, gaussian_state(n, rng), dtype)
+
+
 def maxcut24(n: int = 24, n_rhs: int = 16, seed: int = 1003, n_steps: int = 50) -> Job:
     """Weighted MaxCut on a random 3-regular graph plus 0.5 sum X_i; RHS 0 = |+>^n,
     RHS 1.. = Gaussian states; t=2, 50 steps, budget 4, complex64 bulk."""
