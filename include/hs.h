@@ -164,10 +164,12 @@ typedef struct {
 } hs_batch_job;
 
 typedef struct {
-  int tile_bits; /* log2 amplitudes per tile, 8..11 (0 = 10); jobs with fewer qubits, or whose
+  int tile_bits; /* log2 amplitudes per tile, 8..11 (0 = 9); jobs with fewer qubits, or whose
                     factors do not fit a tile, are evolved with their own launches */
   int low_bits;  /* contiguous low bits of a tile (0 = library choice) */
   int use_graph; /* 1 (default): capture the launch sequence once and replay it as a CUDA graph */
+  int smem_kb;   /* shared memory per CTA for the state tile and factor staging, in KiB (0 = 40);
+                    a smaller budget stages fewer factors ahead but fits more CTAs on an SM */
 } hs_batch_opts;
 
 /* Plan a batch (host only; device tables are uploaded on the first launch's
