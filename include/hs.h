@@ -128,6 +128,9 @@ typedef struct {
                      amplitudes); 0 = library choice (32-byte runs) */
   int max_fuse;   /* FUSED: most factor applications one sweep launch applies (step-fusion
                      depth, 1..64); 0 = 64 */
+  int smem_kb;    /* FUSED: shared memory per CTA for the tile and factor staging, in KiB
+                     (0 = 112); a smaller budget stages fewer factors ahead but fits more CTAs
+                     on an SM.  A tile that needs more for one stage gets what it needs. */
 } hs_evolve_opts;
 
 /* hs_evolve with an explicit method and tiling (opts may be NULL = AUTO). */

@@ -54,7 +54,7 @@ void release(hs_factors* f, cudaStream_t s) {
 
 // Enqueue the launches of one evolution on stream s.
 int enqueue_evolve(const hs_factors* f, const std::vector<hs::Sweep>& sw, void* psi, int n_rhs, int tile_bits,
-                   int rhs_block, void* scratch, cudaStream_t s) {
+                   int rhs_block, size_t smem_budget, void* scratch, cudaStream_t s) {
   const hs::Plan& p = f->plan;
   void* cur = psi;
   void* other = scratch;
@@ -72,7 +72,7 @@ int enqueue_evolve(const hs_factors* f, const std::vector<hs::Sweep>& sw, void* 
       L.rest = hs::runs_of(~uint64_t(w.local_mask) & all, p.n_qubits);
       L.n_factors = int(w.factors.size());
       for (int i = 0; i < L.n_factors; ++i) L.factors[i] = w.factors[i];
-      L.smem_budget = hs::kSweepSmemDefault;
+      L.smem_budget = smem_budget;
       L.pdl = true;
       e = hs::launch_sweep(f, L, s);
     } else {
@@ -414,9 +414,10 @@ int hs_plan_factors(const uint64_t* x, const uint64_t* z, size_t n_terms, int n_
 
 // Resolve evolve options: method, tile bits, rhs block, low bits.
 int resolve_opts(const hs_factors* f, int n_rhs, const hs_evolve_opts* opts, hs_evolve_opts& o, int& tb, int& rb) {
-  o = hs_evolve_opts{HS_METHOD_AUTO, 0, 0, 0, 0, 0};
+  o = hs_evolve_opts{HS_METHOD_AUTO, 0, 0, 0, 0, 0, 0};
   if (opts) o = *opts;
-  if (o.method == HS_METHOD_AUTO && o.tile_bits == 0 && o.rhs_block == 0 && o.low_bits == 0 && o.max_fuse == 0) {
+  if (o.method == HS_METHOD_AUTO && o.tile_bits == 0 && o.rhs_block == 0 && o.low_bits == 0 && o.max_fuse == 0 &&
+      o.smem_kb == 0) {
     hs_evolve_opts t;
     if (hs::tuned_opts(f, n_rhs, &t)) {
       t.use_graph = o.use_graph;
@@ -425,6 +426,7 @@ int resolve_opts(const hs_factors* f, int n_rhs, const hs_evolve_opts* opts, hs_
   }
   if (o.low_bits <= 0) o.low_bits = min_low_bits(f->dtype);
   if (o.max_fuse <= 0 || o.max_fuse > hs::kMaxSweepFactors) o.max_fuse = hs::kMaxSweepFactors;
+  if (o.smem_kb < 0 || size_t(o.smem_kb) * 1024 > hs::kSweepSmemMax) return fail(HS_EINVAL, "smem_kb must be 0..227");
   if (o.low_bits < (f->dtype == HS_C64 ? 1 : 0) || o.low_bits > 12) return fail(HS_EINVAL, "low_bits out of range");
   if (o.method != HS_METHOD_AUTO && o.method != HS_METHOD_PLAIN && o.method != HS_METHOD_FUSED)
     return fail(HS_EINVAL, "unknown method");
@@ -479,9 +481,11 @@ int hs_evolve_ex(const hs_factors* f, void* psi, int n_rhs, int n_steps, const h
   const std::vector<hs::Sweep> sw = hs::plan_sweeps(f->plan, n_steps, tb, o.low_bits, o.method != HS_METHOD_PLAIN,
                                                     hs::kMaxFusedDiags, o.max_fuse);
   const bool scratch_needed = has_plain(sw);
+  const size_t smem_budget = o.smem_kb > 0 ? size_t(o.smem_kb) * 1024 : hs::kSweepSmemDefault;
 
   if (o.use_graph) {
-    hs_factors::GraphKey key{psi, n_rhs, n_steps, int(o.method) * 128 + o.max_fuse, tb, rb * 64 + o.low_bits, nullptr};
+    hs_factors::GraphKey key{psi, n_rhs, n_steps, int(o.method) * 128 + o.max_fuse, tb + 64 * o.smem_kb,
+                             rb * 64 + o.low_bits, nullptr};
     cudaGraphExec_t exec = nullptr;
     {
       std::lock_guard<std::mutex> lk(f->graph_mu);
@@ -495,7 +499,7 @@ int hs_evolve_ex(const hs_factors* f, void* psi, int n_rhs, int n_steps, const h
       if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
       e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
       if (e != cudaSuccess) { cudaStreamDestroy(cs); return cuda_fail(e, "cudaStreamBeginCapture"); }
-      int rc = enqueue_evolve(f, sw, psi, n_rhs, tb, rb, nullptr, cs);
+      int rc = enqueue_evolve(f, sw, psi, n_rhs, tb, rb, smem_budget, nullptr, cs);
       cudaGraph_t graph = nullptr;
       e = cudaStreamEndCapture(cs, &graph);
       cudaStreamDestroy(cs);
@@ -517,7 +521,7 @@ int hs_evolve_ex(const hs_factors* f, void* psi, int n_rhs, int n_steps, const h
     cudaError_t e = hs::pool_malloc(&scratch, state_bytes, s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(scratch state)");
   }
-  int rc = enqueue_evolve(f, sw, psi, n_rhs, tb, rb, scratch, s);
+  int rc = enqueue_evolve(f, sw, psi, n_rhs, tb, rb, smem_budget, scratch, s);
   if (scratch) cudaFreeAsync(scratch, s);
   return rc;
 }

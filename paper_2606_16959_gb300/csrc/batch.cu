@@ -204,7 +204,7 @@ int upload_tables(hs_batch* b, cudaStream_t s) {
 
 int enqueue_batch(hs_batch* b, cudaStream_t s) {
   for (const hs_batch::Sep& j : b->separate) {
-    hs_evolve_opts o{HS_METHOD_AUTO, 0, 0, 0, 0, 0};
+    hs_evolve_opts o{HS_METHOD_AUTO, 0, 0, 0, 0, 0, 0};
     int rc = hs_evolve_ex(j.f, j.psi, j.n_rhs, j.n_steps, &o, s);
     if (rc != HS_OK) return rc;
   }

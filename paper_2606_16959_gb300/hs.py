@@ -50,7 +50,8 @@ class BatchOpts(ctypes.Structure):
 
 class EvolveOpts(ctypes.Structure):
     _fields_ = [("method", ctypes.c_int), ("tile_bits", ctypes.c_int), ("rhs_block", ctypes.c_int),
-                ("use_graph", ctypes.c_int), ("low_bits", ctypes.c_int), ("max_fuse", ctypes.c_int)]
+                ("use_graph", ctypes.c_int), ("low_bits", ctypes.c_int), ("max_fuse", ctypes.c_int),
+                ("smem_kb", ctypes.c_int)]
 
 
 _lib = None
@@ -246,17 +247,20 @@ def hs_evolve(f: Factors, psi, n_steps: int, stream=None) -> None:
 
 
 def hs_evolve_ex(f: Factors, psi, n_steps: int, method: int = HS_METHOD_AUTO, tile_bits: int = 0,
-                 rhs_block: int = 0, use_graph: bool = False, low_bits: int = 0, max_fuse: int = 0,
+                 rhs_block: int = 0, use_graph: bool = False, low_bits: int = 0, max_fuse: int = 0, smem_kb: int = 0,
                  stream=None) -> None:
     ptr, n_rhs = _check_state(f, psi)
-    o = EvolveOpts(int(method), int(tile_bits), int(rhs_block), int(bool(use_graph)), int(low_bits), int(max_fuse))
+    o = EvolveOpts(int(method), int(tile_bits), int(rhs_block), int(bool(use_graph)), int(low_bits), int(max_fuse),
+                   int(smem_kb))
     _check(lib().hs_evolve_ex(f.handle, ptr, n_rhs, int(n_steps), ctypes.byref(o), _stream(stream)))
 
 
 def hs_evolve_plan(f: Factors, n_rhs: int, n_steps: int, method: int = HS_METHOD_AUTO, tile_bits: int = 0,
-                   rhs_block: int = 0, use_graph: bool = False, low_bits: int = 0, max_fuse: int = 0):
+                   rhs_block: int = 0, use_graph: bool = False, low_bits: int = 0, max_fuse: int = 0,
+                   smem_kb: int = 0):
     """(n_sweep_launches, n_plain_launches, tile_bits, rhs_block) hs_evolve_ex would use."""
-    o = EvolveOpts(int(method), int(tile_bits), int(rhs_block), int(bool(use_graph)), int(low_bits), int(max_fuse))
+    o = EvolveOpts(int(method), int(tile_bits), int(rhs_block), int(bool(use_graph)), int(low_bits), int(max_fuse),
+                   int(smem_kb))
     a, b, c, d = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     _check(lib().hs_evolve_plan(f.handle, int(n_rhs), int(n_steps), ctypes.byref(o), ctypes.byref(a), ctypes.byref(b),
                                 ctypes.byref(c), ctypes.byref(d)))
@@ -270,7 +274,7 @@ def hs_autotune(f: Factors, psi, n_steps: int, stream=None) -> dict:
     o = EvolveOpts()
     _check(lib().hs_autotune(f.handle, ptr, n_rhs, int(n_steps), _stream(stream), ctypes.byref(o)))
     return dict(method=o.method, tile_bits=o.tile_bits, rhs_block=o.rhs_block, low_bits=o.low_bits,
-                max_fuse=o.max_fuse)
+                max_fuse=o.max_fuse, smem_kb=o.smem_kb)
 
 
 def hs_apply_factor(f: Factors, g: int, x, y, stream=None) -> None:
