@@ -172,15 +172,22 @@ def max_over_ranks(v, world):
 
 
 TUNE_CACHE = os.path.join(ROOT, "paper_2606_16959_gb300", "_build", "autotune_bench.json")
-PROFILE_SUMMARY = {"heis16": "sweep_kernel_heis16.md", "maxcut24": "sweep_kernel_maxcut24.md",
-                   "batch256": "batch_level_kernel_batch256.md"}
-KERNEL_SOURCES = ("apply.cu", "sweep_core.cuh", "batch.cu", "hs_internal.h", "plan.cpp", "api.cpp")
+# Committed ncu summary per workload, and the kernel it covers.
+PROFILE_SUMMARY = {"heis16": ("sweep_kernel_heis16.md", "sweep_kernel"),
+                   "maxcut24": ("sweep_kernel_maxcut24.md", "sweep_kernel"),
+                   "batch256": ("batch_level_kernel_batch256.md", "batch_level_kernel"),
+                   "taylor16": ("spmv_kernel_taylor16.md", "spmv_kernel")}
+# Device-code sources of each kernel: a summary's DRAM figures count only while
+# these are unchanged since the capture.
+KERNEL_SOURCES = {"sweep_kernel": ("apply.cu", "sweep_core.cuh", "hs_internal.h"),
+                  "batch_level_kernel": ("batch.cu", "sweep_core.cuh", "hs_internal.h"),
+                  "spmv_kernel": ("dia.cu",)}
 
 
-def kernel_source_hash():
+def kernel_source_hash(kernel):
     import hashlib
     h = hashlib.sha256()
-    for name in KERNEL_SOURCES:
+    for name in KERNEL_SOURCES[kernel]:
         with open(os.path.join(ROOT, "paper_2606_16959_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -188,8 +195,11 @@ def kernel_source_hash():
 
 def profiled_traffic(workload):
     """DRAM bytes per launch of the dominant kernel from the committed ncu
-    summary, or None if there is none or the kernel sources changed since."""
-    path = os.path.join(ROOT, "profiles", PROFILE_SUMMARY.get(workload, "-"))
+    summary, or None if there is none or the kernel's sources changed since."""
+    if workload not in PROFILE_SUMMARY:
+        return None
+    fname, kernel = PROFILE_SUMMARY[workload]
+    path = os.path.join(ROOT, "profiles", fname)
     if not os.path.exists(path):
         return None
     vals = {}
@@ -198,7 +208,7 @@ def profiled_traffic(workload):
             if ":" in line and line.strip().startswith(("kernel_source_sha256", "dram_bytes_per_launch")):
                 k, v = line.strip().strip("`").split(":", 1)
                 vals[k.strip()] = v.strip().strip("`")
-    if vals.get("kernel_source_sha256") != kernel_source_hash():
+    if vals.get("kernel_source_sha256") != kernel_source_hash(kernel):
         return None
     try:
         return float(vals["dram_bytes_per_launch"])
@@ -304,6 +314,7 @@ def time_ours(job, args, world, dtype, rank):
     torch.cuda.synchronize()
     if sampler:
         sampler.start()
+    l0 = hs.hs_kernel_launches()
     for _ in range(args.steps):
         flush.zero_()
         s0, s1 = E(enable_timing=True), E(enable_timing=True)
@@ -314,16 +325,16 @@ def time_ours(job, args, world, dtype, rank):
         step_ms.append(s0.elapsed_time(s1))
         evolve_ms.append(e0.elapsed_time(e1))
         keep[-1].close()
+    launches = hs.hs_kernel_launches() - l0
     clocks = sampler.stop() if sampler else None
     barrier(world)
     fid = out4.cpu().numpy()
     G = f0.n_factors
     units = job.n_steps * G * N * R
     total_ms = max_over_ranks(sum(step_ms), world)
-    launches_per_step = 2 + n_sweeps + n_plain + 2
     return dict(units=units, G=G, R=R, N=N, step_ms=step_ms, evolve_ms=evolve_ms, total_ms=total_ms,
                 n_sweeps=n_sweeps, n_plain=n_plain, tile_bits=tb, rhs_block=rb, alg_bytes=alg,
-                launches=launches_per_step * args.steps, clocks=clocks, overlap=fid, tuned=tuned)
+                launches=launches, clocks=clocks, overlap=fid, tuned=tuned)
 
 
 def time_e2e(job, args, dtype):
@@ -426,6 +437,7 @@ def time_batch(jobs, args, world, rank, dtype):
     torch.cuda.synchronize()
     if sampler:
         sampler.start()
+    l0 = hs.hs_kernel_launches()
     for _ in range(args.steps):
         flush.zero_()
         s0, s1 = E(enable_timing=True), E(enable_timing=True)
@@ -444,7 +456,7 @@ def time_batch(jobs, args, world, rank, dtype):
     total_ms = max_over_ranks(sum(step_ms), world)
     return dict(units=info[2], levels=info[0], ctas=info[1], separate=info[3], step_ms=step_ms, launch_ms=launch_ms,
                 total_ms=total_ms, alg_bytes=alg, clocks=clocks, max_norm_drift=float(np.max(np.abs(norms - 1.0))),
-                launches=(2 * len(jobs) + info[0] + 2 * len(jobs)) * args.steps)
+                launches=hs.hs_kernel_launches() - l0)
 
 
 def time_batch_e2e(jobs, args, dtype):
@@ -715,6 +727,7 @@ def time_taylor(job, args, world, rank):
     torch.cuda.synchronize()
     if sampler:
         sampler.start()
+    l0 = hs.hs_kernel_launches()
     for _ in range(args.steps):
         flush.zero_()
         s0, s1 = E(enable_timing=True), E(enable_timing=True)
@@ -729,7 +742,7 @@ def time_taylor(job, args, world, rank):
     N = 1 << job.ham.n_qubits
     return dict(units=info["r"] * N, step_ms=step_ms, evolve_ms=evolve_ms,
                 total_ms=max_over_ranks(sum(step_ms), world), clocks=clocks, info=info,
-                norm2=float(out4[2].item()), N=N)
+                norm2=float(out4[2].item()), N=N, launches=hs.hs_kernel_launches() - l0)
 
 
 def oracle_taylor_sample(budget_s=15.0):
@@ -769,6 +782,7 @@ def run_taylor(args, rank, world):
     launch_s = statistics.mean(res["evolve_ms"]) / 1000.0 / max(1, info["r"])
     per_launch = 8 * info["S"] + 2 * 8 * res["N"]
     achieved = per_launch / launch_s / 1e9
+    traffic = profiled_traffic("taylor16") if not args.qubits else None
     cfg = {"workload": "taylor16", "description": desc, "n_qubits": job.ham.n_qubits, "n_terms": len(job.ham.labels),
            "diag_budget": job.budget, "t": job.t, "n_rhs": 1, "H_diags": info["H_diags"], "n_steps": info["r"],
            "U_diags": info["D"], "taylor_terms": info["K"], "l2": "flushed (512 MiB write) before every timed step"}
@@ -776,9 +790,10 @@ def run_taylor(args, rank, world):
             "ms_per_step": res["total_ms"] / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "c64", "data": "synthetic", "config": cfg,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                         "traffic": None, "peak_source": peak_kind, "kernel": "spmv_kernel",
-                         "algorithmic_bytes_per_launch": per_launch, "avg_launch_us": launch_s * 1e6},
-            "e2e": None, "gpu_launches": None, "clocks": res["clocks"],
+                         "traffic": traffic, "peak_source": peak_kind, "kernel": "spmv_kernel",
+                         "algorithmic_bytes_per_launch": per_launch, "avg_launch_us": launch_s * 1e6,
+                         **dram_fields(traffic, launch_s, hbm)},
+            "e2e": None, "gpu_launches": res["launches"], "clocks": res["clocks"],
             "evolve_ms_per_step": statistics.mean(res["evolve_ms"]), "final_norm2": res["norm2"]}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = oracle_taylor_sample()
@@ -812,9 +827,12 @@ def run_serve(args, rank, world):
     sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
     if sampler:
         sampler.start()
+    from paper_2606_16959_gb300 import hs
+    l0 = hs.hs_kernel_launches()
     for _ in range(args.steps):
         reqs = serve.requests_from_jobs(jobs)
         runs.append(serve.Server().run(reqs, realtime=True))
+    served_launches = hs.hs_kernel_launches() - l0
     clocks = sampler.stop() if sampler else None
     barrier(world)
     updates = sum(r["updates"] for r in runs)
@@ -829,7 +847,7 @@ def run_serve(args, rank, world):
                        "l2": "inputs larger than L2 (factor sets up to 16 GB)"},
             "latency_ms": {"p50": p50, "p99": p99, "mean": statistics.mean([r["mean_ms"] for r in runs])},
             "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 32 * len(jobs)},
-            "gpu_launches": sum(r["launches"] for r in runs), "clocks": clocks, "peak_admitted_bytes": max(r["peak_bytes"] for r in runs)}
+            "gpu_launches": served_launches, "clocks": clocks, "peak_admitted_bytes": max(r["peak_bytes"] for r in runs)}
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

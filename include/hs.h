@@ -264,6 +264,12 @@ int hs_free_factors_async(hs_factors* f, void* cuda_stream);
 /* Message for the last failing call on this thread ("" if none). */
 const char* hs_last_error(void);
 
+/* Number of kernels this process has launched through libhs so far (every
+ * entry point; a replayed CUDA graph adds the kernels it holds).  Telemetry:
+ * the difference across a region counts that region's launches.  Not part of
+ * the paper's method. */
+uint64_t hs_kernel_launches(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <atomic>
 #include <cstring>
 #include <list>
 #include <unordered_map>
@@ -10,6 +11,7 @@
 #include <tuple>
 #include <vector>
 
+#include "counters.h"
 #include "hs_internal.h"
 
 namespace hs {
@@ -21,6 +23,10 @@ cudaError_t launch_inner_scratch(const void* a, const void* b, int64_t N, hs_dty
 namespace {
 
 thread_local std::string g_err;
+
+// Kernels per instantiated evolution graph (added to the launch count on replay).
+std::mutex g_graph_mu;
+std::map<cudaGraphExec_t, uint64_t> g_graph_kernels;
 
 int fail(int code, const std::string& msg) {
   g_err = msg;
@@ -184,6 +190,25 @@ int cached_plan(const uint64_t* x, const uint64_t* z, const double* coeff, size_
 }  // namespace
 
 namespace hs {
+std::atomic<uint64_t> g_launches{0};
+namespace {
+thread_local bool t_capturing = false;
+thread_local uint64_t t_captured = 0;
+}  // namespace
+
+void note_launches(uint64_t n) {
+  if (t_capturing) t_captured += n;
+  else g_launches.fetch_add(n, std::memory_order_relaxed);
+}
+void begin_capture_count() {
+  t_capturing = true;
+  t_captured = 0;
+}
+uint64_t end_capture_count() {
+  t_capturing = false;
+  return t_captured;
+}
+
 // The library's stream-ordered memory pool on the current device: memory freed
 // by hs_free_factors_async / hs_batch_free_async stays in the pool (release
 // threshold unlimited) so that the next factor build reuses it without mapping
@@ -272,6 +297,8 @@ bool hs_factors::GraphKey::operator<(const GraphKey& o) const {
 extern "C" {
 
 const char* hs_last_error(void) { return g_err.c_str(); }
+
+uint64_t hs_kernel_launches(void) { return hs::g_launches.load(std::memory_order_relaxed); }
 
 int hs_build_factors_masks(const uint64_t* x, const uint64_t* z, const double* coeffs, size_t n_terms, int n_qubits,
                            double t, int n_steps, int diag_budget, hs_dtype dtype, void* cuda_stream,
@@ -499,7 +526,9 @@ int hs_evolve_ex(const hs_factors* f, void* psi, int n_rhs, int n_steps, const h
       if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
       e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
       if (e != cudaSuccess) { cudaStreamDestroy(cs); return cuda_fail(e, "cudaStreamBeginCapture"); }
+      hs::begin_capture_count();
       int rc = enqueue_evolve(f, sw, psi, n_rhs, tb, rb, smem_budget, nullptr, cs);
+      const uint64_t n_kernels = hs::end_capture_count();
       cudaGraph_t graph = nullptr;
       e = cudaStreamEndCapture(cs, &graph);
       cudaStreamDestroy(cs);
@@ -510,9 +539,15 @@ int hs_evolve_ex(const hs_factors* f, void* psi, int n_rhs, int n_steps, const h
       if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
       std::lock_guard<std::mutex> lk(f->graph_mu);
       f->graphs[key] = exec;
+      std::lock_guard<std::mutex> lk2(g_graph_mu);
+      g_graph_kernels[exec] = n_kernels;
     }
     cudaError_t e = cudaGraphLaunch(exec, s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+    {
+      std::lock_guard<std::mutex> lk2(g_graph_mu);
+      hs::note_launches(g_graph_kernels[exec]);
+    }
     return HS_OK;
   }
 

@@ -32,6 +32,7 @@
 #include <cstdint>
 #include <mutex>
 
+#include "counters.h"
 #include "hs_internal.h"
 #include "sweep_core.cuh"
 
@@ -172,6 +173,7 @@ cudaError_t launch_apply_plain(const hs_factors* f, int g, const void* x, void* 
     else
       apply_plain_kernel<double, 1><<<blocks, threads, 0, s>>>(v, offs, rb, G.D, (const double2*)x, (double2*)y, p.N, n_rhs);
   }
+  note_launches();
   return cudaGetLastError();
 }
 
@@ -248,7 +250,9 @@ cudaError_t launch_sweep(const hs_factors* f, const SweepLaunch& L, cudaStream_t
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = L.pdl ? 1 : 0;
-  return cudaLaunchKernelEx(&cfg, fn, a);
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, fn, a);
+  if (e == cudaSuccess) note_launches();
+  return e;
 }
 
 }  // namespace hs

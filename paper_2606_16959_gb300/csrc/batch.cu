@@ -20,6 +20,7 @@
 #include <tuple>
 #include <vector>
 
+#include "counters.h"
 #include "hs_internal.h"
 #include "sweep_core.cuh"
 
@@ -138,6 +139,7 @@ LevelFn level_fn(int rows) {
 }  // namespace
 
 struct hs_batch {
+  uint64_t graph_kernels = 0;  // kernels one replay of the captured graph launches
   hs_dtype dtype = HS_C64;
   int tile_bits = 0, low_bits = 0, rows = 1;
   bool use_graph = true;
@@ -224,6 +226,7 @@ int enqueue_batch(hs_batch* b, cudaStream_t s) {
     cfg.numAttrs = 1;
     cudaError_t e = cudaLaunchKernelEx(&cfg, fn, a);
     if (e != cudaSuccess) return hs::report_error(HS_ECUDA, std::string("batch level launch: ") + cudaGetErrorString(e));
+    hs::note_launches();
   }
   return HS_OK;
 }
@@ -391,7 +394,9 @@ extern "C" int hs_batch_launch(hs_batch* b, void* cuda_stream) {
     if (e != cudaSuccess) return hs::report_error(HS_ECUDA, "cudaStreamCreate");
     e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) { cudaStreamDestroy(cs); return hs::report_error(HS_ECUDA, "cudaStreamBeginCapture"); }
+    hs::begin_capture_count();
     int rc = enqueue_batch(b, cs);
+    b->graph_kernels = hs::end_capture_count();
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(cs, &g);
     cudaStreamDestroy(cs);
@@ -402,6 +407,7 @@ extern "C" int hs_batch_launch(hs_batch* b, void* cuda_stream) {
     if (e != cudaSuccess) return hs::report_error(HS_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
   }
   e = cudaGraphLaunch(b->graph, s);
+  if (e == cudaSuccess) hs::note_launches(b->graph_kernels);
   return e == cudaSuccess ? HS_OK : hs::report_error(HS_ECUDA, std::string("cudaGraphLaunch: ") + cudaGetErrorString(e));
 }
 

@@ -14,6 +14,7 @@
 
 #include <cstdint>
 
+#include "counters.h"
 #include "hs_internal.h"
 
 namespace hs {
@@ -141,6 +142,7 @@ __global__ void sincos_kernel(const double* coeff, double dt, double* cs, int n)
 
 cudaError_t launch_sincos(const double* d_coeff, double dt, double* d_cs, int n, cudaStream_t s) {
   sincos_kernel<<<(n + 127) / 128, 128, 0, s>>>(d_coeff, dt, d_cs, n);
+  note_launches();
   return cudaGetLastError();
 }
 
@@ -166,6 +168,7 @@ cudaError_t launch_build(const hs_factors* f, const double* d_cs, const uint64_t
     case 5: build_kernel<32><<<grid, threads, 0, s>>>(a, c64); break;
     default: build_kernel<64><<<grid, threads, 0, s>>>(a, c64); break;
   }
+  note_launches();
   return cudaGetLastError();
 }
 

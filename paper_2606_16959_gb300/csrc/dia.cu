@@ -30,6 +30,7 @@
 #include <vector>
 
 #include "../../include/hs_dia.h"
+#include "counters.h"
 #include "hs_internal.h"
 
 struct hs_dia {
@@ -596,6 +597,7 @@ int finish_stats(const std::vector<int>& block0, const DevBuf& partial, size_t D
   if (e == cudaSuccess) e = d_out.alloc(D * sizeof(Stat), s);
   if (e != cudaSuccess) return cuda_err(e, "statistics buffers");
   stat_final<<<unsigned(D), kThreads, 0, s>>>(partial.as<Stat>(), d_b0.as<int>(), d_out.as<Stat>());
+  hs::note_launches();
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaMemcpyAsync(out.data(), d_out.p, D * sizeof(Stat), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -651,6 +653,7 @@ int combine(const hs_dia* a, const hs_dia* b, const std::vector<int64_t>& offs, 
     combine_kernel<float2, float2><<<grid, kThreads, 0, s>>>(
         (const float2*)a->d_vals, (const float2*)pb, (float2*)m->d_vals, tabs.offs.as<int64_t>(),
         tabs.start.as<int64_t>(), d_src.as<CombineSrc>(), d_task.as<int2>(), m->N);
+  hs::note_launches();
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_err(e, "combine launch");
   out = std::move(m);
@@ -709,6 +712,7 @@ int add_dia(const hs_dia* a, const hs_dia* b, cudaStream_t s, DiaPtr& out) {
   combine_kernel<double2, double2><<<unsigned(task.size()), kThreads, 0, s>>>(
       (const double2*)a->d_vals, (const double2*)b->d_vals, (double2*)m->d_vals, tabs.offs.as<int64_t>(),
       tabs.start.as<int64_t>(), d_src.as<CombineSrc>(), d_task.as<int2>(), m->N);
+  hs::note_launches();
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_err(e, "add launch");
   out = std::move(m);
@@ -720,6 +724,7 @@ int identity_dia(int n_qubits, cudaStream_t s, DiaPtr& out) {
   int rc = make_dia(n_qubits, std::vector<int64_t>{0}, HS_C128, s, m);
   if (rc) return rc;
   ones_kernel<<<152 * 4, kThreads, 0, s>>>((double2*)m->d_vals, m->N);
+  hs::note_launches();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_err(e, "identity");
   out = std::move(m);
@@ -778,6 +783,7 @@ int spgemm_impl(const hs_dia* A, const hs_dia* B, double alpha, cudaStream_t s, 
              tabs.start.as<int64_t>(), d_p0.as<int>(), d_pairs.as<Pair>(), d_task.as<int2>(), N, alpha,
              d_part.as<Stat>()};
   gemm_kernel<<<unsigned(task.size()), kThreads, 0, s>>>(g);
+  hs::note_launches();
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_err(e, "spgemm launch");
   std::vector<Stat> st;
@@ -824,6 +830,7 @@ int spme_impl(const hs_dia* A, double t, double tol, int max_iter, int max_diags
     } else {
       expdiag_kernel<<<152 * 8, kThreads, 0, s>>>((const double2*)A->d_vals, (double2*)U->d_vals, U->N, t);
     }
+    hs::note_launches();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_err(e, "exact diagonal exponential");
     *n_terms = 0;
@@ -883,8 +890,11 @@ cudaError_t launch_spmv_k(const hs_dia* a, const void* x, void* y, int n_rhs, cu
   const int64_t per_sm = std::max(1, 64 / W);  // blocks per SM for a full grid
   cfg.gridDim = dim3(unsigned(std::max<int64_t>(1, std::min<int64_t>(tiles, 152 * per_sm))), 1u, 1u);
   cfg.blockDim = dim3(32 * W, 1u, 1u);
-  return cudaLaunchKernelEx(&cfg, spmv_kernel<R, RB, W, kSpmvRPT>, (const T2*)a->d_vals,
-                            (const int64_t*)a->d_meta, int(a->offs.size()), (const T2*)x, (T2*)y, a->N, n_rhs);
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, spmv_kernel<R, RB, W, kSpmvRPT>, (const T2*)a->d_vals,
+                                           (const int64_t*)a->d_meta, int(a->offs.size()), (const T2*)x, (T2*)y,
+                                           a->N, n_rhs);
+  if (e == cudaSuccess) hs::note_launches();
+  return e;
 }
 
 template <typename R, int RB>
@@ -929,9 +939,12 @@ cudaError_t launch_scale_rows(const hs_dia* a, void* psi, int n_rhs, cudaStream_
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = pdl ? 1 : 0;
-  if (a->dtype == HS_C64)
-    return cudaLaunchKernelEx(&cfg, scale_rows_kernel<float>, (const float2*)a->d_vals, (float2*)psi, a->N, n_rhs);
-  return cudaLaunchKernelEx(&cfg, scale_rows_kernel<double>, (const double2*)a->d_vals, (double2*)psi, a->N, n_rhs);
+  const cudaError_t e =
+      a->dtype == HS_C64
+          ? cudaLaunchKernelEx(&cfg, scale_rows_kernel<float>, (const float2*)a->d_vals, (float2*)psi, a->N, n_rhs)
+          : cudaLaunchKernelEx(&cfg, scale_rows_kernel<double>, (const double2*)a->d_vals, (double2*)psi, a->N, n_rhs);
+  if (e == cudaSuccess) hs::note_launches();
+  return e;
 }
 
 }  // namespace
@@ -1018,6 +1031,7 @@ int hs_dia_from_masks(const uint64_t* x, const uint64_t* z, const double* coeffs
               d_masks.as<uint64_t>(), d_mrange.as<int>(), d_tz.as<uint64_t>(), d_tc.as<double>(), d_ty.as<int>(),
               int(masks.size()), N, d_part.as<Stat>()};
   terms_kernel<<<unsigned(task.size()), kThreads, 0, s>>>(a);
+  hs::note_launches();
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_err(e, "H launch");
   std::vector<Stat> st;

@@ -6,6 +6,7 @@
 
 #include <cstdint>
 
+#include "counters.h"
 #include "hs_internal.h"
 
 namespace hs {
@@ -96,6 +97,7 @@ cudaError_t launch_inner_scratch(const void* a, const void* b, int64_t N, hs_dty
   else
     inner_partial<double2><<<blocks, kRedThreads, 0, s>>>((const double2*)a, (const double2*)b, N, part);
   inner_final<<<1, kRedThreads, 0, s>>>(part, blocks, d_out4);
+  note_launches(2);
   return cudaGetLastError();
 }
 

@@ -29,6 +29,7 @@ EXPORTS = (
     "hs_batch_free_async",
     "hs_dia_from_terms", "hs_dia_from_masks", "hs_dia_create", "hs_spgemm", "hs_spme", "hs_estimate_timesteps",
     "hs_spmv", "hs_dia_evolve", "hs_dia_convert", "hs_dia_info", "hs_dia_get", "hs_dia_free",
+    "hs_kernel_launches",
 )
 
 
@@ -110,11 +111,18 @@ def lib() -> ctypes.CDLL:
         L.hs_dia_get.argtypes = [vp, i64p, dp]
         L.hs_dia_free.argtypes = [vp]
         L.hs_dia_free.restype = None
+        L.hs_kernel_launches.argtypes = []
+        L.hs_kernel_launches.restype = ctypes.c_uint64
         for name in EXPORTS:
-            if name not in ("hs_free_factors", "hs_last_error", "hs_batch_free", "hs_dia_free"):
+            if name not in ("hs_free_factors", "hs_last_error", "hs_batch_free", "hs_dia_free", "hs_kernel_launches"):
                 getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
+
+
+def hs_kernel_launches() -> int:
+    """Kernels launched through libhs so far in this process."""
+    return int(lib().hs_kernel_launches())
 
 
 def _check(rc: int):

@@ -91,7 +91,6 @@ class Server:
         self.keep_results = keep_results
         self.used = 0
         self.peak_used = 0
-        self.launches = 0  # libhs kernel launches enqueued (build, batch levels, reductions)
         self._next_stream = 0
 
     def _masks(self, r: Request):
@@ -138,7 +137,6 @@ class Server:
             b = hs.hs_batch_create([(f, st, r.n_steps) for f, st, r in zip(facs, states, group)],
                                    tile_bits=self.tile_bits, use_graph=False)
             hs.hs_batch_launch(b, stream=s)
-            self.launches += 4 * len(group) + b.n_levels
             out = torch.zeros(len(group), 4, dtype=torch.float64, device="cuda")
             for k, st in enumerate(states):
                 hs.hs_inner_device(st, st, out[k], stream=s)
@@ -153,6 +151,7 @@ class Server:
         """Serve the requests (sorted by arrival).  realtime: wait for arrival times;
         otherwise every request is available at once.  Returns a stats dict."""
         torch = self.torch
+        l0 = hs.hs_kernel_launches()
         pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
         waiting: collections.deque = collections.deque()
         inflight: List[_Group] = []
@@ -218,4 +217,4 @@ class Server:
         return dict(n=len(requests), p50_ms=float(np.percentile(lat, 50) * 1e3), p99_ms=float(np.percentile(lat, 99) * 1e3),
                     mean_ms=float(lat.mean() * 1e3), makespan_s=t_last - t_first, updates=updates,
                     throughput=updates / max(t_last - t_first, 1e-9), peak_bytes=self.peak_used,
-                    launches=self.launches)
+                    launches=hs.hs_kernel_launches() - l0)

@@ -19,7 +19,7 @@ def declared_symbols():
             continue
         src = open(os.path.join(ROOT, "include", h)).read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-        names |= set(re.findall(r"^\s*(?:int|void|const char\*)\s+(hs_\w+)\s*\(", src, flags=re.M))
+        names |= set(re.findall(r"^\s*(?:int|void|uint64_t|const char\*)\s+(hs_\w+)\s*\(", src, flags=re.M))
     return sorted(names)
 
 

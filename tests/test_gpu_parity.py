@@ -316,3 +316,28 @@ def test_fidelity_and_norms(dt, n):
     o = out.cpu().numpy()
     assert o[0] == pytest.approx(ip.real, rel=1e-12, abs=1e-14)
     assert o[1] == pytest.approx(ip.imag, rel=1e-10, abs=1e-12)
+
+
+def test_kernel_launch_counter_counts_each_launch():
+    """hs_kernel_launches advances by exactly the kernels an entry point launches:
+    2 for a factor build (angles, factor values), the planned sweeps for an
+    evolution, 2 for a reduction, and a graph's kernels on every replay."""
+    ham = W.heisenberg_chain(12, np.linspace(0.5, 1.5, 12), periodic=True)
+    l0 = hs.hs_kernel_launches()
+    f = hs.hs_build_factors(ham.labels, ham.coeffs, 1.0, 4, 8, "c64")
+    assert hs.hs_kernel_launches() - l0 == 2
+    psi = torch.from_numpy(W.gaussian_state(12, np.random.default_rng(3))).to("cuda", torch.complex64)
+    opts = dict(method=hs.HS_METHOD_FUSED, tile_bits=8, rhs_block=1, low_bits=1)
+    n_sweeps, n_plain, _, _ = hs.hs_evolve_plan(f, 1, 4, **opts)
+    l1 = hs.hs_kernel_launches()
+    hs.hs_evolve_ex(f, psi, 4, **opts)
+    assert hs.hs_kernel_launches() - l1 == n_sweeps + n_plain > 0
+    out = torch.zeros(4, dtype=torch.float64, device="cuda")
+    l2 = hs.hs_kernel_launches()
+    hs.hs_inner_device(psi, psi, out)
+    assert hs.hs_kernel_launches() - l2 == 2
+    l3 = hs.hs_kernel_launches()
+    hs.hs_evolve_ex(f, psi, 4, use_graph=True, **opts)   # capture + first replay
+    hs.hs_evolve_ex(f, psi, 4, use_graph=True, **opts)   # replay
+    torch.cuda.synchronize()
+    assert hs.hs_kernel_launches() - l3 == 2 * (n_sweeps + n_plain)
