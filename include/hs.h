@@ -131,6 +131,9 @@ typedef struct {
   int smem_kb;    /* FUSED: shared memory per CTA for the tile and factor staging, in KiB
                      (0 = 112); a smaller budget stages fewer factors ahead but fits more CTAs
                      on an SM.  A tile that needs more for one stage gets what it needs. */
+  int no_tables;  /* FUSED: 0 (default): factors whose terms touch at most 8 qubits are read from
+                     their value tables (entries indexed by the row's bits on those qubits; same
+                     values as the stored diagonals); 1: every factor is staged from its diagonals */
 } hs_evolve_opts;
 
 /* hs_evolve with an explicit method and tiling (opts may be NULL = AUTO). */
@@ -173,6 +176,7 @@ typedef struct {
   int use_graph; /* 1 (default): capture the launch sequence once and replay it as a CUDA graph */
   int smem_kb;   /* shared memory per CTA for the state tile and factor staging, in KiB (0 = 40);
                     a smaller budget stages fewer factors ahead but fits more CTAs on an SM */
+  int no_tables; /* as in hs_evolve_opts: 1 stages every factor from its diagonals */
 } hs_batch_opts;
 
 /* Plan a batch (host only; device tables are uploaded on the first launch's

@@ -60,7 +60,7 @@ void release(hs_factors* f, cudaStream_t s) {
 
 // Enqueue the launches of one evolution on stream s.
 int enqueue_evolve(const hs_factors* f, const std::vector<hs::Sweep>& sw, void* psi, int n_rhs, int tile_bits,
-                   int rhs_block, size_t smem_budget, void* scratch, cudaStream_t s) {
+                   int rhs_block, size_t smem_budget, bool value_tables, void* scratch, cudaStream_t s) {
   const hs::Plan& p = f->plan;
   void* cur = psi;
   void* other = scratch;
@@ -80,6 +80,7 @@ int enqueue_evolve(const hs_factors* f, const std::vector<hs::Sweep>& sw, void* 
       for (int i = 0; i < L.n_factors; ++i) L.factors[i] = w.factors[i];
       L.smem_budget = smem_budget;
       L.pdl = true;
+      L.value_tables = value_tables;
       e = hs::launch_sweep(f, L, s);
     } else {
       if (!other) return fail(HS_EINVAL, "internal: plain application without scratch");
@@ -324,7 +325,7 @@ int hs_build_factors_masks(const uint64_t* x, const uint64_t* z, const double* c
   const hs::Plan& p = f->plan;
   const int G = int(p.groups.size());
   const int nd = int(p.offs.size());
-  const size_t vbytes = size_t(p.total_elems) * hs::elem_bytes(dtype);
+  const size_t vbytes = size_t(p.total_elems + p.total_vt) * hs::elem_bytes(dtype);
   hs_factors* fp = f.get();
   auto guard = [&](cudaError_t e2, const char* what) -> int { return e2 == cudaSuccess ? HS_OK : cuda_fail(e2, what); };
   // Stream-ordered allocations (building, using and freeing a factor set never
@@ -335,8 +336,10 @@ int hs_build_factors_masks(const uint64_t* x, const uint64_t* z, const double* c
     release(f.release(), s);
     return rc;
   }
+  fp->d_vt = static_cast<unsigned char*>(fp->d_vals) + size_t(p.total_elems) * hs::elem_bytes(dtype);
   const size_t m = n_terms;
-  std::vector<int> fD(G), fd0(G), gfirst(G), glast(G), xdim(G), pivot(G * hs::kMaxXDim, 0);
+  std::vector<int> fD(G), fd0(G), gfirst(G), glast(G), xdim(G), pivot(G * hs::kMaxXDim, 0), vt0(G);
+  std::vector<uint32_t> smask(G);
   std::vector<uint64_t> basis(G * hs::kMaxXDim, 0);
   for (int g = 0; g < G; ++g) {
     const hs::Group& gr = p.groups[g];
@@ -345,6 +348,8 @@ int hs_build_factors_masks(const uint64_t* x, const uint64_t* z, const double* c
     gfirst[g] = gr.first;
     glast[g] = gr.last;
     xdim[g] = gr.xdim;
+    smask[g] = gr.smask;
+    vt0[g] = gr.vt0;
     for (int i = 0; i < gr.xdim; ++i) {
       basis[g * hs::kMaxXDim + i] = gr.basis[i];
       pivot[g * hs::kMaxXDim + i] = gr.pivot[i];
@@ -365,6 +370,7 @@ int hs_build_factors_masks(const uint64_t* x, const uint64_t* z, const double* c
   const size_t o_cx = put(p.term_cx.data(), m * 4), o_gf = put(gfirst.data(), G * 4), o_gl = put(glast.data(), G * 4);
   const size_t o_b = put(basis.data(), basis.size() * 8), o_xd = put(xdim.data(), G * 4);
   const size_t o_pv = put(pivot.data(), pivot.size() * 4);
+  const size_t o_sm = put(smask.data(), G * 4), o_vt0 = put(vt0.data(), G * 4);
   const size_t o_cs = put(nullptr, m * 16);  // (cos, sin) per term, written on the device
   unsigned char* d_blob = nullptr;
   if ((rc = guard(hs::pool_malloc((void**)&d_blob, blob.size(), s), "cudaMallocAsync(tables)"))) {
@@ -393,6 +399,15 @@ int hs_build_factors_masks(const uint64_t* x, const uint64_t* z, const double* c
                          reinterpret_cast<const int*>(d_blob + o_gf), reinterpret_cast<const int*>(d_blob + o_gl),
                          reinterpret_cast<const uint64_t*>(d_blob + o_b), reinterpret_cast<const int*>(d_blob + o_xd),
                          reinterpret_cast<const int*>(d_blob + o_pv), s);
+  if (e == cudaSuccess)
+    e = hs::launch_value_tables(fp, d_cs, reinterpret_cast<const uint64_t*>(d_blob + o_x),
+                                reinterpret_cast<const uint64_t*>(d_blob + o_z),
+                                reinterpret_cast<const uint32_t*>(d_blob + o_cx),
+                                reinterpret_cast<const int*>(d_blob + o_gf), reinterpret_cast<const int*>(d_blob + o_gl),
+                                reinterpret_cast<const uint64_t*>(d_blob + o_b),
+                                reinterpret_cast<const int*>(d_blob + o_xd), reinterpret_cast<const int*>(d_blob + o_pv),
+                                reinterpret_cast<const uint32_t*>(d_blob + o_sm),
+                                reinterpret_cast<const int*>(d_blob + o_vt0), s);
   if (e != cudaSuccess) {
     cudaStreamSynchronize(s);
     release(f.release(), s);
@@ -427,7 +442,7 @@ int hs_plan_factors(const uint64_t* x, const uint64_t* z, size_t n_terms, int n_
   const int G = int(p.groups.size());
   *n_factors = G;
   *n_offsets = int(p.offs.size());
-  if (value_bytes) *value_bytes = p.total_elems * int64_t(hs::elem_bytes(dtype));
+  if (value_bytes) *value_bytes = (p.total_elems + p.total_vt) * int64_t(hs::elem_bytes(dtype));
   if (group_first && group_last && n_diags && capacity_factors >= G)
     for (int g = 0; g < G; ++g) {
       group_first[g] = p.groups[g].first;
@@ -441,10 +456,10 @@ int hs_plan_factors(const uint64_t* x, const uint64_t* z, size_t n_terms, int n_
 
 // Resolve evolve options: method, tile bits, rhs block, low bits.
 int resolve_opts(const hs_factors* f, int n_rhs, const hs_evolve_opts* opts, hs_evolve_opts& o, int& tb, int& rb) {
-  o = hs_evolve_opts{HS_METHOD_AUTO, 0, 0, 0, 0, 0, 0};
+  o = hs_evolve_opts{HS_METHOD_AUTO, 0, 0, 0, 0, 0, 0, 0};
   if (opts) o = *opts;
   if (o.method == HS_METHOD_AUTO && o.tile_bits == 0 && o.rhs_block == 0 && o.low_bits == 0 && o.max_fuse == 0 &&
-      o.smem_kb == 0) {
+      o.smem_kb == 0 && o.no_tables == 0) {
     hs_evolve_opts t;
     if (hs::tuned_opts(f, n_rhs, &t)) {
       t.use_graph = o.use_graph;
@@ -512,7 +527,7 @@ int hs_evolve_ex(const hs_factors* f, void* psi, int n_rhs, int n_steps, const h
 
   if (o.use_graph) {
     hs_factors::GraphKey key{psi, n_rhs, n_steps, int(o.method) * 128 + o.max_fuse, tb + 64 * o.smem_kb,
-                             rb * 64 + o.low_bits, nullptr};
+                             (rb * 64 + o.low_bits) * 2 + (o.no_tables != 0), nullptr};
     cudaGraphExec_t exec = nullptr;
     {
       std::lock_guard<std::mutex> lk(f->graph_mu);
@@ -527,7 +542,7 @@ int hs_evolve_ex(const hs_factors* f, void* psi, int n_rhs, int n_steps, const h
       e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
       if (e != cudaSuccess) { cudaStreamDestroy(cs); return cuda_fail(e, "cudaStreamBeginCapture"); }
       hs::begin_capture_count();
-      int rc = enqueue_evolve(f, sw, psi, n_rhs, tb, rb, smem_budget, nullptr, cs);
+      int rc = enqueue_evolve(f, sw, psi, n_rhs, tb, rb, smem_budget, o.no_tables == 0, nullptr, cs);
       const uint64_t n_kernels = hs::end_capture_count();
       cudaGraph_t graph = nullptr;
       e = cudaStreamEndCapture(cs, &graph);
@@ -556,7 +571,7 @@ int hs_evolve_ex(const hs_factors* f, void* psi, int n_rhs, int n_steps, const h
     cudaError_t e = hs::pool_malloc(&scratch, state_bytes, s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(scratch state)");
   }
-  int rc = enqueue_evolve(f, sw, psi, n_rhs, tb, rb, smem_budget, scratch, s);
+  int rc = enqueue_evolve(f, sw, psi, n_rhs, tb, rb, smem_budget, o.no_tables == 0, scratch, s);
   if (scratch) cudaFreeAsync(scratch, s);
   return rc;
 }
@@ -614,7 +629,7 @@ int hs_factors_info(const hs_factors* f, int* n_factors, int* n_qubits, int* n_s
   if (n_qubits) *n_qubits = f->plan.n_qubits;
   if (n_steps) *n_steps = f->n_steps;
   if (dtype) *dtype = f->dtype;
-  if (value_bytes) *value_bytes = f->plan.total_elems * int64_t(hs::elem_bytes(f->dtype));
+  if (value_bytes) *value_bytes = (f->plan.total_elems + f->plan.total_vt) * int64_t(hs::elem_bytes(f->dtype));
   return HS_OK;
 }
 

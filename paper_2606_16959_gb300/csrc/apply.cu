@@ -183,6 +183,7 @@ cudaError_t launch_sweep(const hs_factors* f, const SweepLaunch& L, cudaStream_t
   a.src = L.src;
   a.dst = L.dst;
   a.vals = f->d_vals;
+  a.vt = f->d_vt;
   a.slot_u = f->d_slot_u;
   a.slot_tab = f->d_slot_tab;
   a.tab_rb = f->d_tab_rb;
@@ -204,7 +205,7 @@ cudaError_t launch_sweep(const hs_factors* f, const SweepLaunch& L, cudaStream_t
   a.sh = h - lo;
   a.rest = L.rest;
   a.n_factors = L.n_factors;
-  int planes = 1, n_mslot = 0, n_mtab = 0;
+  int planes = 1, n_mslot = 0, n_mtab = 0, n_vt = 0;
   for (int i = 0; i < L.n_factors; ++i) {
     const Group& G = p.groups[L.factors[i]];
     if (G.nslot <= 0) return cudaErrorInvalidValue;
@@ -215,15 +216,21 @@ cudaError_t launch_sweep(const hs_factors* f, const SweepLaunch& L, cudaStream_t
     a.ftab_g[i] = t0;
     a.ftab_s[i] = int16_t(n_mtab);
     a.ftab_n[i] = int16_t(t1 - t0);
+    a.fvts[i] = int16_t(n_vt);
+    const bool table = L.value_tables && G.vt0 >= 0 && n_vt + G.vt_n <= kMaxVtSweep;
+    a.fvt[i] = table ? G.vt0 : -1;
+    a.fsm[i] = table ? G.smask : 0u;
+    if (table) n_vt += G.vt_n;
     n_mslot += G.nslot;
     n_mtab += t1 - t0;
-    planes = G.nslot > planes ? G.nslot : planes;
+    if (!table) planes = G.nslot > planes ? G.nslot : planes;
   }
   if (n_mslot > 32767 || n_mtab > 32767) return cudaErrorInvalidValue;
   a.n_mslot = n_mslot;
   a.n_mtab = n_mtab;
+  a.n_vt = n_vt;
   a.stage_planes = planes;
-  const size_t mb = meta_bytes(n_mslot, n_mtab);
+  const size_t mb = meta_bytes(n_mslot, n_mtab, n_vt, elem_bytes(f->dtype));
   // As many stages (<= 8, <= n_factors) as the shared-memory budget allows.
   int S = 1;
   while (S < 8 && S < L.n_factors &&

@@ -35,6 +35,7 @@ using hs::sweep::SweepArgs;
 struct BJob {
   void* psi;
   const void* vals;
+  const void* vt;
   const uint32_t* slot_u;
   const int32_t* slot_tab;
   const int64_t* tab_rb;
@@ -46,12 +47,15 @@ struct BJob {
 struct BFac {
   int slot0, tab_g;
   int16_t nslot, mslot, tab_s, tab_n;
+  int vt;          // first global value-table entry, -1: staged from the diagonals
+  int16_t vts;     // first shared value-table entry (running prefix)
+  uint32_t sm;     // the factor's support mask
 };
 
 struct BSweep {
   int job;
   int fac_off, n_factors;
-  int n_stages, stage_planes, n_mslot, n_mtab;
+  int n_stages, stage_planes, n_mslot, n_mtab, n_vt;
   uint32_t m0, m1;
   int sh;
   hs::Runs rest;
@@ -90,6 +94,7 @@ __global__ void __launch_bounds__(kBatchThreads) batch_level_kernel(const __grid
     sa->src = bj.psi;
     sa->dst = bj.psi;
     sa->vals = bj.vals;
+    sa->vt = bj.vt;
     sa->slot_u = bj.slot_u;
     sa->slot_tab = bj.slot_tab;
     sa->tab_rb = bj.tab_rb;
@@ -102,6 +107,7 @@ __global__ void __launch_bounds__(kBatchThreads) batch_level_kernel(const __grid
     sa->stage_planes = bs.stage_planes;
     sa->n_mslot = bs.n_mslot;
     sa->n_mtab = bs.n_mtab;
+    sa->n_vt = bs.n_vt;
     sa->m0 = bs.m0;
     sa->m1 = bs.m1;
     sa->sh = bs.sh;
@@ -116,6 +122,9 @@ __global__ void __launch_bounds__(kBatchThreads) batch_level_kernel(const __grid
     sa->fmslot[i] = fe.mslot;
     sa->ftab_s[i] = fe.tab_s;
     sa->ftab_n[i] = fe.tab_n;
+    sa->fvt[i] = fe.vt;
+    sa->fvts[i] = fe.vts;
+    sa->fsm[i] = fe.sm;
   }
   __syncthreads();
   const int tl = bj.n_qubits - p.tile_bits;
@@ -140,6 +149,7 @@ LevelFn level_fn(int rows) {
 
 struct hs_batch {
   uint64_t graph_kernels = 0;  // kernels one replay of the captured graph launches
+  bool value_tables = true;    // read small-support factors from their value tables
   hs_dtype dtype = HS_C64;
   int tile_bits = 0, low_bits = 0, rows = 1;
   bool use_graph = true;
@@ -206,7 +216,7 @@ int upload_tables(hs_batch* b, cudaStream_t s) {
 
 int enqueue_batch(hs_batch* b, cudaStream_t s) {
   for (const hs_batch::Sep& j : b->separate) {
-    hs_evolve_opts o{HS_METHOD_AUTO, 0, 0, 0, 0, 0, 0};
+    hs_evolve_opts o{HS_METHOD_AUTO, 0, 0, 0, 0, 0, 0, 0};
     int rc = hs_evolve_ex(j.f, j.psi, j.n_rhs, j.n_steps, &o, s);
     if (rc != HS_OK) return rc;
   }
@@ -237,7 +247,7 @@ extern "C" int hs_batch_create(const hs_batch_job* jobs, size_t n_jobs, const hs
   if (!out) return hs::report_error(HS_EINVAL, "out is NULL");
   *out = nullptr;
   if (!jobs || n_jobs == 0) return hs::report_error(HS_EINVAL, "no jobs");
-  hs_batch_opts o{0, 0, 1, 0};
+  hs_batch_opts o{0, 0, 1, 0, 0};
   if (opts) o = *opts;
   std::unique_ptr<hs_batch> b(new hs_batch());
   b->dtype = jobs[0].factors ? jobs[0].factors->dtype : HS_C64;
@@ -257,6 +267,7 @@ extern "C" int hs_batch_create(const hs_batch_job* jobs, size_t n_jobs, const hs
   b->tile_bits = o.tile_bits > 0 ? o.tile_bits : 9;
   b->low_bits = o.low_bits > 0 ? o.low_bits : (dt == HS_C64 ? 2 : 1);
   b->use_graph = o.use_graph != 0;
+  b->value_tables = o.no_tables == 0;
   if (b->tile_bits < 8 || b->tile_bits > 11) return hs::report_error(HS_EINVAL, "batch tile_bits must be 8..11");
   b->rows = (1 << b->tile_bits) / kBatchThreads;
   if ((dt == HS_C64 ? level_fn<float>(b->rows) : level_fn<double>(b->rows)) == nullptr)
@@ -287,7 +298,7 @@ extern "C" int hs_batch_create(const hs_batch_job* jobs, size_t n_jobs, const hs
     }
     const int jid = int(hjobs.size());
     const hs_factors* f = J.factors;
-    hjobs.push_back(BJob{J.psi, f->d_vals, f->d_slot_u, f->d_slot_tab, f->d_tab_rb, p.N, p.n_qubits, J.n_rhs});
+    hjobs.push_back(BJob{J.psi, f->d_vals, f->d_vt, f->d_slot_u, f->d_slot_tab, f->d_tab_rb, p.N, p.n_qubits, J.n_rhs});
     job_ctas.push_back((int64_t(1) << (p.n_qubits - T)) * J.n_rhs);
     std::map<std::pair<uint32_t, std::vector<int>>, int> uniq;
     std::vector<int> lv;
@@ -310,19 +321,23 @@ extern "C" int hs_batch_create(const hs_batch_job* jobs, size_t n_jobs, const hs
       bs.m1 = ((1u << wd) - 1u) << lo;
       bs.sh = h - lo;
       bs.rest = hs::runs_of(~uint64_t(lm) & all, p.n_qubits);
-      int planes = 1, n_mslot = 0, n_mtab = 0;
+      int planes = 1, n_mslot = 0, n_mtab = 0, n_vt = 0;
       for (int g : w.factors) {
         const hs::Group& G = p.groups[g];
         const int t0 = p.slot_tab[G.slot0], t1 = p.slot_tab[G.slot0 + G.nslot];
-        hfacs.push_back(BFac{G.slot0, t0, int16_t(G.nslot), int16_t(n_mslot), int16_t(n_mtab), int16_t(t1 - t0)});
+        const bool table = b->value_tables && G.vt0 >= 0 && n_vt + G.vt_n <= hs::kMaxVtSweep;
+        hfacs.push_back(BFac{G.slot0, t0, int16_t(G.nslot), int16_t(n_mslot), int16_t(n_mtab), int16_t(t1 - t0),
+                             table ? G.vt0 : -1, int16_t(n_vt), table ? G.smask : 0u});
         n_mslot += G.nslot;
         n_mtab += t1 - t0;
-        planes = std::max(planes, G.nslot);
+        if (table) n_vt += G.vt_n;
+        else planes = std::max(planes, G.nslot);
       }
       bs.n_mslot = n_mslot;
       bs.n_mtab = n_mtab;
+      bs.n_vt = n_vt;
       bs.stage_planes = planes;
-      const size_t mb = hs::sweep::meta_bytes(n_mslot, n_mtab);
+      const size_t mb = hs::sweep::meta_bytes(n_mslot, n_mtab, n_vt, hs::elem_bytes(dt));
       int S = 1;
       while (S < 8 && S < bs.n_factors && mb + hs::sweep_smem_bytes(dt, 1, T, planes, S + 1) <= budget) ++S;
       bs.n_stages = S;

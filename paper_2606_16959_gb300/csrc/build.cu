@@ -54,34 +54,38 @@ __device__ __forceinline__ void store_val(void* vals, int64_t idx, double2 v, bo
     reinterpret_cast<double2*>(vals)[idx] = v;
 }
 
+// Group g's basis, pivots, slot x-masks and term range, read once per thread.
 template <int MAXS>
-__global__ void __launch_bounds__(256) build_kernel(BuildArgs a, bool c64) {
-  const int g = blockIdx.y;
-  const int xd = a.xdim[g];
-  const int S = 1 << xd;
+struct GroupRows {
+  int xd, S, first, last;
   uint64_t bas[kMaxXDim];
   int piv[kMaxXDim];
+  uint64_t u[MAXS];
+  __device__ __forceinline__ void load(const BuildArgs& a, int g) {
+    xd = a.xdim[g];
+    S = 1 << xd;
 #pragma unroll
-  for (int i = 0; i < kMaxXDim; ++i) {
-    bas[i] = (i < xd) ? a.basis[g * kMaxXDim + i] : 0;
-    piv[i] = (i < xd) ? a.pivot[g * kMaxXDim + i] : 0;
-  }
-  const int first = a.gfirst[g], last = a.glast[g];
-  const int D = a.fac_D[g], d0 = a.fac_diag0[g];
-
-  for (int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; r < a.N; r += int64_t(gridDim.x) * blockDim.x) {
-    double2 w[MAXS], nw[MAXS];
-    uint64_t u[MAXS];
+    for (int i = 0; i < kMaxXDim; ++i) {
+      bas[i] = (i < xd) ? a.basis[g * kMaxXDim + i] : 0;
+      piv[i] = (i < xd) ? a.pivot[g * kMaxXDim + i] : 0;
+    }
+    first = a.gfirst[g];
+    last = a.glast[g];
 #pragma unroll
     for (int s = 0; s < MAXS; ++s) {
-      w[s] = make_double2(s == 0 ? 1.0 : 0.0, 0.0);
       uint64_t m = 0;
 #pragma unroll
       for (int i = 0; i < kMaxXDim; ++i)
         if (i < xd && ((s >> i) & 1)) m ^= bas[i];
       u[s] = m;
     }
-    // Apply R_j^dagger = cos I + i sin P_j for j = last-1 .. first.
+  }
+  // w[s] = slot s of F_g^dagger e_r (the conjugate of row r of F_g at column
+  // r ^ u_s), by applying R_j^dagger = cos I + i sin P_j for j = last-1 .. first.
+  __device__ __forceinline__ void row(const BuildArgs& a, uint64_t r, double2 (&w)[MAXS]) const {
+    double2 nw[MAXS];
+#pragma unroll
+    for (int s = 0; s < MAXS; ++s) w[s] = make_double2(s == 0 ? 1.0 : 0.0, 0.0);
     for (int j = last - 1; j >= first; --j) {
       const double c = a.cs[2 * j], sn = a.cs[2 * j + 1];
       const uint64_t xj = a.x[j], zj = a.z[j];
@@ -93,7 +97,7 @@ __global__ void __launch_bounds__(256) build_kernel(BuildArgs a, bool c64) {
           const int src = s ^ int(cxj);
           // P_j maps slot src (basis state r ^ u[src]) to slot s with phase
           // i^y (-1)^popcount(z & (r ^ u[src])); times i sin.
-          const int par = __popcll(zj & (uint64_t(r) ^ u[src])) & 1;
+          const int par = __popcll(zj & (r ^ u[src])) & 1;
           double2 p = mul_ipow(w[src], y + 1 + 2 * par);
           nw[s] = make_double2(fma(c, w[s].x, sn * p.x), fma(c, w[s].y, sn * p.y));
         }
@@ -102,6 +106,19 @@ __global__ void __launch_bounds__(256) build_kernel(BuildArgs a, bool c64) {
       for (int s = 0; s < MAXS; ++s)
         if (s < S) w[s] = nw[s];
     }
+  }
+};
+
+template <int MAXS>
+__global__ void __launch_bounds__(256) build_kernel(BuildArgs a, bool c64) {
+  const int g = blockIdx.y;
+  GroupRows<MAXS> G;
+  G.load(a, g);
+  const int D = a.fac_D[g], d0 = a.fac_diag0[g];
+
+  for (int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; r < a.N; r += int64_t(gridDim.x) * blockDim.x) {
+    double2 w[MAXS];
+    G.row(a, uint64_t(r), w);
     // Row r of F: F[r, c] = conj(w[coord(r ^ c)]) when r ^ c lies in X.
     for (int k = 0; k < D; ++k) {
       const int64_t d = a.offs[d0 + k];
@@ -112,9 +129,9 @@ __global__ void __launch_bounds__(256) build_kernel(BuildArgs a, bool c64) {
       uint64_t rec = 0;
 #pragma unroll
       for (int i = 0; i < kMaxXDim; ++i)
-        if (i < xd && ((uu >> piv[i]) & 1ull)) {
+        if (i < G.xd && ((uu >> G.piv[i]) & 1ull)) {
           cc |= 1 << i;
-          rec ^= bas[i];
+          rec ^= G.bas[i];
         }
       double2 v = make_double2(0.0, 0.0);
       if (rec == uu) {
@@ -125,6 +142,31 @@ __global__ void __launch_bounds__(256) build_kernel(BuildArgs a, bool c64) {
       store_val(a.vals, a.rowbase[d0 + k] + r, v, c64);
     }
   }
+}
+
+// Value tables: for a factor with one, pattern p of the bits at smask stands
+// for every row r with those bits; row r = the pattern deposited at smask (the
+// other bits do not enter the row's values), entry p * nslot + s = F[r, r ^ u_s]
+// = conj(w[s]), computed by the same arithmetic as the row's stored values.
+template <int MAXS>
+__global__ void __launch_bounds__(256) value_table_kernel(BuildArgs a, const uint32_t* smask, const int* vt0,
+                                                          void* vt, bool c64) {
+  const int g = blockIdx.y;
+  if (vt0[g] < 0) return;
+  const uint32_t sm = smask[g];
+  const int bits = __popc(sm);
+  const int p = int(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (p >= (1 << bits)) return;
+  GroupRows<MAXS> G;
+  G.load(a, g);
+  uint64_t r = 0;
+  int q = 0;
+  for (uint32_t t = sm; t; t &= t - 1u, ++q) r |= uint64_t((p >> q) & 1) << (__ffs(t) - 1);
+  double2 w[MAXS];
+  G.row(a, r, w);
+#pragma unroll
+  for (int s = 0; s < MAXS; ++s)
+    if (s < G.S) store_val(vt, int64_t(vt0[g]) + int64_t(p) * G.S + s, make_double2(w[s].x, -w[s].y), c64);
 }
 
 __global__ void sincos_kernel(const double* coeff, double dt, double* cs, int n) {
@@ -167,6 +209,34 @@ cudaError_t launch_build(const hs_factors* f, const double* d_cs, const uint64_t
     case 4: build_kernel<16><<<grid, threads, 0, s>>>(a, c64); break;
     case 5: build_kernel<32><<<grid, threads, 0, s>>>(a, c64); break;
     default: build_kernel<64><<<grid, threads, 0, s>>>(a, c64); break;
+  }
+  note_launches();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_value_tables(const hs_factors* f, const double* d_cs, const uint64_t* d_x, const uint64_t* d_z,
+                                const uint32_t* d_cx, const int* d_gfirst, const int* d_glast, const uint64_t* d_basis,
+                                const int* d_xdim, const int* d_pivot, const uint32_t* d_smask, const int* d_vt0,
+                                cudaStream_t s) {
+  const Plan& p = f->plan;
+  if (p.total_vt == 0) return cudaSuccess;
+  int maxdim = 0, maxbits = 0;
+  for (const Group& g : p.groups)
+    if (g.vt0 >= 0) {
+      maxdim = g.xdim > maxdim ? g.xdim : maxdim;
+      maxbits = __builtin_popcount(g.smask) > maxbits ? __builtin_popcount(g.smask) : maxbits;
+    }
+  BuildArgs a{f->d_vals, f->d_offs, f->d_rowbase, f->d_fac_D, f->d_fac_diag0, d_cs, d_x, d_z, d_cx,
+              d_gfirst, d_glast, d_basis, d_xdim, d_pivot, p.N};
+  const bool c64 = f->dtype == HS_C64;
+  dim3 grid(unsigned(((1 << maxbits) + 255) / 256), unsigned(p.groups.size()));
+  switch (maxdim) {
+    case 0: value_table_kernel<1><<<grid, 256, 0, s>>>(a, d_smask, d_vt0, f->d_vt, c64); break;
+    case 1: value_table_kernel<2><<<grid, 256, 0, s>>>(a, d_smask, d_vt0, f->d_vt, c64); break;
+    case 2: value_table_kernel<4><<<grid, 256, 0, s>>>(a, d_smask, d_vt0, f->d_vt, c64); break;
+    case 3: value_table_kernel<8><<<grid, 256, 0, s>>>(a, d_smask, d_vt0, f->d_vt, c64); break;
+    case 4: value_table_kernel<16><<<grid, 256, 0, s>>>(a, d_smask, d_vt0, f->d_vt, c64); break;
+    default: value_table_kernel<32><<<grid, 256, 0, s>>>(a, d_smask, d_vt0, f->d_vt, c64); break;
   }
   note_launches();
   return cudaGetLastError();

@@ -20,6 +20,8 @@ constexpr int kMaxSweepFactors = 64;
 constexpr int kMaxFusedDiags = 32;                 // factors with more diagonals use the plain kernel
 constexpr size_t kSweepSmemMax = 227 * 1024;       // opt-in shared memory per CTA
 constexpr size_t kSweepSmemDefault = 112 * 1024;   // two sweep CTAs per SM
+constexpr int kMaxVtBits = 8;       // qubits a factor's terms may touch for a value table
+constexpr int kMaxVtSweep = 2048;   // value-table entries one sweep holds in shared memory
 
 // Storage alignment of each diagonal's row-indexed base, in elements (32 bytes).
 inline int64_t align_elems(hs_dtype dt) { return dt == HS_C64 ? 4 : 2; }
@@ -42,6 +44,13 @@ struct Group {
   // bits of u_s (lowest bit of u_s -> bit 0 of p).
   int slot0 = 0;             // first slot in the global slot arrays
   int nslot = 0;             // 2^xdim, or 0 if the factor has no slot tables
+  // Value table (factors with slot tables whose terms touch at most kMaxVtBits
+  // qubits): entry (r, r ^ u_s) of the factor depends on r only through r's
+  // bits at smask (the union of its terms' x and z masks), so the values sit in
+  // a table indexed p * nslot + s, p = those bits packed (lowest bit first).
+  uint32_t smask = 0;
+  int vt0 = -1;              // first entry in the factor set's value tables, -1 if none
+  int vt_n = 0;              // nslot << popcount(smask)
 };
 
 // Result of planning a factor set on the host.
@@ -56,6 +65,7 @@ struct Plan {
   std::vector<int64_t> rowbase;   // value(row r) of diagonal k sits at element rowbase[k] + r
   std::vector<uint32_t> term_cx;  // per term: coordinates of its x mask in its factor's basis
   int64_t total_elems = 0;        // padded storage size in elements
+  int64_t total_vt = 0;           // value-table entries (stored after the diagonals)
   std::vector<uint32_t> slot_u;   // per slot: its x-mask
   std::vector<int32_t> slot_tab;  // per slot: first entry in tab_rb (one sentinel at the end)
   std::vector<int64_t> tab_rb;    // per (slot, row pattern): row-indexed base of the diagonal
@@ -106,7 +116,8 @@ struct hs_factors {
   int n_steps = 0;
   double t = 0.0;
   int device = 0;
-  void* d_vals = nullptr;        // padded factor values (float2 / double2)
+  void* d_vals = nullptr;        // padded factor values (float2 / double2), then the value tables
+  void* d_vt = nullptr;          // value tables (inside the d_vals allocation)
   void* d_tables = nullptr;      // one allocation holding every table below (and the build inputs)
   int64_t* d_offs = nullptr;     // per diagonal offset
   int64_t* d_rowbase = nullptr;  // per diagonal row-indexed base
@@ -133,6 +144,10 @@ cudaError_t launch_build(const hs_factors* f, const double* d_theta_cs, const ui
                          const uint32_t* d_cx, const int* d_group_first, const int* d_group_last,
                          const uint64_t* d_basis, const int* d_xdim, const int* d_pivot, cudaStream_t s);
 cudaError_t launch_sincos(const double* d_coeff, double dt, double* d_theta_cs, int n, cudaStream_t s);
+cudaError_t launch_value_tables(const hs_factors* f, const double* d_theta_cs, const uint64_t* d_x, const uint64_t* d_z,
+                                const uint32_t* d_cx, const int* d_group_first, const int* d_group_last,
+                                const uint64_t* d_basis, const int* d_xdim, const int* d_pivot,
+                                const uint32_t* d_smask, const int* d_vt0, cudaStream_t s);
 
 cudaError_t launch_apply_plain(const hs_factors* f, int g, const void* x, void* y, int n_rhs, cudaStream_t s);
 
@@ -148,6 +163,7 @@ struct SweepLaunch {
   int factors[kMaxSweepFactors];
   size_t smem_budget;  // shared memory the launch may use (sets the number of factor stages)
   bool pdl;            // launch with programmatic dependent launch
+  bool value_tables;   // read factors that have value tables from them instead of staging planes
 };
 cudaError_t launch_sweep(const hs_factors* f, const SweepLaunch& L, cudaStream_t s);
 size_t sweep_smem_bytes(hs_dtype dt, int rhs_block, int tile_bits, int stage_diags, int n_stages);

@@ -225,6 +225,18 @@ int make_plan(const uint64_t* x, const uint64_t* z, const double* coeff, size_t 
         if ((x[j] >> G.pivot[i]) & 1ull) c |= 1u << i;
       plan.term_cx[j] = c;
     }
+    // Value table of a factor whose terms touch few qubits.
+    if (G.nslot > 0) {
+      uint64_t sm = 0;
+      for (int j = G.first; j < G.last; ++j) sm |= x[j] | z[j];
+      const int bits = __builtin_popcountll(sm);
+      if (bits <= kMaxVtBits && sm < (1ull << 32) && (G.nslot << bits) <= kMaxVtSweep) {
+        G.smask = uint32_t(sm);
+        G.vt0 = int(plan.total_vt);
+        G.vt_n = G.nslot << bits;
+        plan.total_vt += G.vt_n;
+      }
+    }
     plan.groups.push_back(G);
   }
   // One extra aligned block: a 16-byte staging copy that straddles the end of

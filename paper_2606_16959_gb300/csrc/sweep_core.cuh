@@ -30,6 +30,7 @@ struct SweepArgs {
   const void* src;
   void* dst;
   const void* vals;
+  const void* vt;    // the factor set's value tables
   const uint32_t* slot_u;
   const int32_t* slot_tab;
   const int64_t* tab_rb;
@@ -42,6 +43,7 @@ struct SweepArgs {
   int stage_planes;  // planes per stage (max slot count over the sweep's factors)
   int n_mslot;       // slots listed in the shared-memory slot table
   int n_mtab;        // entries in the shared-memory row-base table
+  int n_vt;          // value-table entries held in shared memory
   // Local bits [0, a) U [h, h + w): local index of row r is
   // (r & m0) | ((r >> sh) & m1), with m0 = 2^a - 1, m1 = (2^w - 1) << a, sh = h - a.
   uint32_t m0, m1;
@@ -57,13 +59,20 @@ struct SweepArgs {
   int16_t fmslot[kMaxSweepFactors];
   int16_t ftab_s[kMaxSweepFactors];
   int16_t ftab_n[kMaxSweepFactors];
+  // Value tables: first global entry of the factor's table (-1: the factor is
+  // staged from its diagonals instead), first shared entry (a running prefix,
+  // so factors without a table repeat the next factor's start) and the bit
+  // mask whose bits of a row index the table.
+  int fvt[kMaxSweepFactors];
+  int16_t fvts[kMaxSweepFactors];
+  uint32_t fsm[kMaxSweepFactors];
 };
 
 struct SlotMeta {
   uint32_t u;    // x-mask of the slot
   uint32_t U;    // its local image (u lies inside the tile's local bits)
   int32_t tab;   // first row-base table entry in shared memory
-  int32_t pos;   // plane position in the stage ring (factors staged by the prologue)
+  int32_t pos;   // plane position in the stage ring (factors staged by the prologue); -1: value table
 };
 
 // Scatter the low bits of v into the positions of the runs.
@@ -120,10 +129,13 @@ __device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepco
 __device__ __forceinline__ void grid_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
 
 // The factor loop of a sweep.  NRB = RB when the CTA's block of states is
-// full (no per-state guard), 0 for the last, partial block.
+// full (no per-state guard), 0 for the last, partial block.  grow[i] is the
+// global index of the thread's local row threadIdx.x + i * NT; vts holds the
+// sweep's value tables.
 template <typename T2, int ROWS, int RB, int NRB, typename Issue>
 __device__ __forceinline__ void sweep_body(const SweepArgs& a, int nrb, T2* tile, const T2* stages, uint32_t stage_elems,
-                                           const SlotMeta* mslot, uint32_t TS, int NT, Issue& issue_factor) {
+                                           const SlotMeta* mslot, const T2* vts, const uint32_t (&grow)[ROWS],
+                                           uint32_t TS, int NT, Issue& issue_factor) {
   const int S = a.n_stages;
   int stage = 0;  // fi % S
   for (int fi = 0; fi < a.n_factors; ++fi) {
@@ -131,23 +143,37 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a, int nrb, T2* tile
     __syncthreads();
     const int ns = a.fnslot[fi];
     const SlotMeta* ms = mslot + a.fmslot[fi];
-    const T2* st = stages + size_t(stage) * stage_elems + threadIdx.x;
     T2 acc[ROWS][RB];
 #pragma unroll
     for (int i = 0; i < ROWS; ++i)
 #pragma unroll
       for (int q = 0; q < RB; ++q) acc[i][q] = T2{0, 0};
+    // acc[i][q] += v(j, i) * x[q][row_i ^ U_j] over the factor's slots j.
+    auto multiply = [&](auto value_of) {
 #pragma unroll 2
-    for (int j = 0; j < ns; ++j) {
-      const uint32_t U = ms[j].U;
+      for (int j = 0; j < ns; ++j) {
+        const uint32_t U = ms[j].U;
 #pragma unroll
-      for (int i = 0; i < ROWS; ++i) {
-        const T2 v = st[j * TS + i * NT];
-        const T2* xp = tile + ((threadIdx.x + uint32_t(i) * NT) ^ U);
+        for (int i = 0; i < ROWS; ++i) {
+          const T2 v = value_of(j, i);
+          const T2* xp = tile + ((threadIdx.x + uint32_t(i) * NT) ^ U);
 #pragma unroll
-        for (int q = 0; q < RB; ++q, xp += TS)
-          if (NRB || q < nrb) cfma(acc[i][q], v, *xp);
+          for (int q = 0; q < RB; ++q, xp += TS)
+            if (NRB || q < nrb) cfma(acc[i][q], v, *xp);
+        }
       }
+    };
+    if (a.fvt[fi] >= 0) {
+      // Value table: entry (pattern of the row's bits at fsm) * ns + slot.
+      const T2* tb = vts + a.fvts[fi];
+      const uint32_t sm = a.fsm[fi];
+      uint32_t pat[ROWS];
+#pragma unroll
+      for (int i = 0; i < ROWS; ++i) pat[i] = pattern_of(grow[i], sm) * uint32_t(ns);
+      multiply([&](int j, int i) { return tb[pat[i] + j]; });
+    } else {
+      const T2* st = stages + size_t(stage) * stage_elems + threadIdx.x;
+      multiply([&](int j, int i) { return st[j * TS + i * NT]; });
     }
     __syncthreads();
 #pragma unroll
@@ -183,10 +209,11 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, uint32_t tile_id,
   const uint32_t TS = 1u << a.tile_bits;
   const uint32_t m0 = a.m0, m1 = a.m1;
   const int sh = a.sh;
-  // Shared memory: [slot table][row-base table][tile][factor stages]
+  // Shared memory: [slot table][row-base table][value tables][tile][factor stages]
   SlotMeta* mslot = reinterpret_cast<SlotMeta*>(smem_raw);
   int64_t* mtab = reinterpret_cast<int64_t*>(mslot + a.n_mslot);
-  T2* tile = reinterpret_cast<T2*>(mtab + ((a.n_mtab + 1) & ~1));
+  T2* vts = reinterpret_cast<T2*>(mtab + ((a.n_mtab + 1) & ~1));
+  T2* tile = vts + ((a.n_vt + V - 1) & ~(V - 1));
   T2* stages = tile + size_t(a.rhs_block) * TS;
   const uint32_t stage_elems = uint32_t(a.stage_planes) * TS;
   // src and dst may be the same buffer (in-place sweep): every CTA reads its
@@ -212,7 +239,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, uint32_t tile_id,
     const int gs = a.fslot0[lo] + (t - a.fmslot[lo]);
     const uint32_t u = a.slot_u[gs];
     mslot[t] = SlotMeta{u, local_of(u, m0, m1, sh), a.ftab_s[lo] + (a.slot_tab[gs] - a.ftab_g[lo]),
-                        lo * a.stage_planes + (t - a.fmslot[lo])};
+                        a.fvt[lo] >= 0 ? -1 : lo * a.stage_planes + (t - a.fmslot[lo])};
   }
   for (int e = threadIdx.x; e < a.n_mtab; e += NT) {
     int lo = 0, hi = a.n_factors - 1;
@@ -221,6 +248,19 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, uint32_t tile_id,
       if (a.ftab_s[mid] <= e) lo = mid; else hi = mid - 1;
     }
     mtab[e] = a.tab_rb[a.ftab_g[lo] + (e - a.ftab_s[lo])];
+  }
+  // Value tables: entry e belongs to the last factor whose shared start is <= e
+  // (factors without a table have empty ranges, so that factor owns it).
+  {
+    const T2* __restrict__ gvt = reinterpret_cast<const T2*>(a.vt);
+    for (int e = threadIdx.x; e < a.n_vt; e += NT) {
+      int lo = 0, hi = a.n_factors - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.fvts[mid] <= e) lo = mid; else hi = mid - 1;
+      }
+      vts[e] = gvt[a.fvt[lo] + (e - a.fvts[lo])];
+    }
   }
   __syncthreads();
 
@@ -238,6 +278,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, uint32_t tile_id,
       const int p = p0 + (k >> chunk_log2);
       const uint32_t c = uint32_t(k) & (n_chunks - 1u);
       const SlotMeta m = mslot[p];
+      if (stage < 0 && m.pos < 0) continue;  // read from its value table
       const int pos = stage < 0 ? m.pos : stage * a.stage_planes + (p - p0);
       T2* dst_s = stages + size_t(pos) * TS + c * V;
       const uint32_t r = global_of(c * V, m0, m1, sh) | base;
@@ -252,7 +293,9 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, uint32_t tile_id,
       }
     }
   };
-  auto issue_factor = [&](int fi, int stage) { issue_slots(a.fmslot[fi], a.fmslot[fi] + a.fnslot[fi], stage); };
+  auto issue_factor = [&](int fi, int stage) {
+    if (a.fvt[fi] < 0) issue_slots(a.fmslot[fi], a.fmslot[fi] + a.fnslot[fi], stage);
+  };
 
   // Prologue: the first S factors, as one copy group.
   const int S = a.n_stages;
@@ -272,10 +315,13 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, uint32_t tile_id,
   }
   cp_async_commit();
 
+  uint32_t grow[ROWS];
+#pragma unroll
+  for (int i = 0; i < ROWS; ++i) grow[i] = global_of(threadIdx.x + uint32_t(i) * NT, m0, m1, sh) | base;
   if (nrb == RB)
-    sweep_body<T2, ROWS, RB, RB>(a, nrb, tile, stages, stage_elems, mslot, TS, NT, issue_factor);
+    sweep_body<T2, ROWS, RB, RB>(a, nrb, tile, stages, stage_elems, mslot, vts, grow, TS, NT, issue_factor);
   else
-    sweep_body<T2, ROWS, RB, 0>(a, nrb, tile, stages, stage_elems, mslot, TS, NT, issue_factor);
+    sweep_body<T2, ROWS, RB, 0>(a, nrb, tile, stages, stage_elems, mslot, vts, grow, TS, NT, issue_factor);
 
   // Store the tile.
   for (uint32_t c = threadIdx.x; c < n_chunks; c += NT) {
@@ -287,8 +333,10 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, uint32_t tile_id,
   }
 }
 
-// Shared-memory bytes of the slot and row-base tables of a sweep.
-inline size_t meta_bytes(int n_mslot, int n_mtab) { return size_t(n_mslot) * 16 + size_t((n_mtab + 1) & ~1) * 8; }
+// Shared-memory bytes of the slot, row-base and value tables of a sweep.
+inline size_t meta_bytes(int n_mslot, int n_mtab, int n_vt = 0, size_t elem = 8) {
+  return size_t(n_mslot) * 16 + size_t((n_mtab + 1) & ~1) * 8 + (size_t(n_vt) * elem + 15) / 16 * 16;
+}
 
 }  // namespace sweep
 }  // namespace hs

@@ -57,7 +57,7 @@ extern "C" int hs_autotune(const hs_factors* f, const void* psi, int n_rhs, int 
   if (e != cudaSuccess) return hs::report_error(e == cudaErrorMemoryAllocation ? HS_ENOMEM : HS_ECUDA,
                                                 std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
   std::vector<hs_evolve_opts> cand;
-  cand.push_back(hs_evolve_opts{HS_METHOD_PLAIN, 0, 0, 0, 0, 0, 0});
+  cand.push_back(hs_evolve_opts{HS_METHOD_PLAIN, 0, 0, 0, 0, 0, 0, 0});
   int planes = 1;
   for (const hs::Group& g : f->plan.groups) planes = std::max(planes, g.nslot);
   const int cap = dt == HS_C64 ? 16 : 8;
@@ -70,7 +70,7 @@ extern "C" int hs_autotune(const hs_factors* f, const void* psi, int n_rhs, int 
       for (int lb : {1, 2, 3}) {
         if (dt == HS_C128 && lb == 3) continue;
         if (lb > tb) continue;
-        for (int kb : {0, 48}) cand.push_back(hs_evolve_opts{HS_METHOD_FUSED, tb, rb, 0, lb, 0, kb});
+        for (int kb : {0, 48}) cand.push_back(hs_evolve_opts{HS_METHOD_FUSED, tb, rb, 0, lb, 0, kb, 0});
       }
   }
   cudaEvent_t e0, e1;

@@ -46,13 +46,13 @@ class BatchJob(ctypes.Structure):
 
 class BatchOpts(ctypes.Structure):
     _fields_ = [("tile_bits", ctypes.c_int), ("low_bits", ctypes.c_int), ("use_graph", ctypes.c_int),
-                ("smem_kb", ctypes.c_int)]
+                ("smem_kb", ctypes.c_int), ("no_tables", ctypes.c_int)]
 
 
 class EvolveOpts(ctypes.Structure):
     _fields_ = [("method", ctypes.c_int), ("tile_bits", ctypes.c_int), ("rhs_block", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("low_bits", ctypes.c_int), ("max_fuse", ctypes.c_int),
-                ("smem_kb", ctypes.c_int)]
+                ("smem_kb", ctypes.c_int), ("no_tables", ctypes.c_int)]
 
 
 _lib = None
@@ -256,19 +256,19 @@ def hs_evolve(f: Factors, psi, n_steps: int, stream=None) -> None:
 
 def hs_evolve_ex(f: Factors, psi, n_steps: int, method: int = HS_METHOD_AUTO, tile_bits: int = 0,
                  rhs_block: int = 0, use_graph: bool = False, low_bits: int = 0, max_fuse: int = 0, smem_kb: int = 0,
-                 stream=None) -> None:
+                 no_tables: bool = False, stream=None) -> None:
     ptr, n_rhs = _check_state(f, psi)
     o = EvolveOpts(int(method), int(tile_bits), int(rhs_block), int(bool(use_graph)), int(low_bits), int(max_fuse),
-                   int(smem_kb))
+                   int(smem_kb), int(bool(no_tables)))
     _check(lib().hs_evolve_ex(f.handle, ptr, n_rhs, int(n_steps), ctypes.byref(o), _stream(stream)))
 
 
 def hs_evolve_plan(f: Factors, n_rhs: int, n_steps: int, method: int = HS_METHOD_AUTO, tile_bits: int = 0,
                    rhs_block: int = 0, use_graph: bool = False, low_bits: int = 0, max_fuse: int = 0,
-                   smem_kb: int = 0):
+                   smem_kb: int = 0, no_tables: bool = False):
     """(n_sweep_launches, n_plain_launches, tile_bits, rhs_block) hs_evolve_ex would use."""
     o = EvolveOpts(int(method), int(tile_bits), int(rhs_block), int(bool(use_graph)), int(low_bits), int(max_fuse),
-                   int(smem_kb))
+                   int(smem_kb), int(bool(no_tables)))
     a, b, c, d = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     _check(lib().hs_evolve_plan(f.handle, int(n_rhs), int(n_steps), ctypes.byref(o), ctypes.byref(a), ctypes.byref(b),
                                 ctypes.byref(c), ctypes.byref(d)))
@@ -382,7 +382,8 @@ class Batch:
             pass
 
 
-def hs_batch_create(jobs, tile_bits: int = 0, low_bits: int = 0, use_graph: bool = True, smem_kb: int = 0) -> Batch:
+def hs_batch_create(jobs, tile_bits: int = 0, low_bits: int = 0, use_graph: bool = True, smem_kb: int = 0,
+                    no_tables: bool = False) -> Batch:
     """jobs: sequence of (Factors, state tensor, n_steps)."""
     arr = (BatchJob * len(jobs))()
     keep = []
@@ -390,7 +391,7 @@ def hs_batch_create(jobs, tile_bits: int = 0, low_bits: int = 0, use_graph: bool
         ptr, n_rhs = _check_state(f, psi)
         arr[k] = BatchJob(f.handle.value, ptr, n_rhs, int(n_steps))
         keep.append((f, psi))
-    o = BatchOpts(int(tile_bits), int(low_bits), int(bool(use_graph)), int(smem_kb))
+    o = BatchOpts(int(tile_bits), int(low_bits), int(bool(use_graph)), int(smem_kb), int(bool(no_tables)))
     out = ctypes.c_void_p()
     _check(lib().hs_batch_create(arr, len(jobs), ctypes.byref(o), ctypes.byref(out)))
     return Batch(out.value, keep)

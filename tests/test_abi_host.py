@@ -50,6 +50,22 @@ def test_plan_rejects_bad_input(lib):
         hs.hs_plan_factors([(1 << 13) - 1], [0], 13, 4)  # 13 flipped qubits: over 4096 diagonals
 
 
+def _value_table_entries(x, z, group, n_diags):
+    """Entries of a factor's value table: |X| slots times 2^(qubits its terms
+    touch), for factors with slot tables (<= 32 diagonals) touching <= 8 qubits."""
+    first, last = group
+    if n_diags > 32:
+        return 0
+    support = 0
+    span = set([0])
+    for j in range(first, last):
+        support |= int(x[j]) | int(z[j])
+        span |= {u ^ int(x[j]) for u in span}
+    bits = bin(support).count("1")
+    entries = len(span) << bits
+    return entries if bits <= 8 and entries <= 2048 else 0
+
+
 def _compare(oracle, x, z, n, budget):
     got, vbytes = hs.hs_plan_factors(x, z, n, budget)
     want = oracle.group_terms(x, budget)
@@ -58,7 +74,8 @@ def _compare(oracle, x, z, n, budget):
         assert g[2] == w.offsets
     N = 1 << n
     S = sum(N - abs(d) for g in got for d in g[2])
-    assert S * 8 <= vbytes <= (S + 4 * sum(len(g[2]) for g in got) + 4) * 8
+    V = sum(_value_table_entries(x, z, (g[0], g[1]), len(g[2])) for g in got)
+    assert (S + V) * 8 <= vbytes <= (S + V + 4 * sum(len(g[2]) for g in got) + 4) * 8
 
 
 def test_plan_matches_oracle_families(oracle, lib):

@@ -118,3 +118,22 @@ def test_batch_rejects_mixed_dtypes():
     with pytest.raises(hs.HSError) as e:
         hs.hs_batch_create([(f1, s1, 1), (f2, s2, 1)])
     assert e.value.code == hs.HS_EDTYPE
+
+
+def test_batch_value_tables_bitwise_equal_to_staged_diagonals():
+    jobs = W.batch256(n_jobs=12, n_lo=12, n_hi=15, seed=78)
+    facs, s1, s2 = [], [], []
+    for j in jobs:
+        j.n_steps = min(j.n_steps, 30)
+        facs.append(hs.hs_build_factors(j.ham.labels, j.ham.coeffs, j.t, j.n_steps, j.budget, "c64"))
+        s1.append(torch.from_numpy(j.psi0).to("cuda", torch.complex64))
+        s2.append(torch.from_numpy(j.psi0).to("cuda", torch.complex64))
+    b1 = hs.hs_batch_create([(f, s, j.n_steps) for f, s, j in zip(facs, s1, jobs)])
+    b2 = hs.hs_batch_create([(f, s, j.n_steps) for f, s, j in zip(facs, s2, jobs)], no_tables=True)
+    hs.hs_batch_launch(b1)
+    hs.hs_batch_launch(b2)
+    torch.cuda.synchronize()
+    for a, b in zip(s1, s2):
+        assert torch.equal(a, b)
+    b1.close()
+    b2.close()

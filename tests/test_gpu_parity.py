@@ -320,12 +320,13 @@ def test_fidelity_and_norms(dt, n):
 
 def test_kernel_launch_counter_counts_each_launch():
     """hs_kernel_launches advances by exactly the kernels an entry point launches:
-    2 for a factor build (angles, factor values), the planned sweeps for an
-    evolution, 2 for a reduction, and a graph's kernels on every replay."""
+    3 for a factor build with value tables (angles, factor values, tables), the
+    planned sweeps for an evolution, 2 for a reduction, and a graph's kernels on
+    every replay."""
     ham = W.heisenberg_chain(12, np.linspace(0.5, 1.5, 12), periodic=True)
     l0 = hs.hs_kernel_launches()
     f = hs.hs_build_factors(ham.labels, ham.coeffs, 1.0, 4, 8, "c64")
-    assert hs.hs_kernel_launches() - l0 == 2
+    assert hs.hs_kernel_launches() - l0 == 3
     psi = torch.from_numpy(W.gaussian_state(12, np.random.default_rng(3))).to("cuda", torch.complex64)
     opts = dict(method=hs.HS_METHOD_FUSED, tile_bits=8, rhs_block=1, low_bits=1)
     n_sweeps, n_plain, _, _ = hs.hs_evolve_plan(f, 1, 4, **opts)
@@ -341,3 +342,31 @@ def test_kernel_launch_counter_counts_each_launch():
     hs.hs_evolve_ex(f, psi, 4, use_graph=True, **opts)   # replay
     torch.cuda.synchronize()
     assert hs.hs_kernel_launches() - l3 == 2 * (n_sweeps + n_plain)
+
+
+@pytest.mark.parametrize("dt", ["c64", "c128"])
+def test_value_tables_bitwise_equal_to_staged_diagonals(dt):
+    """Factors whose terms touch few qubits are read from value tables (one entry
+    per pattern of the row's bits on those qubits) instead of their stored
+    diagonals; the values are the same numbers, so the evolution is bitwise equal."""
+    rng = np.random.default_rng(77)
+    tdt = torch.complex64 if dt == "c64" else torch.complex128
+    lb = 2 if dt == "c64" else 1
+    labels = ["".join(rng.choice(list("IXYZ"), p=[0.7, 0.1, 0.1, 0.1], size=12)) for _ in range(10)]
+    hams = [W.heisenberg_chain(14, rng.uniform(0.5, 1.5, 14), periodic=True),
+            W.tfim_chain(13, 1.0, 0.6, periodic=False),
+            W.Hamiltonian("random", 12, labels, rng.uniform(-1, 1, 10))]
+    for ham, budget in zip(hams, (8, 4, 16)):
+        f = hs.hs_build_factors(ham.labels, ham.coeffs, 0.7, 6, budget, dt)
+        psi = torch.from_numpy(np.stack([W.gaussian_state(ham.n_qubits, rng) for _ in range(2)])).to("cuda", tdt)
+        a, b = psi.clone(), psi.clone()
+        opts = dict(method=hs.HS_METHOD_FUSED, tile_bits=9, rhs_block=1, low_bits=lb)
+        hs.hs_evolve_ex(f, a, 6, **opts)
+        hs.hs_evolve_ex(f, b, 6, no_tables=True, **opts)
+        torch.cuda.synchronize()
+        assert torch.equal(a, b), ham.family
+        x, z, _ = O.parse_terms(ham.labels)
+        want = O.evolve_direct(x, z, ham.coeffs, 0.7, 6, psi.cpu().numpy())
+        tol = 1e-12 if dt == "c128" else 1e-5
+        assert np.max(np.abs(a.cpu().numpy() - want)) <= tol
+        f.close()
