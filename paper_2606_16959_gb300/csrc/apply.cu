@@ -230,6 +230,11 @@ cudaError_t launch_sweep(const hs_factors* f, const SweepLaunch& L, cudaStream_t
   a.n_mtab = n_mtab;
   a.n_vt = n_vt;
   a.stage_planes = planes;
+  // Register path: every factor from a value table, one row per thread, one
+  // state per tile; lane-only factors are those whose slots' local images are
+  // below 32 (lane bits of the thread's row).
+  a.all_tables = 0;
+  a.flane = 0;
   const size_t mb = meta_bytes(n_mslot, n_mtab, n_vt, elem_bytes(f->dtype));
   // As many stages (<= 8, <= n_factors) as the shared-memory budget allows.
   int S = 1;
@@ -242,6 +247,21 @@ cudaError_t launch_sweep(const hs_factors* f, const SweepLaunch& L, cudaStream_t
   const int TS = 1 << L.tile_bits;
   const int rows = TS > kSweepMaxThreads ? TS / kSweepMaxThreads : 1;
   const int threads = TS / rows;
+  if (rows == 1 && L.rhs_block == 1 && TS >= 32) {
+    bool all = n_vt > 0;
+    for (int i = 0; i < L.n_factors; ++i) {
+      if (a.fvt[i] < 0) { all = false; break; }
+      const Group& G = p.groups[L.factors[i]];
+      bool lane = true;
+      for (int sl = 0; sl < G.nslot; ++sl) {
+        const uint32_t u = p.slot_u[G.slot0 + sl];
+        const uint32_t U = (u & a.m0) | ((u >> a.sh) & a.m1);
+        if (U >= 32u) lane = false;
+      }
+      if (lane) a.flane |= 1ull << i;
+    }
+    a.all_tables = all ? 1 : 0;
+  }
   const bool c64 = f->dtype == HS_C64;
   if (TS < (c64 ? 2 : 1)) return cudaErrorInvalidValue;
   SweepFn fn = c64 ? sweep_fn<float>(rows, L.rhs_block) : sweep_fn<double>(rows, L.rhs_block);

@@ -108,6 +108,8 @@ __global__ void __launch_bounds__(kBatchThreads) batch_level_kernel(const __grid
     sa->n_mslot = bs.n_mslot;
     sa->n_mtab = bs.n_mtab;
     sa->n_vt = bs.n_vt;
+    sa->all_tables = 0;
+    sa->flane = 0;
     sa->m0 = bs.m0;
     sa->m1 = bs.m1;
     sa->sh = bs.sh;

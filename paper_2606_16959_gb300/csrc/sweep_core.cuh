@@ -66,6 +66,11 @@ struct SweepArgs {
   int fvt[kMaxSweepFactors];
   int16_t fvts[kMaxSweepFactors];
   uint32_t fsm[kMaxSweepFactors];
+  // Register path (one row per thread, one state per tile, every factor from a
+  // value table): bit i of flane set when factor i's slots flip only local
+  // bits 0..4, i.e. exchange amplitudes within a warp.
+  int all_tables;
+  uint64_t flane;
 };
 
 struct SlotMeta {
@@ -189,6 +194,46 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a, int nrb, T2* tile
     stage = (stage + 1 == S) ? 0 : stage + 1;
   }
   __syncthreads();
+}
+
+// Register-resident sweep: one row per thread, one state per tile, every
+// factor read from its value table.  The thread keeps its row's amplitude in
+// a register; a factor whose slots flip only lane bits gets its partner
+// amplitudes by warp shuffles (no shared memory, no barrier); any other factor
+// exchanges through one of two shared-memory buffers with one barrier (a
+// buffer is written again only after a later barrier, by which every thread
+// has finished reading it).  Each row's sum is the one the shared-memory path
+// forms, in the same slot order.
+template <typename T2>
+__device__ __forceinline__ void sweep_reg(const SweepArgs& a, T2* tile, T2* other, const SlotMeta* mslot,
+                                          const T2* vts, uint32_t grow, T2* dst_row) {
+  cp_async_wait(0);
+  __syncthreads();
+  T2 xr = tile[threadIdx.x];
+  bool second = false;
+  for (int fi = 0; fi < a.n_factors; ++fi) {
+    const int ns = a.fnslot[fi];
+    const SlotMeta* ms = mslot + a.fmslot[fi];
+    const T2* tb = vts + a.fvts[fi] + pattern_of(grow, a.fsm[fi]) * uint32_t(ns);
+    T2 acc = T2{0, 0};
+    if ((a.flane >> fi) & 1ull) {
+      for (int j = 0; j < ns; ++j) {
+        const int U = int(ms[j].U);
+        T2 x;
+        x.x = __shfl_xor_sync(0xffffffffu, xr.x, U);
+        x.y = __shfl_xor_sync(0xffffffffu, xr.y, U);
+        cfma(acc, tb[j], x);
+      }
+    } else {
+      T2* t = second ? other : tile;
+      t[threadIdx.x] = xr;
+      __syncthreads();
+      for (int j = 0; j < ns; ++j) cfma(acc, tb[j], t[threadIdx.x ^ ms[j].U]);
+      second = !second;
+    }
+    xr = acc;
+  }
+  *dst_row = xr;
 }
 
 // Block of TS / ROWS threads; thread t owns local rows t + i * blockDim.x.
@@ -318,6 +363,12 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, uint32_t tile_id,
   uint32_t grow[ROWS];
 #pragma unroll
   for (int i = 0; i < ROWS; ++i) grow[i] = global_of(threadIdx.x + uint32_t(i) * NT, m0, m1, sh) | base;
+  if constexpr (ROWS == 1 && RB == 1) {
+    if (a.all_tables) {
+      sweep_reg<T2>(a, tile, stages, mslot, vts, grow[0], dst + int64_t(rhs0) * a.N + grow[0]);
+      return;
+    }
+  }
   if (nrb == RB)
     sweep_body<T2, ROWS, RB, RB>(a, nrb, tile, stages, stage_elems, mslot, vts, grow, TS, NT, issue_factor);
   else
