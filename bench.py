@@ -654,7 +654,7 @@ def run_batch(args, rank, world):
     achieved = res["alg_bytes"] / launch_s / 1e9
     traffic = profiled_traffic("batch256") if args.batch_jobs == 256 else None
     cfg = {"workload": "batch256", "description": desc, "n_jobs": len(jobs), "levels_per_step": res["levels"],
-           "ctas_per_step": res["ctas"], "separate_jobs": res["separate"], "tile_bits": 9, "smem_kb_per_cta": 40,
+           "ctas_per_step": res["ctas"], "separate_jobs": res["separate"], "tile_bits": 10, "smem_kb_per_cta": 24,
            "l2": "flushed (512 MiB write) before every timed step"}
     line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": K, "warmup": args.warmup,
             "ms_per_step": res["total_ms"] / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,

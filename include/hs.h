@@ -170,11 +170,11 @@ typedef struct {
 } hs_batch_job;
 
 typedef struct {
-  int tile_bits; /* log2 amplitudes per tile, 8..11 (0 = 9); jobs with fewer qubits, or whose
+  int tile_bits; /* log2 amplitudes per tile, 8..11 (0 = 10); jobs with fewer qubits, or whose
                     factors do not fit a tile, are evolved with their own launches */
   int low_bits;  /* contiguous low bits of a tile (0 = library choice) */
   int use_graph; /* 1 (default): capture the launch sequence once and replay it as a CUDA graph */
-  int smem_kb;   /* shared memory per CTA for the state tile and factor staging, in KiB (0 = 40);
+  int smem_kb;   /* shared memory per CTA for the state tile and factor staging, in KiB (0 = 24);
                     a smaller budget stages fewer factors ahead but fits more CTAs on an SM */
   int no_tables; /* as in hs_evolve_opts: 1 stages every factor from its diagonals */
 } hs_batch_opts;

@@ -247,7 +247,9 @@ cudaError_t launch_sweep(const hs_factors* f, const SweepLaunch& L, cudaStream_t
   const int TS = 1 << L.tile_bits;
   const int rows = TS > kSweepMaxThreads ? TS / kSweepMaxThreads : 1;
   const int threads = TS / rows;
-  if (rows == 1 && L.rhs_block == 1 && TS >= 32) {
+  // (The path's second exchange buffer is the stage ring, which holds at least
+  // one plane of a whole tile.)
+  if (L.rhs_block == 1 && threads >= 32) {
     bool all = n_vt > 0;
     for (int i = 0; i < L.n_factors; ++i) {
       if (a.fvt[i] < 0) { all = false; break; }
@@ -256,7 +258,7 @@ cudaError_t launch_sweep(const hs_factors* f, const SweepLaunch& L, cudaStream_t
       for (int sl = 0; sl < G.nslot; ++sl) {
         const uint32_t u = p.slot_u[G.slot0 + sl];
         const uint32_t U = (u & a.m0) | ((u >> a.sh) & a.m1);
-        if (U >= 32u) lane = false;
+        if ((U & uint32_t(threads - 1)) >= 32u) lane = false;
       }
       if (lane) a.flane |= 1ull << i;
     }

@@ -56,6 +56,8 @@ struct BSweep {
   int job;
   int fac_off, n_factors;
   int n_stages, stage_planes, n_mslot, n_mtab, n_vt;
+  int all_tables;     // register path (see SweepArgs)
+  uint64_t flane;
   uint32_t m0, m1;
   int sh;
   hs::Runs rest;
@@ -71,7 +73,7 @@ struct LevelArgs {
   int tile_bits;
 };
 
-constexpr int kBatchThreads = 256;
+constexpr int kBatchThreads = 512;  // at most; a tile of 2^T rows gets min(2^T, 512) threads
 constexpr size_t kArgsBytes = (sizeof(SweepArgs) + 15) / 16 * 16;
 
 template <typename R, int ROWS>
@@ -108,8 +110,8 @@ __global__ void __launch_bounds__(kBatchThreads) batch_level_kernel(const __grid
     sa->n_mslot = bs.n_mslot;
     sa->n_mtab = bs.n_mtab;
     sa->n_vt = bs.n_vt;
-    sa->all_tables = 0;
-    sa->flane = 0;
+    sa->all_tables = bs.all_tables;
+    sa->flane = bs.flane;
     sa->m0 = bs.m0;
     sa->m1 = bs.m1;
     sa->sh = bs.sh;
@@ -228,7 +230,7 @@ int enqueue_batch(hs_batch* b, cudaStream_t s) {
     LevelArgs a{b->d_jobs, b->d_sweeps, b->d_facs, b->d_lvl_sweep, b->d_lvl_prefix, L.off, L.count, b->tile_bits};
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(unsigned(L.ctas), 1u, 1u);
-    cfg.blockDim = dim3(unsigned(kBatchThreads), 1u, 1u);
+    cfg.blockDim = dim3(unsigned((1 << b->tile_bits) / b->rows), 1u, 1u);
     cfg.dynamicSmemBytes = b->smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
@@ -263,21 +265,22 @@ extern "C" int hs_batch_create(const hs_batch_job* jobs, size_t n_jobs, const hs
     min_n = std::min(min_n, J.factors->plan.n_qubits);
   }
   const hs_dtype dt = b->dtype;
-  // Defaults measured on the 256-instance TFIM/Heisenberg batch (complex64):
-  // tiles of 2^9 rows with 40 KiB per CTA ran it in 833 ms, against 960 ms for
-  // 2^10 rows with 112 KiB (two CTAs per SM) and 867-899 ms for 16-28 KiB.
-  b->tile_bits = o.tile_bits > 0 ? o.tile_bits : 9;
+  // Defaults measured on the 256-instance TFIM/Heisenberg batch (complex64,
+  // value tables and the register path on): tiles of 2^10 rows with 24 KiB per
+  // CTA ran it in 561 ms, against 576 ms with 40 KiB, 584 ms with 64 KiB,
+  // 652 ms for 2^11 rows and 747 ms for 2^9.
+  b->tile_bits = o.tile_bits > 0 ? o.tile_bits : 10;
   b->low_bits = o.low_bits > 0 ? o.low_bits : (dt == HS_C64 ? 2 : 1);
   b->use_graph = o.use_graph != 0;
   b->value_tables = o.no_tables == 0;
   if (b->tile_bits < 8 || b->tile_bits > 11) return hs::report_error(HS_EINVAL, "batch tile_bits must be 8..11");
-  b->rows = (1 << b->tile_bits) / kBatchThreads;
+  b->rows = (1 << b->tile_bits) > kBatchThreads ? (1 << b->tile_bits) / kBatchThreads : 1;
   if ((dt == HS_C64 ? level_fn<float>(b->rows) : level_fn<double>(b->rows)) == nullptr)
     return hs::report_error(HS_EINVAL, "batch tile_bits too large for complex128");
   const int T = b->tile_bits;
   if (o.smem_kb < 0 || size_t(o.smem_kb) * 1024 > hs::kSweepSmemMax)
     return hs::report_error(HS_EINVAL, "batch smem_kb must be 0..227");
-  const size_t budget = size_t(o.smem_kb > 0 ? o.smem_kb : 40) * 1024;
+  const size_t budget = size_t(o.smem_kb > 0 ? o.smem_kb : 24) * 1024;
 
   std::vector<BJob> hjobs;
   std::vector<BSweep> hsweeps;
@@ -339,6 +342,23 @@ extern "C" int hs_batch_create(const hs_batch_job* jobs, size_t n_jobs, const hs
       bs.n_mtab = n_mtab;
       bs.n_vt = n_vt;
       bs.stage_planes = planes;
+      bs.all_tables = 0;
+      bs.flane = 0;
+      {
+        const uint32_t thr_mask = uint32_t((1 << T) / b->rows - 1);
+        bool all = n_vt > 0;
+        for (size_t i = 0; i < w.factors.size(); ++i) {
+          const hs::Group& G = p.groups[w.factors[i]];
+          if (hfacs[bs.fac_off + i].vt < 0) all = false;
+          bool lane = true;
+          for (int sl = 0; sl < G.nslot; ++sl) {
+            const uint32_t u = p.slot_u[G.slot0 + sl];
+            if ((((u & bs.m0) | ((u >> bs.sh) & bs.m1)) & thr_mask) >= 32u) lane = false;
+          }
+          if (lane) bs.flane |= 1ull << i;
+        }
+        bs.all_tables = all ? 1 : 0;
+      }
       const size_t mb = hs::sweep::meta_bytes(n_mslot, n_mtab, n_vt, hs::elem_bytes(dt));
       int S = 1;
       while (S < 8 && S < bs.n_factors && mb + hs::sweep_smem_bytes(dt, 1, T, planes, S + 1) <= budget) ++S;

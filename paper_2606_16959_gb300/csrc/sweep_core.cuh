@@ -196,44 +196,71 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a, int nrb, T2* tile
   __syncthreads();
 }
 
-// Register-resident sweep: one row per thread, one state per tile, every
-// factor read from its value table.  The thread keeps its row's amplitude in
-// a register; a factor whose slots flip only lane bits gets its partner
-// amplitudes by warp shuffles (no shared memory, no barrier); any other factor
-// exchanges through one of two shared-memory buffers with one barrier (a
-// buffer is written again only after a later barrier, by which every thread
-// has finished reading it).  Each row's sum is the one the shared-memory path
-// forms, in the same slot order.
-template <typename T2>
+// Register-resident sweep: one state per tile, every factor read from its
+// value table.  The thread keeps its rows' amplitudes (local rows t + i * NT)
+// in registers.  A factor whose slots' local images U have no bits between the
+// lane bits (0..4) and the row-select bits (log2 NT and up) is applied without
+// shared memory or barriers: the partner of row i is row i ^ (U >> log2 NT) of
+// lane lane ^ (U & 31), fetched by a warp shuffle.  Any other factor exchanges
+// through one of two shared-memory buffers with one barrier (a buffer is
+// written again only after a later barrier, by which every thread has finished
+// reading it).  Each row's sum is the one the shared-memory path forms, in the
+// same slot order.
+template <typename T2, int ROWS>
 __device__ __forceinline__ void sweep_reg(const SweepArgs& a, T2* tile, T2* other, const SlotMeta* mslot,
-                                          const T2* vts, uint32_t grow, T2* dst_row) {
+                                          const T2* vts, const uint32_t (&grow)[ROWS], int NT, int lg_nt,
+                                          T2* dst_state) {
   cp_async_wait(0);
   __syncthreads();
-  T2 xr = tile[threadIdx.x];
+  T2 xr[ROWS];
+#pragma unroll
+  for (int i = 0; i < ROWS; ++i) xr[i] = tile[threadIdx.x + i * NT];
   bool second = false;
   for (int fi = 0; fi < a.n_factors; ++fi) {
     const int ns = a.fnslot[fi];
     const SlotMeta* ms = mslot + a.fmslot[fi];
-    const T2* tb = vts + a.fvts[fi] + pattern_of(grow, a.fsm[fi]) * uint32_t(ns);
-    T2 acc = T2{0, 0};
+    const T2* tb = vts + a.fvts[fi];
+    const uint32_t sm = a.fsm[fi];
+    uint32_t pat[ROWS];
+#pragma unroll
+    for (int i = 0; i < ROWS; ++i) pat[i] = pattern_of(grow[i], sm) * uint32_t(ns);
+    T2 acc[ROWS];
+#pragma unroll
+    for (int i = 0; i < ROWS; ++i) acc[i] = T2{0, 0};
     if ((a.flane >> fi) & 1ull) {
       for (int j = 0; j < ns; ++j) {
-        const int U = int(ms[j].U);
-        T2 x;
-        x.x = __shfl_xor_sync(0xffffffffu, xr.x, U);
-        x.y = __shfl_xor_sync(0xffffffffu, xr.y, U);
-        cfma(acc, tb[j], x);
+        const uint32_t U = ms[j].U;
+        const int hi = int(U >> lg_nt);
+        const int lane_x = int(U & 31u);
+#pragma unroll
+        for (int i = 0; i < ROWS; ++i) {
+          T2 src = xr[0];
+#pragma unroll
+          for (int k = 1; k < ROWS; ++k)
+            if (k == (i ^ hi)) src = xr[k];
+          T2 x;
+          x.x = __shfl_xor_sync(0xffffffffu, src.x, lane_x);
+          x.y = __shfl_xor_sync(0xffffffffu, src.y, lane_x);
+          cfma(acc[i], tb[pat[i] + j], x);
+        }
       }
     } else {
       T2* t = second ? other : tile;
-      t[threadIdx.x] = xr;
+#pragma unroll
+      for (int i = 0; i < ROWS; ++i) t[threadIdx.x + i * NT] = xr[i];
       __syncthreads();
-      for (int j = 0; j < ns; ++j) cfma(acc, tb[j], t[threadIdx.x ^ ms[j].U]);
+      for (int j = 0; j < ns; ++j) {
+        const uint32_t U = ms[j].U;
+#pragma unroll
+        for (int i = 0; i < ROWS; ++i) cfma(acc[i], tb[pat[i] + j], t[(threadIdx.x + uint32_t(i) * NT) ^ U]);
+      }
       second = !second;
     }
-    xr = acc;
+#pragma unroll
+    for (int i = 0; i < ROWS; ++i) xr[i] = acc[i];
   }
-  *dst_row = xr;
+#pragma unroll
+  for (int i = 0; i < ROWS; ++i) dst_state[grow[i]] = xr[i];
 }
 
 // Block of TS / ROWS threads; thread t owns local rows t + i * blockDim.x.
@@ -363,9 +390,9 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, uint32_t tile_id,
   uint32_t grow[ROWS];
 #pragma unroll
   for (int i = 0; i < ROWS; ++i) grow[i] = global_of(threadIdx.x + uint32_t(i) * NT, m0, m1, sh) | base;
-  if constexpr (ROWS == 1 && RB == 1) {
+  if constexpr (RB == 1) {
     if (a.all_tables) {
-      sweep_reg<T2>(a, tile, stages, mslot, vts, grow[0], dst + int64_t(rhs0) * a.N + grow[0]);
+      sweep_reg<T2, ROWS>(a, tile, stages, mslot, vts, grow, NT, __ffs(NT) - 1, dst + int64_t(rhs0) * a.N);
       return;
     }
   }
