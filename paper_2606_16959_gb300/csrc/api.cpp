@@ -394,12 +394,6 @@ int hs_build_factors_masks(const uint64_t* x, const uint64_t* z, const double* c
   double* d_cs = reinterpret_cast<double*>(d_blob + o_cs);
   e = hs::launch_sincos(reinterpret_cast<const double*>(d_blob + o_c), dt, d_cs, int(m), s);
   if (e == cudaSuccess)
-    e = hs::launch_build(fp, d_cs, reinterpret_cast<const uint64_t*>(d_blob + o_x),
-                         reinterpret_cast<const uint64_t*>(d_blob + o_z), reinterpret_cast<const uint32_t*>(d_blob + o_cx),
-                         reinterpret_cast<const int*>(d_blob + o_gf), reinterpret_cast<const int*>(d_blob + o_gl),
-                         reinterpret_cast<const uint64_t*>(d_blob + o_b), reinterpret_cast<const int*>(d_blob + o_xd),
-                         reinterpret_cast<const int*>(d_blob + o_pv), s);
-  if (e == cudaSuccess)
     e = hs::launch_value_tables(fp, d_cs, reinterpret_cast<const uint64_t*>(d_blob + o_x),
                                 reinterpret_cast<const uint64_t*>(d_blob + o_z),
                                 reinterpret_cast<const uint32_t*>(d_blob + o_cx),
@@ -408,6 +402,13 @@ int hs_build_factors_masks(const uint64_t* x, const uint64_t* z, const double* c
                                 reinterpret_cast<const int*>(d_blob + o_xd), reinterpret_cast<const int*>(d_blob + o_pv),
                                 reinterpret_cast<const uint32_t*>(d_blob + o_sm),
                                 reinterpret_cast<const int*>(d_blob + o_vt0), s);
+  if (e == cudaSuccess)
+    e = hs::launch_build(fp, d_cs, reinterpret_cast<const uint64_t*>(d_blob + o_x),
+                         reinterpret_cast<const uint64_t*>(d_blob + o_z), reinterpret_cast<const uint32_t*>(d_blob + o_cx),
+                         reinterpret_cast<const int*>(d_blob + o_gf), reinterpret_cast<const int*>(d_blob + o_gl),
+                         reinterpret_cast<const uint64_t*>(d_blob + o_b), reinterpret_cast<const int*>(d_blob + o_xd),
+                         reinterpret_cast<const int*>(d_blob + o_pv), reinterpret_cast<const uint32_t*>(d_blob + o_sm),
+                         reinterpret_cast<const int*>(d_blob + o_vt0), s);
   if (e != cudaSuccess) {
     cudaStreamSynchronize(s);
     release(f.release(), s);

@@ -36,6 +36,9 @@ struct BuildArgs {
   const int* xdim;
   const int* pivot;       // kMaxXDim per group
   int64_t N;
+  const uint32_t* smask;  // per group: support mask of its value table
+  const int* vt0;         // per group: first value-table entry, -1 if none
+  const void* vt;         // value tables (filled before the diagonals)
 };
 
 __device__ __forceinline__ double2 mul_ipow(double2 v, int k) {
@@ -109,16 +112,40 @@ struct GroupRows {
   }
 };
 
+__device__ __forceinline__ double2 load_val(const void* vals, int64_t idx, bool c64) {
+  if (c64) {
+    const float2 v = reinterpret_cast<const float2*>(vals)[idx];
+    return make_double2(v.x, v.y);
+  }
+  return reinterpret_cast<const double2*>(vals)[idx];
+}
+
 template <int MAXS>
 __global__ void __launch_bounds__(256) build_kernel(BuildArgs a, bool c64) {
   const int g = blockIdx.y;
   GroupRows<MAXS> G;
   G.load(a, g);
   const int D = a.fac_D[g], d0 = a.fac_diag0[g];
+  const int vt0 = a.vt0[g];
+  const uint32_t sm = a.smask[g];
 
   for (int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; r < a.N; r += int64_t(gridDim.x) * blockDim.x) {
     double2 w[MAXS];
-    G.row(a, uint64_t(r), w);
+    if (vt0 >= 0) {
+      // The row's values are those of its pattern at smask, already in the
+      // value table (rounded to the storage type, so copying them is exact).
+      uint32_t pat = 0;
+      int q = 0;
+      for (uint32_t t = sm; t; t &= t - 1u, ++q) pat |= uint32_t((uint64_t(r) >> (__ffs(t) - 1)) & 1u) << q;
+#pragma unroll
+      for (int s = 0; s < MAXS; ++s)
+        if (s < G.S) {
+          const double2 v = load_val(a.vt, int64_t(vt0) + int64_t(pat) * G.S + s, c64);
+          w[s] = make_double2(v.x, -v.y);  // the table holds conj(w)
+        }
+    } else {
+      G.row(a, uint64_t(r), w);
+    }
     // Row r of F: F[r, c] = conj(w[coord(r ^ c)]) when r ^ c lies in X.
     for (int k = 0; k < D; ++k) {
       const int64_t d = a.offs[d0 + k];
@@ -190,12 +217,13 @@ cudaError_t launch_sincos(const double* d_coeff, double dt, double* d_cs, int n,
 
 cudaError_t launch_build(const hs_factors* f, const double* d_cs, const uint64_t* d_x, const uint64_t* d_z,
                          const uint32_t* d_cx, const int* d_gfirst, const int* d_glast, const uint64_t* d_basis,
-                         const int* d_xdim, const int* d_pivot, cudaStream_t s) {
+                         const int* d_xdim, const int* d_pivot, const uint32_t* d_smask, const int* d_vt0,
+                         cudaStream_t s) {
   const Plan& p = f->plan;
   int maxdim = 0;
   for (const Group& g : p.groups) maxdim = g.xdim > maxdim ? g.xdim : maxdim;
   BuildArgs a{f->d_vals, f->d_offs, f->d_rowbase, f->d_fac_D, f->d_fac_diag0, d_cs, d_x, d_z, d_cx,
-              d_gfirst, d_glast, d_basis, d_xdim, d_pivot, p.N};
+              d_gfirst, d_glast, d_basis, d_xdim, d_pivot, p.N, d_smask, d_vt0, f->d_vt};
   const bool c64 = f->dtype == HS_C64;
   const int threads = 256;
   int64_t blocks_x = (p.N + threads - 1) / threads;
@@ -227,7 +255,7 @@ cudaError_t launch_value_tables(const hs_factors* f, const double* d_cs, const u
       maxbits = __builtin_popcount(g.smask) > maxbits ? __builtin_popcount(g.smask) : maxbits;
     }
   BuildArgs a{f->d_vals, f->d_offs, f->d_rowbase, f->d_fac_D, f->d_fac_diag0, d_cs, d_x, d_z, d_cx,
-              d_gfirst, d_glast, d_basis, d_xdim, d_pivot, p.N};
+              d_gfirst, d_glast, d_basis, d_xdim, d_pivot, p.N, d_smask, d_vt0, f->d_vt};
   const bool c64 = f->dtype == HS_C64;
   dim3 grid(unsigned(((1 << maxbits) + 255) / 256), unsigned(p.groups.size()));
   switch (maxdim) {

@@ -140,9 +140,11 @@ struct hs_factors {
 namespace hs {
 
 // Kernel launchers (defined in the .cu files).
+// Factor values; groups with a value table copy it (launch_value_tables first).
 cudaError_t launch_build(const hs_factors* f, const double* d_theta_cs, const uint64_t* d_x, const uint64_t* d_z,
                          const uint32_t* d_cx, const int* d_group_first, const int* d_group_last,
-                         const uint64_t* d_basis, const int* d_xdim, const int* d_pivot, cudaStream_t s);
+                         const uint64_t* d_basis, const int* d_xdim, const int* d_pivot, const uint32_t* d_smask,
+                         const int* d_vt0, cudaStream_t s);
 cudaError_t launch_sincos(const double* d_coeff, double dt, double* d_theta_cs, int n, cudaStream_t s);
 cudaError_t launch_value_tables(const hs_factors* f, const double* d_theta_cs, const uint64_t* d_x, const uint64_t* d_z,
                                 const uint32_t* d_cx, const int* d_group_first, const int* d_group_last,
