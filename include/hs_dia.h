@@ -96,6 +96,15 @@ int hs_estimate_timesteps(const hs_dia* a, double t, int diag_budget, double tol
  * HS_EINVAL, HS_ECUDA.  Enqueues only. */
 int hs_spmv(const hs_dia* a, const void* x, void* y, int n_rhs, void* cuda_stream);
 
+/* Expectation values <psi_r|A|psi_r> for n_rhs states (an observable on the
+ * compact-layout H; the paper itself evaluates state fidelities only).  psi: device buffer of A's dtype (n_rhs x 2^n, rhs-major).  Each row's
+ * (A psi)_i = sum_k A(i, i+d_k) psi[i+d_k] and conj(psi_i) (A psi)_i are
+ * formed and summed in FP64 (fixed-order tree, deterministic).  values: host
+ * array of 2 * n_rhs doubles (Re, Im per state); norms (may be NULL): host
+ * array of n_rhs doubles, <psi_r|psi_r>.  Errors: HS_EINVAL, HS_ENOMEM,
+ * HS_ECUDA.  Synchronises cuda_stream. */
+int hs_expectation(const hs_dia* a, const void* psi, int n_rhs, void* cuda_stream, double* values, double* norms);
+
 /* psi <- U^n_steps psi (the loop of Alg. 3), psi in U's dtype, updated in
  * place (n_rhs x 2^n).  A one-diagonal U (offset 0) is applied in place; a
  * general U ping-pongs with a stream-ordered scratch state.  Errors:

@@ -6,7 +6,8 @@ diagonals dropped (the numeric counts of Tab. 3), the diagonal-pair product of
 two such matrices (SpGEMM paragraph, Sec. 3.3), the truncated Taylor
 exponential (Alg. 2), the diagonal-budget step search (Eq. 5 and the adaptive
 timestep flowchart of Sec. 3.1), and the repeated diagonal-times-vector
-evolution (Alg. 1 inside Alg. 3).  Only ``tests/``, ``__graft_entry__.smoke()``
+evolution (Alg. 1 inside Alg. 3), plus expectation values <psi|A|psi> on the
+compact layout.  Only ``tests/``, ``__graft_entry__.smoke()``
 and ``bench.py``'s CPU-baseline leg may use it; the product package never does.
 
 A matrix is a ``Dia``: N and {offset d: values}, the value of entry
@@ -30,7 +31,8 @@ Readings of the paper used here (it is silent or ambiguous on each):
 
 Parity status: every function is pinned by tests/test_taylor_pins.py (dense
 Kronecker sums, numpy matrix products, eigh-based exponentials with the Taylor
-remainder bound, elementwise exponentials, brute-force step scans, Tab. 3).
+remainder bound, elementwise exponentials, brute-force step scans, Tab. 3,
+dense quadratic forms and a closed-form eigenstate energy).
 """
 from __future__ import annotations
 
@@ -211,6 +213,13 @@ def spmv(A: Dia, x) -> np.ndarray:
         i = np.arange(lo, hi)
         y[..., i] += v[np.minimum(i, i + d)] * x[..., i + d]
     return y
+
+
+def expectation(A: Dia, psi) -> np.ndarray:
+    """<psi|A|psi> per state (rows of psi): the plain definition, conj(psi) . (A psi)."""
+    x = np.atleast_2d(np.asarray(psi, dtype=np.complex128))
+    y = spmv(A, x)
+    return np.array([np.vdot(x[k], y[k]) for k in range(x.shape[0])])
 
 
 def evolve(U: Dia, psi, n_steps: int) -> np.ndarray:

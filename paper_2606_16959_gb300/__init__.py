@@ -10,5 +10,5 @@ from .hs import (  # noqa: F401
     hs_apply_factor, hs_autotune, hs_build_factors, hs_build_factors_masks, hs_evolve, hs_evolve_ex, hs_evolve_plan, hs_fidelity,
     hs_inner_device, hs_plan_factors,
     Dia, hs_dia_convert, hs_dia_create, hs_dia_evolve, hs_dia_from_masks, hs_dia_from_terms, hs_estimate_timesteps,
-    hs_spgemm, hs_spme, hs_spmv,
+    hs_spgemm, hs_spme, hs_spmv, hs_expectation, hs_kernel_launches,
 )

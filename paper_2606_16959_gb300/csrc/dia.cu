@@ -437,6 +437,81 @@ __global__ void __launch_bounds__(32 * W) spmv_kernel(const typename CT<R>::T2* 
   }
 }
 
+// Expectation values: block b of state r sums conj(psi_i) (A psi)_i and |psi_i|^2
+// over a grid-stride set of rows in FP64; partial[r * gridDim.x + b] gets the
+// block sums (re, im, norm, unused).
+template <typename T2>
+__global__ void __launch_bounds__(kThreads) expect_kernel(const T2* __restrict__ vals,
+                                                          const int64_t* __restrict__ meta, int D,
+                                                          const T2* __restrict__ psi, int64_t N, double4* partial) {
+  const int r = blockIdx.y;
+  const T2* x = psi + int64_t(r) * N;
+  const int64_t* offs = meta;
+  const int64_t* rb = meta + D;
+  double re = 0.0, im = 0.0, nn = 0.0;
+  for (int64_t i = int64_t(blockIdx.x) * kThreads + threadIdx.x; i < N; i += int64_t(gridDim.x) * kThreads) {
+    double yr = 0.0, yi = 0.0;
+    for (int k = 0; k < D; ++k) {
+      const int64_t c = i + __ldg(offs + k);
+      if (uint64_t(c) >= uint64_t(N)) continue;
+      const double2 v = ld(vals, __ldg(rb + k) + i), u = ld(x, c);
+      yr = fma(v.x, u.x, fma(-v.y, u.y, yr));
+      yi = fma(v.x, u.y, fma(v.y, u.x, yi));
+    }
+    const double2 p = ld(x, i);
+    re = fma(p.x, yr, fma(p.y, yi, re));   // conj(p) * y
+    im = fma(p.x, yi, fma(-p.y, yr, im));
+    nn = fma(p.x, p.x, fma(p.y, p.y, nn));
+  }
+  __shared__ double part_re[kThreads / 32], part_im[kThreads / 32], part_nn[kThreads / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    re += __shfl_xor_sync(0xffffffffu, re, o);
+    im += __shfl_xor_sync(0xffffffffu, im, o);
+    nn += __shfl_xor_sync(0xffffffffu, nn, o);
+  }
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    part_re[wid] = re;
+    part_im[wid] = im;
+    part_nn[wid] = nn;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+    for (int w = 0; w < kThreads / 32; ++w) {
+      a0 += part_re[w];
+      a1 += part_im[w];
+      a2 += part_nn[w];
+    }
+    partial[int64_t(r) * gridDim.x + blockIdx.x] = make_double4(a0, a1, a2, 0.0);
+  }
+}
+
+// One block per state: the blocks' partial sums in block order.
+__global__ void __launch_bounds__(kThreads) expect_final(const double4* partial, int nb, double4* out) {
+  const int r = blockIdx.x;
+  __shared__ double4 sh[kThreads];
+  double4 acc = make_double4(0.0, 0.0, 0.0, 0.0);
+  for (int b = threadIdx.x; b < nb; b += kThreads) {
+    const double4 p = partial[int64_t(r) * nb + b];
+    acc.x += p.x;
+    acc.y += p.y;
+    acc.z += p.z;
+  }
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int st = kThreads / 2; st > 0; st >>= 1) {
+    if (int(threadIdx.x) < st) {
+      sh[threadIdx.x].x += sh[threadIdx.x + st].x;
+      sh[threadIdx.x].y += sh[threadIdx.x + st].y;
+      sh[threadIdx.x].z += sh[threadIdx.x + st].z;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[r] = sh[0];
+}
+
 // psi[r][i] *= v[i] in place (one diagonal, offset 0).
 template <typename R>
 __global__ void __launch_bounds__(kThreads) scale_rows_kernel(const typename CT<R>::T2* __restrict__ v,
@@ -1246,6 +1321,41 @@ int hs_spmv(const hs_dia* a, const void* x, void* y, int n_rhs, void* cuda_strea
   cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
   cudaError_t e = launch_spmv(a, x, y, n_rhs, s, false);
   if (e != cudaSuccess) return cuda_err(e, "spmv launch");
+  return HS_OK;
+}
+
+int hs_expectation(const hs_dia* a, const void* psi, int n_rhs, void* cuda_stream, double* values, double* norms) {
+  int rc = check_matrix(a, "a");
+  if (rc) return rc;
+  if (!psi || !values) return report_error(HS_EINVAL, "null argument");
+  if (!aligned16(psi)) return report_error(HS_EINVAL, "psi must be 16-byte aligned");
+  if (n_rhs < 1 || n_rhs > 65535) return report_error(HS_EINVAL, "n_rhs must be 1..65535");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+  const int nb = int(std::max<int64_t>(1, std::min<int64_t>((a->N + kThreads - 1) / kThreads, 152 * 4)));
+  DevBuf part, out;
+  cudaError_t e = part.alloc(size_t(nb) * n_rhs * sizeof(double4), s);
+  if (e == cudaSuccess) e = out.alloc(size_t(n_rhs) * sizeof(double4), s);
+  if (e != cudaSuccess) return cuda_err(e, "expectation buffers");
+  const int D = int(a->offs.size());
+  const dim3 grid{unsigned(nb), unsigned(n_rhs), 1u};
+  if (a->dtype == HS_C64)
+    expect_kernel<float2><<<grid, kThreads, 0, s>>>((const float2*)a->d_vals, (const int64_t*)a->d_meta, D,
+                                                    (const float2*)psi, a->N, part.as<double4>());
+  else
+    expect_kernel<double2><<<grid, kThreads, 0, s>>>((const double2*)a->d_vals, (const int64_t*)a->d_meta, D,
+                                                     (const double2*)psi, a->N, part.as<double4>());
+  expect_final<<<unsigned(n_rhs), kThreads, 0, s>>>(part.as<double4>(), nb, out.as<double4>());
+  hs::note_launches(2);
+  std::vector<double4> h(n_rhs);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), out.p, h.size() * sizeof(double4), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_err(e, "expectation");
+  for (int r = 0; r < n_rhs; ++r) {
+    values[2 * r] = h[r].x;
+    values[2 * r + 1] = h[r].y;
+    if (norms) norms[r] = h[r].z;
+  }
   return HS_OK;
 }
 

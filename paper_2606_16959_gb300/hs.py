@@ -29,7 +29,7 @@ EXPORTS = (
     "hs_batch_free_async",
     "hs_dia_from_terms", "hs_dia_from_masks", "hs_dia_create", "hs_spgemm", "hs_spme", "hs_estimate_timesteps",
     "hs_spmv", "hs_dia_evolve", "hs_dia_convert", "hs_dia_info", "hs_dia_get", "hs_dia_free",
-    "hs_kernel_launches",
+    "hs_kernel_launches", "hs_expectation",
 )
 
 
@@ -111,6 +111,7 @@ def lib() -> ctypes.CDLL:
         L.hs_dia_get.argtypes = [vp, i64p, dp]
         L.hs_dia_free.argtypes = [vp]
         L.hs_dia_free.restype = None
+        L.hs_expectation.argtypes = [vp, vp, i, vp, dp, dp]
         L.hs_kernel_launches.argtypes = []
         L.hs_kernel_launches.restype = ctypes.c_uint64
         for name in EXPORTS:
@@ -534,3 +535,13 @@ def hs_dia_evolve(u: Dia, psi, n_steps: int, stream=None) -> None:
 
 def hs_dia_convert(a: Dia, dtype, stream=None) -> Dia:
     return _new_dia(lib().hs_dia_convert, a.handle, _dtype_code(dtype), _stream(stream))
+
+
+def hs_expectation(a: Dia, psi, stream=None):
+    """(<psi_r|A|psi_r> as complex128 array of n_rhs, <psi_r|psi_r> array), FP64."""
+    p, n_rhs = _dia_state(a, psi)
+    vals = np.zeros(2 * n_rhs, dtype=np.float64)
+    norms = np.zeros(n_rhs, dtype=np.float64)
+    _check(lib().hs_expectation(a.handle, p, n_rhs, _stream(stream), vals.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                norms.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return vals.view(np.complex128), norms

@@ -241,3 +241,19 @@ def test_taylor_evolution_tracks_exact():
     assert K > 4
     Ubad = OT.expm_taylor(A, 1.0 / r, 1e-6, K - 5)[0]
     assert np.linalg.norm(OT.evolve(Ubad, psi, r) - want) > r * 1e-6 / (1 - nx / (K + 1))
+
+
+def test_expectation_dense_and_eigenstate():
+    """<psi|H|psi> equals the dense quadratic form; a TFIM at h = 0 has |0...0> as
+    an eigenstate with energy -J * (number of bonds)."""
+    rng = np.random.default_rng(31)
+    ham = W.heisenberg_chain(5, rng.uniform(0.5, 1.5, 5), periodic=True)
+    H = dense_h(ham.labels, ham.coeffs)
+    psi = np.stack([W.gaussian_state(5, rng) for _ in range(3)])
+    got = OT.expectation(_dia(ham), psi)
+    want = np.einsum("ri,ij,rj->r", psi.conj(), H, psi)
+    assert np.max(np.abs(got - want)) < 1e-13
+    assert np.max(np.abs(got.imag)) < 1e-13  # Hermitian
+    tf = W.tfim_chain(6, 0.8, 0.0, periodic=False)
+    e = OT.expectation(_dia(tf), W.basis_state(6))
+    assert abs(e[0] - (-0.8 * 5)) < 1e-14
