@@ -8,7 +8,8 @@ Python half (this file): Pauli-label parsing, the budgeted next-fit grouping
 with its structural offset sets (the structural dry run of the diagonal-set
 estimation paragraph, Sec. 3.2), and the canonical diagonal order of Tab. 1.
 Numeric half (``hs_oracle.c``, loaded through ctypes): Pauli rotations,
-direct Trotter evolution (Eq. 4), factor materialisation into the compact
+direct Trotter evolution (Eq. 4) and, in Python over the same rotations, the
+second- and fourth-order product formulas, factor materialisation into the compact
 layout (Eq. 6), the diagonal-times-vector product (Alg. 1), pairwise sums.
 
 Readings of the paper used here (the paper is silent or ambiguous on each):
@@ -258,6 +259,58 @@ def evolve_direct(x, z, coeffs, t: float, n_steps: int, psi) -> np.ndarray:
     _lib().orc_evolve_direct(shape[-1], psi2.shape[0], len(x), _ptr(x, ctypes.c_uint64),
                              _ptr(z, ctypes.c_uint64), c.ctypes.data, float(t), int(n_steps), psi2.ctypes.data)
     return psi2.reshape(shape)
+
+
+# ----------------------------------------------------------------------------
+# Higher-order product formulas (the paper's future-work passage on second-
+# and fourth-order formulas; readings: symmetric Strang splitting and Suzuki's
+# fourth-order recursion of it)
+# ----------------------------------------------------------------------------
+
+SUZUKI_P = 1.0 / (4.0 - 4.0 ** (1.0 / 3.0))
+
+
+def step_stages(order: int, dt: float):
+    """One step of the product formula of the given order as a list of
+    (angle scale h, direction): every term j is applied as exp(-i c_j h P_j),
+    terms in input order for direction +1 and in reverse order for -1.
+      order 1: [(dt, +1)]
+      order 2 (Strang): [(dt/2, +1), (dt/2, -1)]
+      order 4 (Suzuki): S2(p dt) S2(p dt) S2((1-4p) dt) S2(p dt) S2(p dt), p = 1/(4 - 4^(1/3))."""
+    if order == 1:
+        return [(dt, 1)]
+    if order == 2:
+        return [(dt * 0.5, 1), (dt * 0.5, -1)]
+    if order == 4:
+        hp = (SUZUKI_P * dt) * 0.5
+        hq = ((1.0 - 4.0 * SUZUKI_P) * dt) * 0.5
+        out = []
+        for h in (hp, hp, hq, hp, hp):
+            out += [(h, 1), (h, -1)]
+        return out
+    raise ValueError("order must be 1, 2 or 4")
+
+
+def evolve_direct_order(x, z, coeffs, t: float, n_steps: int, psi, order: int) -> np.ndarray:
+    """Direct evolution by the product formula of the given order (term by term,
+    FP64); psi is (N,) or (n_rhs, N); returns a copy."""
+    psi = _c128(psi).copy()
+    shape = psi.shape
+    rows = psi.reshape(-1, shape[-1])
+    x, z = _u64(x), _u64(z)
+    c = np.asarray(coeffs, dtype=np.float64)
+    dt = float(t) / float(n_steps)
+    lib = _lib()
+    stages = step_stages(order, dt)
+    for r in range(rows.shape[0]):
+        row = np.ascontiguousarray(rows[r])
+        for _ in range(n_steps):
+            for h, direction in stages:
+                js = range(len(x)) if direction > 0 else range(len(x) - 1, -1, -1)
+                for j in js:
+                    lib.orc_rotate(row.size, int(x[j]), int(z[j]), float(c[j]) * h, row.ctypes.data)
+        rows[r] = row
+    return rows.reshape(shape)
 
 
 def dia_apply(offsets, starts, values, xvec) -> np.ndarray:
