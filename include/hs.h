@@ -88,6 +88,27 @@ int hs_build_factors_masks(const uint64_t* x, const uint64_t* z, const double* c
                            int n_qubits, double t, int n_steps, int diag_budget, hs_dtype dtype,
                            void* cuda_stream, hs_factors** out);
 
+/* Same with a product formula of the given order (the higher-order formulas
+ * the paper names as future work; readings of this library): 1 = the
+ * first-order step above; 2 = symmetric Strang splitting, one step applying
+ * every term with angle c_j dt/2 in input order and then in reverse order;
+ * 4 = Suzuki's fourth-order recursion S2(p dt) S2(p dt) S2((1-4p) dt) S2(p dt)
+ * S2(p dt), p = 1/(4 - 4^(1/3)), of that Strang step S2.  The grouping is the
+ * first-order one; for order 2 each group is stored twice (forward factor
+ * F_g = R_last ... R_first and reversed factor R_first ... R_last, both at
+ * dt/2), for order 4 twice per angle (p dt/2 and (1-4p) dt/2).  One step
+ * applies the factors hs_factors_sequence lists.  Errors as hs_build_factors,
+ * and HS_EINVAL for another order. */
+int hs_build_factors_ex(const uint64_t* x, const uint64_t* z, const double* coeffs, size_t n_terms,
+                        int n_qubits, double t, int n_steps, int diag_budget, int order, hs_dtype dtype,
+                        void* cuda_stream, hs_factors** out);
+
+/* The product-formula order of a factor set and the factors one step applies
+ * (indices for hs_factor_get, in application order).  seq may be NULL (then
+ * only the length is returned); otherwise it holds capacity ints.  Errors:
+ * HS_EINVAL (NULL f, capacity too small). */
+int hs_factors_sequence(const hs_factors* f, int* order, int* seq, int capacity, int* seq_len);
+
 /* Structural dry run on the host only (no GPU call): the grouping, each
  * factor's offsets in canonical order and the device bytes of the padded
  * factor values -- what the diagonal-set estimation paragraph (Sec. 3.2)

@@ -142,8 +142,13 @@ PlanCache& plan_cache() {
   static PlanCache c;
   return c;
 }
-std::string plan_key(const uint64_t* x, size_t n, int n_qubits, int budget, hs_dtype dt) {
+// The z masks are part of the key: a factor's value table is indexed by the
+// qubits its terms touch through x or z.
+std::string plan_key(const uint64_t* x, const uint64_t* z, size_t n, int n_qubits, int budget, hs_dtype dt,
+                     int order) {
   std::string k(reinterpret_cast<const char*>(x), n * sizeof(uint64_t));
+  k.append(reinterpret_cast<const char*>(z), n * sizeof(uint64_t));
+  k.append(reinterpret_cast<const char*>(&order), sizeof(int));
   k.append(reinterpret_cast<const char*>(&n_qubits), sizeof(int));
   k.append(reinterpret_cast<const char*>(&budget), sizeof(int));
   const int d = int(dt);
@@ -151,8 +156,8 @@ std::string plan_key(const uint64_t* x, size_t n, int n_qubits, int budget, hs_d
   return k;
 }
 int cached_plan(const uint64_t* x, const uint64_t* z, const double* coeff, size_t n, int n_qubits, int budget,
-                hs_dtype dt, hs::Plan& plan, std::string* err) {
-  const std::string key = plan_key(x, n, n_qubits, budget, dt);
+                hs_dtype dt, int order, hs::Plan& plan, std::string* err) {
+  const std::string key = plan_key(x, z, n, n_qubits, budget, dt, order);
   PlanCache& c = plan_cache();
   {
     std::lock_guard<std::mutex> lk(c.mu);
@@ -165,7 +170,7 @@ int cached_plan(const uint64_t* x, const uint64_t* z, const double* coeff, size_
     }
   }
   if (plan.n_qubits == 0) {
-    int rc = hs::make_plan(x, z, coeff, n, n_qubits, budget, dt, plan, err);
+    int rc = hs::make_plan(x, z, coeff, n, n_qubits, budget, dt, plan, err, order);
     if (rc != HS_OK) return rc;
     std::lock_guard<std::mutex> lk(c.mu);
     if (c.map.find(key) == c.map.end()) {
@@ -301,9 +306,9 @@ const char* hs_last_error(void) { return g_err.c_str(); }
 
 uint64_t hs_kernel_launches(void) { return hs::g_launches.load(std::memory_order_relaxed); }
 
-int hs_build_factors_masks(const uint64_t* x, const uint64_t* z, const double* coeffs, size_t n_terms, int n_qubits,
-                           double t, int n_steps, int diag_budget, hs_dtype dtype, void* cuda_stream,
-                           hs_factors** out) {
+int hs_build_factors_ex(const uint64_t* x, const uint64_t* z, const double* coeffs, size_t n_terms, int n_qubits,
+                        double t, int n_steps, int diag_budget, int order, hs_dtype dtype, void* cuda_stream,
+                        hs_factors** out) {
   if (!out) return fail(HS_EINVAL, "out is NULL");
   *out = nullptr;
   if (!x || !z || !coeffs) return fail(HS_EINVAL, "null term arrays");
@@ -313,7 +318,8 @@ int hs_build_factors_masks(const uint64_t* x, const uint64_t* z, const double* c
   if (diag_budget < 1) return fail(HS_EINVAL, "diag_budget must be >= 1");
   std::unique_ptr<hs_factors> f(new hs_factors());
   std::string err;
-  int rc = cached_plan(x, z, coeffs, n_terms, n_qubits, diag_budget, dtype, f->plan, &err);
+  if (order != 1 && order != 2 && order != 4) return fail(HS_EINVAL, "order must be 1, 2 or 4");
+  int rc = cached_plan(x, z, coeffs, n_terms, n_qubits, diag_budget, dtype, order, f->plan, &err);
   if (rc != HS_OK) return fail(rc, err);
   f->dtype = dtype;
   f->n_steps = n_steps;
@@ -338,7 +344,8 @@ int hs_build_factors_masks(const uint64_t* x, const uint64_t* z, const double* c
   }
   fp->d_vt = static_cast<unsigned char*>(fp->d_vals) + size_t(p.total_elems) * hs::elem_bytes(dtype);
   const size_t m = n_terms;
-  std::vector<int> fD(G), fd0(G), gfirst(G), glast(G), xdim(G), pivot(G * hs::kMaxXDim, 0), vt0(G);
+  std::vector<int> fD(G), fd0(G), gfirst(G), glast(G), xdim(G), pivot(G * hs::kMaxXDim, 0), vt0(G), gkind(G),
+      gdir(G);
   std::vector<uint32_t> smask(G);
   std::vector<uint64_t> basis(G * hs::kMaxXDim, 0);
   for (int g = 0; g < G; ++g) {
@@ -350,6 +357,8 @@ int hs_build_factors_masks(const uint64_t* x, const uint64_t* z, const double* c
     xdim[g] = gr.xdim;
     smask[g] = gr.smask;
     vt0[g] = gr.vt0;
+    gkind[g] = gr.kind;
+    gdir[g] = gr.dir;
     for (int i = 0; i < gr.xdim; ++i) {
       basis[g * hs::kMaxXDim + i] = gr.basis[i];
       pivot[g * hs::kMaxXDim + i] = gr.pivot[i];
@@ -371,7 +380,10 @@ int hs_build_factors_masks(const uint64_t* x, const uint64_t* z, const double* c
   const size_t o_b = put(basis.data(), basis.size() * 8), o_xd = put(xdim.data(), G * 4);
   const size_t o_pv = put(pivot.data(), pivot.size() * 4);
   const size_t o_sm = put(smask.data(), G * 4), o_vt0 = put(vt0.data(), G * 4);
-  const size_t o_cs = put(nullptr, m * 16);  // (cos, sin) per term, written on the device
+  const size_t o_kind = put(gkind.data(), G * 4), o_dir = put(gdir.data(), G * 4);
+  const std::vector<double> hk = hs::kind_steps(p.order, t / double(n_steps));
+  const size_t o_h = put(hk.data(), hk.size() * 8);
+  const size_t o_cs = put(nullptr, m * 16 * hk.size());  // (cos, sin) per term and angle kind, written on the device
   unsigned char* d_blob = nullptr;
   if ((rc = guard(hs::pool_malloc((void**)&d_blob, blob.size(), s), "cudaMallocAsync(tables)"))) {
     release(f.release(), s);
@@ -390,9 +402,9 @@ int hs_build_factors_masks(const uint64_t* x, const uint64_t* z, const double* c
     release(f.release(), s);
     return rc;
   }
-  const double dt = t / double(n_steps);
   double* d_cs = reinterpret_cast<double*>(d_blob + o_cs);
-  e = hs::launch_sincos(reinterpret_cast<const double*>(d_blob + o_c), dt, d_cs, int(m), s);
+  e = hs::launch_sincos(reinterpret_cast<const double*>(d_blob + o_c), reinterpret_cast<const double*>(d_blob + o_h),
+                        int(hk.size()), d_cs, int(m), s);
   if (e == cudaSuccess)
     e = hs::launch_value_tables(fp, d_cs, reinterpret_cast<const uint64_t*>(d_blob + o_x),
                                 reinterpret_cast<const uint64_t*>(d_blob + o_z),
@@ -401,20 +413,40 @@ int hs_build_factors_masks(const uint64_t* x, const uint64_t* z, const double* c
                                 reinterpret_cast<const uint64_t*>(d_blob + o_b),
                                 reinterpret_cast<const int*>(d_blob + o_xd), reinterpret_cast<const int*>(d_blob + o_pv),
                                 reinterpret_cast<const uint32_t*>(d_blob + o_sm),
-                                reinterpret_cast<const int*>(d_blob + o_vt0), s);
+                                reinterpret_cast<const int*>(d_blob + o_vt0), reinterpret_cast<const int*>(d_blob + o_kind),
+                                reinterpret_cast<const int*>(d_blob + o_dir), s);
   if (e == cudaSuccess)
     e = hs::launch_build(fp, d_cs, reinterpret_cast<const uint64_t*>(d_blob + o_x),
                          reinterpret_cast<const uint64_t*>(d_blob + o_z), reinterpret_cast<const uint32_t*>(d_blob + o_cx),
                          reinterpret_cast<const int*>(d_blob + o_gf), reinterpret_cast<const int*>(d_blob + o_gl),
                          reinterpret_cast<const uint64_t*>(d_blob + o_b), reinterpret_cast<const int*>(d_blob + o_xd),
                          reinterpret_cast<const int*>(d_blob + o_pv), reinterpret_cast<const uint32_t*>(d_blob + o_sm),
-                         reinterpret_cast<const int*>(d_blob + o_vt0), s);
+                         reinterpret_cast<const int*>(d_blob + o_vt0), reinterpret_cast<const int*>(d_blob + o_kind),
+                         reinterpret_cast<const int*>(d_blob + o_dir), s);
   if (e != cudaSuccess) {
     cudaStreamSynchronize(s);
     release(f.release(), s);
     return cuda_fail(e, "factor build launch");
   }
   *out = f.release();
+  return HS_OK;
+}
+
+int hs_build_factors_masks(const uint64_t* x, const uint64_t* z, const double* coeffs, size_t n_terms, int n_qubits,
+                           double t, int n_steps, int diag_budget, hs_dtype dtype, void* cuda_stream,
+                           hs_factors** out) {
+  return hs_build_factors_ex(x, z, coeffs, n_terms, n_qubits, t, n_steps, diag_budget, 1, dtype, cuda_stream, out);
+}
+
+int hs_factors_sequence(const hs_factors* f, int* order, int* seq, int capacity, int* seq_len) {
+  if (!f) return fail(HS_EINVAL, "factors is NULL");
+  const std::vector<int>& q = f->plan.step_seq;
+  if (order) *order = f->plan.order;
+  if (seq_len) *seq_len = int(q.size());
+  if (seq) {
+    if (capacity < int(q.size())) return fail(HS_EINVAL, "seq capacity too small");
+    for (size_t k = 0; k < q.size(); ++k) seq[k] = q[k];
+  }
   return HS_OK;
 }
 

@@ -291,7 +291,7 @@ extern "C" int hs_batch_create(const hs_batch_job* jobs, size_t n_jobs, const hs
   for (size_t j = 0; j < n_jobs; ++j) {
     const hs_batch_job& J = jobs[j];
     const hs::Plan& p = J.factors->plan;
-    b->updates += int64_t(J.n_steps) * int64_t(p.groups.size()) * p.N * J.n_rhs;
+    b->updates += int64_t(J.n_steps) * int64_t(p.step_seq.size()) * p.N * J.n_rhs;
     if (J.n_steps == 0) continue;
     std::vector<hs::Sweep> sw = p.n_qubits >= T ? hs::plan_sweeps(p, J.n_steps, T, b->low_bits, true)
                                                 : std::vector<hs::Sweep>{};

@@ -39,6 +39,9 @@ struct BuildArgs {
   const uint32_t* smask;  // per group: support mask of its value table
   const int* vt0;         // per group: first value-table entry, -1 if none
   const void* vt;         // value tables (filled before the diagonals)
+  const int* kind;        // per group: angle kind (cs holds m (cos, sin) pairs per kind)
+  const int* dir;         // per group: +1 terms first..last act in order, -1 reversed
+  int m;                  // number of terms
 };
 
 __device__ __forceinline__ double2 mul_ipow(double2 v, int k) {
@@ -60,7 +63,8 @@ __device__ __forceinline__ void store_val(void* vals, int64_t idx, double2 v, bo
 // Group g's basis, pivots, slot x-masks and term range, read once per thread.
 template <int MAXS>
 struct GroupRows {
-  int xd, S, first, last;
+  int xd, S, first, last, dir;
+  const double* cs;  // this group's angle kind
   uint64_t bas[kMaxXDim];
   int piv[kMaxXDim];
   uint64_t u[MAXS];
@@ -74,6 +78,8 @@ struct GroupRows {
     }
     first = a.gfirst[g];
     last = a.glast[g];
+    dir = a.dir[g];
+    cs = a.cs + size_t(2) * a.m * a.kind[g];
 #pragma unroll
     for (int s = 0; s < MAXS; ++s) {
       uint64_t m = 0;
@@ -84,13 +90,17 @@ struct GroupRows {
     }
   }
   // w[s] = slot s of F_g^dagger e_r (the conjugate of row r of F_g at column
-  // r ^ u_s), by applying R_j^dagger = cos I + i sin P_j for j = last-1 .. first.
+  // r ^ u_s), by applying R_j^dagger = cos I + i sin P_j in the reverse of the
+  // order in which F_g applies the R_j: j = last-1 .. first for a forward
+  // factor (F_g = R_last ... R_first), j = first .. last-1 for a reversed one.
   __device__ __forceinline__ void row(const BuildArgs& a, uint64_t r, double2 (&w)[MAXS]) const {
     double2 nw[MAXS];
 #pragma unroll
     for (int s = 0; s < MAXS; ++s) w[s] = make_double2(s == 0 ? 1.0 : 0.0, 0.0);
-    for (int j = last - 1; j >= first; --j) {
-      const double c = a.cs[2 * j], sn = a.cs[2 * j + 1];
+    const int n_t = last - first;
+    for (int q = 0; q < n_t; ++q) {
+      const int j = dir > 0 ? last - 1 - q : first + q;
+      const double c = cs[2 * j], sn = cs[2 * j + 1];
       const uint64_t xj = a.x[j], zj = a.z[j];
       const int y = __popcll(xj & zj);
       const uint32_t cxj = a.cx[j];
@@ -196,21 +206,23 @@ __global__ void __launch_bounds__(256) value_table_kernel(BuildArgs a, const uin
     if (s < G.S) store_val(vt, int64_t(vt0[g]) + int64_t(p) * G.S + s, make_double2(w[s].x, -w[s].y), c64);
 }
 
-__global__ void sincos_kernel(const double* coeff, double dt, double* cs, int n) {
-  int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j < n) {
-    const double theta = coeff[j] * dt;
+// cs[2 (k n + j) + {0, 1}] = (cos, sin)(coeff[j] * h[k]) for kind k.
+__global__ void sincos_kernel(const double* coeff, const double* h, int n_kinds, double* cs, int n) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n * n_kinds) {
+    const int k = e / n, j = e - k * n;
+    const double theta = coeff[j] * h[k];
     double s, c;
     sincos(theta, &s, &c);
-    cs[2 * j] = c;
-    cs[2 * j + 1] = s;
+    cs[2 * e] = c;
+    cs[2 * e + 1] = s;
   }
 }
 
 }  // namespace
 
-cudaError_t launch_sincos(const double* d_coeff, double dt, double* d_cs, int n, cudaStream_t s) {
-  sincos_kernel<<<(n + 127) / 128, 128, 0, s>>>(d_coeff, dt, d_cs, n);
+cudaError_t launch_sincos(const double* d_coeff, const double* d_h, int n_kinds, double* d_cs, int n, cudaStream_t s) {
+  sincos_kernel<<<(n * n_kinds + 127) / 128, 128, 0, s>>>(d_coeff, d_h, n_kinds, d_cs, n);
   note_launches();
   return cudaGetLastError();
 }
@@ -218,12 +230,13 @@ cudaError_t launch_sincos(const double* d_coeff, double dt, double* d_cs, int n,
 cudaError_t launch_build(const hs_factors* f, const double* d_cs, const uint64_t* d_x, const uint64_t* d_z,
                          const uint32_t* d_cx, const int* d_gfirst, const int* d_glast, const uint64_t* d_basis,
                          const int* d_xdim, const int* d_pivot, const uint32_t* d_smask, const int* d_vt0,
-                         cudaStream_t s) {
+                         const int* d_kind, const int* d_dir, cudaStream_t s) {
   const Plan& p = f->plan;
   int maxdim = 0;
   for (const Group& g : p.groups) maxdim = g.xdim > maxdim ? g.xdim : maxdim;
   BuildArgs a{f->d_vals, f->d_offs, f->d_rowbase, f->d_fac_D, f->d_fac_diag0, d_cs, d_x, d_z, d_cx,
-              d_gfirst, d_glast, d_basis, d_xdim, d_pivot, p.N, d_smask, d_vt0, f->d_vt};
+              d_gfirst, d_glast, d_basis, d_xdim, d_pivot, p.N, d_smask, d_vt0, f->d_vt, d_kind, d_dir,
+              int(p.x.size())};
   const bool c64 = f->dtype == HS_C64;
   const int threads = 256;
   int64_t blocks_x = (p.N + threads - 1) / threads;
@@ -245,7 +258,7 @@ cudaError_t launch_build(const hs_factors* f, const double* d_cs, const uint64_t
 cudaError_t launch_value_tables(const hs_factors* f, const double* d_cs, const uint64_t* d_x, const uint64_t* d_z,
                                 const uint32_t* d_cx, const int* d_gfirst, const int* d_glast, const uint64_t* d_basis,
                                 const int* d_xdim, const int* d_pivot, const uint32_t* d_smask, const int* d_vt0,
-                                cudaStream_t s) {
+                                const int* d_kind, const int* d_dir, cudaStream_t s) {
   const Plan& p = f->plan;
   if (p.total_vt == 0) return cudaSuccess;
   int maxdim = 0, maxbits = 0;
@@ -255,7 +268,8 @@ cudaError_t launch_value_tables(const hs_factors* f, const double* d_cs, const u
       maxbits = __builtin_popcount(g.smask) > maxbits ? __builtin_popcount(g.smask) : maxbits;
     }
   BuildArgs a{f->d_vals, f->d_offs, f->d_rowbase, f->d_fac_D, f->d_fac_diag0, d_cs, d_x, d_z, d_cx,
-              d_gfirst, d_glast, d_basis, d_xdim, d_pivot, p.N, d_smask, d_vt0, f->d_vt};
+              d_gfirst, d_glast, d_basis, d_xdim, d_pivot, p.N, d_smask, d_vt0, f->d_vt, d_kind, d_dir,
+              int(p.x.size())};
   const bool c64 = f->dtype == HS_C64;
   dim3 grid(unsigned(((1 << maxbits) + 255) / 256), unsigned(p.groups.size()));
   switch (maxdim) {

@@ -51,6 +51,11 @@ struct Group {
   uint32_t smask = 0;
   int vt0 = -1;              // first entry in the factor set's value tables, -1 if none
   int vt_n = 0;              // nslot << popcount(smask)
+  // Product formula stage this factor belongs to: angle kind (which multiple
+  // of the step its rotations use) and direction (+1: terms first..last act in
+  // order, -1: last..first).
+  int kind = 0;
+  int dir = 1;
 };
 
 // Result of planning a factor set on the host.
@@ -66,6 +71,9 @@ struct Plan {
   std::vector<uint32_t> term_cx;  // per term: coordinates of its x mask in its factor's basis
   int64_t total_elems = 0;        // padded storage size in elements
   int64_t total_vt = 0;           // value-table entries (stored after the diagonals)
+  int order = 1;                  // product formula: 1, 2 (Strang) or 4 (Suzuki)
+  int n_kinds = 1;                // distinct angle multiples of the step
+  std::vector<int> step_seq;      // factors one step applies, in order
   std::vector<uint32_t> slot_u;   // per slot: its x-mask
   std::vector<int32_t> slot_tab;  // per slot: first entry in tab_rb (one sentinel at the end)
   std::vector<int64_t> tab_rb;    // per (slot, row pattern): row-indexed base of the diagonal
@@ -76,8 +84,13 @@ int parse_labels(const char* const* labels, size_t n, std::vector<uint64_t>& x, 
                  int& n_qubits, std::string* err);
 
 // Group, order offsets and lay out storage.  Returns HS_OK or HS_EINVAL.
+// order 2 / 4 lays out each group twice per angle kind (forward and reversed
+// term order) and sets step_seq to the formula's sequence of factors.
 int make_plan(const uint64_t* x, const uint64_t* z, const double* coeff, size_t n, int n_qubits, int budget,
-              hs_dtype dt, Plan& plan, std::string* err);
+              hs_dtype dt, Plan& plan, std::string* err, int order = 1);
+
+// Angle multiples of the step dt for each kind of a product formula of the given order.
+std::vector<double> kind_steps(int order, double dt);
 
 // A tile partition: `local` bits (held by one CTA) and the rest (enumerated by the grid).
 struct Runs {
@@ -141,15 +154,19 @@ namespace hs {
 
 // Kernel launchers (defined in the .cu files).
 // Factor values; groups with a value table copy it (launch_value_tables first).
+// d_kind / d_dir: per group angle kind and direction.
 cudaError_t launch_build(const hs_factors* f, const double* d_theta_cs, const uint64_t* d_x, const uint64_t* d_z,
                          const uint32_t* d_cx, const int* d_group_first, const int* d_group_last,
                          const uint64_t* d_basis, const int* d_xdim, const int* d_pivot, const uint32_t* d_smask,
-                         const int* d_vt0, cudaStream_t s);
-cudaError_t launch_sincos(const double* d_coeff, double dt, double* d_theta_cs, int n, cudaStream_t s);
+                         const int* d_vt0, const int* d_kind, const int* d_dir, cudaStream_t s);
+// (cos, sin) of coeff[j] * h[k] for every term j and angle kind k, kind-major.
+cudaError_t launch_sincos(const double* d_coeff, const double* d_h, int n_kinds, double* d_theta_cs, int n,
+                          cudaStream_t s);
 cudaError_t launch_value_tables(const hs_factors* f, const double* d_theta_cs, const uint64_t* d_x, const uint64_t* d_z,
                                 const uint32_t* d_cx, const int* d_group_first, const int* d_group_last,
                                 const uint64_t* d_basis, const int* d_xdim, const int* d_pivot,
-                                const uint32_t* d_smask, const int* d_vt0, cudaStream_t s);
+                                const uint32_t* d_smask, const int* d_vt0, const int* d_kind, const int* d_dir,
+                                cudaStream_t s);
 
 cudaError_t launch_apply_plain(const hs_factors* f, int g, const void* x, void* y, int n_rhs, cudaStream_t s);
 

@@ -116,9 +116,21 @@ int parse_labels(const char* const* labels, size_t n, std::vector<uint64_t>& x, 
   return HS_OK;
 }
 
+std::vector<double> kind_steps(int order, double dt) {
+  if (order == 2) return {dt * 0.5};
+  if (order == 4) {
+    // Suzuki's fourth-order recursion S2(p dt)^2 S2((1 - 4p) dt) S2(p dt)^2,
+    // p = 1 / (4 - 4^(1/3)); each Strang stage turns its step into two halves.
+    const double p = 1.0 / (4.0 - std::pow(4.0, 1.0 / 3.0));
+    return {(p * dt) * 0.5, ((1.0 - 4.0 * p) * dt) * 0.5};
+  }
+  return {dt};
+}
+
 int make_plan(const uint64_t* x, const uint64_t* z, const double* coeff, size_t n, int n_qubits, int budget,
-              hs_dtype dt, Plan& plan, std::string* err) {
+              hs_dtype dt, Plan& plan, std::string* err, int order) {
   if (n == 0) { *err = "no terms"; return HS_EINVAL; }
+  if (order != 1 && order != 2 && order != 4) { *err = "order must be 1, 2 or 4"; return HS_EINVAL; }
   if (n_qubits < 1 || n_qubits > HS_MAX_QUBITS) {
     *err = "n_qubits must be 1.." + std::to_string(HS_MAX_QUBITS);
     return HS_EINVAL;
@@ -168,12 +180,37 @@ int make_plan(const uint64_t* x, const uint64_t* z, const double* coeff, size_t 
   }
   closed.emplace_back(first, std::move(g));
 
+  // Stored factors: each group once per (angle kind, direction) of the
+  // product formula, and the sequence one step applies.
+  const int G0 = int(closed.size());
+  struct Stage { int kind, dir; };
+  std::vector<Stage> stages;
+  if (order == 1) stages = {{0, 1}};
+  else if (order == 2) stages = {{0, 1}, {0, -1}};
+  else stages = {{0, 1}, {0, -1}, {1, 1}, {1, -1}};
+  plan.order = order;
+  plan.n_kinds = order == 4 ? 2 : 1;
+  auto strang = [&](int kind) {  // forward groups, then the reversed groups in reverse order
+    for (int i = 0; i < G0; ++i) plan.step_seq.push_back((2 * kind) * G0 + i);
+    for (int i = G0 - 1; i >= 0; --i) plan.step_seq.push_back((2 * kind + 1) * G0 + i);
+  };
+  if (order == 1) {
+    for (int i = 0; i < G0; ++i) plan.step_seq.push_back(i);
+  } else if (order == 2) {
+    strang(0);
+  } else {
+    for (int kind : {0, 0, 1, 0, 0}) strang(kind);
+  }
+
   // Canonical order, padded layout, bases.
   const int64_t A = align_elems(dt);
   int64_t cursor = 0;
-  for (size_t gi = 0; gi < closed.size(); ++gi) {
+  for (size_t rep = 0; rep < stages.size() * closed.size(); ++rep) {
+    const size_t gi = rep % closed.size();
     OpenGroup& og = closed[gi].second;
     Group G;
+    G.kind = stages[rep / closed.size()].kind;
+    G.dir = stages[rep / closed.size()].dir;
     G.first = closed[gi].first;
     G.last = (gi + 1 < closed.size()) ? closed[gi + 1].first : int(n);
     std::vector<int64_t> o = og.offs;
@@ -292,7 +329,7 @@ std::vector<Sweep> plan_sweeps(const Plan& p, int n_steps, int tile_bits, int mi
   Sweep cur;
   uint64_t used = 0;
   for (int st = 0; st < n_steps; ++st) {
-    for (int g = 0; g < int(p.groups.size()); ++g) {
+    for (int g : p.step_seq) {
       const uint64_t span = p.groups[g].span;
       const bool fits_alone = fused && p.groups[g].D <= max_fused_diags && p.groups[g].nslot > 0 &&
                               min_low_bits <= tile_bits &&

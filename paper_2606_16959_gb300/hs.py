@@ -29,7 +29,7 @@ EXPORTS = (
     "hs_batch_free_async",
     "hs_dia_from_terms", "hs_dia_from_masks", "hs_dia_create", "hs_spgemm", "hs_spme", "hs_estimate_timesteps",
     "hs_spmv", "hs_dia_evolve", "hs_dia_convert", "hs_dia_info", "hs_dia_get", "hs_dia_free",
-    "hs_kernel_launches", "hs_expectation",
+    "hs_kernel_launches", "hs_expectation", "hs_build_factors_ex", "hs_factors_sequence",
 )
 
 
@@ -112,6 +112,9 @@ def lib() -> ctypes.CDLL:
         L.hs_dia_free.argtypes = [vp]
         L.hs_dia_free.restype = None
         L.hs_expectation.argtypes = [vp, vp, i, vp, dp, dp]
+        L.hs_build_factors_ex.argtypes = [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
+                                          dp, sz, i, d, i, i, i, i, vp, ctypes.POINTER(vp)]
+        L.hs_factors_sequence.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), i, ctypes.POINTER(i)]
         L.hs_kernel_launches.argtypes = []
         L.hs_kernel_launches.restype = ctypes.c_uint64
         for name in EXPORTS:
@@ -172,6 +175,12 @@ class Factors:
         _check(lib().hs_factors_info(self.handle, ctypes.byref(nf), ctypes.byref(nq), ctypes.byref(ns),
                                      ctypes.byref(dt), ctypes.byref(vb)))
         self.n_factors, self.n_qubits, self.n_steps, self.dtype_code = nf.value, nq.value, ns.value, dt.value
+        order, ln = ctypes.c_int(), ctypes.c_int()
+        _check(lib().hs_factors_sequence(self.handle, ctypes.byref(order), None, 0, ctypes.byref(ln)))
+        seq = (ctypes.c_int * max(1, ln.value))()
+        _check(lib().hs_factors_sequence(self.handle, None, seq, ln.value, ctypes.byref(ln)))
+        self.order = order.value
+        self.sequence = [int(seq[k]) for k in range(ln.value)]  # factors one step applies
         self.value_bytes = vb.value
 
     @property
@@ -213,7 +222,23 @@ class Factors:
 
 
 def hs_build_factors(labels: Sequence[str], coeffs, t: float, n_steps: int, diag_budget: int, dtype="c64",
-                     stream=None) -> Factors:
+                     stream=None, order: int = 1) -> Factors:
+    if order != 1:
+        x = np.zeros(len(labels), dtype=np.uint64)
+        z = np.zeros(len(labels), dtype=np.uint64)
+        n = len(labels[0]) if labels else 0
+        for j, lab in enumerate(labels):
+            if len(lab) != n:
+                raise ValueError("labels differ in length")
+            for p_, ch in enumerate(lab):
+                bit = np.uint64(1 << (n - 1 - p_))
+                if ch in "XY":
+                    x[j] |= bit
+                if ch in "ZY":
+                    z[j] |= bit
+                if ch not in "IXYZ":
+                    raise ValueError(f"invalid Pauli character {ch!r}")
+        return hs_build_factors_masks(x, z, coeffs, n, t, n_steps, diag_budget, dtype, stream, order)
     arr = (ctypes.c_char_p * len(labels))(*[l.encode() for l in labels])
     c = np.ascontiguousarray(np.asarray(coeffs, dtype=np.float64))
     if c.size != len(labels):
@@ -226,18 +251,18 @@ def hs_build_factors(labels: Sequence[str], coeffs, t: float, n_steps: int, diag
 
 
 def hs_build_factors_masks(x, z, coeffs, n_qubits: int, t: float, n_steps: int, diag_budget: int, dtype="c64",
-                           stream=None) -> Factors:
+                           stream=None, order: int = 1) -> Factors:
     xa = np.ascontiguousarray(np.asarray(x, dtype=np.uint64))
     za = np.ascontiguousarray(np.asarray(z, dtype=np.uint64))
     c = np.ascontiguousarray(np.asarray(coeffs, dtype=np.float64))
     if not (xa.size == za.size == c.size):
         raise ValueError("x, z and coeffs differ in length")
     out = ctypes.c_void_p()
-    _check(lib().hs_build_factors_masks(xa.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
-                                        za.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
-                                        c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), xa.size, int(n_qubits),
-                                        float(t), int(n_steps), int(diag_budget), _dtype_code(dtype), _stream(stream),
-                                        ctypes.byref(out)))
+    _check(lib().hs_build_factors_ex(xa.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                     za.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                     c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), xa.size, int(n_qubits),
+                                     float(t), int(n_steps), int(diag_budget), int(order), _dtype_code(dtype),
+                                     _stream(stream), ctypes.byref(out)))
     return Factors(out.value)
 
 
