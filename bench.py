@@ -54,6 +54,8 @@ def parse_args():
     ap.add_argument("--tile-bits", type=int, default=0)
     ap.add_argument("--rhs-block", type=int, default=0)
     ap.add_argument("--graph", type=int, default=0)
+    ap.add_argument("--order", type=int, default=1, choices=[1, 2, 4],
+                    help="product formula: 1 (first order), 2 (Strang), 4 (Suzuki)")
     ap.add_argument("--qubits", type=int, default=0,
                     help="maxcut24 only: a smaller instance of the same family (profiling cases)")
     return ap.parse_args()
@@ -248,7 +250,7 @@ def algorithmic_bytes(f, job, n_rhs):
     s = 8 if f.dtype == "c64" else 16
     N = 1 << f.n_qubits
     per_step = 0
-    for g in range(f.n_factors):
+    for g in f.sequence:
         _, _, offs, _ = f.factor(g, values=False)
         S = int(np.sum(N - np.abs(offs)))
         per_step += s * S + 2 * s * N * n_rhs
@@ -273,7 +275,8 @@ def time_ours(job, args, world, dtype, rank):
 
     def step(keep):
         work.copy_(psi0)
-        f = hs.hs_build_factors(job.ham.labels, job.ham.coeffs, job.t, job.n_steps, job.budget, dtype)
+        f = hs.hs_build_factors(job.ham.labels, job.ham.coeffs, job.t, job.n_steps, job.budget, dtype,
+                                order=args.order)
         e0, e1 = E(enable_timing=True), E(enable_timing=True)
         e0.record()
         hs.hs_evolve_ex(f, work, job.n_steps, **opts)
@@ -284,12 +287,13 @@ def time_ours(job, args, world, dtype, rank):
 
     tuned = None
     if args.autotune and not any((args.method, args.tile_bits, args.rhs_block)):
-        key = f"{args.workload}:{job.ham.n_qubits}:{dtype}:{torch.cuda.get_device_name()}"
+        key = f"{args.workload}:{job.ham.n_qubits}:o{args.order}:{dtype}:{torch.cuda.get_device_name()}"
         cache = load_tune_cache()
         if key in cache:
             tuned = cache[key]
         else:
-            ft = hs.hs_build_factors(job.ham.labels, job.ham.coeffs, job.t, job.n_steps, job.budget, dtype)
+            ft = hs.hs_build_factors(job.ham.labels, job.ham.coeffs, job.t, job.n_steps, job.budget, dtype,
+                                     order=args.order)
             tuned = hs.hs_autotune(ft, psi0, min(job.n_steps, 10))
             ft.close()
             cache[key] = tuned
@@ -329,7 +333,7 @@ def time_ours(job, args, world, dtype, rank):
     clocks = sampler.stop() if sampler else None
     barrier(world)
     fid = out4.cpu().numpy()
-    G = f0.n_factors
+    G = len(f0.sequence)  # factor applications per step (n_factors for the first-order formula)
     units = job.n_steps * G * N * R
     total_ms = max_over_ranks(sum(step_ms), world)
     return dict(units=units, G=G, R=R, N=N, step_ms=step_ms, evolve_ms=evolve_ms, total_ms=total_ms,
@@ -358,7 +362,8 @@ def time_e2e(job, args, dtype):
 
     def step():
         work.copy_(host_in, non_blocking=True)
-        f = hs.hs_build_factors(job.ham.labels, job.ham.coeffs, job.t, job.n_steps, job.budget, dtype)
+        f = hs.hs_build_factors(job.ham.labels, job.ham.coeffs, job.t, job.n_steps, job.budget, dtype,
+                                order=args.order)
         hs.hs_evolve_ex(f, work, job.n_steps, **opts)
         hs.hs_inner_device(work[0], work[0], out4)
         host_out.copy_(work, non_blocking=True)
@@ -517,8 +522,8 @@ def oracle_batch_sample(jobs, budget_s=15.0):
                        "single thread; units counted as steps x G x N per instance")
 
 
-def oracle_sample(job, G, budget_s=15.0):
-    """Time the FP64 oracle (single-threaded C) on a bounded sample of the same
+def oracle_sample(job, G, budget_s=15.0, order=1):
+    """Time the FP64 oracle (single-threaded) on a bounded sample of the same
     workload: whole Trotter steps of state 0, as many as fit ~budget_s."""
     import oracle
     x, z, n = oracle.parse_terms(job.ham.labels)
@@ -526,30 +531,38 @@ def oracle_sample(job, G, budget_s=15.0):
     psi = psi[0] if psi.ndim == 2 else psi
     N = 1 << n
     dt = job.t / job.n_steps
+
+    def run(k):
+        if order == 1:
+            return oracle.evolve_direct(x, z, job.ham.coeffs, dt * k, k, psi)
+        return oracle.evolve_direct_order(x, z, job.ham.coeffs, dt * k, k, psi, order)
+
     t0 = time.perf_counter()
-    oracle.evolve_direct(x, z, job.ham.coeffs, dt, 1, psi)
+    run(1)
     t1 = time.perf_counter() - t0
     k = int(max(1, min(job.n_steps, budget_s // max(t1, 1e-9))))
     if k > 1:
         t0 = time.perf_counter()
-        oracle.evolve_direct(x, z, job.ham.coeffs, dt * k, k, psi)
+        run(k)
         t1 = time.perf_counter() - t0
     else:
         k = 1
     units = k * G * N
-    R = psi.shape[0] if np.asarray(job.psi0).ndim == 2 else 1
     R = np.asarray(job.psi0).shape[0] if np.asarray(job.psi0).ndim == 2 else 1
+    kind = "first-order" if order == 1 else f"order-{order} product-formula"
     return dict(value=units / t1, seconds=t1, steps=k,
-                sample=f"{k} of {job.n_steps} Trotter steps of state 0 (of {R}), direct term-by-term FP64 "
-                       f"evolution, single thread; units counted as steps x G={G} factors x N={N}")
+                sample=f"{k} of {job.n_steps} {kind} steps of state 0 (of {R}), direct term-by-term FP64 "
+                       f"evolution, single thread; units counted as steps x {G} factor applications x N={N}")
 
 
 def config_of(args, job, desc, res=None):
     c = {"workload": args.workload, "description": desc, "n_qubits": job.ham.n_qubits, "n_terms": len(job.ham.labels),
          "n_steps": job.n_steps, "diag_budget": job.budget, "n_rhs": int(np.asarray(job.psi0).shape[0]) if np.asarray(job.psi0).ndim == 2 else 1,
          "t": job.t, "l2": "flushed (512 MiB write) before every timed step"}
+    if getattr(args, "order", 1) != 1:
+        c["product_formula_order"] = args.order
     if res:
-        c.update({"n_factors": res["G"], "tile_bits": res["tile_bits"], "rhs_block": res["rhs_block"],
+        c.update({"factor_applications_per_step": res["G"], "tile_bits": res["tile_bits"], "rhs_block": res["rhs_block"],
                   "sweep_launches_per_step": res["n_sweeps"], "plain_launches_per_step": res["n_plain"]})
     return c
 
@@ -630,7 +643,7 @@ def run_ours(args):
         line["c128"] = {"value": r2["units"] * K * world / (r2["total_ms"] / 1000.0),
                         "ms_per_step": r2["total_ms"] / K, "evolve_ms_per_step": statistics.mean(r2["evolve_ms"])}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cb = oracle_sample(job, res["G"])
+        cb = oracle_sample(job, res["G"], order=args.order)
         line["cpu_baseline"] = {"value": cb["value"], "unit": METRIC, "cores": 1, "kind": "oracle",
                                 "sample": cb["sample"]}
     if rank == 0:
