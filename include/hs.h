@@ -198,6 +198,8 @@ typedef struct {
   int smem_kb;   /* shared memory per CTA for the state tile and factor staging, in KiB (0 = 24);
                     a smaller budget stages fewer factors ahead but fits more CTAs on an SM */
   int no_tables; /* as in hs_evolve_opts: 1 stages every factor from its diagonals */
+  int tiles_per_cta; /* tiles one CTA evolves back to back, loading its sweep's tables once
+                        (0 = library choice, at most 64) */
 } hs_batch_opts;
 
 /* Plan a batch (host only; device tables are uploaded on the first launch's

@@ -77,11 +77,13 @@ __global__ void __launch_bounds__(256) apply_plain_kernel(const typename C2<R>::
 template <typename R, int ROWS, int RB>
 __global__ void __launch_bounds__(512) sweep_kernel(const __grid_constant__ sweep::SweepArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  sweep::sweep_tile<R, ROWS, RB>(a, blockIdx.x & ((1u << a.n_tiles_log2) - 1u), int(blockIdx.x >> a.n_tiles_log2),
-                                 smem_raw);
+  const uint32_t u0 = blockIdx.x * uint32_t(a.tiles_per_cta);
+  const uint32_t u1 = min(uint32_t(a.n_units), u0 + uint32_t(a.tiles_per_cta));
+  sweep::sweep_tiles<R, ROWS, RB, RB == 1>(a, u0, u1, smem_raw);
 }
 
 constexpr int kSweepMaxThreads = 512;
+constexpr int kSweepMaxTilesPerCta = 8;
 
 // Accumulators per thread (rows x states) kept in registers: 16 complex for
 // complex64, 8 for complex128.
@@ -270,7 +272,14 @@ cudaError_t launch_sweep(const hs_factors* f, const SweepLaunch& L, cudaStream_t
   if (!fn) return cudaErrorInvalidValue;
   const int n_rhs_blocks = (L.n_rhs + L.rhs_block - 1) / L.rhs_block;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(unsigned((1 << a.n_tiles_log2) * n_rhs_blocks), 1u, 1u);
+  // One-state tiles: several units per CTA once the grid is large (tables
+  // loaded once per CTA), keeping at least ~16 CTAs per SM.  A multi-state
+  // tile already carries enough work for its tables (measured: 8 units per
+  // CTA slowed the 16-state MaxCut sweeps by 12%).
+  a.n_units = (1 << a.n_tiles_log2) * n_rhs_blocks;
+  a.tiles_per_cta =
+      L.rhs_block == 1 ? std::max(1, std::min(kSweepMaxTilesPerCta, a.n_units / (152 * 16))) : 1;
+  cfg.gridDim = dim3(unsigned((a.n_units + a.tiles_per_cta - 1) / a.tiles_per_cta), 1u, 1u);
   cfg.blockDim = dim3(unsigned(threads), 1u, 1u);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;

@@ -71,6 +71,7 @@ struct LevelArgs {
   const int* lvl_prefix;  // per entry: first CTA of the entry within the level
   int off, count;         // the level's entries
   int tile_bits;
+  int tiles_per_cta;      // units (tile, state) one CTA runs back to back
 };
 
 constexpr int kBatchThreads = 512;  // at most; a tile of 2^T rows gets min(2^T, 512) threads
@@ -111,6 +112,8 @@ __global__ void __launch_bounds__(kBatchThreads) batch_level_kernel(const __grid
     sa->n_mtab = bs.n_mtab;
     sa->n_vt = bs.n_vt;
     sa->all_tables = bs.all_tables;
+    sa->tiles_per_cta = 1;
+    sa->n_units = 0;
     sa->flane = bs.flane;
     sa->m0 = bs.m0;
     sa->m1 = bs.m1;
@@ -131,9 +134,10 @@ __global__ void __launch_bounds__(kBatchThreads) batch_level_kernel(const __grid
     sa->fsm[i] = fe.sm;
   }
   __syncthreads();
-  const int tl = bj.n_qubits - p.tile_bits;
-  hs::sweep::sweep_tile<R, ROWS, 1>(*sa, uint32_t(local) & ((1u << tl) - 1u), local >> tl,
-                                    smem + kArgsBytes + size_t((p.count + 3) & ~3) * sizeof(int));
+  const uint32_t units = (1u << (bj.n_qubits - p.tile_bits)) * uint32_t(bj.n_rhs);
+  const uint32_t u0 = uint32_t(local) * uint32_t(p.tiles_per_cta);
+  const uint32_t u1 = min(units, u0 + uint32_t(p.tiles_per_cta));
+  hs::sweep::sweep_tiles<R, ROWS, 1>(*sa, u0, u1, smem + kArgsBytes + size_t((p.count + 3) & ~3) * sizeof(int));
 }
 
 using LevelFn = void (*)(LevelArgs);
@@ -154,6 +158,7 @@ LevelFn level_fn(int rows) {
 struct hs_batch {
   uint64_t graph_kernels = 0;  // kernels one replay of the captured graph launches
   bool value_tables = true;    // read small-support factors from their value tables
+  int tiles_per_cta = 1;       // units one CTA runs back to back (tables loaded once)
   hs_dtype dtype = HS_C64;
   int tile_bits = 0, low_bits = 0, rows = 1;
   bool use_graph = true;
@@ -227,7 +232,8 @@ int enqueue_batch(hs_batch* b, cudaStream_t s) {
   LevelFn fn = b->dtype == HS_C64 ? level_fn<float>(b->rows) : level_fn<double>(b->rows);
   if (!fn) return hs::report_error(HS_EINVAL, "internal: no batch kernel for this tile size");
   for (const hs_batch::Level& L : b->levels) {
-    LevelArgs a{b->d_jobs, b->d_sweeps, b->d_facs, b->d_lvl_sweep, b->d_lvl_prefix, L.off, L.count, b->tile_bits};
+    LevelArgs a{b->d_jobs, b->d_sweeps, b->d_facs, b->d_lvl_sweep, b->d_lvl_prefix, L.off, L.count, b->tile_bits,
+                b->tiles_per_cta};
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(unsigned(L.ctas), 1u, 1u);
     cfg.blockDim = dim3(unsigned((1 << b->tile_bits) / b->rows), 1u, 1u);
@@ -251,7 +257,7 @@ extern "C" int hs_batch_create(const hs_batch_job* jobs, size_t n_jobs, const hs
   if (!out) return hs::report_error(HS_EINVAL, "out is NULL");
   *out = nullptr;
   if (!jobs || n_jobs == 0) return hs::report_error(HS_EINVAL, "no jobs");
-  hs_batch_opts o{0, 0, 1, 0, 0};
+  hs_batch_opts o{0, 0, 1, 0, 0, 0};
   if (opts) o = *opts;
   std::unique_ptr<hs_batch> b(new hs_batch());
   b->dtype = jobs[0].factors ? jobs[0].factors->dtype : HS_C64;
@@ -273,6 +279,9 @@ extern "C" int hs_batch_create(const hs_batch_job* jobs, size_t n_jobs, const hs
   b->low_bits = o.low_bits > 0 ? o.low_bits : (dt == HS_C64 ? 2 : 1);
   b->use_graph = o.use_graph != 0;
   b->value_tables = o.no_tables == 0;
+  if (o.tiles_per_cta < 0 || o.tiles_per_cta > 64) return hs::report_error(HS_EINVAL, "tiles_per_cta must be 0..64");
+  // 8 measured best on the 256-instance batch (458 ms against 574 ms for 1).
+  b->tiles_per_cta = o.tiles_per_cta > 0 ? o.tiles_per_cta : 8;
   if (b->tile_bits < 8 || b->tile_bits > 11) return hs::report_error(HS_EINVAL, "batch tile_bits must be 8..11");
   b->rows = (1 << b->tile_bits) > kBatchThreads ? (1 << b->tile_bits) / kBatchThreads : 1;
   if ((dt == HS_C64 ? level_fn<float>(b->rows) : level_fn<double>(b->rows)) == nullptr)
@@ -304,7 +313,8 @@ extern "C" int hs_batch_create(const hs_batch_job* jobs, size_t n_jobs, const hs
     const int jid = int(hjobs.size());
     const hs_factors* f = J.factors;
     hjobs.push_back(BJob{J.psi, f->d_vals, f->d_vt, f->d_slot_u, f->d_slot_tab, f->d_tab_rb, p.N, p.n_qubits, J.n_rhs});
-    job_ctas.push_back((int64_t(1) << (p.n_qubits - T)) * J.n_rhs);
+    const int64_t units = (int64_t(1) << (p.n_qubits - T)) * J.n_rhs;
+    job_ctas.push_back((units + b->tiles_per_cta - 1) / b->tiles_per_cta);
     std::map<std::pair<uint32_t, std::vector<int>>, int> uniq;
     std::vector<int> lv;
     const uint64_t all = (1ull << p.n_qubits) - 1;

@@ -50,6 +50,8 @@ struct SweepArgs {
   int sh;
   Runs rest;         // the other bits, enumerated by the CTA index
   int n_factors;
+  int tiles_per_cta;  // units one CTA of a per-sweep launch runs back to back
+  int n_units;        // 2^n_tiles_log2 * rhs blocks
   // Per factor of the sweep: first global slot, slot count, position of its
   // first slot in the shared slot table, first global / shared row-base table
   // entry and the number of entries.
@@ -273,8 +275,13 @@ __device__ __forceinline__ void sweep_reg(const SweepArgs& a, T2* tile, T2* othe
 // found through the slot's row-base table -- into plane u of the stage, and
 // the multiply is acc[l] += plane_u[l] * x[l ^ U] with U the local image of u.
 // The sum is the diagonal-times-vector product without its zero terms.
-template <typename R, int ROWS, int RB>
-__device__ __forceinline__ void sweep_tile(const SweepArgs& a, uint32_t tile_id, int rhs_blk, unsigned char* smem_raw) {
+//
+// Units u0 .. u1-1 (unit = rhs block * 2^n_tiles_log2 + tile) run one after
+// the other on this CTA: the sweep's tables are loaded once for all of them.
+// MULTI = false compiles a single unit (u1 = u0 + 1), which keeps the
+// multi-state instantiations at their single-tile register count.
+template <typename R, int ROWS, int RB, bool MULTI = true>
+__device__ __forceinline__ void sweep_tiles(const SweepArgs& a, uint32_t u0, uint32_t u1, unsigned char* smem_raw) {
   using T2 = typename C2<R>::T;
   constexpr int V = 16 / sizeof(T2);  // elements per 16-byte chunk
   const int NT = blockDim.x;
@@ -294,9 +301,6 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, uint32_t tile_id,
   T2* dst = reinterpret_cast<T2*>(a.dst);
   const T2* __restrict__ vals = reinterpret_cast<const T2*>(a.vals);
 
-  const int rhs0 = rhs_blk * a.rhs_block;
-  const int nrb = min(a.rhs_block, a.n_rhs - rhs0);
-  const uint32_t base = deposit_runs(tile_id, a.rest);
   const uint32_t n_chunks = TS / V;
 
   // Slot and row-base tables of every factor of the sweep, loaded once: each
@@ -336,6 +340,16 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, uint32_t tile_id,
   }
   __syncthreads();
 
+  const uint32_t u_end = MULTI ? u1 : u0 + 1;
+  for (uint32_t unit = u0; unit < u_end; ++unit) {
+  const uint32_t tile_id = unit & ((1u << a.n_tiles_log2) - 1u);
+  const int rhs_blk = int(unit >> a.n_tiles_log2);
+  const int rhs0 = rhs_blk * a.rhs_block;
+  const int nrb = min(a.rhs_block, a.n_rhs - rhs0);
+  const uint32_t base = deposit_runs(tile_id, a.rest);
+  // the previous unit's threads are done with the tile and the stages
+  if (unit != u0) __syncthreads();
+
   // Stage slots [p0, p1) of the slot table for the tile rows: plane u of a
   // factor receives, for every tile row r, the value of entry (r, r ^ u).  The
   // items (slot, 16-byte chunk) are independent, so one flat loop keeps many
@@ -373,12 +387,14 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, uint32_t tile_id,
   const int S = a.n_stages;
   issue_slots(0, S < a.n_factors ? a.fmslot[S] : a.n_mslot, -1);
   cp_async_commit();
-  // The state written by the previous launch is visible only after this.
-  grid_dependency_wait();
-  // Let the next sweep start its own prologue (tables and factor staging, which
-  // read no state) while this one computes; it waits for this grid to finish
-  // before it touches the state.
-  grid_launch_dependents();
+  if (unit == u0) {
+    // The state written by the previous launch is visible only after this.
+    grid_dependency_wait();
+    // Let the next sweep start its own prologue (tables and factor staging,
+    // which read no state) while this one computes; it waits for this grid to
+    // finish before it touches the state.
+    grid_launch_dependents();
+  }
   for (uint32_t c = threadIdx.x; c < n_chunks; c += NT) {
     const uint32_t l = c * V;
     const T2* sp = src + int64_t(rhs0) * a.N + (global_of(l, m0, m1, sh) | base);
@@ -393,7 +409,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, uint32_t tile_id,
   if constexpr (RB == 1) {
     if (a.all_tables) {
       sweep_reg<T2, ROWS>(a, tile, stages, mslot, vts, grow, NT, __ffs(NT) - 1, dst + int64_t(rhs0) * a.N);
-      return;
+      continue;
     }
   }
   if (nrb == RB)
@@ -409,6 +425,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, uint32_t tile_id,
     for (int q = 0; q < nrb; ++q, dp += a.N, tp += TS)
       *reinterpret_cast<uint4*>(dp) = *reinterpret_cast<const uint4*>(tp);
   }
+  }  // units
 }
 
 // Shared-memory bytes of the slot, row-base and value tables of a sweep.

@@ -46,7 +46,7 @@ class BatchJob(ctypes.Structure):
 
 class BatchOpts(ctypes.Structure):
     _fields_ = [("tile_bits", ctypes.c_int), ("low_bits", ctypes.c_int), ("use_graph", ctypes.c_int),
-                ("smem_kb", ctypes.c_int), ("no_tables", ctypes.c_int)]
+                ("smem_kb", ctypes.c_int), ("no_tables", ctypes.c_int), ("tiles_per_cta", ctypes.c_int)]
 
 
 class EvolveOpts(ctypes.Structure):
@@ -409,7 +409,7 @@ class Batch:
 
 
 def hs_batch_create(jobs, tile_bits: int = 0, low_bits: int = 0, use_graph: bool = True, smem_kb: int = 0,
-                    no_tables: bool = False) -> Batch:
+                    no_tables: bool = False, tiles_per_cta: int = 0) -> Batch:
     """jobs: sequence of (Factors, state tensor, n_steps)."""
     arr = (BatchJob * len(jobs))()
     keep = []
@@ -417,7 +417,8 @@ def hs_batch_create(jobs, tile_bits: int = 0, low_bits: int = 0, use_graph: bool
         ptr, n_rhs = _check_state(f, psi)
         arr[k] = BatchJob(f.handle.value, ptr, n_rhs, int(n_steps))
         keep.append((f, psi))
-    o = BatchOpts(int(tile_bits), int(low_bits), int(bool(use_graph)), int(smem_kb), int(bool(no_tables)))
+    o = BatchOpts(int(tile_bits), int(low_bits), int(bool(use_graph)), int(smem_kb), int(bool(no_tables)),
+                  int(tiles_per_cta))
     out = ctypes.c_void_p()
     _check(lib().hs_batch_create(arr, len(jobs), ctypes.byref(o), ctypes.byref(out)))
     return Batch(out.value, keep)
