@@ -9,7 +9,8 @@ with its structural offset sets (the structural dry run of the diagonal-set
 estimation paragraph, Sec. 3.2), and the canonical diagonal order of Tab. 1.
 Numeric half (``hs_oracle.c``, loaded through ctypes): Pauli rotations,
 direct Trotter evolution (Eq. 4) and, in Python over the same rotations, the
-second- and fourth-order product formulas, factor materialisation into the compact
+second- and fourth-order product formulas and time-dependent evolution under
+H0 + f(t) H1, factor materialisation into the compact
 layout (Eq. 6), the diagonal-times-vector product (Alg. 1), pairwise sums.
 
 Readings of the paper used here (the paper is silent or ambiguous on each):
@@ -25,7 +26,10 @@ Readings of the paper used here (the paper is silent or ambiguous on each):
 
 Parity status: every function here is pinned by tests/test_oracle_pins.py
 (dense Kronecker products, scipy expm, numpy eigh, closed forms, Tab. 1,
-Tab. 3 and the appendix quick-start example); none is "parity unpinned".
+Tab. 3 and the appendix quick-start example), the product formulas by
+tests/test_order_pins.py and the time-dependent evolution by
+tests/test_td_pins.py (per-step scipy exponentials, exact diagonal phases, an
+independent ODE solver); none is "parity unpinned".
 """
 from __future__ import annotations
 
@@ -305,6 +309,46 @@ def evolve_direct_order(x, z, coeffs, t: float, n_steps: int, psi, order: int) -
     for r in range(rows.shape[0]):
         row = np.ascontiguousarray(rows[r])
         for _ in range(n_steps):
+            for h, direction in stages:
+                js = range(len(x)) if direction > 0 else range(len(x) - 1, -1, -1)
+                for j in js:
+                    lib.orc_rotate(row.size, int(x[j]), int(z[j]), float(c[j]) * h, row.ctypes.data)
+        rows[r] = row
+    return rows.reshape(shape)
+
+
+# ----------------------------------------------------------------------------
+# Time-dependent Hamiltonians H(t) = H0 + f(t) H1 (the paper's outlook on
+# time-dependent Hamiltonians).  Readings: term j carries two real
+# coefficients, a_j in H0 and b_j in H1 (either may be zero); step s freezes
+# H at the caller's sample f_s of f for that step, so every term uses
+# c_j(s) = a_j + f_s b_j (the product rounded before the sum), and the step is
+# the product formula of the given order with those coefficients.  Sampling f
+# at the step midpoints gives the exponential midpoint rule.
+# ----------------------------------------------------------------------------
+
+def td_coeffs(a, b, f: float) -> np.ndarray:
+    """c_j = a_j + f b_j for one frozen value f of the drive."""
+    return np.asarray(a, dtype=np.float64) + float(f) * np.asarray(b, dtype=np.float64)
+
+
+def evolve_direct_td(x, z, a, b, f_values, t: float, psi, order: int = 1) -> np.ndarray:
+    """Direct evolution under H(t) = H0 + f(t) H1 with one step per entry of
+    f_values (dt = t / len(f_values)); psi is (N,) or (n_rhs, N); returns a copy."""
+    psi = _c128(psi).copy()
+    shape = psi.shape
+    rows = psi.reshape(-1, shape[-1])
+    x, z = _u64(x), _u64(z)
+    fv = np.asarray(f_values, dtype=np.float64).ravel()
+    n_steps = len(fv)
+    dt = float(t) / float(n_steps)
+    lib = _lib()
+    stages = step_stages(order, dt)
+    coeffs = [td_coeffs(a, b, fv[s]) for s in range(n_steps)]
+    for r in range(rows.shape[0]):
+        row = np.ascontiguousarray(rows[r])
+        for s in range(n_steps):
+            c = coeffs[s]
             for h, direction in stages:
                 js = range(len(x)) if direction > 0 else range(len(x) - 1, -1, -1)
                 for j in js:

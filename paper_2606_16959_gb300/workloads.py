@@ -183,6 +183,47 @@ def tsp_onehot(n_cities: int, seed: int) -> Hamiltonian:
                        {"n_cities": nc, "dist": d, "A": A})
 
 
+@dataclass
+class DrivenHamiltonian:
+    """H(t) = H0 + f(t) H1 on one term list: term j has coefficient a[j] in H0
+    and b[j] in H1 (zero where it belongs to one of them only)."""
+    family: str
+    n_qubits: int
+    labels: List[str]
+    a: np.ndarray   # float64, H0 coefficient per label
+    b: np.ndarray   # float64, H1 coefficient per label
+    meta: Dict = field(default_factory=dict)
+
+
+def anneal_maxcut(n: int, seed: int, mixer: float = 0.5) -> DrivenHamiltonian:
+    """Annealing from the transverse mixer to weighted MaxCut on a random
+    3-regular graph: H(s) = (1 - s) mixer sum X_i + s H_C with s = f(t) (a
+    linear ramp s = t / T in the benchmark).  Term order: the mixer X_i, then the
+    identity and the ZZ edges of H_C, so that the flip factors and the one
+    diagonal factor of H_C group apart."""
+    cost = maxcut_3regular(n, seed, mixer=0.0)
+    labels = [label_of(n, {i: "X"}) for i in range(n)] + list(cost.labels)
+    a = np.concatenate([np.full(n, float(mixer)), np.zeros(len(cost.labels))])
+    b = np.concatenate([np.full(n, -float(mixer)), cost.coeffs])
+    return DrivenHamiltonian("anneal_maxcut", n, labels, a, b, dict(cost.meta, mixer=mixer))
+
+
+def driven_tfim(n: int, J: float = 1.0, h: float = 1.0, periodic: bool = False) -> DrivenHamiltonian:
+    """Transverse-field Ising chain with a driven field: H0 = -J sum Z_i Z_{i+1},
+    H1 = -h sum X_i (term order as tfim_chain)."""
+    base = tfim_chain(n, J, h, periodic)
+    n_b = len(base.meta["bonds"])
+    a = np.concatenate([base.coeffs[:n_b], np.zeros(n)])
+    b = np.concatenate([np.zeros(n_b), base.coeffs[n_b:]])
+    return DrivenHamiltonian("driven_tfim", n, list(base.labels), a, b, dict(base.meta))
+
+
+def midpoint_samples(fn, t: float, n_steps: int) -> np.ndarray:
+    """f at the midpoints (s + 1/2) t / n_steps of the n_steps steps of [0, t]."""
+    dt = float(t) / n_steps
+    return np.array([float(fn((s + 0.5) * dt)) for s in range(n_steps)], dtype=np.float64)
+
+
 # ----------------------------------------------------------------------------
 # Initial states
 # ----------------------------------------------------------------------------
