@@ -42,7 +42,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="heis16",
-                    choices=["heis16", "maxcut24", "tfim10", "batch256", "serve", "taylor16"])
+                    choices=["heis16", "maxcut24", "tfim10", "batch256", "serve", "taylor16", "anneal24"])
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--serve-rate", type=float, default=500.0)
     ap.add_argument("--autotune", type=int, default=1)
@@ -70,6 +70,11 @@ def make_job(name, dtype=None, qubits=0):
     elif name == "heis16":
         job = W.heis16(dtype or "c64")
         desc = "Heisenberg XXX periodic chain n=16, J_i~U[0.5,1.5] (seed 1002), Gaussian state, t=1, 100 steps, budget 8"
+    elif name == "anneal24":
+        job = W.anneal24()
+        desc = ("MaxCut annealing H(s) = (1-s) 0.5 sum X + s H_C on the n=24 weighted random 3-regular graph "
+                "(seed 1003), linear ramp s = t/T at step midpoints, T=2, 50 steps, 16 states (|+> and Gaussians), "
+                "budget 4; factors of the driven terms rebuilt on the GPU every step")
     elif name == "maxcut24":
         job = W.maxcut24()
         desc = ("weighted MaxCut random 3-regular n=24 (seed 1003) + 0.5 sum X, 16 states (|+> and Gaussians), "
@@ -257,6 +262,22 @@ def algorithmic_bytes(f, job, n_rhs):
     return per_step * job.n_steps
 
 
+def build_job(hs, job, dtype, order):
+    """The job's factor set: static, or time-dependent when the job has a drive."""
+    if job.drive is not None:
+        x, z, n = hs.label_masks(job.ham.labels)
+        return hs.hs_build_factors_td(x, z, job.ham.a, job.ham.b, n, job.t, job.n_steps, job.budget, dtype,
+                                      order=order)
+    return hs.hs_build_factors(job.ham.labels, job.ham.coeffs, job.t, job.n_steps, job.budget, dtype, order=order)
+
+
+def evolve_job(hs, f, psi, job, **opts):
+    if job.drive is not None:
+        hs.hs_evolve_td(f, psi, job.drive, **opts)
+    else:
+        hs.hs_evolve_ex(f, psi, job.n_steps, **opts)
+
+
 def time_ours(job, args, world, dtype, rank):
     """Device-timed steps with inputs resident in HBM.  Returns dict."""
     import torch
@@ -275,11 +296,10 @@ def time_ours(job, args, world, dtype, rank):
 
     def step(keep):
         work.copy_(psi0)
-        f = hs.hs_build_factors(job.ham.labels, job.ham.coeffs, job.t, job.n_steps, job.budget, dtype,
-                                order=args.order)
+        f = build_job(hs, job, dtype, args.order)
         e0, e1 = E(enable_timing=True), E(enable_timing=True)
         e0.record()
-        hs.hs_evolve_ex(f, work, job.n_steps, **opts)
+        evolve_job(hs, f, work, job, **opts)
         e1.record()
         hs.hs_inner_device(psi0[0], work[0], out4)
         keep.append(f)
@@ -292,8 +312,7 @@ def time_ours(job, args, world, dtype, rank):
         if key in cache:
             tuned = cache[key]
         else:
-            ft = hs.hs_build_factors(job.ham.labels, job.ham.coeffs, job.t, job.n_steps, job.budget, dtype,
-                                     order=args.order)
+            ft = build_job(hs, job, dtype, args.order)
             tuned = hs.hs_autotune(ft, psi0, min(job.n_steps, 10))
             ft.close()
             cache[key] = tuned
@@ -307,7 +326,11 @@ def time_ours(job, args, world, dtype, rank):
         step(keep)
     torch.cuda.synchronize()
     f0 = keep[0]
-    n_sweeps, n_plain, tb, rb = hs.hs_evolve_plan(f0, R, job.n_steps, **opts)
+    if job.drive is not None:  # one step's schedule, repeated (no sweep spans two steps)
+        n_sweeps, n_plain, tb, rb = hs.hs_evolve_plan(f0, R, 1, **opts)
+        n_sweeps, n_plain = n_sweeps * job.n_steps, n_plain * job.n_steps
+    else:
+        n_sweeps, n_plain, tb, rb = hs.hs_evolve_plan(f0, R, job.n_steps, **opts)
     alg = algorithmic_bytes(f0, job, R)
     for f in keep:
         f.close()
@@ -362,9 +385,8 @@ def time_e2e(job, args, dtype):
 
     def step():
         work.copy_(host_in, non_blocking=True)
-        f = hs.hs_build_factors(job.ham.labels, job.ham.coeffs, job.t, job.n_steps, job.budget, dtype,
-                                order=args.order)
-        hs.hs_evolve_ex(f, work, job.n_steps, **opts)
+        f = build_job(hs, job, dtype, args.order)
+        evolve_job(hs, f, work, job, **opts)
         hs.hs_inner_device(work[0], work[0], out4)
         host_out.copy_(work, non_blocking=True)
         out4_h.copy_(out4, non_blocking=True)
@@ -387,6 +409,8 @@ def time_e2e(job, args, dtype):
         f.close()
     m = len(job.ham.labels)
     term_bytes = 28 * m + 256  # masks, coefficients and group tables uploaded by the build
+    if job.drive is not None:
+        term_bytes += 8 * m + 8 * len(job.drive)  # H1 coefficients and drive samples
     return dict(ms=statistics.mean(times), h2d=int(host_in.numel() * host_in.element_size()) + term_bytes,
                 d2h=int(host_out.numel() * host_out.element_size()) + 32)
 
@@ -533,6 +557,8 @@ def oracle_sample(job, G, budget_s=15.0, order=1):
     dt = job.t / job.n_steps
 
     def run(k):
+        if job.drive is not None:
+            return oracle.evolve_direct_td(x, z, job.ham.a, job.ham.b, job.drive[:k], dt * k, psi, order)
         if order == 1:
             return oracle.evolve_direct(x, z, job.ham.coeffs, dt * k, k, psi)
         return oracle.evolve_direct_order(x, z, job.ham.coeffs, dt * k, k, psi, order)
@@ -550,6 +576,8 @@ def oracle_sample(job, G, budget_s=15.0, order=1):
     units = k * G * N
     R = np.asarray(job.psi0).shape[0] if np.asarray(job.psi0).ndim == 2 else 1
     kind = "first-order" if order == 1 else f"order-{order} product-formula"
+    if job.drive is not None:
+        kind += " time-dependent"
     return dict(value=units / t1, seconds=t1, steps=k,
                 sample=f"{k} of {job.n_steps} {kind} steps of state 0 (of {R}), direct term-by-term FP64 "
                        f"evolution, single thread; units counted as steps x {G} factor applications x N={N}")
@@ -561,6 +589,9 @@ def config_of(args, job, desc, res=None):
          "t": job.t, "l2": "flushed (512 MiB write) before every timed step"}
     if getattr(args, "order", 1) != 1:
         c["product_formula_order"] = args.order
+    if job.drive is not None:
+        c["time_dependent"] = "H0 + f(t) H1, f frozen per step at the caller's sample"
+        c["driven_terms"] = int(np.count_nonzero(job.ham.b))
     if res:
         c.update({"factor_applications_per_step": res["G"], "tile_bits": res["tile_bits"], "rhs_block": res["rhs_block"],
                   "sweep_launches_per_step": res["n_sweeps"], "plain_launches_per_step": res["n_plain"]})
@@ -633,7 +664,9 @@ def run_ours(args):
                          "traffic": traffic, "peak_source": peak_kind,
                          "kernel": "sweep_kernel" if res["n_sweeps"] else "apply_plain_kernel",
                          "algorithmic_bytes_per_launch": per_launch_bytes,
-                         "avg_launch_us": avg_launch_s * 1e6, **dram_fields(traffic, avg_launch_s, hbm)},
+                         "avg_launch_us": avg_launch_s * 1e6, **dram_fields(traffic, avg_launch_s, hbm),
+                         **({"note": "evolution time per sweep launch, including the per-step rebuild "
+                                     "launches of the driven factors"} if job.drive is not None else {})},
             "e2e": {"value": res["units"] / (e2e["ms"] / 1000.0), "unit": METRIC,
                     "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"]},
             "gpu_launches": res["launches"], "clocks": res["clocks"],

@@ -33,8 +33,9 @@
  *     created, and a call rejected before any launch leaves caller buffers
  *     untouched.
  *   - The library never frees caller memory.  hs_factors objects are owned
- *     by the library (device-resident, immutable after the build) and freed
- *     only by hs_free_factors.
+ *     by the library (device-resident, immutable after the build except for
+ *     the values of a time-dependent set, which hs_evolve_td and
+ *     hs_factors_set_drive rebuild) and freed only by hs_free_factors.
  */
 #ifndef HS_H
 #define HS_H
@@ -160,6 +161,45 @@ typedef struct {
 /* hs_evolve with an explicit method and tiling (opts may be NULL = AUTO). */
 int hs_evolve_ex(const hs_factors* f, void* psi, int n_rhs, int n_steps, const hs_evolve_opts* opts,
                  void* cuda_stream);
+
+/* Time-dependent Hamiltonians H(t) = H0 + f(t) H1 (the paper's outlook on
+ * time-dependent Hamiltonians: the grouping and layout are fixed once and
+ * serve every time step).  Term j has coefficient coeffs0[j] in H0 and
+ * coeffs1[j] in H1 (host arrays of n_terms finite FP64 values; zero where the
+ * term belongs to one of them only).  Step k of an evolution freezes the drive
+ * at a caller-given sample f_k and applies the product formula of `order`
+ * (as hs_build_factors_ex) with coefficients c_j = coeffs0[j] + f_k coeffs1[j]
+ * (the product rounded before the sum), dt = t / n_steps.  The structure
+ * depends only on the masks, so it is the one hs_build_factors_ex gives; the
+ * values are built for f = 0 (H0).  Errors as hs_build_factors_ex; HS_EINVAL
+ * if coeffs1 is NULL or holds a non-finite value. */
+int hs_build_factors_td(const uint64_t* x, const uint64_t* z, const double* coeffs0, const double* coeffs1,
+                        size_t n_terms, int n_qubits, double t, int n_steps, int diag_budget, int order,
+                        hs_dtype dtype, void* cuda_stream, hs_factors** out);
+
+/* Evolve psi in place by n_steps steps of a time-dependent factor set (each
+ * of length dt = t / n_steps of the build), step k with the drive sample
+ * drive[k] (host array of n_steps finite values, copied
+ * before the call returns; sampling f at the step midpoints gives the
+ * exponential midpoint rule).  Each step first rebuilds, on the device in
+ * FP64, the values of the factors that hold a term with coeffs1[j] != 0 (their
+ * value tables, and the stored diagonals of factors that have no table or that
+ * the chosen method reads from diagonals), then applies the step as
+ * hs_evolve_ex would; sweeps never span two steps.  The factor values are
+ * those of drive[n_steps - 1] afterwards, so calls on one factor set must be
+ * ordered (one stream).  opts as hs_evolve_ex (NULL = AUTO); use_graph
+ * captures the whole evolution once per (psi, n_rhs, n_steps, options) and
+ * replays it with the new drive samples.  Errors: HS_EINVAL (static factor
+ * set, NULL or non-finite drive, bad psi / n_rhs / options), HS_ENOMEM,
+ * HS_ECUDA. */
+int hs_evolve_td(hs_factors* f, void* psi, int n_rhs, const double* drive, int n_steps, const hs_evolve_opts* opts,
+                 void* cuda_stream);
+
+/* Rebuild the values of a time-dependent factor set for one frozen drive
+ * value (every dependent factor: value tables and stored diagonals), enqueued
+ * on cuda_stream; hs_evolve / hs_factor_get then see H0 + drive H1.
+ * Errors: HS_EINVAL (static factor set, non-finite drive), HS_ECUDA. */
+int hs_factors_set_drive(hs_factors* f, double drive, void* cuda_stream);
 
 /* Launch plan of hs_evolve_ex for these arguments, computed on the host
  * without launching anything: the number of fused tile-sweep launches, of

@@ -55,6 +55,7 @@ void release(hs_factors* f, cudaStream_t s) {
   }
   if (f->d_vals) cudaFreeAsync(f->d_vals, s);
   if (f->d_tables) cudaFreeAsync(f->d_tables, s);
+  if (f->d_drive) cudaFreeAsync(f->d_drive, s);
   delete f;
 }
 
@@ -296,19 +297,17 @@ int report_error(int code, const std::string& msg) { return fail(code, msg); }
 }  // namespace hs
 
 bool hs_factors::GraphKey::operator<(const GraphKey& o) const {
-  return std::tie(psi, n_rhs, n_steps, method, tile_bits, rhs_block, stream) <
-         std::tie(o.psi, o.n_rhs, o.n_steps, o.method, o.tile_bits, o.rhs_block, o.stream);
+  return std::tie(psi, n_rhs, n_steps, method, tile_bits, rhs_block, stream, variant) <
+         std::tie(o.psi, o.n_rhs, o.n_steps, o.method, o.tile_bits, o.rhs_block, o.stream, o.variant);
 }
 
-extern "C" {
+namespace {
 
-const char* hs_last_error(void) { return g_err.c_str(); }
-
-uint64_t hs_kernel_launches(void) { return hs::g_launches.load(std::memory_order_relaxed); }
-
-int hs_build_factors_ex(const uint64_t* x, const uint64_t* z, const double* coeffs, size_t n_terms, int n_qubits,
-                        double t, int n_steps, int diag_budget, int order, hs_dtype dtype, void* cuda_stream,
-                        hs_factors** out) {
+// Build a factor set; coeffs1 non-NULL makes it time-dependent (H0 + f(t) H1,
+// values built for f = 0).
+int build_impl(const uint64_t* x, const uint64_t* z, const double* coeffs, const double* coeffs1, size_t n_terms,
+               int n_qubits, double t, int n_steps, int diag_budget, int order, hs_dtype dtype, void* cuda_stream,
+               hs_factors** out) {
   if (!out) return fail(HS_EINVAL, "out is NULL");
   *out = nullptr;
   if (!x || !z || !coeffs) return fail(HS_EINVAL, "null term arrays");
@@ -316,9 +315,12 @@ int hs_build_factors_ex(const uint64_t* x, const uint64_t* z, const double* coef
   if (!(std::isfinite(t) && t > 0)) return fail(HS_EINVAL, "t must be finite and > 0");
   if (n_steps < 1) return fail(HS_EINVAL, "n_steps must be >= 1");
   if (diag_budget < 1) return fail(HS_EINVAL, "diag_budget must be >= 1");
+  if (order != 1 && order != 2 && order != 4) return fail(HS_EINVAL, "order must be 1, 2 or 4");
+  if (coeffs1)
+    for (size_t j = 0; j < n_terms; ++j)
+      if (!std::isfinite(coeffs1[j])) return fail(HS_EINVAL, "non-finite H1 coefficient at term " + std::to_string(j));
   std::unique_ptr<hs_factors> f(new hs_factors());
   std::string err;
-  if (order != 1 && order != 2 && order != 4) return fail(HS_EINVAL, "order must be 1, 2 or 4");
   int rc = cached_plan(x, z, coeffs, n_terms, n_qubits, diag_budget, dtype, order, f->plan, &err);
   if (rc != HS_OK) return fail(rc, err);
   f->dtype = dtype;
@@ -336,8 +338,8 @@ int hs_build_factors_ex(const uint64_t* x, const uint64_t* z, const double* coef
   auto guard = [&](cudaError_t e2, const char* what) -> int { return e2 == cudaSuccess ? HS_OK : cuda_fail(e2, what); };
   // Stream-ordered allocations (building, using and freeing a factor set never
   // synchronises the device): one for the values and one for every table --
-  // the persistent per-diagonal / per-factor / slot tables and the build-only
-  // term tables -- filled by a single host-to-device copy.
+  // the persistent per-diagonal / per-factor / slot tables and the term tables
+  // the values are built from -- filled by a single host-to-device copy.
   if ((rc = guard(hs::pool_malloc(&fp->d_vals, vbytes, s), "cudaMallocAsync(values)"))) {
     release(f.release(), s);
     return rc;
@@ -345,7 +347,7 @@ int hs_build_factors_ex(const uint64_t* x, const uint64_t* z, const double* coef
   fp->d_vt = static_cast<unsigned char*>(fp->d_vals) + size_t(p.total_elems) * hs::elem_bytes(dtype);
   const size_t m = n_terms;
   std::vector<int> fD(G), fd0(G), gfirst(G), glast(G), xdim(G), pivot(G * hs::kMaxXDim, 0), vt0(G), gkind(G),
-      gdir(G);
+      gdir(G), dep_all, dep_notab, dep_tab;
   std::vector<uint32_t> smask(G);
   std::vector<uint64_t> basis(G * hs::kMaxXDim, 0);
   for (int g = 0; g < G; ++g) {
@@ -363,6 +365,12 @@ int hs_build_factors_ex(const uint64_t* x, const uint64_t* z, const double* coef
       basis[g * hs::kMaxXDim + i] = gr.basis[i];
       pivot[g * hs::kMaxXDim + i] = gr.pivot[i];
     }
+    bool dep = false;
+    for (int j = gr.first; coeffs1 && j < gr.last; ++j) dep = dep || coeffs1[j] != 0.0;
+    if (dep) {
+      dep_all.push_back(g);
+      (gr.vt0 >= 0 ? dep_tab : dep_notab).push_back(g);
+    }
   }
   std::vector<unsigned char> blob;
   auto put = [&](const void* src, size_t bytes) {
@@ -376,14 +384,19 @@ int hs_build_factors_ex(const uint64_t* x, const uint64_t* z, const double* coef
   const size_t o_su = put(p.slot_u.data(), p.slot_u.size() * 4), o_st = put(p.slot_tab.data(), p.slot_tab.size() * 4);
   const size_t o_tab = put(p.tab_rb.data(), p.tab_rb.size() * 8);
   const size_t o_x = put(p.x.data(), m * 8), o_z = put(p.z.data(), m * 8), o_c = put(p.coeff.data(), m * 8);
+  const size_t o_c1 = coeffs1 ? put(coeffs1, m * 8) : 0;
   const size_t o_cx = put(p.term_cx.data(), m * 4), o_gf = put(gfirst.data(), G * 4), o_gl = put(glast.data(), G * 4);
   const size_t o_b = put(basis.data(), basis.size() * 8), o_xd = put(xdim.data(), G * 4);
   const size_t o_pv = put(pivot.data(), pivot.size() * 4);
   const size_t o_sm = put(smask.data(), G * 4), o_vt0 = put(vt0.data(), G * 4);
   const size_t o_kind = put(gkind.data(), G * 4), o_dir = put(gdir.data(), G * 4);
+  const size_t o_da = put(dep_all.data(), dep_all.size() * 4), o_dn = put(dep_notab.data(), dep_notab.size() * 4);
+  const size_t o_dt = put(dep_tab.data(), dep_tab.size() * 4);
   const std::vector<double> hk = hs::kind_steps(p.order, t / double(n_steps));
   const size_t o_h = put(hk.data(), hk.size() * 8);
+  const size_t o_fv = put(nullptr, 8);                   // drive value of hs_factors_set_drive
   const size_t o_cs = put(nullptr, m * 16 * hk.size());  // (cos, sin) per term and angle kind, written on the device
+  const size_t o_th = put(nullptr, m * 8 * hk.size());   // the angles themselves
   unsigned char* d_blob = nullptr;
   if ((rc = guard(hs::pool_malloc((void**)&d_blob, blob.size(), s), "cudaMallocAsync(tables)"))) {
     release(f.release(), s);
@@ -397,32 +410,40 @@ int hs_build_factors_ex(const uint64_t* x, const uint64_t* z, const double* coef
   fp->d_slot_u = reinterpret_cast<uint32_t*>(d_blob + o_su);
   fp->d_slot_tab = reinterpret_cast<int32_t*>(d_blob + o_st);
   fp->d_tab_rb = reinterpret_cast<int64_t*>(d_blob + o_tab);
-  if ((rc = guard(cudaError_t(stage_upload(d_blob, blob.data(), o_cs, s)), "table upload"))) {
+  hs_build_inputs& bi = fp->bin;
+  bi.x = reinterpret_cast<const uint64_t*>(d_blob + o_x);
+  bi.z = reinterpret_cast<const uint64_t*>(d_blob + o_z);
+  bi.coeff = reinterpret_cast<const double*>(d_blob + o_c);
+  bi.coeff1 = coeffs1 ? reinterpret_cast<const double*>(d_blob + o_c1) : nullptr;
+  bi.cx = reinterpret_cast<const uint32_t*>(d_blob + o_cx);
+  bi.gfirst = reinterpret_cast<const int*>(d_blob + o_gf);
+  bi.glast = reinterpret_cast<const int*>(d_blob + o_gl);
+  bi.basis = reinterpret_cast<const uint64_t*>(d_blob + o_b);
+  bi.xdim = reinterpret_cast<const int*>(d_blob + o_xd);
+  bi.pivot = reinterpret_cast<const int*>(d_blob + o_pv);
+  bi.smask = reinterpret_cast<const uint32_t*>(d_blob + o_sm);
+  bi.vt0 = reinterpret_cast<const int*>(d_blob + o_vt0);
+  bi.kind = reinterpret_cast<const int*>(d_blob + o_kind);
+  bi.dir = reinterpret_cast<const int*>(d_blob + o_dir);
+  bi.h = reinterpret_cast<const double*>(d_blob + o_h);
+  bi.cs = reinterpret_cast<double*>(d_blob + o_cs);
+  bi.th = reinterpret_cast<double*>(d_blob + o_th);
+  bi.fval = reinterpret_cast<double*>(d_blob + o_fv);
+  bi.n_kinds = int(hk.size());
+  bi.dep_all = reinterpret_cast<const int*>(d_blob + o_da);
+  bi.dep_notab = reinterpret_cast<const int*>(d_blob + o_dn);
+  bi.dep_tab = reinterpret_cast<const int*>(d_blob + o_dt);
+  bi.n_dep_all = int(dep_all.size());
+  bi.n_dep_notab = int(dep_notab.size());
+  bi.n_dep_tab = int(dep_tab.size());
+  if ((rc = guard(cudaError_t(stage_upload(d_blob, blob.data(), o_fv, s)), "table upload"))) {
     cudaStreamSynchronize(s);
     release(f.release(), s);
     return rc;
   }
-  double* d_cs = reinterpret_cast<double*>(d_blob + o_cs);
-  e = hs::launch_sincos(reinterpret_cast<const double*>(d_blob + o_c), reinterpret_cast<const double*>(d_blob + o_h),
-                        int(hk.size()), d_cs, int(m), s);
-  if (e == cudaSuccess)
-    e = hs::launch_value_tables(fp, d_cs, reinterpret_cast<const uint64_t*>(d_blob + o_x),
-                                reinterpret_cast<const uint64_t*>(d_blob + o_z),
-                                reinterpret_cast<const uint32_t*>(d_blob + o_cx),
-                                reinterpret_cast<const int*>(d_blob + o_gf), reinterpret_cast<const int*>(d_blob + o_gl),
-                                reinterpret_cast<const uint64_t*>(d_blob + o_b),
-                                reinterpret_cast<const int*>(d_blob + o_xd), reinterpret_cast<const int*>(d_blob + o_pv),
-                                reinterpret_cast<const uint32_t*>(d_blob + o_sm),
-                                reinterpret_cast<const int*>(d_blob + o_vt0), reinterpret_cast<const int*>(d_blob + o_kind),
-                                reinterpret_cast<const int*>(d_blob + o_dir), s);
-  if (e == cudaSuccess)
-    e = hs::launch_build(fp, d_cs, reinterpret_cast<const uint64_t*>(d_blob + o_x),
-                         reinterpret_cast<const uint64_t*>(d_blob + o_z), reinterpret_cast<const uint32_t*>(d_blob + o_cx),
-                         reinterpret_cast<const int*>(d_blob + o_gf), reinterpret_cast<const int*>(d_blob + o_gl),
-                         reinterpret_cast<const uint64_t*>(d_blob + o_b), reinterpret_cast<const int*>(d_blob + o_xd),
-                         reinterpret_cast<const int*>(d_blob + o_pv), reinterpret_cast<const uint32_t*>(d_blob + o_sm),
-                         reinterpret_cast<const int*>(d_blob + o_vt0), reinterpret_cast<const int*>(d_blob + o_kind),
-                         reinterpret_cast<const int*>(d_blob + o_dir), s);
+  e = hs::launch_sincos(fp, nullptr, s);
+  if (e == cudaSuccess) e = hs::launch_value_tables(fp, nullptr, 0, s);
+  if (e == cudaSuccess) e = hs::launch_build(fp, nullptr, 0, s);
   if (e != cudaSuccess) {
     cudaStreamSynchronize(s);
     release(f.release(), s);
@@ -430,6 +451,32 @@ int hs_build_factors_ex(const uint64_t* x, const uint64_t* z, const double* coef
   }
   *out = f.release();
   return HS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* hs_last_error(void) { return g_err.c_str(); }
+
+uint64_t hs_kernel_launches(void) { return hs::g_launches.load(std::memory_order_relaxed); }
+
+int hs_build_factors_ex(const uint64_t* x, const uint64_t* z, const double* coeffs, size_t n_terms, int n_qubits,
+                        double t, int n_steps, int diag_budget, int order, hs_dtype dtype, void* cuda_stream,
+                        hs_factors** out) {
+  return build_impl(x, z, coeffs, nullptr, n_terms, n_qubits, t, n_steps, diag_budget, order, dtype, cuda_stream,
+                    out);
+}
+
+int hs_build_factors_td(const uint64_t* x, const uint64_t* z, const double* coeffs0, const double* coeffs1,
+                        size_t n_terms, int n_qubits, double t, int n_steps, int diag_budget, int order,
+                        hs_dtype dtype, void* cuda_stream, hs_factors** out) {
+  if (!coeffs1) {
+    if (out) *out = nullptr;
+    return fail(HS_EINVAL, "coeffs1 is NULL");
+  }
+  return build_impl(x, z, coeffs0, coeffs1, n_terms, n_qubits, t, n_steps, diag_budget, order, dtype, cuda_stream,
+                    out);
 }
 
 int hs_build_factors_masks(const uint64_t* x, const uint64_t* z, const double* coeffs, size_t n_terms, int n_qubits,
@@ -560,7 +607,7 @@ int hs_evolve_ex(const hs_factors* f, void* psi, int n_rhs, int n_steps, const h
 
   if (o.use_graph) {
     hs_factors::GraphKey key{psi, n_rhs, n_steps, int(o.method) * 128 + o.max_fuse, tb + 64 * o.smem_kb,
-                             (rb * 64 + o.low_bits) * 2 + (o.no_tables != 0), nullptr};
+                             (rb * 64 + o.low_bits) * 2 + (o.no_tables != 0), nullptr, 0};
     cudaGraphExec_t exec = nullptr;
     {
       std::lock_guard<std::mutex> lk(f->graph_mu);
@@ -611,6 +658,153 @@ int hs_evolve_ex(const hs_factors* f, void* psi, int n_rhs, int n_steps, const h
 
 int hs_evolve(const hs_factors* f, void* psi, int n_rhs, int n_steps, void* cuda_stream) {
   return hs_evolve_ex(f, psi, n_rhs, n_steps, nullptr, cuda_stream);
+}
+
+// Rebuild the values of the groups that depend on the drive for the drive
+// value at d_fval: angles, the value tables of those groups, then the stored
+// diagonals of the listed groups.
+cudaError_t enqueue_drive_rebuild(const hs_factors* f, const double* d_fval, const int* diag_groups, int n_diag,
+                                  cudaStream_t s) {
+  const hs_build_inputs& b = f->bin;
+  cudaError_t e = hs::launch_sincos(f, d_fval, s);
+  if (e == cudaSuccess && b.n_dep_tab > 0) e = hs::launch_value_tables(f, b.dep_tab, b.n_dep_tab, s);
+  if (e == cudaSuccess && n_diag > 0) e = hs::launch_build(f, diag_groups, n_diag, s);
+  return e;
+}
+
+int hs_factors_set_drive(hs_factors* f, double drive, void* cuda_stream) {
+  if (!f) return fail(HS_EINVAL, "factors is NULL");
+  if (!f->bin.coeff1) return fail(HS_EINVAL, "factors are not time-dependent (built without H1 coefficients)");
+  if (!std::isfinite(drive)) return fail(HS_EINVAL, "drive value must be finite");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+  cudaError_t e = cudaError_t(stage_upload(f->bin.fval, &drive, sizeof(double), s));
+  if (e == cudaSuccess) e = enqueue_drive_rebuild(f, f->bin.fval, f->bin.dep_all, f->bin.n_dep_all, s);
+  return e == cudaSuccess ? HS_OK : cuda_fail(e, "drive rebuild");
+}
+
+int hs_evolve_td(hs_factors* f, void* psi, int n_rhs, const double* drive, int n_steps, const hs_evolve_opts* opts,
+                 void* cuda_stream) {
+  if (!f) return fail(HS_EINVAL, "factors is NULL");
+  if (!f->bin.coeff1) return fail(HS_EINVAL, "factors are not time-dependent (built without H1 coefficients)");
+  if (!psi) return fail(HS_EINVAL, "psi is NULL");
+  if (n_rhs < 1) return fail(HS_EINVAL, "n_rhs must be >= 1");
+  if (n_steps < 0) return fail(HS_EINVAL, "n_steps must be >= 0");
+  if (n_steps > 0 && !drive) return fail(HS_EINVAL, "drive is NULL");
+  if (reinterpret_cast<uintptr_t>(psi) % 16) return fail(HS_EINVAL, "psi must be 16-byte aligned");
+  for (int k = 0; k < n_steps; ++k)
+    if (!std::isfinite(drive[k])) return fail(HS_EINVAL, "non-finite drive value at step " + std::to_string(k));
+  hs_evolve_opts o;
+  int tb = 0, rb = 0;
+  int rc0 = resolve_opts(f, n_rhs, opts, o, tb, rb);
+  if (rc0 != HS_OK) return rc0;
+  if (n_steps == 0) return HS_OK;
+  {
+    cudaError_t e = hs::prepare_kernels();
+    if (e != cudaSuccess) return cuda_fail(e, "kernel attributes");
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+  // One step's launches: the values change from step to step, so no sweep
+  // spans a step boundary.
+  const std::vector<hs::Sweep> sw = hs::plan_sweeps(f->plan, 1, tb, o.low_bits, o.method != HS_METHOD_PLAIN,
+                                                    hs::kMaxFusedDiags, o.max_fuse);
+  const bool scratch_needed = has_plain(sw);
+  const size_t smem_budget = o.smem_kb > 0 ? size_t(o.smem_kb) * 1024 : hs::kSweepSmemDefault;
+  const bool tables = o.no_tables == 0;
+  // Sweeps that read value tables need only the tables of table groups
+  // rebuilt each step; plain launches and table-free sweeps read diagonals.
+  const hs_build_inputs& b = f->bin;
+  const bool diag_all = !tables || scratch_needed;
+  const int* diag_groups = diag_all ? b.dep_all : b.dep_notab;
+  const int n_diag = diag_all ? b.n_dep_all : b.n_dep_notab;
+
+  // Drive samples in a library-owned device buffer (captured graphs read it).
+  if (f->drive_cap < n_steps) {
+    cudaStreamSynchronize(s);
+    {
+      std::lock_guard<std::mutex> lk(f->graph_mu);
+      for (auto it = f->graphs.begin(); it != f->graphs.end();) {
+        if (it->first.variant == 1) {
+          cudaGraphExecDestroy(it->second);
+          it = f->graphs.erase(it);
+        } else {
+          ++it;
+        }
+      }
+    }
+    if (f->d_drive) cudaFreeAsync(f->d_drive, s);
+    f->d_drive = nullptr;
+    f->drive_cap = 0;
+    const int cap = std::max(n_steps, 64);
+    cudaError_t e = hs::pool_malloc((void**)&f->d_drive, size_t(cap) * sizeof(double), s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(drive)");
+    f->drive_cap = cap;
+  }
+  {
+    cudaError_t e = cudaError_t(stage_upload(f->d_drive, drive, size_t(n_steps) * sizeof(double), s));
+    if (e != cudaSuccess) return cuda_fail(e, "drive upload");
+  }
+  auto enqueue_all = [&](cudaStream_t cs, void* scratch) -> int {
+    for (int k = 0; k < n_steps; ++k) {
+      cudaError_t e = enqueue_drive_rebuild(f, f->d_drive + k, diag_groups, n_diag, cs);
+      if (e != cudaSuccess) return cuda_fail(e, "drive rebuild");
+      int rc = enqueue_evolve(f, sw, psi, n_rhs, tb, rb, smem_budget, tables, scratch, cs);
+      if (rc != HS_OK) return rc;
+    }
+    // Leave every stored value at the last step's drive.
+    if (!diag_all && b.n_dep_tab > 0) {
+      cudaError_t e = hs::launch_build(f, b.dep_tab, b.n_dep_tab, cs);
+      if (e != cudaSuccess) return cuda_fail(e, "factor build launch");
+    }
+    return HS_OK;
+  };
+
+  if (o.use_graph) {
+    if (scratch_needed) return fail(HS_EINVAL, "use_graph needs a schedule without plain fallbacks");
+    hs_factors::GraphKey key{psi, n_rhs, n_steps, int(o.method) * 128 + o.max_fuse, tb + 64 * o.smem_kb,
+                             (rb * 64 + o.low_bits) * 2 + (o.no_tables != 0), nullptr, 1};
+    cudaGraphExec_t exec = nullptr;
+    {
+      std::lock_guard<std::mutex> lk(f->graph_mu);
+      auto it = f->graphs.find(key);
+      if (it != f->graphs.end()) exec = it->second;
+    }
+    if (!exec) {
+      cudaStream_t cs;
+      cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
+      e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) { cudaStreamDestroy(cs); return cuda_fail(e, "cudaStreamBeginCapture"); }
+      hs::begin_capture_count();
+      int rc = enqueue_all(cs, nullptr);
+      const uint64_t n_kernels = hs::end_capture_count();
+      cudaGraph_t graph = nullptr;
+      e = cudaStreamEndCapture(cs, &graph);
+      cudaStreamDestroy(cs);
+      if (rc != HS_OK) { if (graph) cudaGraphDestroy(graph); return rc; }
+      if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+      e = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+      std::lock_guard<std::mutex> lk(f->graph_mu);
+      f->graphs[key] = exec;
+      std::lock_guard<std::mutex> lk2(g_graph_mu);
+      g_graph_kernels[exec] = n_kernels;
+    }
+    cudaError_t e = cudaGraphLaunch(exec, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+    std::lock_guard<std::mutex> lk2(g_graph_mu);
+    hs::note_launches(g_graph_kernels[exec]);
+    return HS_OK;
+  }
+
+  void* scratch = nullptr;
+  if (scratch_needed) {
+    cudaError_t e = hs::pool_malloc(&scratch, size_t(n_rhs) * size_t(f->plan.N) * hs::elem_bytes(f->dtype), s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(scratch state)");
+  }
+  int rc = enqueue_all(s, scratch);
+  if (scratch) cudaFreeAsync(scratch, s);
+  return rc;
 }
 
 int hs_apply_factor(const hs_factors* f, int g, const void* x, void* y, int n_rhs, void* cuda_stream) {

@@ -27,6 +27,7 @@ struct BuildArgs {
   const int* fac_D;
   const int* fac_diag0;
   const double* cs;  // (cos, sin) per term
+  const double* th;  // theta per term (same indexing as cs / 2)
   const uint64_t* x;
   const uint64_t* z;
   const uint32_t* cx;
@@ -42,7 +43,12 @@ struct BuildArgs {
   const int* kind;        // per group: angle kind (cs holds m (cos, sin) pairs per kind)
   const int* dir;         // per group: +1 terms first..last act in order, -1 reversed
   int m;                  // number of terms
+  const int* glist;       // groups of grid row blockIdx.y (NULL: group blockIdx.y)
 };
+
+__device__ __forceinline__ int group_of(const BuildArgs& a) {
+  return a.glist ? a.glist[blockIdx.y] : int(blockIdx.y);
+}
 
 __device__ __forceinline__ double2 mul_ipow(double2 v, int k) {
   switch (k & 3) {
@@ -65,6 +71,7 @@ template <int MAXS>
 struct GroupRows {
   int xd, S, first, last, dir;
   const double* cs;  // this group's angle kind
+  const double* th;
   uint64_t bas[kMaxXDim];
   int piv[kMaxXDim];
   uint64_t u[MAXS];
@@ -80,6 +87,7 @@ struct GroupRows {
     last = a.glast[g];
     dir = a.dir[g];
     cs = a.cs + size_t(2) * a.m * a.kind[g];
+    th = a.th + size_t(a.m) * a.kind[g];
 #pragma unroll
     for (int s = 0; s < MAXS; ++s) {
       uint64_t m = 0;
@@ -93,15 +101,46 @@ struct GroupRows {
   // r ^ u_s), by applying R_j^dagger = cos I + i sin P_j in the reverse of the
   // order in which F_g applies the R_j: j = last-1 .. first for a forward
   // factor (F_g = R_last ... R_first), j = first .. last-1 for a reversed one.
+  // A run of consecutive diagonal terms (x_j = 0) commutes and multiplies each
+  // slot by a phase: R_j^dagger scales basis state b by exp(+i theta_j
+  // (-1)^popcount(z_j & b)), so the run's angles are summed per slot and
+  // applied with one FP64 sincos per slot when the run ends.
   __device__ __forceinline__ void row(const BuildArgs& a, uint64_t r, double2 (&w)[MAXS]) const {
     double2 nw[MAXS];
+    double phi[MAXS];
 #pragma unroll
-    for (int s = 0; s < MAXS; ++s) w[s] = make_double2(s == 0 ? 1.0 : 0.0, 0.0);
+    for (int s = 0; s < MAXS; ++s) {
+      w[s] = make_double2(s == 0 ? 1.0 : 0.0, 0.0);
+      phi[s] = 0.0;
+    }
+    bool pending = false;
     const int n_t = last - first;
-    for (int q = 0; q < n_t; ++q) {
+    for (int q = 0; q <= n_t; ++q) {
       const int j = dir > 0 ? last - 1 - q : first + q;
+      const uint64_t xj = q < n_t ? a.x[j] : 1;
+      if (q < n_t && xj == 0) {
+        const double t = th[j];
+        const uint64_t zj = a.z[j];
+#pragma unroll
+        for (int s = 0; s < MAXS; ++s)
+          if (s < S) phi[s] += (__popcll(zj & (r ^ u[s])) & 1) ? -t : t;
+        pending = true;
+        continue;
+      }
+      if (pending) {
+#pragma unroll
+        for (int s = 0; s < MAXS; ++s)
+          if (s < S) {
+            double sn, c;
+            sincos(phi[s], &sn, &c);
+            w[s] = make_double2(c * w[s].x - sn * w[s].y, c * w[s].y + sn * w[s].x);
+            phi[s] = 0.0;
+          }
+        pending = false;
+      }
+      if (q == n_t) break;
       const double c = cs[2 * j], sn = cs[2 * j + 1];
-      const uint64_t xj = a.x[j], zj = a.z[j];
+      const uint64_t zj = a.z[j];
       const int y = __popcll(xj & zj);
       const uint32_t cxj = a.cx[j];
 #pragma unroll
@@ -132,7 +171,7 @@ __device__ __forceinline__ double2 load_val(const void* vals, int64_t idx, bool 
 
 template <int MAXS>
 __global__ void __launch_bounds__(256) build_kernel(BuildArgs a, bool c64) {
-  const int g = blockIdx.y;
+  const int g = group_of(a);
   GroupRows<MAXS> G;
   G.load(a, g);
   const int D = a.fac_D[g], d0 = a.fac_diag0[g];
@@ -188,7 +227,7 @@ __global__ void __launch_bounds__(256) build_kernel(BuildArgs a, bool c64) {
 template <int MAXS>
 __global__ void __launch_bounds__(256) value_table_kernel(BuildArgs a, const uint32_t* smask, const int* vt0,
                                                           void* vt, bool c64) {
-  const int g = blockIdx.y;
+  const int g = group_of(a);
   if (vt0[g] < 0) return;
   const uint32_t sm = smask[g];
   const int bits = __popc(sm);
@@ -206,42 +245,55 @@ __global__ void __launch_bounds__(256) value_table_kernel(BuildArgs a, const uin
     if (s < G.S) store_val(vt, int64_t(vt0[g]) + int64_t(p) * G.S + s, make_double2(w[s].x, -w[s].y), c64);
 }
 
-// cs[2 (k n + j) + {0, 1}] = (cos, sin)(coeff[j] * h[k]) for kind k.
-__global__ void sincos_kernel(const double* coeff, const double* h, int n_kinds, double* cs, int n) {
+// cs[2 (k n + j) + {0, 1}] = (cos, sin)(c_j * h[k]) for kind k, with c_j =
+// coeff[j], or coeff[j] + f coeff1[j] (f = *fval, the product rounded before
+// the sum, no fused multiply-add) for a time-dependent set.
+__global__ void sincos_kernel(const double* coeff, const double* coeff1, const double* fval, const double* h,
+                              int n_kinds, double* cs, double* th, int n) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e < n * n_kinds) {
     const int k = e / n, j = e - k * n;
-    const double theta = coeff[j] * h[k];
-    double s, c;
-    sincos(theta, &s, &c);
-    cs[2 * e] = c;
+    double c = coeff[j];
+    if (coeff1) c = __dadd_rn(c, __dmul_rn(fval ? *fval : 0.0, coeff1[j]));
+    const double theta = c * h[k];
+    th[e] = theta;
+    double s, co;
+    sincos(theta, &s, &co);
+    cs[2 * e] = co;
     cs[2 * e + 1] = s;
   }
 }
 
+BuildArgs build_args(const hs_factors* f, const int* glist) {
+  const hs_build_inputs& b = f->bin;
+  return BuildArgs{f->d_vals, f->d_offs, f->d_rowbase, f->d_fac_D, f->d_fac_diag0, b.cs, b.th, b.x, b.z, b.cx,
+                   b.gfirst, b.glast, b.basis, b.xdim, b.pivot, f->plan.N, b.smask, b.vt0, f->d_vt, b.kind,
+                   b.dir, int(f->plan.x.size()), glist};
+}
+
 }  // namespace
 
-cudaError_t launch_sincos(const double* d_coeff, const double* d_h, int n_kinds, double* d_cs, int n, cudaStream_t s) {
-  sincos_kernel<<<(n * n_kinds + 127) / 128, 128, 0, s>>>(d_coeff, d_h, n_kinds, d_cs, n);
+cudaError_t launch_sincos(const hs_factors* f, const double* d_fval, cudaStream_t s) {
+  const hs_build_inputs& b = f->bin;
+  const int n = int(f->plan.x.size());
+  sincos_kernel<<<(n * b.n_kinds + 127) / 128, 128, 0, s>>>(b.coeff, b.coeff1, d_fval, b.h, b.n_kinds, b.cs, b.th,
+                                                            n);
   note_launches();
   return cudaGetLastError();
 }
 
-cudaError_t launch_build(const hs_factors* f, const double* d_cs, const uint64_t* d_x, const uint64_t* d_z,
-                         const uint32_t* d_cx, const int* d_gfirst, const int* d_glast, const uint64_t* d_basis,
-                         const int* d_xdim, const int* d_pivot, const uint32_t* d_smask, const int* d_vt0,
-                         const int* d_kind, const int* d_dir, cudaStream_t s) {
+cudaError_t launch_build(const hs_factors* f, const int* d_groups, int n_groups, cudaStream_t s) {
   const Plan& p = f->plan;
+  const int G = d_groups ? n_groups : int(p.groups.size());
+  if (G <= 0) return cudaSuccess;
   int maxdim = 0;
   for (const Group& g : p.groups) maxdim = g.xdim > maxdim ? g.xdim : maxdim;
-  BuildArgs a{f->d_vals, f->d_offs, f->d_rowbase, f->d_fac_D, f->d_fac_diag0, d_cs, d_x, d_z, d_cx,
-              d_gfirst, d_glast, d_basis, d_xdim, d_pivot, p.N, d_smask, d_vt0, f->d_vt, d_kind, d_dir,
-              int(p.x.size())};
+  const BuildArgs a = build_args(f, d_groups);
   const bool c64 = f->dtype == HS_C64;
   const int threads = 256;
   int64_t blocks_x = (p.N + threads - 1) / threads;
   if (blocks_x > 4096) blocks_x = 4096;
-  dim3 grid(unsigned(blocks_x), unsigned(p.groups.size()));
+  const dim3 grid{unsigned(blocks_x), unsigned(G), 1u};
   switch (maxdim) {
     case 0: build_kernel<1><<<grid, threads, 0, s>>>(a, c64); break;
     case 1: build_kernel<2><<<grid, threads, 0, s>>>(a, c64); break;
@@ -255,30 +307,28 @@ cudaError_t launch_build(const hs_factors* f, const double* d_cs, const uint64_t
   return cudaGetLastError();
 }
 
-cudaError_t launch_value_tables(const hs_factors* f, const double* d_cs, const uint64_t* d_x, const uint64_t* d_z,
-                                const uint32_t* d_cx, const int* d_gfirst, const int* d_glast, const uint64_t* d_basis,
-                                const int* d_xdim, const int* d_pivot, const uint32_t* d_smask, const int* d_vt0,
-                                const int* d_kind, const int* d_dir, cudaStream_t s) {
+cudaError_t launch_value_tables(const hs_factors* f, const int* d_groups, int n_groups, cudaStream_t s) {
   const Plan& p = f->plan;
   if (p.total_vt == 0) return cudaSuccess;
+  const int G = d_groups ? n_groups : int(p.groups.size());
+  if (G <= 0) return cudaSuccess;
   int maxdim = 0, maxbits = 0;
   for (const Group& g : p.groups)
     if (g.vt0 >= 0) {
       maxdim = g.xdim > maxdim ? g.xdim : maxdim;
       maxbits = __builtin_popcount(g.smask) > maxbits ? __builtin_popcount(g.smask) : maxbits;
     }
-  BuildArgs a{f->d_vals, f->d_offs, f->d_rowbase, f->d_fac_D, f->d_fac_diag0, d_cs, d_x, d_z, d_cx,
-              d_gfirst, d_glast, d_basis, d_xdim, d_pivot, p.N, d_smask, d_vt0, f->d_vt, d_kind, d_dir,
-              int(p.x.size())};
+  const BuildArgs a = build_args(f, d_groups);
   const bool c64 = f->dtype == HS_C64;
-  dim3 grid(unsigned(((1 << maxbits) + 255) / 256), unsigned(p.groups.size()));
+  const hs_build_inputs& b = f->bin;
+  const dim3 grid{unsigned(((1 << maxbits) + 255) / 256), unsigned(G), 1u};
   switch (maxdim) {
-    case 0: value_table_kernel<1><<<grid, 256, 0, s>>>(a, d_smask, d_vt0, f->d_vt, c64); break;
-    case 1: value_table_kernel<2><<<grid, 256, 0, s>>>(a, d_smask, d_vt0, f->d_vt, c64); break;
-    case 2: value_table_kernel<4><<<grid, 256, 0, s>>>(a, d_smask, d_vt0, f->d_vt, c64); break;
-    case 3: value_table_kernel<8><<<grid, 256, 0, s>>>(a, d_smask, d_vt0, f->d_vt, c64); break;
-    case 4: value_table_kernel<16><<<grid, 256, 0, s>>>(a, d_smask, d_vt0, f->d_vt, c64); break;
-    default: value_table_kernel<32><<<grid, 256, 0, s>>>(a, d_smask, d_vt0, f->d_vt, c64); break;
+    case 0: value_table_kernel<1><<<grid, 256, 0, s>>>(a, b.smask, b.vt0, f->d_vt, c64); break;
+    case 1: value_table_kernel<2><<<grid, 256, 0, s>>>(a, b.smask, b.vt0, f->d_vt, c64); break;
+    case 2: value_table_kernel<4><<<grid, 256, 0, s>>>(a, b.smask, b.vt0, f->d_vt, c64); break;
+    case 3: value_table_kernel<8><<<grid, 256, 0, s>>>(a, b.smask, b.vt0, f->d_vt, c64); break;
+    case 4: value_table_kernel<16><<<grid, 256, 0, s>>>(a, b.smask, b.vt0, f->d_vt, c64); break;
+    default: value_table_kernel<32><<<grid, 256, 0, s>>>(a, b.smask, b.vt0, f->d_vt, c64); break;
   }
   note_launches();
   return cudaGetLastError();

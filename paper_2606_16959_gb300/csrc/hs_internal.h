@@ -122,6 +122,36 @@ uint64_t two_run_mask(uint64_t used, int n, int T, int low_bits);
 
 }  // namespace hs
 
+// Device-resident inputs of a factor build (inside hs_factors::d_tables), kept
+// so that the values can be rebuilt for new coefficients on the same structure.
+struct hs_build_inputs {
+  const uint64_t* x = nullptr;
+  const uint64_t* z = nullptr;
+  const double* coeff = nullptr;   // a_j (the only coefficients of a static set)
+  const double* coeff1 = nullptr;  // b_j of H(t) = H0 + f(t) H1; NULL for a static set
+  const uint32_t* cx = nullptr;
+  const int* gfirst = nullptr;
+  const int* glast = nullptr;
+  const uint64_t* basis = nullptr;
+  const int* xdim = nullptr;
+  const int* pivot = nullptr;
+  const uint32_t* smask = nullptr;
+  const int* vt0 = nullptr;
+  const int* kind = nullptr;
+  const int* dir = nullptr;
+  const double* h = nullptr;       // angle multiple of each kind
+  double* cs = nullptr;            // (cos, sin) per kind and term, written on the device
+  double* th = nullptr;            // the angle per kind and term, written on the device
+  double* fval = nullptr;          // one drive value (hs_factors_set_drive)
+  int n_kinds = 1;
+  // Groups holding a term with b_j != 0: all of them, those without a value
+  // table, those with one.
+  const int* dep_all = nullptr;
+  const int* dep_notab = nullptr;
+  const int* dep_tab = nullptr;
+  int n_dep_all = 0, n_dep_notab = 0, n_dep_tab = 0;
+};
+
 // Opaque object behind the C ABI.
 struct hs_factors {
   hs::Plan plan;
@@ -139,11 +169,15 @@ struct hs_factors {
   uint32_t* d_slot_u = nullptr;  // slot tables (see Group)
   int32_t* d_slot_tab = nullptr;
   int64_t* d_tab_rb = nullptr;
+  hs_build_inputs bin;           // build inputs (device pointers into d_tables)
+  double* d_drive = nullptr;     // drive samples of hs_evolve_td (library-owned)
+  int drive_cap = 0;
   // cached CUDA graphs of evolve launch sequences
   struct GraphKey {
     void* psi;
     int n_rhs, n_steps, method, tile_bits, rhs_block;
     cudaStream_t stream;
+    int variant;  // 0: hs_evolve_ex, 1: hs_evolve_td
     bool operator<(const GraphKey& o) const;
   };
   mutable std::mutex graph_mu;
@@ -153,20 +187,15 @@ struct hs_factors {
 namespace hs {
 
 // Kernel launchers (defined in the .cu files).
-// Factor values; groups with a value table copy it (launch_value_tables first).
-// d_kind / d_dir: per group angle kind and direction.
-cudaError_t launch_build(const hs_factors* f, const double* d_theta_cs, const uint64_t* d_x, const uint64_t* d_z,
-                         const uint32_t* d_cx, const int* d_group_first, const int* d_group_last,
-                         const uint64_t* d_basis, const int* d_xdim, const int* d_pivot, const uint32_t* d_smask,
-                         const int* d_vt0, const int* d_kind, const int* d_dir, cudaStream_t s);
-// (cos, sin) of coeff[j] * h[k] for every term j and angle kind k, kind-major.
-cudaError_t launch_sincos(const double* d_coeff, const double* d_h, int n_kinds, double* d_theta_cs, int n,
-                          cudaStream_t s);
-cudaError_t launch_value_tables(const hs_factors* f, const double* d_theta_cs, const uint64_t* d_x, const uint64_t* d_z,
-                                const uint32_t* d_cx, const int* d_group_first, const int* d_group_last,
-                                const uint64_t* d_basis, const int* d_xdim, const int* d_pivot,
-                                const uint32_t* d_smask, const int* d_vt0, const int* d_kind, const int* d_dir,
-                                cudaStream_t s);
+// (cos, sin) of c_j * h_k for every term j and angle kind k, kind-major, into
+// f->bin.cs; c_j = a_j, or a_j + f b_j with f read from d_fval when the set is
+// time-dependent (d_fval NULL: f = 0).
+cudaError_t launch_sincos(const hs_factors* f, const double* d_fval, cudaStream_t s);
+// Value tables of the listed groups (d_groups NULL: every group with a table).
+cudaError_t launch_value_tables(const hs_factors* f, const int* d_groups, int n_groups, cudaStream_t s);
+// Factor values of the listed groups (d_groups NULL: all); groups with a value
+// table copy it, so their tables must be current (launch_value_tables first).
+cudaError_t launch_build(const hs_factors* f, const int* d_groups, int n_groups, cudaStream_t s);
 
 cudaError_t launch_apply_plain(const hs_factors* f, int g, const void* x, void* y, int n_rhs, cudaStream_t s);
 

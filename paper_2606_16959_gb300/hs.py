@@ -30,6 +30,7 @@ EXPORTS = (
     "hs_dia_from_terms", "hs_dia_from_masks", "hs_dia_create", "hs_spgemm", "hs_spme", "hs_estimate_timesteps",
     "hs_spmv", "hs_dia_evolve", "hs_dia_convert", "hs_dia_info", "hs_dia_get", "hs_dia_free",
     "hs_kernel_launches", "hs_expectation", "hs_build_factors_ex", "hs_factors_sequence",
+    "hs_build_factors_td", "hs_evolve_td", "hs_factors_set_drive",
 )
 
 
@@ -115,6 +116,10 @@ def lib() -> ctypes.CDLL:
         L.hs_build_factors_ex.argtypes = [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
                                           dp, sz, i, d, i, i, i, i, vp, ctypes.POINTER(vp)]
         L.hs_factors_sequence.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), i, ctypes.POINTER(i)]
+        L.hs_build_factors_td.argtypes = [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
+                                          dp, dp, sz, i, d, i, i, i, i, vp, ctypes.POINTER(vp)]
+        L.hs_evolve_td.argtypes = [vp, vp, i, dp, i, ctypes.POINTER(EvolveOpts), vp]
+        L.hs_factors_set_drive.argtypes = [vp, d, vp]
         L.hs_kernel_launches.argtypes = []
         L.hs_kernel_launches.restype = ctypes.c_uint64
         for name in EXPORTS:
@@ -221,23 +226,30 @@ class Factors:
             pass
 
 
+def label_masks(labels: Sequence[str]):
+    """(x, z, n_qubits) of Pauli labels (rightmost character = qubit 0):
+    argument marshalling for the mask-based entry points."""
+    x = np.zeros(len(labels), dtype=np.uint64)
+    z = np.zeros(len(labels), dtype=np.uint64)
+    n = len(labels[0]) if labels else 0
+    for j, lab in enumerate(labels):
+        if len(lab) != n:
+            raise ValueError("labels differ in length")
+        for p_, ch in enumerate(lab):
+            bit = np.uint64(1 << (n - 1 - p_))
+            if ch in "XY":
+                x[j] |= bit
+            if ch in "ZY":
+                z[j] |= bit
+            if ch not in "IXYZ":
+                raise ValueError(f"invalid Pauli character {ch!r}")
+    return x, z, n
+
+
 def hs_build_factors(labels: Sequence[str], coeffs, t: float, n_steps: int, diag_budget: int, dtype="c64",
                      stream=None, order: int = 1) -> Factors:
     if order != 1:
-        x = np.zeros(len(labels), dtype=np.uint64)
-        z = np.zeros(len(labels), dtype=np.uint64)
-        n = len(labels[0]) if labels else 0
-        for j, lab in enumerate(labels):
-            if len(lab) != n:
-                raise ValueError("labels differ in length")
-            for p_, ch in enumerate(lab):
-                bit = np.uint64(1 << (n - 1 - p_))
-                if ch in "XY":
-                    x[j] |= bit
-                if ch in "ZY":
-                    z[j] |= bit
-                if ch not in "IXYZ":
-                    raise ValueError(f"invalid Pauli character {ch!r}")
+        x, z, n = label_masks(labels)
         return hs_build_factors_masks(x, z, coeffs, n, t, n_steps, diag_budget, dtype, stream, order)
     arr = (ctypes.c_char_p * len(labels))(*[l.encode() for l in labels])
     c = np.ascontiguousarray(np.asarray(coeffs, dtype=np.float64))
@@ -266,6 +278,26 @@ def hs_build_factors_masks(x, z, coeffs, n_qubits: int, t: float, n_steps: int, 
     return Factors(out.value)
 
 
+def hs_build_factors_td(x, z, coeffs0, coeffs1, n_qubits: int, t: float, n_steps: int, diag_budget: int,
+                        dtype="c64", stream=None, order: int = 1) -> Factors:
+    """Factor set of H(t) = H0 + f(t) H1 (term j: coeffs0[j] in H0, coeffs1[j]
+    in H1), values built for f = 0; evolve it with hs_evolve_td."""
+    xa = np.ascontiguousarray(np.asarray(x, dtype=np.uint64))
+    za = np.ascontiguousarray(np.asarray(z, dtype=np.uint64))
+    a = np.ascontiguousarray(np.asarray(coeffs0, dtype=np.float64))
+    b = np.ascontiguousarray(np.asarray(coeffs1, dtype=np.float64))
+    if not (xa.size == za.size == a.size == b.size):
+        raise ValueError("x, z, coeffs0 and coeffs1 differ in length")
+    out = ctypes.c_void_p()
+    dp = ctypes.POINTER(ctypes.c_double)
+    _check(lib().hs_build_factors_td(xa.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                     za.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                     a.ctypes.data_as(dp), b.ctypes.data_as(dp), xa.size, int(n_qubits), float(t),
+                                     int(n_steps), int(diag_budget), int(order), _dtype_code(dtype),
+                                     _stream(stream), ctypes.byref(out)))
+    return Factors(out.value)
+
+
 def _check_state(f: Factors, psi):
     ptr, n_rhs, n, code = _state_args(psi)
     if n != f.n_qubits:
@@ -287,6 +319,22 @@ def hs_evolve_ex(f: Factors, psi, n_steps: int, method: int = HS_METHOD_AUTO, ti
     o = EvolveOpts(int(method), int(tile_bits), int(rhs_block), int(bool(use_graph)), int(low_bits), int(max_fuse),
                    int(smem_kb), int(bool(no_tables)))
     _check(lib().hs_evolve_ex(f.handle, ptr, n_rhs, int(n_steps), ctypes.byref(o), _stream(stream)))
+
+
+def hs_evolve_td(f: Factors, psi, drive, method: int = HS_METHOD_AUTO, tile_bits: int = 0, rhs_block: int = 0,
+                 use_graph: bool = False, low_bits: int = 0, max_fuse: int = 0, smem_kb: int = 0,
+                 no_tables: bool = False, stream=None) -> None:
+    """One step per entry of `drive` (the frozen value of f for that step)."""
+    ptr, n_rhs = _check_state(f, psi)
+    fv = np.ascontiguousarray(np.asarray(drive, dtype=np.float64).ravel())
+    o = EvolveOpts(int(method), int(tile_bits), int(rhs_block), int(bool(use_graph)), int(low_bits), int(max_fuse),
+                   int(smem_kb), int(bool(no_tables)))
+    _check(lib().hs_evolve_td(f.handle, ptr, n_rhs, fv.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), fv.size,
+                              ctypes.byref(o), _stream(stream)))
+
+
+def hs_factors_set_drive(f: Factors, drive: float, stream=None) -> None:
+    _check(lib().hs_factors_set_drive(f.handle, float(drive), _stream(stream)))
 
 
 def hs_evolve_plan(f: Factors, n_rhs: int, n_steps: int, method: int = HS_METHOD_AUTO, tile_bits: int = 0,

@@ -259,6 +259,7 @@ class Job:
     dtype: str = "c64"        # "c64" or "c128"
     arrival: float = 0.0      # seconds, serving only
     seed: int = 0             # seed of the initial state when psi0 is None
+    drive: Optional[np.ndarray] = None  # time-dependent jobs (ham is a DrivenHamiltonian): f per step
 
 
 def tfim10() -> Job:
@@ -291,6 +292,17 @@ def maxcut24(n: int = 24, n_rhs: int = 16, seed: int = 1003, n_steps: int = 50) 
     rng = np.random.default_rng(seed + 7919)
     rows = [plus_state(n)] + [gaussian_state(n, rng) for _ in range(n_rhs - 1)]
     return Job(ham, 2.0, n_steps, 4, np.stack(rows), "c64")
+
+
+def anneal24(n: int = 24, n_rhs: int = 16, seed: int = 1003, n_steps: int = 50, T: float = 2.0) -> Job:
+    """MaxCut annealing on the weighted 3-regular graph of maxcut24 (same seed):
+    H(s) = (1 - s) 0.5 sum X_i + s H_C with the linear ramp s = t / T sampled at
+    the step midpoints; RHS 0 = |+>^n (the mixer's ground state), RHS 1.. =
+    Gaussian states; T = 2, 50 steps, budget 4, complex64 bulk."""
+    ham = anneal_maxcut(n, seed, 0.5)
+    rng = np.random.default_rng(seed + 7919)
+    rows = [plus_state(n)] + [gaussian_state(n, rng) for _ in range(n_rhs - 1)]
+    return Job(ham, T, n_steps, 4, np.stack(rows), "c64", drive=midpoint_samples(lambda u: u / T, T, n_steps))
 
 
 def batch256(n_jobs: int = 256, seed: int = 1004, n_lo: int = 12, n_hi: int = 20, dtype: str = "c64") -> List[Job]:
