@@ -222,6 +222,7 @@ cudaError_t launch_sweep(const hs_factors* f, const SweepLaunch& L, cudaStream_t
     const bool table = L.value_tables && G.vt0 >= 0 && n_vt + G.vt_n <= kMaxVtSweep;
     a.fvt[i] = table ? G.vt0 : -1;
     a.fsm[i] = table ? G.smask : 0u;
+    a.fsh[i] = sweep::pattern_shift(a.fsm[i]);
     if (table) n_vt += G.vt_n;
     n_mslot += G.nslot;
     n_mtab += t1 - t0;

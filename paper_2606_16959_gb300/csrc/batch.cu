@@ -49,7 +49,8 @@ struct BFac {
   int16_t nslot, mslot, tab_s, tab_n;
   int vt;          // first global value-table entry, -1: staged from the diagonals
   int16_t vts;     // first shared value-table entry (running prefix)
-  uint32_t sm;     // the factor's support mask
+  int8_t sh;       // pattern shift of sm (see pattern_fast)
+  uint32_t sm;     // the factor's value-table index mask
 };
 
 struct BSweep {
@@ -132,6 +133,7 @@ __global__ void __launch_bounds__(kBatchThreads) batch_level_kernel(const __grid
     sa->fvt[i] = fe.vt;
     sa->fvts[i] = fe.vts;
     sa->fsm[i] = fe.sm;
+    sa->fsh[i] = fe.sh;
   }
   __syncthreads();
   const uint32_t units = (1u << (bj.n_qubits - p.tile_bits)) * uint32_t(bj.n_rhs);
@@ -342,7 +344,8 @@ extern "C" int hs_batch_create(const hs_batch_job* jobs, size_t n_jobs, const hs
         const int t0 = p.slot_tab[G.slot0], t1 = p.slot_tab[G.slot0 + G.nslot];
         const bool table = b->value_tables && G.vt0 >= 0 && n_vt + G.vt_n <= hs::kMaxVtSweep;
         hfacs.push_back(BFac{G.slot0, t0, int16_t(G.nslot), int16_t(n_mslot), int16_t(n_mtab), int16_t(t1 - t0),
-                             table ? G.vt0 : -1, int16_t(n_vt), table ? G.smask : 0u});
+                             table ? G.vt0 : -1, int16_t(n_vt),
+                             hs::sweep::pattern_shift(table ? G.smask : 0u), table ? G.smask : 0u});
         n_mslot += G.nslot;
         n_mtab += t1 - t0;
         if (table) n_vt += G.vt_n;

@@ -46,8 +46,11 @@ struct Group {
   int nslot = 0;             // 2^xdim, or 0 if the factor has no slot tables
   // Value table (factors with slot tables whose terms touch at most kMaxVtBits
   // qubits): entry (r, r ^ u_s) of the factor depends on r only through r's
-  // bits at smask (the union of its terms' x and z masks), so the values sit in
-  // a table indexed p * nslot + s, p = those bits packed (lowest bit first).
+  // bits at the union of its terms' x and z masks, so the values sit in a
+  // table indexed p * nslot + s, p = r's bits at smask packed (lowest bit
+  // first).  smask is that union, or the window of consecutive bits covering
+  // it (then p = (r & smask) >> lowest bit, and rows differing only at the
+  // window's other bits share values).
   uint32_t smask = 0;
   int vt0 = -1;              // first entry in the factor set's value tables, -1 if none
   int vt_n = 0;              // nslot << popcount(smask)

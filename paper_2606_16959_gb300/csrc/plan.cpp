@@ -262,11 +262,21 @@ int make_plan(const uint64_t* x, const uint64_t* z, const double* coeff, size_t 
         if ((x[j] >> G.pivot[i]) & 1ull) c |= 1u << i;
       plan.term_cx[j] = c;
     }
-    // Value table of a factor whose terms touch few qubits.
+    // Value table of a factor whose terms touch few qubits.  A support that
+    // spans at most kMaxVtBits consecutive qubits with at most two gaps is
+    // indexed by the whole window (the entries of the gap bits repeat), so a
+    // row's index is a shift and a mask.
     if (G.nslot > 0) {
       uint64_t sm = 0;
       for (int j = G.first; j < G.last; ++j) sm |= x[j] | z[j];
-      const int bits = __builtin_popcountll(sm);
+      int bits = __builtin_popcountll(sm);
+      if (sm) {
+        const int lo = __builtin_ctzll(sm), span = 64 - __builtin_clzll(sm) - lo;
+        if (span <= kMaxVtBits && span <= bits + 2) {
+          sm = ((1ull << span) - 1ull) << lo;
+          bits = span;
+        }
+      }
       if (bits <= kMaxVtBits && sm < (1ull << 32) && (G.nslot << bits) <= kMaxVtSweep) {
         G.smask = uint32_t(sm);
         G.vt0 = int(plan.total_vt);

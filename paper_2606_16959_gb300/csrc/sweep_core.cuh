@@ -68,6 +68,7 @@ struct SweepArgs {
   int fvt[kMaxSweepFactors];
   int16_t fvts[kMaxSweepFactors];
   uint32_t fsm[kMaxSweepFactors];
+  int8_t fsh[kMaxSweepFactors];  // lowest bit of fsm when its bits are consecutive, else -1
   // Register path (one row per thread, one state per tile, every factor from a
   // value table): bit i of flane set when factor i's slots flip only local
   // bits 0..4, i.e. exchange amplitudes within a warp.
@@ -105,6 +106,18 @@ __device__ __forceinline__ uint32_t pattern_of(uint32_t r, uint32_t u) {
   int j = 0;
   for (uint32_t t = u; t; t &= t - 1u, ++j) p |= ((r >> (__ffs(t) - 1)) & 1u) << j;
   return p;
+}
+// The same with sh = the lowest bit of u when u's bits are consecutive (a
+// shift and a mask), -1 otherwise.
+__device__ __forceinline__ uint32_t pattern_fast(uint32_t r, uint32_t u, int sh) {
+  return sh >= 0 ? (r & u) >> sh : pattern_of(r, u);
+}
+// Host side: the shift pattern_fast takes for mask u.
+inline int8_t pattern_shift(uint32_t u) {
+  if (!u) return 0;
+  const int lo = __builtin_ctz(u);
+  const uint32_t w = u >> lo;
+  return (w & (w + 1u)) == 0 ? int8_t(lo) : int8_t(-1);
 }
 
 // The copies carry no memory clobber: shared memory they write is read only
@@ -174,9 +187,10 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a, int nrb, T2* tile
       // Value table: entry (pattern of the row's bits at fsm) * ns + slot.
       const T2* tb = vts + a.fvts[fi];
       const uint32_t sm = a.fsm[fi];
+      const int psh = a.fsh[fi];
       uint32_t pat[ROWS];
 #pragma unroll
-      for (int i = 0; i < ROWS; ++i) pat[i] = pattern_of(grow[i], sm) * uint32_t(ns);
+      for (int i = 0; i < ROWS; ++i) pat[i] = pattern_fast(grow[i], sm, psh) * uint32_t(ns);
       multiply([&](int j, int i) { return tb[pat[i] + j]; });
     } else {
       const T2* st = stages + size_t(stage) * stage_elems + threadIdx.x;
@@ -223,9 +237,10 @@ __device__ __forceinline__ void sweep_reg(const SweepArgs& a, T2* tile, T2* othe
     const SlotMeta* ms = mslot + a.fmslot[fi];
     const T2* tb = vts + a.fvts[fi];
     const uint32_t sm = a.fsm[fi];
+    const int psh = a.fsh[fi];
     uint32_t pat[ROWS];
 #pragma unroll
-    for (int i = 0; i < ROWS; ++i) pat[i] = pattern_of(grow[i], sm) * uint32_t(ns);
+    for (int i = 0; i < ROWS; ++i) pat[i] = pattern_fast(grow[i], sm, psh) * uint32_t(ns);
     T2 acc[ROWS];
 #pragma unroll
     for (int i = 0; i < ROWS; ++i) acc[i] = T2{0, 0};

@@ -51,8 +51,10 @@ def test_plan_rejects_bad_input(lib):
 
 
 def _value_table_entries(x, z, group, n_diags):
-    """Entries of a factor's value table: |X| slots times 2^(qubits its terms
-    touch), for factors with slot tables (<= 32 diagonals) touching <= 8 qubits."""
+    """Entries of a factor's value table: |X| slots times 2^(index bits), for
+    factors with slot tables (<= 32 diagonals) touching <= 8 qubits.  The index
+    bits are the qubits the terms touch, or the window of consecutive qubits
+    covering them when it is at most 8 wide with at most two gaps."""
     first, last = group
     if n_diags > 32:
         return 0
@@ -62,6 +64,11 @@ def _value_table_entries(x, z, group, n_diags):
         support |= int(x[j]) | int(z[j])
         span |= {u ^ int(x[j]) for u in span}
     bits = bin(support).count("1")
+    if support:
+        lo = (support & -support).bit_length() - 1
+        width = support.bit_length() - lo
+        if width <= 8 and width <= bits + 2:
+            bits = width
     entries = len(span) << bits
     return entries if bits <= 8 and entries <= 2048 else 0
 
