@@ -159,6 +159,71 @@ struct GroupRows {
         if (s < S) w[s] = nw[s];
     }
   }
+
+  // Rows r and r ^ u_1 of a factor with a two-element x-mask set {0, u_1}, r
+  // without the pivot bit: the slots of both rows are the basis states r and
+  // r ^ u_1, so a diagonal run's phases are formed once for the pair.  With
+  // s_j(b) = (-1)^popcount(z_j & b), s_j(r ^ u_1) = s_j(r) (-1)^popcount(z_j & u_1):
+  // the run's angles s_j(r) theta_j sum to A over terms with an even overlap
+  // with u_1 and to B over the others, and phi(r) = A + B, phi(r ^ u_1) = A - B.
+  __device__ __forceinline__ void row_pair(const BuildArgs& a, uint64_t r, double2 (&w0)[2], double2 (&w1)[2]) const {
+    const uint64_t u1 = bas[0];
+    const uint64_t r1 = r ^ u1;
+    w0[0] = make_double2(1.0, 0.0);
+    w0[1] = make_double2(0.0, 0.0);
+    w1[0] = w0[0];
+    w1[1] = w0[1];
+    double A = 0.0, B = 0.0;
+    bool pending = false;
+    const int n_t = last - first;
+    for (int q = 0; q <= n_t; ++q) {
+      const int j = dir > 0 ? last - 1 - q : first + q;
+      const uint64_t xj = q < n_t ? a.x[j] : 1;
+      if (q < n_t && xj == 0) {
+        const double t = th[j];
+        const uint64_t zj = a.z[j];
+        const double st = (__popcll(zj & r) & 1) ? -t : t;
+        if (__popcll(zj & u1) & 1) B += st;
+        else A += st;
+        pending = true;
+        continue;
+      }
+      if (pending) {
+        double s0, c0, s1, c1;
+        sincos(A + B, &s0, &c0);  // basis state r
+        sincos(A - B, &s1, &c1);  // basis state r ^ u_1
+        auto mulp = [](double2& v, double c, double sn) {
+          v = make_double2(c * v.x - sn * v.y, c * v.y + sn * v.x);
+        };
+        mulp(w0[0], c0, s0);  // row r, slot 0: state r
+        mulp(w0[1], c1, s1);  // row r, slot 1: state r ^ u_1
+        mulp(w1[0], c1, s1);  // row r ^ u_1, slot 0: state r ^ u_1
+        mulp(w1[1], c0, s0);  // row r ^ u_1, slot 1: state r
+        A = B = 0.0;
+        pending = false;
+      }
+      if (q == n_t) break;
+      const double c = cs[2 * j], sn = cs[2 * j + 1];
+      const uint64_t zj = a.z[j];
+      const int y = __popcll(xj & zj);
+      const int cxj = int(a.cx[j]);
+      auto rot = [&](uint64_t rr, double2 (&w)[2]) {
+        double2 nw[2];
+#pragma unroll
+        for (int s2 = 0; s2 < 2; ++s2) {
+          const int src = s2 ^ cxj;
+          const int par = __popcll(zj & (rr ^ (src ? u1 : 0ull))) & 1;
+          const double2 p = mul_ipow(src ? w[1] : w[0], y + 1 + 2 * par);
+          const double2 ws = s2 ? w[1] : w[0];
+          nw[s2] = make_double2(fma(c, ws.x, sn * p.x), fma(c, ws.y, sn * p.y));
+        }
+        w[0] = nw[0];
+        w[1] = nw[1];
+      };
+      rot(r, w0);
+      rot(r1, w1);
+    }
+  }
 };
 
 __device__ __forceinline__ double2 load_val(const void* vals, int64_t idx, bool c64) {
@@ -169,6 +234,34 @@ __device__ __forceinline__ double2 load_val(const void* vals, int64_t idx, bool 
   return reinterpret_cast<const double2*>(vals)[idx];
 }
 
+// Row r of F on every structural diagonal: F[r, c] = conj(w[coord(r ^ c)])
+// when r ^ c lies in X, an exact zero otherwise.
+template <int NS, int MAXS>
+__device__ __forceinline__ void write_row(const BuildArgs& a, const GroupRows<MAXS>& G, int D, int d0, int64_t r,
+                                          const double2 (&w)[NS], bool c64) {
+  for (int k = 0; k < D; ++k) {
+    const int64_t d = a.offs[d0 + k];
+    const int64_t col = r + d;
+    if (col < 0 || col >= a.N) continue;
+    const uint64_t uu = uint64_t(r) ^ uint64_t(col);
+    int cc = 0;
+    uint64_t rec = 0;
+#pragma unroll
+    for (int i = 0; i < kMaxXDim; ++i)
+      if (i < G.xd && ((uu >> G.piv[i]) & 1ull)) {
+        cc |= 1 << i;
+        rec ^= G.bas[i];
+      }
+    double2 v = make_double2(0.0, 0.0);
+    if (rec == uu) {
+#pragma unroll
+      for (int s = 0; s < NS; ++s)
+        if (s == cc) v = make_double2(w[s].x, -w[s].y);
+    }
+    store_val(a.vals, a.rowbase[d0 + k] + r, v, c64);
+  }
+}
+
 template <int MAXS>
 __global__ void __launch_bounds__(256) build_kernel(BuildArgs a, bool c64) {
   const int g = group_of(a);
@@ -177,8 +270,22 @@ __global__ void __launch_bounds__(256) build_kernel(BuildArgs a, bool c64) {
   const int D = a.fac_D[g], d0 = a.fac_diag0[g];
   const int vt0 = a.vt0[g];
   const uint32_t sm = a.smask[g];
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
 
-  for (int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; r < a.N; r += int64_t(gridDim.x) * blockDim.x) {
+  if (MAXS >= 2 && vt0 < 0 && G.xd == 1) {
+    // Two-element x-mask set: one thread per pair of rows (r, r ^ u_1).
+    const int p = G.piv[0];
+    const uint64_t lowm = (1ull << p) - 1ull;
+    for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < (a.N >> 1); k += stride) {
+      const uint64_t r = ((uint64_t(k) >> p) << (p + 1)) | (uint64_t(k) & lowm);
+      double2 w0[2], w1[2];
+      G.row_pair(a, r, w0, w1);
+      write_row(a, G, D, d0, int64_t(r), w0, c64);
+      write_row(a, G, D, d0, int64_t(r ^ G.bas[0]), w1, c64);
+    }
+    return;
+  }
+  for (int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; r < a.N; r += stride) {
     double2 w[MAXS];
     if (vt0 >= 0) {
       // The row's values are those of its pattern at smask, already in the
@@ -195,28 +302,7 @@ __global__ void __launch_bounds__(256) build_kernel(BuildArgs a, bool c64) {
     } else {
       G.row(a, uint64_t(r), w);
     }
-    // Row r of F: F[r, c] = conj(w[coord(r ^ c)]) when r ^ c lies in X.
-    for (int k = 0; k < D; ++k) {
-      const int64_t d = a.offs[d0 + k];
-      const int64_t col = r + d;
-      if (col < 0 || col >= a.N) continue;
-      const uint64_t uu = uint64_t(r) ^ uint64_t(col);
-      int cc = 0;
-      uint64_t rec = 0;
-#pragma unroll
-      for (int i = 0; i < kMaxXDim; ++i)
-        if (i < G.xd && ((uu >> G.piv[i]) & 1ull)) {
-          cc |= 1 << i;
-          rec ^= G.bas[i];
-        }
-      double2 v = make_double2(0.0, 0.0);
-      if (rec == uu) {
-#pragma unroll
-        for (int s = 0; s < MAXS; ++s)
-          if (s == cc) v = make_double2(w[s].x, -w[s].y);
-      }
-      store_val(a.vals, a.rowbase[d0 + k] + r, v, c64);
-    }
+    write_row(a, G, D, d0, r, w, c64);
   }
 }
 
