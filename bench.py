@@ -183,7 +183,8 @@ TUNE_CACHE = os.path.join(ROOT, "paper_2606_16959_gb300", "_build", "autotune_be
 PROFILE_SUMMARY = {"heis16": ("sweep_kernel_heis16.md", "sweep_kernel"),
                    "maxcut24": ("sweep_kernel_maxcut24.md", "sweep_kernel"),
                    "batch256": ("batch_level_kernel_batch256.md", "batch_level_kernel"),
-                   "taylor16": ("spmv_kernel_taylor16.md", "spmv_kernel")}
+                   "taylor16": ("spmv_kernel_taylor16.md", "spmv_kernel"),
+                   "anneal24": ("sweep_kernel_anneal24.md", "sweep_kernel")}
 # Device-code sources of each kernel: a summary's DRAM figures count only while
 # these are unchanged since the capture.
 KERNEL_SOURCES = {"sweep_kernel": ("apply.cu", "sweep_core.cuh", "hs_internal.h"),
