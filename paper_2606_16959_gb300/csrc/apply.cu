@@ -162,18 +162,30 @@ cudaError_t launch_apply_plain(const hs_factors* f, int g, const void* x, void* 
   if (blocks > 152 * 16) blocks = 152 * 16;
   const int64_t* offs = f->d_offs + G.diag0;
   const int64_t* rb = f->d_rowbase + G.diag0;
+  // States per pass: the factor's values are read once per block of RB
+  // states, so the block is as large as the accumulators allow.
   if (f->dtype == HS_C64) {
     auto v = reinterpret_cast<const float2*>(f->d_vals);
-    if (n_rhs >= 4)
-      apply_plain_kernel<float, 4><<<blocks, threads, 0, s>>>(v, offs, rb, G.D, (const float2*)x, (float2*)y, p.N, n_rhs);
+    auto xs = static_cast<const float2*>(x);
+    auto ys = static_cast<float2*>(y);
+    if (n_rhs >= 16)
+      apply_plain_kernel<float, 16><<<blocks, threads, 0, s>>>(v, offs, rb, G.D, xs, ys, p.N, n_rhs);
+    else if (n_rhs >= 8)
+      apply_plain_kernel<float, 8><<<blocks, threads, 0, s>>>(v, offs, rb, G.D, xs, ys, p.N, n_rhs);
+    else if (n_rhs >= 4)
+      apply_plain_kernel<float, 4><<<blocks, threads, 0, s>>>(v, offs, rb, G.D, xs, ys, p.N, n_rhs);
     else
-      apply_plain_kernel<float, 1><<<blocks, threads, 0, s>>>(v, offs, rb, G.D, (const float2*)x, (float2*)y, p.N, n_rhs);
+      apply_plain_kernel<float, 1><<<blocks, threads, 0, s>>>(v, offs, rb, G.D, xs, ys, p.N, n_rhs);
   } else {
     auto v = reinterpret_cast<const double2*>(f->d_vals);
-    if (n_rhs >= 4)
-      apply_plain_kernel<double, 4><<<blocks, threads, 0, s>>>(v, offs, rb, G.D, (const double2*)x, (double2*)y, p.N, n_rhs);
+    auto xs = static_cast<const double2*>(x);
+    auto ys = static_cast<double2*>(y);
+    if (n_rhs >= 8)
+      apply_plain_kernel<double, 8><<<blocks, threads, 0, s>>>(v, offs, rb, G.D, xs, ys, p.N, n_rhs);
+    else if (n_rhs >= 4)
+      apply_plain_kernel<double, 4><<<blocks, threads, 0, s>>>(v, offs, rb, G.D, xs, ys, p.N, n_rhs);
     else
-      apply_plain_kernel<double, 1><<<blocks, threads, 0, s>>>(v, offs, rb, G.D, (const double2*)x, (double2*)y, p.N, n_rhs);
+      apply_plain_kernel<double, 1><<<blocks, threads, 0, s>>>(v, offs, rb, G.D, xs, ys, p.N, n_rhs);
   }
   note_launches();
   return cudaGetLastError();

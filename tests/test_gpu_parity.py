@@ -122,7 +122,7 @@ def test_build_rejects_bad_input():
 # ----------------------------------------------------------------------------
 
 @pytest.mark.parametrize("dt", ["c128", "c64"])
-@pytest.mark.parametrize("n_rhs", [1, 3, 6])
+@pytest.mark.parametrize("n_rhs", [1, 3, 6, 9, 20])
 def test_apply_factor_matches_oracle(dt, n_rhs):
     rng = np.random.default_rng(200 + n_rhs)
     ham = W.heisenberg_chain(12, rng.uniform(0.5, 1.5, 12))
