@@ -29,6 +29,9 @@ Readings of the paper used here (it is silent or ambiguous on each):
     counts; r is feasible iff the Taylor loop converges within max_iter terms
     and num_diags(U(t/r)) <= D_max (Eq. 5).
 
+Time-dependent H0 + f(t) H1 (ham_dia_td, estimate_timesteps_td, evolve_td)
+is pinned by tests/test_taylor_td_pins.py.
+
 Parity status: every function is pinned by tests/test_taylor_pins.py (dense
 Kronecker sums, numpy matrix products, eigh-based exponentials with the Taylor
 remainder bound, elementwise exponentials, brute-force step scans, Tab. 3,
@@ -228,3 +231,45 @@ def evolve(U: Dia, psi, n_steps: int) -> np.ndarray:
     for _ in range(n_steps):
         x = spmv(U, x)
     return x
+
+
+# ----------------------------------------------------------------------------
+# Time-dependent H(t) = H0 + f(t) H1 in the single-factor mode (the outlook on
+# time-dependent Hamiltonians).  Readings: step k freezes the drive at the
+# caller's sample f_k; H(f_k) is formed from the terms with c_j = a_j + f_k b_j
+# (product rounded before the sum) and exactly-zero diagonals dropped, then
+# exponentiated by SpME at dt = t / (number of samples) and applied once.  One
+# step count serves every step: the smallest r meeting Eq. 5 for each distinct
+# sample (each searched as for a static H), so the search runs once before the
+# evolution and not per step.
+# ----------------------------------------------------------------------------
+
+def ham_dia_td(x, z, a, b, f: float, n_qubits: int) -> Dia:
+    """H0 + f H1 in the compact layout."""
+    c = np.asarray(a, dtype=np.float64) + float(f) * np.asarray(b, dtype=np.float64)
+    return ham_dia(x, z, c, n_qubits)
+
+
+def estimate_timesteps_td(x, z, a, b, drive, n_qubits: int, t: float, budget: int, tol: float = 1e-6,
+                          max_iter: int = 100, max_steps: int = 1 << 20) -> int:
+    """Steps r over [0, t] such that U(t/r) of every sampled H(f_k) has at most
+    budget diagonals: the largest of the static searches over distinct samples."""
+    r = 1
+    for f in sorted(set(float(v) for v in np.asarray(drive, dtype=np.float64).ravel())):
+        r = max(r, estimate_timesteps(ham_dia_td(x, z, a, b, f, n_qubits), t, budget, tol, max_iter, max_steps))
+    return r
+
+
+def evolve_td(x, z, a, b, drive, n_qubits: int, t: float, psi, tol: float = 1e-6,
+              max_iter: int = 100) -> np.ndarray:
+    """One step per drive sample, dt = t / len(drive): psi <- U_k psi with
+    U_k = SpME(H(f_k), dt) (exact for a diagonal H(f_k))."""
+    fv = np.asarray(drive, dtype=np.float64).ravel()
+    dt = float(t) / len(fv)
+    out = np.asarray(psi, dtype=np.complex128).copy()
+    for f in fv:
+        U, _, ok = expm(ham_dia_td(x, z, a, b, f, n_qubits), dt, tol, max_iter)
+        if not ok:
+            raise ValueError("Taylor series did not converge within max_iter terms")
+        out = spmv(U, out)
+    return out
