@@ -111,6 +111,24 @@ int hs_expectation(const hs_dia* a, const void* psi, int n_rhs, void* cuda_strea
  * HS_EINVAL, HS_ENOMEM, HS_ECUDA.  Enqueues only. */
 int hs_dia_evolve(const hs_dia* u, void* psi, int n_rhs, int n_steps, void* cuda_stream);
 
+/* Time-dependent H(t) = H0 + f(t) H1 in the single-factor mode (the outlook
+ * on time-dependent Hamiltonians, Future Work): for step k = 0..n_steps-1 the
+ * drive is frozen at drive[k]; H(f_k) = sum_j c_j P_j with c_j = coeffs0[j] +
+ * drive[k] * coeffs1[j] (the product rounded before the sum) is formed as by
+ * hs_dia_from_masks, U_k = exp(-i dt H(f_k)) by hs_spme (tol, max_iter),
+ * dt = t / n_steps, stored as dtype, and psi <- U_k psi (hs_dia_evolve, one
+ * step).  x, z, coeffs0, coeffs1: n_terms host entries (masks as
+ * hs_dia_from_masks; coefficients finite); drive: n_steps finite host values
+ * (step midpoints give the exponential midpoint rule); psi: device buffer of
+ * n_rhs states of dtype, updated in place.  The caller chooses n_steps (for
+ * example the largest hs_estimate_timesteps over the distinct samples).
+ * Errors: HS_EINVAL (bad argument, non-finite value, a step whose Taylor loop
+ * does not converge: psi then holds the steps before it), HS_EDTYPE,
+ * HS_ENOMEM, HS_ECUDA.  Synchronises every step. */
+int hs_dia_evolve_td(const uint64_t* x, const uint64_t* z, const double* coeffs0, const double* coeffs1,
+                     size_t n_terms, int n_qubits, double t, const double* drive, int n_steps, double tol,
+                     int max_iter, void* psi, int n_rhs, hs_dtype dtype, void* cuda_stream);
+
 /* A copy of A stored as dtype (HS_C64 rounds each FP64 part once).  Enqueues only. */
 int hs_dia_convert(const hs_dia* a, hs_dtype dtype, void* cuda_stream, hs_dia** out);
 

@@ -11,5 +11,5 @@ from .hs import (  # noqa: F401
     hs_inner_device, hs_plan_factors,
     Dia, hs_dia_convert, hs_dia_create, hs_dia_evolve, hs_dia_from_masks, hs_dia_from_terms, hs_estimate_timesteps,
     hs_spgemm, hs_spme, hs_spmv, hs_expectation, hs_kernel_launches,
-    hs_build_factors_td, hs_evolve_td, hs_factors_set_drive,
+    hs_build_factors_td, hs_evolve_td, hs_factors_set_drive, hs_dia_evolve_td,
 )

@@ -30,7 +30,7 @@ EXPORTS = (
     "hs_dia_from_terms", "hs_dia_from_masks", "hs_dia_create", "hs_spgemm", "hs_spme", "hs_estimate_timesteps",
     "hs_spmv", "hs_dia_evolve", "hs_dia_convert", "hs_dia_info", "hs_dia_get", "hs_dia_free",
     "hs_kernel_launches", "hs_expectation", "hs_build_factors_ex", "hs_factors_sequence",
-    "hs_build_factors_td", "hs_evolve_td", "hs_factors_set_drive",
+    "hs_build_factors_td", "hs_evolve_td", "hs_factors_set_drive", "hs_dia_evolve_td",
 )
 
 
@@ -120,6 +120,8 @@ def lib() -> ctypes.CDLL:
                                           dp, dp, sz, i, d, i, i, i, i, vp, ctypes.POINTER(vp)]
         L.hs_evolve_td.argtypes = [vp, vp, i, dp, i, ctypes.POINTER(EvolveOpts), vp]
         L.hs_factors_set_drive.argtypes = [vp, d, vp]
+        L.hs_dia_evolve_td.argtypes = [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64), dp, dp, sz,
+                                       i, d, dp, i, d, i, vp, i, i, vp]
         L.hs_kernel_launches.argtypes = []
         L.hs_kernel_launches.restype = ctypes.c_uint64
         for name in EXPORTS:
@@ -605,6 +607,26 @@ def hs_spmv(a: Dia, x, y, stream=None) -> None:
 def hs_dia_evolve(u: Dia, psi, n_steps: int, stream=None) -> None:
     p, n_rhs = _dia_state(u, psi)
     _check(lib().hs_dia_evolve(u.handle, p, n_rhs, int(n_steps), _stream(stream)))
+
+
+def hs_dia_evolve_td(x, z, coeffs0, coeffs1, n_qubits: int, t: float, drive, psi, tol: float = 1e-6,
+                     max_iter: int = 100, stream=None) -> None:
+    """One single-factor Taylor step per drive sample under H0 + f H1, psi in place."""
+    xa = np.ascontiguousarray(np.asarray(x, dtype=np.uint64))
+    za = np.ascontiguousarray(np.asarray(z, dtype=np.uint64))
+    a = np.ascontiguousarray(np.asarray(coeffs0, dtype=np.float64))
+    b = np.ascontiguousarray(np.asarray(coeffs1, dtype=np.float64))
+    if not (xa.size == za.size == a.size == b.size):
+        raise ValueError("x, z, coeffs0 and coeffs1 differ in length")
+    fv = np.ascontiguousarray(np.asarray(drive, dtype=np.float64).ravel())
+    ptr, n_rhs, n, code = _state_args(psi)
+    if n != int(n_qubits):
+        raise ValueError("state size does not match n_qubits")
+    dp = ctypes.POINTER(ctypes.c_double)
+    _check(lib().hs_dia_evolve_td(xa.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                  za.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), a.ctypes.data_as(dp),
+                                  b.ctypes.data_as(dp), xa.size, int(n_qubits), float(t), fv.ctypes.data_as(dp),
+                                  fv.size, float(tol), int(max_iter), ptr, n_rhs, code, _stream(stream)))
 
 
 def hs_dia_convert(a: Dia, dtype, stream=None) -> Dia:
