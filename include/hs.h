@@ -299,9 +299,12 @@ int hs_inner_device(const void* a, const void* b, int n_qubits, hs_dtype dtype, 
  * for each pair.  Scratch is a static per-device array of 4864 partial sums
  * (152 KiB, held by every GPU that loads the library until exit): a call
  * needs n_states * min(ceil(2^n_qubits / 256), 608) of them and is rejected
- * with HS_EINVAL above that (at least 8 states of any size per call).  The
- * first call on a device looks up the array's device address (make it before
- * any stream capture); calls that overlap on the GPU race on the array.
+ * with HS_EINVAL above that (at least 8 states of any size per call).  Every
+ * call looks up the array's device address on the current device (a host-side
+ * lookup, valid after a context is re-created); the first call on a device
+ * also loads the module there, so make it before any stream capture.  Calls
+ * that overlap on the GPU race on the array.  Its two kernels are counted by
+ * hs_kernel_launches.
  * Does not synchronise.  Errors: HS_EINVAL, HS_EDTYPE, HS_ECUDA. */
 int hs_inner_batch_noalloc(const void* a, const void* b, int n_qubits, int n_states, hs_dtype dtype,
                            double* out_device, void* cuda_stream);

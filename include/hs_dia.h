@@ -124,7 +124,9 @@ int hs_dia_evolve(const hs_dia* u, void* psi, int n_rhs, int n_steps, void* cuda
  * example the largest hs_estimate_timesteps over the distinct samples).
  * Errors: HS_EINVAL (bad argument, non-finite value, a step whose Taylor loop
  * does not converge: psi then holds the steps before it), HS_EDTYPE,
- * HS_ENOMEM, HS_ECUDA.  Synchronises every step. */
+ * HS_ENOMEM, HS_ECUDA.  Each step synchronises cuda_stream once (hs_spme
+ * decides on the host when the Taylor loop stops); the step's matrices are
+ * freed in stream order on cuda_stream, so other streams are not waited for. */
 int hs_dia_evolve_td(const uint64_t* x, const uint64_t* z, const double* coeffs0, const double* coeffs1,
                      size_t n_terms, int n_qubits, double t, const double* drive, int n_steps, double tol,
                      int max_iter, void* psi, int n_rhs, hs_dtype dtype, void* cuda_stream);

@@ -1024,6 +1024,12 @@ cudaError_t launch_scale_rows(const hs_dia* a, void* psi, int n_rhs, cudaStream_
 
 }  // namespace
 
+namespace hs {
+// Free a matrix in stream order on s (no device synchronisation): its memory
+// returns to the pool once the work already enqueued on s has run.
+void dia_free_async(hs_dia* m, cudaStream_t s) { destroy_async(m, s); }
+}  // namespace hs
+
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------

@@ -7,11 +7,14 @@
 #include <string>
 #include <vector>
 
+#include <cuda_runtime.h>
+
 #include "../../include/hs.h"
 #include "../../include/hs_dia.h"
 
 namespace hs {
 int report_error(int code, const std::string& msg);
+void dia_free_async(hs_dia* m, cudaStream_t s);
 }  // namespace hs
 
 extern "C" int hs_dia_evolve_td(const uint64_t* x, const uint64_t* z, const double* coeffs0, const double* coeffs1,
@@ -30,6 +33,10 @@ extern "C" int hs_dia_evolve_td(const uint64_t* x, const uint64_t* z, const doub
   for (size_t j = 0; j < n_terms; ++j)
     if (!std::isfinite(coeffs1[j])) return hs::report_error(HS_EINVAL, "non-finite H1 coefficient at term " + std::to_string(j));
   if (n_steps == 0) return HS_OK;
+  // Every matrix of a step is freed in stream order on this stream, so a step
+  // waits for nothing but its own stream (hs_spme synchronises it to decide
+  // when the Taylor loop stops); other streams keep running.
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
   const double dt = t / double(n_steps);
   std::vector<double> c(n_terms);
   for (int k = 0; k < n_steps; ++k) {
@@ -45,22 +52,22 @@ extern "C" int hs_dia_evolve_td(const uint64_t* x, const uint64_t* z, const doub
     hs_dia* U = nullptr;
     int n_taylor = 0, converged = 0;
     rc = hs_spme(H, dt, tol, max_iter, cuda_stream, &U, &n_taylor, &converged);
-    hs_dia_free(H);
+    hs::dia_free_async(H, s);
     if (rc != HS_OK) return rc;
     if (!converged) {
-      hs_dia_free(U);
+      hs::dia_free_async(U, s);
       return hs::report_error(HS_EINVAL, "Taylor series did not converge within max_iter terms at step " +
                                              std::to_string(k));
     }
     if (dtype == HS_C64) {
       hs_dia* U32 = nullptr;
       rc = hs_dia_convert(U, HS_C64, cuda_stream, &U32);
-      hs_dia_free(U);
+      hs::dia_free_async(U, s);
       if (rc != HS_OK) return rc;
       U = U32;
     }
     rc = hs_dia_evolve(U, psi, n_rhs, 1, cuda_stream);
-    hs_dia_free(U);  // waits for the step before the matrix goes
+    hs::dia_free_async(U, s);  // after the step, in stream order
     if (rc != HS_OK) return rc;
   }
   return HS_OK;

@@ -11,18 +11,19 @@
 //
 // The array is a fixed 152 KiB that every GPU loading the library holds until
 // the process exits.  In host code `g_noalloc_partials` only names a host-side
-// stand-in, not a device address: its device address is fetched once per
-// device with cudaGetSymbolAddress (with that device current) on the first
-// call made on that device, and that first call should be made before any
-// stream capture.  All calls share the array and it keeps the contents of the
-// last call; every partial sum a call reads was written earlier in that same
-// call, so nothing needs clearing, but calls that overlap on the GPU (for
-// example on two streams) race on it.
+// stand-in, not a device address: every call looks up its device address on
+// the current device with cudaGetSymbolAddress (a host-side lookup, no stream
+// work), so a context that was torn down and created again never sees a stale
+// address.  The first call on a device also loads the module there; make it
+// before any stream capture.  All calls share the array and it keeps the
+// contents of the last call; every partial sum a call reads was written
+// earlier in that same call, so nothing needs clearing, but calls that overlap
+// on the GPU (for example on two streams) race on it.
 #include <cuda_runtime.h>
 
-#include <mutex>
 #include <string>
 
+#include "counters.h"
 #include "hs_internal.h"
 
 namespace hs {
@@ -109,23 +110,13 @@ __global__ void __launch_bounds__(kNaThreads) na_final(const NaAcc* partials, in
   }
 }
 
-std::mutex g_na_mu;
-NaAcc* g_na_ptr[64] = {};
-
-// Device address of g_noalloc_partials on the current device (looked up once per device).
+// Device address of g_noalloc_partials on the current device, looked up on
+// every call.
 cudaError_t noalloc_partials(NaAcc** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lk(g_na_mu);
-  if (!g_na_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_partials);
-    if (e != cudaSuccess) return e;
-    g_na_ptr[dev] = static_cast<NaAcc*>(p);
-  }
-  *out = g_na_ptr[dev];
+  *out = static_cast<NaAcc*>(p);
   return cudaSuccess;
 }
 
@@ -158,5 +149,6 @@ extern "C" int hs_inner_batch_noalloc(const void* a, const void* b, int n_qubits
   na_final<<<n_states, kNaThreads, 0, s>>>(partials, int(blocks), out_device);
   e = cudaGetLastError();
   if (e != cudaSuccess) return hs::report_error(HS_ECUDA, std::string("launch: ") + cudaGetErrorString(e));
+  hs::note_launches(2);
   return HS_OK;
 }

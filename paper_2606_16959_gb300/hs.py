@@ -380,12 +380,25 @@ def hs_fidelity(a, b, stream=None) -> Tuple[float, float, float]:
     return fid.value, n1.value, n2.value
 
 
+def _check_out(out, n_doubles: int, like) -> None:
+    """out must be a contiguous float64 CUDA tensor of at least n_doubles
+    elements on the device of `like` (the library writes 8-byte values)."""
+    import torch
+    if not isinstance(out, torch.Tensor) or not out.is_cuda or out.dtype != torch.float64:
+        raise ValueError("out must be a CUDA float64 tensor")
+    if out.device != like.device:
+        raise ValueError("out must be on the device of the states")
+    if not out.is_contiguous() or out.numel() < n_doubles:
+        raise ValueError(f"out must be contiguous with at least {n_doubles} elements")
+
+
 def hs_inner_device(a, b, out, stream=None) -> None:
     """out (CUDA float64 tensor of 4) <- (Re<a|b>, Im<a|b>, |a|^2, |b|^2), no synchronisation."""
     pa, ra, na, ca = _state_args(a)
     pb, rb, nb, cb = _state_args(b)
     if (ra, na, ca) != (1, nb, cb) or rb != 1:
         raise ValueError("inner product takes two single states of equal size and dtype")
+    _check_out(out, 4, a)
     _check(lib().hs_inner_device(pa, pb, na, ca, out.data_ptr(), _stream(stream)))
 
 
@@ -425,8 +438,7 @@ def hs_inner_batch_noalloc(a, b, out, stream=None) -> None:
     pb, rb, nb, cb = _state_args(b)
     if (ra, na, ca) != (rb, nb, cb):
         raise ValueError("a and b differ in shape or dtype")
-    if out.numel() < 4 * ra or not out.is_cuda or not out.is_contiguous():
-        raise ValueError("out must be a contiguous CUDA float64 tensor of 4 * n_states elements")
+    _check_out(out, 4 * ra, a)
     _check(lib().hs_inner_batch_noalloc(pa, pb, na, ra, ca, out.data_ptr(), _stream(stream)))
 
 
