@@ -7,8 +7,11 @@ factor applications of the evolution, and the FP64 overlap/norm reduction.
 
 Metric: amplitude-updates/s = sum over the step of n_steps * G * N * R (one
 update = one output amplitude of one factor application to one state).
+The default workload is the largest single-GPU configuration: weighted MaxCut
+on 24 qubits with the transverse mixer, 16 states, 50 steps, complex64 (the
+complex128 run of the same workload is reported beside it).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload heis16|maxcut24|tfim10]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload maxcut24|heis16|batch256|...]
                   [--impl ours|reference] [--no-cpu-baseline] [--no-c128]
 
 Under torchrun (N > 1) every rank evolves its own replica of the instance
@@ -41,7 +44,7 @@ def parse_args():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default="heis16",
+    ap.add_argument("--workload", default="maxcut24",
                     choices=["heis16", "maxcut24", "tfim10", "batch256", "serve", "taylor16", "anneal24"])
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--serve-rate", type=float, default=500.0)
@@ -584,6 +587,66 @@ def oracle_sample(job, G, budget_s=15.0, order=1):
                        f"evolution, single thread; units counted as steps x {G} factor applications x N={N}")
 
 
+def oracle_fanout_sample(job, G, steps, order=1):
+    """The same oracle on every host core at once: one spawned process per core,
+    each evolving `steps` whole steps of one state of the workload (states
+    taken in order, repeated when there are more cores than states)."""
+    import oracle
+    from oracle import fanout
+    x, z, n = oracle.parse_terms(job.ham.labels)
+    psi = np.asarray(job.psi0)
+    rows = psi if psi.ndim == 2 else psi[None, :]
+    cores = fanout.host_cores()
+    dt = job.t / job.n_steps
+    tasks = []
+    for c in range(cores):
+        p0 = rows[c % rows.shape[0]]
+        if job.drive is not None:
+            tasks.append(("td", (x, z, job.ham.a, job.ham.b, job.drive[:steps], dt * steps, p0, order)))
+        elif order == 1:
+            tasks.append(("direct", (x, z, job.ham.coeffs, dt * steps, steps, p0)))
+        else:
+            tasks.append(("order", (x, z, job.ham.coeffs, dt * steps, steps, p0, order)))
+    t0 = time.perf_counter()
+    fanout.run_many(tasks, workers=cores)
+    wall = time.perf_counter() - t0
+    units = cores * steps * G * (1 << n)
+    return dict(value=units / wall, seconds=wall, cores=cores,
+                sample=f"{cores} spawned processes, one per host core, each {steps} whole step(s) of one of the "
+                       f"{rows.shape[0]} states (direct term-by-term FP64, unchanged oracle); wall time includes "
+                       "process start-up; units counted as processes x steps x "
+                       f"{G} factor applications x N={1 << n}")
+
+
+def oracle_batch_fanout(jobs, budget_s=15.0):
+    """Whole batch instances on every host core at once (one spawned process
+    per instance, as many instances as fit ~budget_s of single-core work)."""
+    import oracle
+    from oracle import fanout
+    cores = fanout.host_cores()
+    tasks, units = [], 0
+    for j in jobs[: 4 * cores]:
+        x, z, n = oracle.parse_terms(j.ham.labels)
+        G = len(oracle.group_terms(x, j.budget))
+        tasks.append(("direct", (x, z, j.ham.coeffs, j.t, j.n_steps, j.psi0)))
+        units += j.n_steps * G * (1 << n)
+    t0 = time.perf_counter()
+    fanout.run_many(tasks, workers=cores)
+    wall = time.perf_counter() - t0
+    return dict(value=units / wall, seconds=wall, cores=cores,
+                sample=f"the first {len(tasks)} of {len(jobs)} instances, whole evolutions, on {cores} spawned "
+                       "processes (one per host core, direct term-by-term FP64, unchanged oracle)")
+
+
+def cpu_baseline_of(job, G, order=1):
+    """Single-thread oracle on a bounded sample, and the all-cores fan-out."""
+    cb = oracle_sample(job, G, order=order)
+    fo = oracle_fanout_sample(job, G, cb["steps"], order=order)
+    return {"value": cb["value"], "unit": METRIC, "cores": 1, "kind": "oracle", "sample": cb["sample"],
+            "all_cores": {"value": fo["value"], "unit": METRIC, "cores": fo["cores"], "kind": "oracle",
+                          "sample": fo["sample"]}}
+
+
 def config_of(args, job, desc, res=None):
     c = {"workload": args.workload, "description": desc, "n_qubits": job.ham.n_qubits, "n_terms": len(job.ham.labels),
          "n_steps": job.n_steps, "diag_budget": job.budget, "n_rhs": int(np.asarray(job.psi0).shape[0]) if np.asarray(job.psi0).ndim == 2 else 1,
@@ -604,18 +667,22 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    # Each reference step: the unchanged FP64 oracle on every host core at once
+    # (one spawned process per core, independent states or instances), a
+    # bounded sample of the workload sized so that the run ends in minutes.
     per_step_budget = max(1.0, 150.0 / max(1, args.steps + args.warmup))
     if args.workload == "batch256":
         jobs, desc = batch_jobs(args)
         job = jobs[0]
-        sample = lambda: oracle_batch_sample(jobs, per_step_budget)
+        sample = lambda: oracle_batch_fanout(jobs, per_step_budget)
         cfg = {"workload": "batch256", "description": desc, "n_jobs": len(jobs)}
     else:
         job, desc = make_job(args.workload)
         import oracle as _o
         x, z, n = _o.parse_terms(job.ham.labels)
-        G = len(_o.group_terms(x, job.budget))
-        sample = lambda: oracle_sample(job, G, per_step_budget)
+        G = len(_o.group_terms(x, job.budget)) * (1 if args.order == 1 else 2 if args.order == 2 else 10)
+        probe = oracle_sample(job, G, per_step_budget, order=args.order)
+        sample = lambda: oracle_fanout_sample(job, G, probe["steps"], order=args.order)
         cfg = config_of(args, job, desc)
     for _ in range(args.warmup):
         sample()
@@ -629,7 +696,8 @@ def run_reference(args):
             "warmup": args.warmup, "ms_per_step": 1000 * statistics.mean(secs), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic", "impl": "reference",
             "config": cfg,
-            "cpu_baseline": {"value": v, "unit": METRIC, "cores": 1, "kind": "oracle", "sample": r["sample"]},
+            "cpu_baseline": {"value": v, "unit": METRIC, "cores": r["cores"], "kind": "oracle",
+                             "sample": r["sample"]},
             "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -672,14 +740,12 @@ def run_ours(args):
                     "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"]},
             "gpu_launches": res["launches"], "clocks": res["clocks"],
             "evolve_ms_per_step": statistics.mean(res["evolve_ms"]), "autotuned": res["tuned"]}
-    if args.workload == "heis16" and not args.no_c128 and world >= 1:
+    if args.workload in ("heis16", "maxcut24") and not args.qubits and not args.no_c128 and world >= 1:
         r2 = time_ours(make_job(args.workload, "c128")[0], args, world, "c128", rank)
         line["c128"] = {"value": r2["units"] * K * world / (r2["total_ms"] / 1000.0),
                         "ms_per_step": r2["total_ms"] / K, "evolve_ms_per_step": statistics.mean(r2["evolve_ms"])}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cb = oracle_sample(job, res["G"], order=args.order)
-        line["cpu_baseline"] = {"value": cb["value"], "unit": METRIC, "cores": 1, "kind": "oracle",
-                                "sample": cb["sample"]}
+        line["cpu_baseline"] = cpu_baseline_of(job, res["G"], order=args.order)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
@@ -717,7 +783,10 @@ def run_batch(args, rank, world):
             "batch_launch_ms_per_step": statistics.mean(res["launch_ms"]), "max_norm_drift": res["max_norm_drift"]}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = oracle_batch_sample(jobs)
-        line["cpu_baseline"] = {"value": cb["value"], "unit": METRIC, "cores": 1, "kind": "oracle", "sample": cb["sample"]}
+        fo = oracle_batch_fanout(jobs)
+        line["cpu_baseline"] = {"value": cb["value"], "unit": METRIC, "cores": 1, "kind": "oracle", "sample": cb["sample"],
+                                "all_cores": {"value": fo["value"], "unit": METRIC, "cores": fo["cores"],
+                                              "kind": "oracle", "sample": fo["sample"]}}
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
