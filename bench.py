@@ -323,7 +323,7 @@ def time_ours(job, args, world, dtype, rank):
             save_tune_cache(cache)
         opts = dict(method=tuned["method"], tile_bits=tuned["tile_bits"], rhs_block=tuned["rhs_block"],
                     low_bits=tuned["low_bits"], max_fuse=tuned.get("max_fuse", 0), smem_kb=tuned.get("smem_kb", 0),
-                    use_graph=bool(args.graph))
+                    reg_bits=tuned.get("reg_bits", 0), use_graph=bool(args.graph))
     args.tuned_opts = opts
     keep = []
     for _ in range(args.warmup):

@@ -138,7 +138,14 @@ int hs_evolve(const hs_factors* f, void* psi, int n_rhs, int n_steps, void* cuda
 typedef enum {
   HS_METHOD_AUTO = 0,  /* fused tile sweeps where possible (same as hs_evolve) */
   HS_METHOD_PLAIN = 1, /* one row-parallel diagonal-times-vector launch per factor application */
-  HS_METHOD_FUSED = 2  /* tile sweeps; factors that do not fit a tile fall back to PLAIN */
+  HS_METHOD_FUSED = 2, /* tile sweeps; factors that do not fit a tile fall back to PLAIN */
+  HS_METHOD_REG = 3    /* register-blocked tile sweeps, one state per tile: each thread keeps 2^reg_bits
+                          rows in registers; a factor with a value table of at most two slots is read from
+                          it, any other factor is applied term by term (exact rotations from the build's
+                          FP64 cos/sin, runs of diagonal terms as phases generated from (z_j, theta_j) per
+                          row, the future-work fusion of the factor values into the apply), so no stored
+                          diagonal is read.  A sweep with a term that flips more than two qubits falls back
+                          to PLAIN launches.  Needs n_qubits >= reg_bits + 5; smaller states use FUSED. */
 } hs_method;
 
 typedef struct {
@@ -156,6 +163,10 @@ typedef struct {
   int no_tables;  /* FUSED: 0 (default): factors whose terms touch at most 8 qubits are read from
                      their value tables (entries indexed by the row's bits on those qubits; same
                      values as the stored diagonals); 1: every factor is staged from its diagonals */
+  int reg_bits;   /* REG: rows per thread 2^reg_bits, 4 or 5 (complex128: 4); 0 = library choice
+                     (5 for complex64, 4 for complex128).  REG tiles: tile_bits 0 = min(13, n_qubits)
+                     for complex64, min(12, n_qubits) for complex128; at most reg_bits + 8 (complex64)
+                     or 13 (complex128) */
 } hs_evolve_opts;
 
 /* hs_evolve with an explicit method and tiling (opts may be NULL = AUTO). */

@@ -5,6 +5,7 @@
 #include <atomic>
 #include <cstring>
 #include <list>
+#include <map>
 #include <unordered_map>
 #include <memory>
 #include <string>
@@ -13,6 +14,7 @@
 
 #include "counters.h"
 #include "hs_internal.h"
+#include "qsweep.h"
 
 namespace hs {
 size_t inner_scratch_bytes();
@@ -59,16 +61,25 @@ void release(hs_factors* f, cudaStream_t s) {
   delete f;
 }
 
+// Register-blocked launches of a schedule: one descriptor per fused sweep
+// (shared by the sweeps that repeat), or null where the sweep is launched
+// otherwise.
+using QPlans = std::vector<std::shared_ptr<hs::q::Args>>;
+
 // Enqueue the launches of one evolution on stream s.
 int enqueue_evolve(const hs_factors* f, const std::vector<hs::Sweep>& sw, void* psi, int n_rhs, int tile_bits,
-                   int rhs_block, size_t smem_budget, bool value_tables, void* scratch, cudaStream_t s) {
+                   int rhs_block, size_t smem_budget, bool value_tables, void* scratch, cudaStream_t s,
+                   const QPlans* qp = nullptr, int reg_bits = 0) {
   const hs::Plan& p = f->plan;
   void* cur = psi;
   void* other = scratch;
   const uint64_t all = (1ull << p.n_qubits) - 1;
-  for (const hs::Sweep& w : sw) {
+  for (size_t wi = 0; wi < sw.size(); ++wi) {
+    const hs::Sweep& w = sw[wi];
     cudaError_t e;
-    if (w.fused) {
+    if (qp && (*qp)[wi]) {
+      e = hs::q::launch_qsweep(f, *(*qp)[wi], cur, cur, n_rhs, reg_bits, true, s);
+    } else if (w.fused) {
       hs::SweepLaunch L;
       L.src = cur;
       L.dst = cur;
@@ -102,6 +113,47 @@ bool has_plain(const std::vector<hs::Sweep>& sw) {
   for (const hs::Sweep& w : sw)
     if (!w.fused) return true;
   return false;
+}
+
+// Register-blocked descriptors for the fused sweeps of sw (method REG): each
+// distinct sweep is planned once; a sweep that cannot be expressed as register
+// ops is replaced by plain launches of its factors.
+void plan_reg(const hs_factors* f, std::vector<hs::Sweep>& sw, int tile_bits, int reg_bits, QPlans& qp) {
+  std::map<std::pair<uint32_t, std::vector<int>>, std::shared_ptr<hs::q::Args>> memo;
+  std::vector<hs::Sweep> out;
+  QPlans plans;
+  for (hs::Sweep& w : sw) {
+    if (!w.fused) {
+      out.push_back(std::move(w));
+      plans.push_back(nullptr);
+      continue;
+    }
+    const auto key = std::make_pair(w.local_mask, w.factors);
+    auto it = memo.find(key);
+    std::shared_ptr<hs::q::Args> a;
+    if (it != memo.end()) {
+      a = it->second;
+    } else {
+      a = std::make_shared<hs::q::Args>();
+      std::string why;
+      if (!hs::q::plan_qsweep(f, w.factors, w.local_mask, tile_bits, reg_bits, *a, &why)) a = nullptr;
+      memo[key] = a;
+    }
+    if (a) {
+      out.push_back(std::move(w));
+      plans.push_back(a);
+    } else {
+      for (int g : w.factors) {
+        hs::Sweep pl;
+        pl.fused = false;
+        pl.factors.push_back(g);
+        out.push_back(std::move(pl));
+        plans.push_back(nullptr);
+      }
+    }
+  }
+  sw = std::move(out);
+  qp = std::move(plans);
 }
 
 // Largest number of staged planes (slots) among the factors a sweep may hold.
@@ -550,8 +602,30 @@ int resolve_opts(const hs_factors* f, int n_rhs, const hs_evolve_opts* opts, hs_
   if (o.max_fuse <= 0 || o.max_fuse > hs::kMaxSweepFactors) o.max_fuse = hs::kMaxSweepFactors;
   if (o.smem_kb < 0 || size_t(o.smem_kb) * 1024 > hs::kSweepSmemMax) return fail(HS_EINVAL, "smem_kb must be 0..227");
   if (o.low_bits < (f->dtype == HS_C64 ? 1 : 0) || o.low_bits > 12) return fail(HS_EINVAL, "low_bits out of range");
-  if (o.method != HS_METHOD_AUTO && o.method != HS_METHOD_PLAIN && o.method != HS_METHOD_FUSED)
+  if (o.method != HS_METHOD_AUTO && o.method != HS_METHOD_PLAIN && o.method != HS_METHOD_FUSED &&
+      o.method != HS_METHOD_REG)
     return fail(HS_EINVAL, "unknown method");
+  if (o.reg_bits != 0 && o.reg_bits != 4 && o.reg_bits != 5) return fail(HS_EINVAL, "reg_bits must be 0, 4 or 5");
+  if (o.method == HS_METHOD_REG) {
+    const bool c64 = f->dtype == HS_C64;
+    const int B = o.reg_bits > 0 ? o.reg_bits : (c64 ? 5 : 4);
+    if (!c64 && B != 4) return fail(HS_EINVAL, "complex128 register sweeps use reg_bits 4");
+    const int n = f->plan.n_qubits;
+    if (n >= B + 5) {
+      o.reg_bits = B;
+      rb = 1;
+      tb = o.tile_bits > 0 ? o.tile_bits : std::min(c64 ? 13 : 12, n);
+      if (tb > n) tb = n;
+      if (tb < B + 5 || tb > 13) return fail(HS_EINVAL, "register sweeps take tile_bits reg_bits + 5 .. 13");
+      return HS_OK;
+    }
+    // States too small for a register tile: fused sweeps with their defaults.
+    o.method = HS_METHOD_FUSED;
+    o.reg_bits = 0;
+    o.tile_bits = 0;
+    o.rhs_block = 0;
+  }
+  o.reg_bits = 0;
   rb = o.rhs_block > 0 ? o.rhs_block : pick_rhs_block(f->dtype, n_rhs);
   if (rb != 1 && rb != 2 && rb != 4 && rb != 8 && !(rb == 16 && f->dtype == HS_C64))
     return fail(HS_EINVAL, "rhs_block must be 1, 2, 4, 8 (or 16 for complex64)");
@@ -573,6 +647,8 @@ int hs_evolve_plan(const hs_factors* f, int n_rhs, int n_steps, const hs_evolve_
   if (rc != HS_OK) return rc;
   std::vector<hs::Sweep> sw = hs::plan_sweeps(f->plan, n_steps, tb, o.low_bits, o.method != HS_METHOD_PLAIN,
                                               hs::kMaxFusedDiags, o.max_fuse);
+  QPlans qp;
+  if (o.method == HS_METHOD_REG) plan_reg(f, sw, tb, o.reg_bits, qp);
   int ns = 0, np = 0;
   for (const hs::Sweep& w : sw) (w.fused ? ns : np) += 1;
   if (n_sweeps) *n_sweeps = ns;
@@ -600,14 +676,21 @@ int hs_evolve_ex(const hs_factors* f, void* psi, int n_rhs, int n_steps, const h
   }
   cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
   const size_t state_bytes = size_t(n_rhs) * size_t(f->plan.N) * hs::elem_bytes(f->dtype);
-  const std::vector<hs::Sweep> sw = hs::plan_sweeps(f->plan, n_steps, tb, o.low_bits, o.method != HS_METHOD_PLAIN,
-                                                    hs::kMaxFusedDiags, o.max_fuse);
+  std::vector<hs::Sweep> sw = hs::plan_sweeps(f->plan, n_steps, tb, o.low_bits, o.method != HS_METHOD_PLAIN,
+                                              hs::kMaxFusedDiags, o.max_fuse);
+  QPlans qp;
+  if (o.method == HS_METHOD_REG) {
+    cudaError_t e = hs::q::prepare_qsweep();
+    if (e != cudaSuccess) return cuda_fail(e, "kernel attributes");
+    plan_reg(f, sw, tb, o.reg_bits, qp);
+  }
+  const QPlans* qpp = qp.empty() ? nullptr : &qp;
   const bool scratch_needed = has_plain(sw);
   const size_t smem_budget = o.smem_kb > 0 ? size_t(o.smem_kb) * 1024 : hs::kSweepSmemDefault;
 
   if (o.use_graph) {
-    hs_factors::GraphKey key{psi, n_rhs, n_steps, int(o.method) * 128 + o.max_fuse, tb + 64 * o.smem_kb,
-                             (rb * 64 + o.low_bits) * 2 + (o.no_tables != 0), nullptr, 0};
+    hs_factors::GraphKey key{psi, n_rhs, n_steps, int(o.method) * 128 + o.max_fuse + 16384 * o.reg_bits,
+                             tb + 64 * o.smem_kb, (rb * 64 + o.low_bits) * 2 + (o.no_tables != 0), nullptr, 0};
     cudaGraphExec_t exec = nullptr;
     {
       std::lock_guard<std::mutex> lk(f->graph_mu);
@@ -622,7 +705,8 @@ int hs_evolve_ex(const hs_factors* f, void* psi, int n_rhs, int n_steps, const h
       e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
       if (e != cudaSuccess) { cudaStreamDestroy(cs); return cuda_fail(e, "cudaStreamBeginCapture"); }
       hs::begin_capture_count();
-      int rc = enqueue_evolve(f, sw, psi, n_rhs, tb, rb, smem_budget, o.no_tables == 0, nullptr, cs);
+      int rc = enqueue_evolve(f, sw, psi, n_rhs, tb, rb, smem_budget, o.no_tables == 0, nullptr, cs, qpp,
+                              o.reg_bits);
       const uint64_t n_kernels = hs::end_capture_count();
       cudaGraph_t graph = nullptr;
       e = cudaStreamEndCapture(cs, &graph);
@@ -651,7 +735,7 @@ int hs_evolve_ex(const hs_factors* f, void* psi, int n_rhs, int n_steps, const h
     cudaError_t e = hs::pool_malloc(&scratch, state_bytes, s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(scratch state)");
   }
-  int rc = enqueue_evolve(f, sw, psi, n_rhs, tb, rb, smem_budget, o.no_tables == 0, scratch, s);
+  int rc = enqueue_evolve(f, sw, psi, n_rhs, tb, rb, smem_budget, o.no_tables == 0, scratch, s, qpp, o.reg_bits);
   if (scratch) cudaFreeAsync(scratch, s);
   return rc;
 }
@@ -705,17 +789,28 @@ int hs_evolve_td(hs_factors* f, void* psi, int n_rhs, const double* drive, int n
   cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
   // One step's launches: the values change from step to step, so no sweep
   // spans a step boundary.
-  const std::vector<hs::Sweep> sw = hs::plan_sweeps(f->plan, 1, tb, o.low_bits, o.method != HS_METHOD_PLAIN,
-                                                    hs::kMaxFusedDiags, o.max_fuse);
+  std::vector<hs::Sweep> sw = hs::plan_sweeps(f->plan, 1, tb, o.low_bits, o.method != HS_METHOD_PLAIN,
+                                              hs::kMaxFusedDiags, o.max_fuse);
+  QPlans qp;
+  if (o.method == HS_METHOD_REG) {
+    cudaError_t e = hs::q::prepare_qsweep();
+    if (e != cudaSuccess) return cuda_fail(e, "kernel attributes");
+    plan_reg(f, sw, tb, o.reg_bits, qp);
+  }
+  const QPlans* qpp = qp.empty() ? nullptr : &qp;
   const bool scratch_needed = has_plain(sw);
   const size_t smem_budget = o.smem_kb > 0 ? size_t(o.smem_kb) * 1024 : hs::kSweepSmemDefault;
   const bool tables = o.no_tables == 0;
   // Sweeps that read value tables need only the tables of table groups
   // rebuilt each step; plain launches and table-free sweeps read diagonals.
+  // Register sweeps read value tables, the angles and their cos/sin (all
+  // rebuilt each step) and no diagonals, so a schedule of register sweeps
+  // alone rebuilds no diagonals until the end.
   const hs_build_inputs& b = f->bin;
+  const bool reg_only = qpp && !scratch_needed;
   const bool diag_all = !tables || scratch_needed;
-  const int* diag_groups = diag_all ? b.dep_all : b.dep_notab;
-  const int n_diag = diag_all ? b.n_dep_all : b.n_dep_notab;
+  const int* diag_groups = reg_only ? nullptr : (diag_all ? b.dep_all : b.dep_notab);
+  const int n_diag = reg_only ? 0 : (diag_all ? b.n_dep_all : b.n_dep_notab);
 
   // Drive samples in a library-owned device buffer (captured graphs read it).
   if (f->drive_cap < n_steps) {
@@ -747,11 +842,14 @@ int hs_evolve_td(hs_factors* f, void* psi, int n_rhs, const double* drive, int n
     for (int k = 0; k < n_steps; ++k) {
       cudaError_t e = enqueue_drive_rebuild(f, f->d_drive + k, diag_groups, n_diag, cs);
       if (e != cudaSuccess) return cuda_fail(e, "drive rebuild");
-      int rc = enqueue_evolve(f, sw, psi, n_rhs, tb, rb, smem_budget, tables, scratch, cs);
+      int rc = enqueue_evolve(f, sw, psi, n_rhs, tb, rb, smem_budget, tables, scratch, cs, qpp, o.reg_bits);
       if (rc != HS_OK) return rc;
     }
     // Leave every stored value at the last step's drive.
-    if (!diag_all && b.n_dep_tab > 0) {
+    if (reg_only && b.n_dep_all > 0) {
+      cudaError_t e = hs::launch_build(f, b.dep_all, b.n_dep_all, cs);
+      if (e != cudaSuccess) return cuda_fail(e, "factor build launch");
+    } else if (!diag_all && b.n_dep_tab > 0) {
       cudaError_t e = hs::launch_build(f, b.dep_tab, b.n_dep_tab, cs);
       if (e != cudaSuccess) return cuda_fail(e, "factor build launch");
     }
@@ -760,8 +858,8 @@ int hs_evolve_td(hs_factors* f, void* psi, int n_rhs, const double* drive, int n
 
   if (o.use_graph) {
     if (scratch_needed) return fail(HS_EINVAL, "use_graph needs a schedule without plain fallbacks");
-    hs_factors::GraphKey key{psi, n_rhs, n_steps, int(o.method) * 128 + o.max_fuse, tb + 64 * o.smem_kb,
-                             (rb * 64 + o.low_bits) * 2 + (o.no_tables != 0), nullptr, 1};
+    hs_factors::GraphKey key{psi, n_rhs, n_steps, int(o.method) * 128 + o.max_fuse + 16384 * o.reg_bits,
+                             tb + 64 * o.smem_kb, (rb * 64 + o.low_bits) * 2 + (o.no_tables != 0), nullptr, 1};
     cudaGraphExec_t exec = nullptr;
     {
       std::lock_guard<std::mutex> lk(f->graph_mu);

@@ -1,0 +1,310 @@
+// Host planner of the register-blocked tile sweep (qsweep.h): the factors of
+// a fused sweep become register ops (TAB, ROT, PHASE) and the register
+// layouts between them.
+#include <algorithm>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "hs_internal.h"
+#include "qsweep.h"
+
+namespace hs {
+namespace q {
+
+namespace {
+
+struct HOp {
+  uint8_t type;
+  int g;                  // factor
+  int term;               // ROT: term index
+  std::vector<int> terms; // PHASE: term indices
+  uint32_t need;          // ROT / TAB: local bits the op flips
+};
+
+// Lowest bit of u when u's bits are consecutive (patterns are then a shift and
+// a mask), -1 otherwise (patterns gather the bits one by one).
+int8_t pattern_shift_of(uint32_t u) {
+  if (!u) return 0;
+  const int lo = __builtin_ctz(u);
+  const uint32_t w = u >> lo;
+  return (w & (w + 1u)) == 0 ? int8_t(lo) : int8_t(-1);
+}
+
+// pext over a 32-bit mask: the bits of v at the set bits of m, packed.
+uint32_t pext32(uint32_t v, uint32_t m) {
+  uint32_t out = 0;
+  int j = 0;
+  for (uint32_t t = m; t; t &= t - 1u, ++j)
+    if (v & (t & (0u - t))) out |= 1u << j;
+  return out;
+}
+
+}  // namespace
+
+bool plan_qsweep(const hs_factors* f, const std::vector<int>& factors, uint32_t local_mask, int T, int B,
+                 Args& a, std::string* why) {
+  const Plan& p = f->plan;
+  const int n = p.n_qubits;
+  const int m = int(p.x.size());
+  auto fail = [&](const std::string& s) {
+    if (why) *why = s;
+    return false;
+  };
+  if (B < 4 || B > kMaxB || T < B + 5 || T > n || __builtin_popcount(local_mask) != T)
+    return fail("tile and register bits out of range");
+  const bool c64 = f->dtype == HS_C64;
+  if (!c64 && B != 4) return fail("complex128 uses 4 register bits");
+  // Two-run local mask [0, lo) U [h, h + w).
+  int lo = 0;
+  while (lo < 32 && ((local_mask >> lo) & 1u)) ++lo;
+  const uint32_t hi = lo < 32 ? (local_mask & ~((1u << lo) - 1u)) : 0u;
+  const int w = __builtin_popcount(hi);
+  const int h = hi ? __builtin_ctz(hi) : lo;
+  if (lo + w != T || (hi && hi != (((1u << w) - 1u) << h))) return fail("local mask is not two runs");
+  if (c64 && lo < 1) return fail("complex64 tiles keep bit 0");
+  a = Args();
+  a.tile_bits = T;
+  a.m0 = lo >= 32 ? 0xffffffffu : ((1u << lo) - 1u);
+  a.m1 = ((1u << w) - 1u) << lo;
+  a.sh = h - lo;
+  const uint64_t all = (1ull << n) - 1ull;
+  a.rest = runs_of(~uint64_t(local_mask) & all, n);
+  auto loc = [&](uint64_t g) -> uint32_t {  // local image of global bits inside the tile
+    const uint32_t v = uint32_t(g & local_mask);
+    return (v & a.m0) | ((v >> a.sh) & a.m1);
+  };
+  auto glob = [&](uint32_t l) -> uint32_t { return (l & a.m0) | ((l & a.m1) << a.sh); };
+
+  // 1. Ops of every factor, in application order.
+  std::vector<HOp> ops;
+  for (int g : factors) {
+    const Group& G = p.groups[g];
+    if ((G.span & ~uint64_t(local_mask)) != 0) return fail("factor flips outside the tile");
+    if (G.vt0 >= 0 && G.nslot >= 1 && G.nslot <= 2 && G.vt_n <= kMaxVt) {
+      const uint32_t u = G.nslot == 2 ? p.slot_u[G.slot0 + 1] : 0u;
+      if (__builtin_popcount(loc(u)) <= 2) {
+        ops.push_back(HOp{OP_TAB, g, -1, {}, loc(u)});
+        continue;
+      }
+    }
+    std::vector<int> run;
+    const int cnt = G.last - G.first;
+    for (int q = 0; q < cnt; ++q) {
+      const int j = G.dir > 0 ? G.first + q : G.last - 1 - q;
+      if (p.x[j] == 0) {
+        run.push_back(j);
+        continue;
+      }
+      if (!run.empty()) {
+        ops.push_back(HOp{OP_PHASE, g, -1, run, 0});
+        run.clear();
+      }
+      const uint32_t need = loc(p.x[j]);
+      if (__builtin_popcount(need) > 2) return fail("a term flips more than two qubits");
+      ops.push_back(HOp{OP_ROT, g, j, {}, need});
+    }
+    if (!run.empty()) ops.push_back(HOp{OP_PHASE, g, -1, run, 0});
+  }
+
+  // 2. Register layouts: a register op needs its flips (and, for complex64,
+  // local bit 0, which a 16-byte chunk keeps in one thread) in the register
+  // bits; a new layout takes the needs of as many following ops as fit.
+  const uint32_t pin = c64 ? 1u : 0u;
+  const uint32_t tile_all = (T >= 32) ? 0xffffffffu : ((1u << T) - 1u);
+  auto fill = [&](uint32_t R) {
+    for (int b = 0; b < T && __builtin_popcount(R) < B; ++b) R |= 1u << b;
+    return R;
+  };
+  std::vector<uint32_t> lay_of(ops.size(), 0);
+  uint32_t cur = 0;
+  bool have = false;
+  for (size_t i = 0; i < ops.size(); ++i) {
+    const bool reg = ops[i].type != OP_PHASE;
+    if (reg && (!have || ((ops[i].need | pin) & ~cur))) {
+      uint32_t R = ops[i].need | pin;
+      if (__builtin_popcount(R) > B) return fail("an op needs more register bits than a thread has");
+      for (size_t j = i + 1; j < ops.size(); ++j) {
+        if (ops[j].type == OP_PHASE) continue;
+        if (__builtin_popcount(R | ops[j].need) > B) break;
+        R |= ops[j].need;
+      }
+      cur = fill(R);
+      if (!have)  // ops before the first register op run in the first layout
+        for (size_t k = 0; k < i; ++k) lay_of[k] = cur;
+      have = true;
+    }
+    lay_of[i] = have ? cur : 0u;
+  }
+  if (!have) {
+    cur = fill(pin);
+    for (size_t i = 0; i < ops.size(); ++i) lay_of[i] = cur;
+  }
+
+  // 3. Emit the descriptor.
+  std::map<uint32_t, int> lay_id;
+  std::map<int, int> rot_id, tab_id;
+  std::map<std::tuple<int, int, uint32_t>, int> phase_id;  // (factor, first term of the run, layout)
+  auto add_layout = [&](uint32_t R) -> int {
+    auto it = lay_id.find(R);
+    if (it != lay_id.end()) return it->second;
+    if (a.n_lay >= kMaxLayouts) return -1;
+    Layout& L = a.lay[a.n_lay];
+    L = Layout();
+    L.reg = R;
+    int i = 0;
+    for (uint32_t t = R; t; t &= t - 1u, ++i) {
+      const int rp = __builtin_ctz(t);
+      const uint32_t bit = 1u << rp;
+      L.qoff[i] = (c64 && rp == 0) ? 0u : swz(c64 ? (bit >> 1) : bit);
+      L.goff[i] = glob(bit);
+    }
+    // Thread positions: three lanes whose chunk bits differ mod 3 first (the
+    // eight threads of a quarter-warp then hit distinct 16-byte bank groups),
+    // then the rest in ascending order.
+    std::vector<int> thr;
+    for (int b = 0; b < T; ++b)
+      if (!((R >> b) & 1u)) thr.push_back(b);
+    std::vector<int> order, restp;
+    bool used_res[3] = {false, false, false};
+    for (int b : thr) {
+      const int res = (c64 ? b - 1 : b) % 3;
+      if (order.size() < 3 && res >= 0 && !used_res[res]) {
+        used_res[res] = true;
+        order.push_back(b);
+      } else {
+        restp.push_back(b);
+      }
+    }
+    order.insert(order.end(), restp.begin(), restp.end());
+    L.n_thr = int(order.size());
+    for (size_t k = 0; k < order.size(); ++k) L.thr[k] = int8_t(order[k]);
+    lay_id[R] = a.n_lay;
+    return a.n_lay++;
+  };
+  auto reg_coords = [&](uint32_t lmask, uint32_t R) { return pext32(lmask & R, R); };
+
+  uint32_t emitted = 0xffffffffu;  // no layout yet
+  std::vector<PClass> cls;
+  std::vector<PTerm> pts;
+  for (size_t i = 0; i < ops.size(); ++i) {
+    const HOp& h = ops[i];
+    const uint32_t R = lay_of[i];
+    if (R != emitted) {
+      const int li = add_layout(R);
+      if (li < 0) return fail("too many register layouts");
+      if (a.n_ops >= kMaxOps) return fail("too many ops");
+      Op& o = a.ops[a.n_ops++];
+      o = Op();
+      o.type = OP_LAYOUT;
+      o.idx = int16_t(li);
+      emitted = R;
+    }
+    if (a.n_ops >= kMaxOps) return fail("too many ops");
+    const Group& G = p.groups[h.g];
+    Op o = Op();
+    o.type = h.type;
+    if (h.type == OP_TAB) {
+      auto it = tab_id.find(h.g);
+      int ti;
+      if (it != tab_id.end()) {
+        ti = it->second;
+      } else {
+        if (a.n_tab >= kMaxTab || a.n_vt + G.vt_n > kMaxVt) return fail("value tables exceed the sweep's limits");
+        ti = a.n_tab++;
+        Tab& t = a.tab[ti];
+        t.vt0 = G.vt0;
+        t.s0 = a.n_vt;
+        t.n = G.vt_n;
+        t.sm = G.smask;
+        t.sh = pattern_shift_of(G.smask);
+        t.ns = int8_t(G.nslot);
+        a.n_vt += G.vt_n;
+        tab_id[h.g] = ti;
+      }
+      o.idx = int16_t(ti);
+      o.ku = uint8_t(reg_coords(h.need, R));
+    } else if (h.type == OP_ROT) {
+      const int key = G.kind * m + h.term;
+      auto it = rot_id.find(key);
+      int ri;
+      if (it != rot_id.end()) {
+        ri = it->second;
+      } else {
+        if (a.n_rot >= kMaxRot) return fail("too many rotations");
+        ri = a.n_rot++;
+        a.rot[ri].cs = key;
+        rot_id[key] = ri;
+      }
+      const uint64_t x = p.x[h.term], z = p.z[h.term];
+      const int y = __builtin_popcountll(x & z);
+      o.idx = int16_t(ri);
+      o.ku = uint8_t(reg_coords(h.need, R));
+      const uint32_t zl = loc(z);
+      o.zk = uint8_t(reg_coords(zl, R));
+      o.zthr = zl & ~R & tile_all;
+      o.zrest = uint32_t(z & ~uint64_t(local_mask));
+      o.flags = uint8_t((z == 0 ? 1 : 0) | (((y + 3) & 3) << 1));
+    } else {
+      const auto key = std::make_tuple(h.g, h.terms.front(), R);
+      auto it = phase_id.find(key);
+      int pi;
+      if (it != phase_id.end()) {
+        pi = it->second;
+      } else {
+        if (a.n_phase >= kMaxPhase) return fail("too many phase runs");
+        pi = a.n_phase++;
+        // Classes by local part of z_j; the constant class first.
+        std::map<uint32_t, std::vector<int>> by_local;
+        by_local[0];
+        for (int j : h.terms) by_local[loc(p.z[j])].push_back(j);
+        std::vector<std::pair<uint32_t, uint32_t>> keys;  // (mu, local part), constant class excluded
+        for (auto& kv : by_local)
+          if (kv.first) keys.push_back({reg_coords(kv.first, R), kv.first});
+        std::sort(keys.begin(), keys.end());
+        Phase& P = a.ph[pi];
+        P = Phase();
+        P.cls0 = int16_t(cls.size());
+        P.ncls = int16_t(1 + keys.size());
+        auto add_class = [&](uint32_t lpart, int c0p) {
+          PClass c{};
+          c.thr = lpart & ~R & tile_all;
+          c.t0 = int16_t(pts.size());
+          c.c0p = int16_t(c0p);
+          for (int j : by_local[lpart]) pts.push_back(PTerm{G.kind * m + j, uint32_t(p.z[j] & ~uint64_t(local_mask))});
+          c.nt = int16_t(int(pts.size()) - c.t0);
+          cls.push_back(c);
+        };
+        add_class(0u, pi);
+        const int NR = 1 << B;
+        int pos = 1;
+        size_t kk = 0;
+        for (int mu = 0; mu < NR; ++mu) {
+          P.mu_beg[mu] = int16_t(pos);
+          while (kk < keys.size() && int(keys[kk].first) == mu) {
+            add_class(keys[kk].second, -1);
+            ++kk;
+            ++pos;
+          }
+          if (pos > P.mu_beg[mu]) P.mu_mask |= 1u << mu;
+        }
+        P.mu_beg[NR] = int16_t(pos);
+        if (kk != keys.size()) return fail("internal: phase class outside the register patterns");
+        if (int(cls.size()) > kMaxClasses || int(pts.size()) > kMaxPTerms) return fail("phase runs too long");
+        phase_id[key] = pi;
+      }
+      o.idx = int16_t(pi);
+    }
+    a.ops[a.n_ops++] = o;
+  }
+  if (a.n_ops == 0) return fail("empty sweep");
+  a.n_cls = int(cls.size());
+  a.n_pterm = int(pts.size());
+  std::copy(cls.begin(), cls.end(), a.cls);
+  std::copy(pts.begin(), pts.end(), a.pt);
+  return true;
+}
+
+}  // namespace q
+}  // namespace hs

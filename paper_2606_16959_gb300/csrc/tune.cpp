@@ -73,13 +73,25 @@ extern "C" int hs_autotune(const hs_factors* f, const void* psi, int n_rhs, int 
         for (int kb : {0, 48}) cand.push_back(hs_evolve_opts{HS_METHOD_FUSED, tb, rb, 0, lb, 0, kb, 0});
       }
   }
+  // Register-blocked sweeps: register bits, tile bits, contiguous low bits.
+  const int n = f->plan.n_qubits;
+  for (int B : {5, 4}) {
+    if (dt == HS_C128 && B != 4) continue;
+    for (int tb = std::min(13, n); tb >= std::max(B + 5, std::min(13, n) - 2); --tb)
+      for (int lb : {2, 3, 4}) {
+        if (lb > tb) continue;
+        hs_evolve_opts o{HS_METHOD_REG, tb, 1, 0, lb, 0, 0, 0};
+        o.reg_bits = B;
+        cand.push_back(o);
+      }
+  }
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   float best_ms = 1e30f;
   hs_evolve_opts best_o = cand[0];
   int rc = HS_OK;
-  for (const hs_evolve_opts& o : cand) {
+  auto measure = [&](const hs_evolve_opts& o) {
     float t_min = 1e30f;
     bool ok = true;
     for (int rep = 0; rep < 2 && ok; ++rep) {
@@ -92,10 +104,24 @@ extern "C" int hs_autotune(const hs_factors* f, const void* psi, int n_rhs, int 
       cudaEventElapsedTime(&ms, e0, e1);
       t_min = std::min(t_min, ms);
     }
-    if (rc != HS_OK) break;
-    if (ok && t_min < best_ms) {
+    if (rc == HS_OK && ok && t_min < best_ms) {
       best_ms = t_min;
       best_o = o;
+    }
+  };
+  for (const hs_evolve_opts& o : cand) {
+    measure(o);
+    if (rc != HS_OK) break;
+  }
+  // Step-fusion depth: the most factor applications one sweep launch applies,
+  // tried on the winner (the default is the limit, 64).
+  if (rc == HS_OK && best_o.method != HS_METHOD_PLAIN) {
+    const hs_evolve_opts win = best_o;
+    for (int mf : {8, 16, 32}) {
+      hs_evolve_opts o = win;
+      o.max_fuse = mf;
+      measure(o);
+      if (rc != HS_OK) break;
     }
   }
   cudaEventDestroy(e0);

@@ -14,7 +14,7 @@ import numpy as np
 
 HS_OK, HS_EINVAL, HS_ENOMEM, HS_ECUDA, HS_ETIMEOUT, HS_EDTYPE = 0, -1, -2, -3, -4, -5
 HS_C64, HS_C128 = 1, 2
-HS_METHOD_AUTO, HS_METHOD_PLAIN, HS_METHOD_FUSED = 0, 1, 2
+HS_METHOD_AUTO, HS_METHOD_PLAIN, HS_METHOD_FUSED, HS_METHOD_REG = 0, 1, 2, 3
 HS_MAX_QUBITS = 30
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -53,7 +53,7 @@ class BatchOpts(ctypes.Structure):
 class EvolveOpts(ctypes.Structure):
     _fields_ = [("method", ctypes.c_int), ("tile_bits", ctypes.c_int), ("rhs_block", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("low_bits", ctypes.c_int), ("max_fuse", ctypes.c_int),
-                ("smem_kb", ctypes.c_int), ("no_tables", ctypes.c_int)]
+                ("smem_kb", ctypes.c_int), ("no_tables", ctypes.c_int), ("reg_bits", ctypes.c_int)]
 
 
 _lib = None
@@ -314,23 +314,26 @@ def hs_evolve(f: Factors, psi, n_steps: int, stream=None) -> None:
     _check(lib().hs_evolve(f.handle, ptr, n_rhs, int(n_steps), _stream(stream)))
 
 
+def _opts(method, tile_bits, rhs_block, use_graph, low_bits, max_fuse, smem_kb, no_tables, reg_bits) -> EvolveOpts:
+    return EvolveOpts(int(method), int(tile_bits), int(rhs_block), int(bool(use_graph)), int(low_bits), int(max_fuse),
+                      int(smem_kb), int(bool(no_tables)), int(reg_bits))
+
+
 def hs_evolve_ex(f: Factors, psi, n_steps: int, method: int = HS_METHOD_AUTO, tile_bits: int = 0,
                  rhs_block: int = 0, use_graph: bool = False, low_bits: int = 0, max_fuse: int = 0, smem_kb: int = 0,
-                 no_tables: bool = False, stream=None) -> None:
+                 no_tables: bool = False, reg_bits: int = 0, stream=None) -> None:
     ptr, n_rhs = _check_state(f, psi)
-    o = EvolveOpts(int(method), int(tile_bits), int(rhs_block), int(bool(use_graph)), int(low_bits), int(max_fuse),
-                   int(smem_kb), int(bool(no_tables)))
+    o = _opts(method, tile_bits, rhs_block, use_graph, low_bits, max_fuse, smem_kb, no_tables, reg_bits)
     _check(lib().hs_evolve_ex(f.handle, ptr, n_rhs, int(n_steps), ctypes.byref(o), _stream(stream)))
 
 
 def hs_evolve_td(f: Factors, psi, drive, method: int = HS_METHOD_AUTO, tile_bits: int = 0, rhs_block: int = 0,
                  use_graph: bool = False, low_bits: int = 0, max_fuse: int = 0, smem_kb: int = 0,
-                 no_tables: bool = False, stream=None) -> None:
+                 no_tables: bool = False, reg_bits: int = 0, stream=None) -> None:
     """One step per entry of `drive` (the frozen value of f for that step)."""
     ptr, n_rhs = _check_state(f, psi)
     fv = np.ascontiguousarray(np.asarray(drive, dtype=np.float64).ravel())
-    o = EvolveOpts(int(method), int(tile_bits), int(rhs_block), int(bool(use_graph)), int(low_bits), int(max_fuse),
-                   int(smem_kb), int(bool(no_tables)))
+    o = _opts(method, tile_bits, rhs_block, use_graph, low_bits, max_fuse, smem_kb, no_tables, reg_bits)
     _check(lib().hs_evolve_td(f.handle, ptr, n_rhs, fv.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), fv.size,
                               ctypes.byref(o), _stream(stream)))
 
@@ -341,10 +344,9 @@ def hs_factors_set_drive(f: Factors, drive: float, stream=None) -> None:
 
 def hs_evolve_plan(f: Factors, n_rhs: int, n_steps: int, method: int = HS_METHOD_AUTO, tile_bits: int = 0,
                    rhs_block: int = 0, use_graph: bool = False, low_bits: int = 0, max_fuse: int = 0,
-                   smem_kb: int = 0, no_tables: bool = False):
+                   smem_kb: int = 0, no_tables: bool = False, reg_bits: int = 0):
     """(n_sweep_launches, n_plain_launches, tile_bits, rhs_block) hs_evolve_ex would use."""
-    o = EvolveOpts(int(method), int(tile_bits), int(rhs_block), int(bool(use_graph)), int(low_bits), int(max_fuse),
-                   int(smem_kb), int(bool(no_tables)))
+    o = _opts(method, tile_bits, rhs_block, use_graph, low_bits, max_fuse, smem_kb, no_tables, reg_bits)
     a, b, c, d = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     _check(lib().hs_evolve_plan(f.handle, int(n_rhs), int(n_steps), ctypes.byref(o), ctypes.byref(a), ctypes.byref(b),
                                 ctypes.byref(c), ctypes.byref(d)))
@@ -358,7 +360,7 @@ def hs_autotune(f: Factors, psi, n_steps: int, stream=None) -> dict:
     o = EvolveOpts()
     _check(lib().hs_autotune(f.handle, ptr, n_rhs, int(n_steps), _stream(stream), ctypes.byref(o)))
     return dict(method=o.method, tile_bits=o.tile_bits, rhs_block=o.rhs_block, low_bits=o.low_bits,
-                max_fuse=o.max_fuse, smem_kb=o.smem_kb)
+                max_fuse=o.max_fuse, smem_kb=o.smem_kb, reg_bits=o.reg_bits)
 
 
 def hs_apply_factor(f: Factors, g: int, x, y, stream=None) -> None:

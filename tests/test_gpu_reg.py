@@ -1,0 +1,221 @@
+"""GPU parity of the register-blocked sweeps (HS_METHOD_REG) against the FP64 oracle.
+
+The register sweep applies a factor with a small value table from the table,
+and any other factor term by term: exact rotations for the non-diagonal terms
+and, for runs of diagonal terms, phases generated for every row from
+(z_j, theta_j) instead of read from stored diagonals.  The tests cover both
+kinds of factor (TFIM and MaxCut groups with wide ZZ runs, Heisenberg bond
+tables including the non-window wrap-around bond, one-hot TSP as a pure phase,
+random Pauli sums with Y and Z on register, thread and tile bits, terms that
+flip three qubits and fall back to plain launches), both register widths,
+several tile and low-bit choices, 16-state MaxCut, the higher-order formulas,
+time-dependent H(t), graph replay, and the launch plan.
+Tolerances: complex128 max-abs 1e-12; complex64 max-abs 1e-5, infidelity 1e-6.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2606_16959_gb300 import hs, workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+REG = hs.HS_METHOD_REG
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2606_16959_gb300 import _build
+    _build.build()
+    O.build()
+    hs.lib()
+
+
+def _tdt(dt):
+    return torch.complex64 if dt == "c64" else torch.complex128
+
+
+def _check(got, want, dt, what=""):
+    got = np.asarray(got, np.complex128).reshape(np.shape(want))
+    err = float(np.max(np.abs(got - want)))
+    if dt == "c128":
+        assert err <= 1e-12, f"{what}: max-abs {err:.3e}"
+        return
+    assert err <= 1e-5, f"{what}: max-abs {err:.3e}"
+    g2, w2 = got.reshape(-1, got.shape[-1]), np.asarray(want).reshape(-1, got.shape[-1])
+    for a, b in zip(g2, w2):
+        assert 1 - O.fidelity(a, b) <= 1e-6, what
+
+
+def _evolve(ham, t, steps, budget, dt, psi0, order=1, **kw):
+    f = hs.hs_build_factors(ham.labels, ham.coeffs, t, steps, budget, dt, order=order)
+    psi = torch.from_numpy(np.ascontiguousarray(psi0)).to("cuda", _tdt(dt))
+    hs.hs_evolve_ex(f, psi, steps, **kw)
+    out = psi.cpu().numpy()
+    f.close()
+    return out
+
+
+def _oracle(ham, t, steps, psi0, order=1):
+    x, z, _ = O.parse_terms(ham.labels)
+    if order == 1:
+        return O.evolve_direct(x, z, ham.coeffs, t, steps, psi0)
+    return O.evolve_direct_order(x, z, ham.coeffs, t, steps, psi0, order)
+
+
+def _random_ham(rng, n, m):
+    """Pauli sums whose terms flip at most two qubits (register ops) plus a few
+    diagonal terms with wide z support (phase runs)."""
+    labels = []
+    for _ in range(m):
+        k = int(rng.integers(1, 4))
+        qs = rng.choice(n, size=k, replace=False)
+        ops = {int(q): str(rng.choice(list("XYZ"))) for q in qs}
+        if sum(1 for p in ops.values() if p in "XY") > 2:
+            ops[int(qs[0])] = "Z"
+        labels.append(W.label_of(n, ops))
+    for _ in range(3):
+        qs = rng.choice(n, size=int(rng.integers(2, n)), replace=False)
+        labels.append(W.label_of(n, {int(q): "Z" for q in qs}))
+    return W.Hamiltonian("random", n, labels, rng.uniform(-1.2, 1.2, len(labels)))
+
+
+@pytest.mark.parametrize("dt", ["c128", "c64"])
+def test_reg_random_pauli_sums(dt):
+    rng = np.random.default_rng(4100)
+    for n in (10, 11, 13, 15):
+        ham = _random_ham(rng, n, 14)
+        psi0 = np.stack([W.gaussian_state(n, rng) for _ in range(2)])
+        want = _oracle(ham, 0.8, 3, psi0)
+        for budget in (4, 8, 16):
+            for B in ((4, 5) if dt == "c64" else (4,)):
+                got = _evolve(ham, 0.8, 3, budget, dt, psi0, method=REG, reg_bits=B)
+                _check(got, want, dt, f"n={n} budget={budget} B={B}")
+
+
+@pytest.mark.parametrize("dt", ["c128", "c64"])
+def test_reg_chains_tiles_and_low_bits(dt):
+    rng = np.random.default_rng(4101)
+    n = 14
+    hams = [(W.tfim_chain(n, 1.0, 0.7), 4), (W.tfim_chain(n, 0.8, 1.3), 8), (W.tfim_chain(n, 1.1, 0.4), 16),
+            (W.heisenberg_chain(n, rng.uniform(0.5, 1.5, n), periodic=True), 8),
+            (W.heisenberg_chain(n, rng.uniform(0.5, 1.5, n), periodic=True), 4)]
+    psi0 = np.stack([W.gaussian_state(n, rng) for _ in range(3)])
+    for ham, budget in hams:
+        want = _oracle(ham, 1.0, 5, psi0)
+        for tb, lb in ((0, 0), (10, 1), (11, 3), (12, 2), (13, 4)):
+            if dt == "c128" and tb and tb < 9:
+                continue
+            got = _evolve(ham, 1.0, 5, budget, dt, psi0, method=REG, tile_bits=tb, low_bits=lb, reg_bits=4)
+            _check(got, want, dt, f"{ham.family} budget={budget} tb={tb} lb={lb}")
+
+
+def test_reg_maxcut_sixteen_states_and_tsp():
+    job = W.maxcut24(n=16, n_rhs=16, n_steps=6)
+    want = _oracle(job.ham, job.t, job.n_steps, job.psi0)
+    for B in (5, 4):
+        got = _evolve(job.ham, job.t, job.n_steps, job.budget, "c64", job.psi0, method=REG, reg_bits=B)
+        _check(got, want, "c64", f"maxcut16 B={B}")
+    # one-hot TSP (16 qubits, every term diagonal): one phase run per step
+    rng = np.random.default_rng(4102)
+    tsp = W.tsp_onehot(4, 1234)
+    psi0 = np.stack([W.gaussian_state(16, rng) for _ in range(2)])
+    want = _oracle(tsp, 0.7, 4, psi0)
+    for dt in ("c64", "c128"):
+        got = _evolve(tsp, 0.7, 4, 1, dt, psi0, method=REG)
+        _check(got, want, dt, f"tsp {dt}")
+
+
+@pytest.mark.parametrize("order", [2, 4])
+def test_reg_higher_order(order):
+    rng = np.random.default_rng(4103 + order)
+    n = 12
+    for ham, budget in ((W.tfim_chain(n, 1.0, 0.9), 8), (W.heisenberg_chain(n, rng.uniform(0.5, 1.5, n)), 8),
+                        (W.maxcut_3regular(n, 55), 4)):
+        psi0 = W.gaussian_state(n, rng)
+        want = _oracle(ham, 0.9, 3, psi0, order)
+        for dt in ("c64", "c128"):
+            got = _evolve(ham, 0.9, 3, budget, dt, psi0, order=order, method=REG)
+            _check(got, want, dt, f"{ham.family} order {order} {dt}")
+
+
+def test_reg_three_qubit_flips_fall_back_to_plain():
+    rng = np.random.default_rng(4104)
+    n = 12
+    labels = [W.label_of(n, {0: "X", 5: "X", 9: "Y"}), W.label_of(n, {2: "Z", 3: "Z", 11: "Z"}),
+              W.label_of(n, {4: "X"}), W.label_of(n, {1: "Y", 7: "Z"})]
+    ham = W.Hamiltonian("random", n, labels, rng.uniform(-1, 1, len(labels)))
+    f = hs.hs_build_factors(ham.labels, ham.coeffs, 0.6, 3, 8, "c64")
+    n_sw, n_plain, _, _ = hs.hs_evolve_plan(f, 1, 3, method=REG)
+    assert n_plain >= 3  # the factor holding the three-qubit flip, once per step
+    f.close()
+    psi0 = W.gaussian_state(n, rng)
+    _check(_evolve(ham, 0.6, 3, 8, "c64", psi0, method=REG), _oracle(ham, 0.6, 3, psi0), "c64", "fallback")
+
+
+def test_reg_time_dependent_and_graph():
+    rng = np.random.default_rng(4105)
+    t, steps = 0.9, 6
+    fv = W.midpoint_samples(lambda s: np.cos(2.3 * s) + 0.4 * s, t, steps)
+    for ham, budget in ((W.anneal_maxcut(14, seed=77), 4), (W.driven_tfim(13, 1.0, 0.9), 8)):
+        x, z, n = O.parse_terms(ham.labels)
+        psi0 = np.stack([W.gaussian_state(n, rng) for _ in range(2)])
+        for dt in ("c64", "c128"):
+            want = O.evolve_direct_td(x, z, ham.a, ham.b, fv, t, psi0, 1)
+            for graph in (False, True):
+                f = hs.hs_build_factors_td(x, z, ham.a, ham.b, n, t, steps, budget, dt)
+                psi = torch.from_numpy(psi0).to("cuda", _tdt(dt))
+                hs.hs_evolve_td(f, psi, fv, method=REG, use_graph=graph)
+                _check(psi.cpu().numpy(), want, dt, f"{ham.family} td {dt} graph={graph}")
+                # the stored values are left at the last drive sample
+                _, _, _, vals = f.factor(0)
+                g = hs.hs_build_factors_masks(x, z, ham.a + fv[-1] * ham.b, n, t, steps, budget, dt)
+                _, _, _, ref = g.factor(0)
+                assert np.max(np.abs(vals - ref)) <= (1e-13 if dt == "c128" else 1e-7)
+                g.close()
+                f.close()
+
+
+def test_reg_graph_replay_and_steps_compose():
+    rng = np.random.default_rng(4106)
+    ham = W.tfim_chain(15, 1.0, 0.8)
+    f = hs.hs_build_factors(ham.labels, ham.coeffs, 1.0, 20, 8, "c64")
+    psi0 = W.gaussian_state(15, rng)
+    a = torch.from_numpy(psi0).to("cuda", torch.complex64)
+    hs.hs_evolve_ex(f, a, 20, method=REG)
+    b = torch.from_numpy(psi0).to("cuda", torch.complex64)
+    hs.hs_evolve_ex(f, b, 20, method=REG, use_graph=True)
+    c = torch.from_numpy(psi0).to("cuda", torch.complex64)
+    hs.hs_evolve_ex(f, c, 20, method=REG, use_graph=True)  # replay
+    torch.cuda.synchronize()
+    assert torch.equal(a, b) and torch.equal(a, c)
+    d = torch.from_numpy(psi0).to("cuda", torch.complex64)
+    hs.hs_evolve_ex(f, d, 7, method=REG)
+    hs.hs_evolve_ex(f, d, 13, method=REG)
+    assert torch.max(torch.abs(a - d)).item() < 1e-6
+    _check(a.cpu().numpy(), _oracle(ham, 1.0, 20, psi0), "c64", "tfim15")
+    f.close()
+
+
+def test_reg_maxcut24_against_fused_path():
+    """The full 24-qubit, 16-state MaxCut instance for two steps: the register
+    sweeps against the staged sweeps (both complex64) and state 0 against the
+    oracle on every amplitude."""
+    job = W.maxcut24(n_steps=50)
+    f = hs.hs_build_factors(job.ham.labels, job.ham.coeffs, job.t / 25, 2, job.budget, "c64")
+    a = torch.from_numpy(job.psi0).to("cuda", torch.complex64)
+    b = a.clone()
+    hs.hs_evolve_ex(f, a, 2, method=REG)
+    hs.hs_evolve_ex(f, b, 2, method=hs.HS_METHOD_FUSED)
+    torch.cuda.synchronize()
+    assert torch.max(torch.abs(a - b)).item() < 1e-6
+    n_sw, n_plain, tb, rb = hs.hs_evolve_plan(f, 16, 2, method=REG)
+    assert n_plain == 0 and tb == 13 and rb == 1 and n_sw <= 5
+    got0 = a[0].cpu().numpy()
+    f.close()
+    x, z, _ = O.parse_terms(job.ham.labels)
+    want0 = O.evolve_direct(x, z, job.ham.coeffs, job.t / 25, 2, job.psi0[0])
+    _check(got0, want0, "c64", "maxcut24 state 0")
