@@ -269,7 +269,7 @@ def algorithmic_bytes(f, job, n_rhs):
 def build_job(hs, job, dtype, order):
     """The job's factor set: static, or time-dependent when the job has a drive."""
     if job.drive is not None:
-        x, z, n = hs.label_masks(job.ham.labels)
+        x, z, n = hs.hs_parse_terms(job.ham.labels)
         return hs.hs_build_factors_td(x, z, job.ham.a, job.ham.b, n, job.t, job.n_steps, job.budget, dtype,
                                       order=order)
     return hs.hs_build_factors(job.ham.labels, job.ham.coeffs, job.t, job.n_steps, job.budget, dtype, order=order)

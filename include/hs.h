@@ -83,6 +83,16 @@ typedef struct hs_factors hs_factors;
 int hs_build_factors(const char* const* pauli_terms, const double* coeffs, size_t n_terms, double t,
                      int n_steps, int diag_budget, hs_dtype dtype, void* cuda_stream, hs_factors** out);
 
+/* Term canonicalisation alone (the HamLib Pauli strings of Sec. 4.4 turned
+ * into the masks every other entry point takes): label j becomes x[j] (bit q
+ * set where character n_qubits-1-q is X or Y) and z[j] (Z or Y), so that
+ * P_j|b> = i^popcount(x&z) (-1)^popcount(z&b) |b xor x>.  labels: n_terms
+ * NUL-terminated host strings of equal length 1..HS_MAX_QUBITS; x, z: host
+ * arrays of n_terms entries, written only on success; *n_qubits receives the
+ * label length.  Host only, no GPU call.  Errors: HS_EINVAL (NULL argument,
+ * no terms, invalid character, labels of different lengths). */
+int hs_parse_terms(const char* const* labels, size_t n_terms, uint64_t* x, uint64_t* z, int* n_qubits);
+
 /* Same as hs_build_factors with pre-parsed terms: x[j], z[j] are the flip and
  * phase masks of term j (bits >= n_qubits must be zero). */
 int hs_build_factors_masks(const uint64_t* x, const uint64_t* z, const double* coeffs, size_t n_terms,
@@ -274,6 +284,16 @@ int hs_batch_info(const hs_batch* b, int* n_levels, int64_t* n_ctas, int64_t* n_
 
 /* Free a batch (NULL is a no-op).  Synchronises the device first. */
 void hs_batch_free(hs_batch* b);
+
+/* One call over job arrays (the batched form of hs_evolve): job k evolves
+ * psi[k] (n_rhs[k] states, device buffer of the factors' dtype) in place by
+ * n_steps[k] steps of f[k].  Plans a batch with the default options,
+ * enqueues its launches on cuda_stream (directly, no graph) and frees the
+ * batch's tables in stream order; the same work as hs_batch_create +
+ * hs_batch_launch + hs_batch_free_async.  All arrays are host arrays of
+ * n_jobs entries.  Errors as hs_batch_create and hs_batch_launch. */
+int hs_evolve_batch(const hs_factors* const* f, void* const* psi, const int* n_rhs, const int* n_steps,
+                    size_t n_jobs, void* cuda_stream);
 
 /* Free a batch in stream order without synchronising (its tables return to the
  * pool after the work already enqueued on cuda_stream); every launch of b must

@@ -1,6 +1,7 @@
 // C ABI of libhs (declared in include/hs.h).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <atomic>
 #include <cstring>
@@ -546,6 +547,19 @@ int hs_factors_sequence(const hs_factors* f, int* order, int* seq, int capacity,
     if (capacity < int(q.size())) return fail(HS_EINVAL, "seq capacity too small");
     for (size_t k = 0; k < q.size(); ++k) seq[k] = q[k];
   }
+  return HS_OK;
+}
+
+int hs_parse_terms(const char* const* labels, size_t n_terms, uint64_t* x, uint64_t* z, int* n_qubits) {
+  if (!x || !z || !n_qubits) return fail(HS_EINVAL, "null output array");
+  std::vector<uint64_t> xv, zv;
+  int nq = 0;
+  std::string err;
+  int rc = hs::parse_labels(labels, n_terms, xv, zv, nq, &err);
+  if (rc != HS_OK) return fail(rc, err);
+  std::copy(xv.begin(), xv.end(), x);
+  std::copy(zv.begin(), zv.end(), z);
+  *n_qubits = nq;
   return HS_OK;
 }
 

@@ -481,3 +481,17 @@ extern "C" int hs_batch_free_async(hs_batch* b, void* cuda_stream) {
   if (b) batch_release(b, reinterpret_cast<cudaStream_t>(cuda_stream));
   return HS_OK;
 }
+
+extern "C" int hs_evolve_batch(const hs_factors* const* f, void* const* psi, const int* n_rhs, const int* n_steps,
+                               size_t n_jobs, void* cuda_stream) {
+  if (!f || !psi || !n_rhs || !n_steps || n_jobs == 0) return hs::report_error(HS_EINVAL, "null job arrays or no jobs");
+  std::vector<hs_batch_job> jobs(n_jobs);
+  for (size_t k = 0; k < n_jobs; ++k) jobs[k] = hs_batch_job{f[k], psi[k], n_rhs[k], n_steps[k]};
+  hs_batch_opts o{0, 0, 0, 0, 0, 0};
+  hs_batch* b = nullptr;
+  int rc = hs_batch_create(jobs.data(), n_jobs, &o, &b);
+  if (rc != HS_OK) return rc;
+  rc = hs_batch_launch(b, cuda_stream);
+  hs_batch_free_async(b, cuda_stream);
+  return rc;
+}

@@ -31,6 +31,7 @@ EXPORTS = (
     "hs_spmv", "hs_dia_evolve", "hs_dia_convert", "hs_dia_info", "hs_dia_get", "hs_dia_free",
     "hs_kernel_launches", "hs_expectation", "hs_build_factors_ex", "hs_factors_sequence",
     "hs_build_factors_td", "hs_evolve_td", "hs_factors_set_drive", "hs_dia_evolve_td",
+    "hs_parse_terms", "hs_evolve_batch",
 )
 
 
@@ -122,6 +123,10 @@ def lib() -> ctypes.CDLL:
         L.hs_factors_set_drive.argtypes = [vp, d, vp]
         L.hs_dia_evolve_td.argtypes = [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64), dp, dp, sz,
                                        i, d, dp, i, d, i, vp, i, i, vp]
+        L.hs_parse_terms.argtypes = [ctypes.POINTER(ctypes.c_char_p), sz, ctypes.POINTER(ctypes.c_uint64),
+                                     ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(i)]
+        L.hs_evolve_batch.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(i), ctypes.POINTER(i), sz,
+                                      vp]
         L.hs_kernel_launches.argtypes = []
         L.hs_kernel_launches.restype = ctypes.c_uint64
         for name in EXPORTS:
@@ -228,30 +233,23 @@ class Factors:
             pass
 
 
-def label_masks(labels: Sequence[str]):
-    """(x, z, n_qubits) of Pauli labels (rightmost character = qubit 0):
-    argument marshalling for the mask-based entry points."""
-    x = np.zeros(len(labels), dtype=np.uint64)
-    z = np.zeros(len(labels), dtype=np.uint64)
-    n = len(labels[0]) if labels else 0
-    for j, lab in enumerate(labels):
-        if len(lab) != n:
-            raise ValueError("labels differ in length")
-        for p_, ch in enumerate(lab):
-            bit = np.uint64(1 << (n - 1 - p_))
-            if ch in "XY":
-                x[j] |= bit
-            if ch in "ZY":
-                z[j] |= bit
-            if ch not in "IXYZ":
-                raise ValueError(f"invalid Pauli character {ch!r}")
-    return x, z, n
+def hs_parse_terms(labels: Sequence[str]):
+    """(x, z, n_qubits) of Pauli labels, parsed by the library (rightmost
+    character = qubit 0)."""
+    n_terms = len(labels)
+    arr = (ctypes.c_char_p * max(1, n_terms))(*[l.encode() for l in labels])
+    x = np.zeros(max(1, n_terms), dtype=np.uint64)
+    z = np.zeros(max(1, n_terms), dtype=np.uint64)
+    nq = ctypes.c_int()
+    _check(lib().hs_parse_terms(arr, n_terms, x.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                z.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), ctypes.byref(nq)))
+    return x[:n_terms], z[:n_terms], nq.value
 
 
 def hs_build_factors(labels: Sequence[str], coeffs, t: float, n_steps: int, diag_budget: int, dtype="c64",
                      stream=None, order: int = 1) -> Factors:
     if order != 1:
-        x, z, n = label_masks(labels)
+        x, z, n = hs_parse_terms(labels)
         return hs_build_factors_masks(x, z, coeffs, n, t, n_steps, diag_budget, dtype, stream, order)
     arr = (ctypes.c_char_p * len(labels))(*[l.encode() for l in labels])
     c = np.ascontiguousarray(np.asarray(coeffs, dtype=np.float64))
@@ -490,6 +488,20 @@ def hs_batch_create(jobs, tile_bits: int = 0, low_bits: int = 0, use_graph: bool
 
 def hs_batch_launch(b: Batch, stream=None) -> None:
     _check(lib().hs_batch_launch(b.handle, _stream(stream)))
+
+
+def hs_evolve_batch(jobs, stream=None) -> None:
+    """jobs: sequence of (Factors, state tensor, n_steps); one call plans,
+    launches and frees (in stream order) a batch of them."""
+    n = len(jobs)
+    fs = (ctypes.c_void_p * max(1, n))()
+    ps = (ctypes.c_void_p * max(1, n))()
+    nr = (ctypes.c_int * max(1, n))()
+    ns = (ctypes.c_int * max(1, n))()
+    for k, (f, psi, n_steps) in enumerate(jobs):
+        ptr, n_rhs = _check_state(f, psi)
+        fs[k], ps[k], nr[k], ns[k] = f.handle.value, ptr, n_rhs, int(n_steps)
+    _check(lib().hs_evolve_batch(fs, ps, nr, ns, n, _stream(stream)))
 
 
 # ---------------------------------------------------------------------------

@@ -10,6 +10,16 @@ states stay on the device; memory is returned in stream order when a group
 finishes.  Completion times come from CUDA events measured against a start
 event, so latency = GPU completion time - arrival time.
 
+A request's device bytes come from the structural dry run of its terms,
+cached per Hamiltonian structure (labels and budget), so admission does no
+planning work for a structure it has seen.  A build that fails for lack of
+device memory (HS_ENOMEM) puts its group back at the head of the queue and
+admission pauses until an in-flight group retires; a request that fails three
+times is reported failed and the stream goes on.  cancel() withdraws a request:
+a waiting one never runs, an in-flight one finishes on the device and its
+result is dropped.  The `fault` hook (called as fault(stage, request) before
+each request's build) lets tests inject such failures on the host.
+
 All computation runs in libhs; this module only schedules.  shard_jobs splits
 a request stream across ranks (independent jobs, no data exchange).
 """
@@ -43,6 +53,9 @@ class Request:
     updates: int = 0
     norm2: Optional[float] = None
     result: Optional[np.ndarray] = None
+    attempts: int = 0
+    cancelled: bool = False
+    error: Optional[str] = None
 
 
 def requests_from_jobs(jobs) -> List[Request]:
@@ -92,36 +105,56 @@ class Server:
         self.used = 0
         self.peak_used = 0
         self._next_stream = 0
+        self._plan_bytes = collections.OrderedDict()  # (labels, budget) -> factor bytes
+        self._cancel = set()
+        self._paused = False  # admission paused after an allocation failure
+        self.fault = None     # fault(stage, request): host-side fault injection (tests)
+        self.n_alloc_failures = 0
 
-    def _masks(self, r: Request):
-        x = np.zeros(len(r.labels), dtype=np.uint64)
-        z = np.zeros(len(r.labels), dtype=np.uint64)
-        n = r.n_qubits
-        for j, lab in enumerate(r.labels):
-            xv = zv = 0
-            for p, ch in enumerate(lab):
-                q = n - 1 - p
-                if ch in "XY":
-                    xv |= 1 << q
-                if ch in "ZY":
-                    zv |= 1 << q
-            x[j], z[j] = xv, zv
-        return x, z
+    def cancel(self, rid: int) -> None:
+        """Withdraw request rid: if it is still waiting it never runs; if it is in
+        flight its result is dropped when its group finishes."""
+        self._cancel.add(rid)
 
     def _bytes(self, r: Request) -> int:
         """Device bytes a request holds while in flight: its factor values (structural
-        dry run), its state, and a margin for tables."""
-        x, z = self._masks(r)
-        _, vbytes = hs.hs_plan_factors(x, z, r.n_qubits, r.budget, self.dtype)
+        dry run, cached per structure), its state, and a margin for tables."""
+        key = (tuple(r.labels), r.budget)
+        vbytes = self._plan_bytes.get(key)
+        if vbytes is None:
+            x, z, n = hs.hs_parse_terms(r.labels)
+            _, vbytes = hs.hs_plan_factors(x, z, n, r.budget, self.dtype)
+            self._plan_bytes[key] = vbytes
+            if len(self._plan_bytes) > 4096:
+                self._plan_bytes.popitem(last=False)
+        else:
+            self._plan_bytes.move_to_end(key)
         return int(vbytes) + (1 << r.n_qubits) * self.esize + (1 << 20)
 
     def _launch(self, group: List[Request], t0_event):
+        """Build and launch one group; None if a build ran out of device memory
+        (everything built so far is released in stream order)."""
         torch = self.torch
         s = self.streams[self._next_stream % len(self.streams)]
         self._next_stream += 1
         states, facs = [], []
+        try:
+            return self._launch_on(group, s, states, facs)
+        except hs.HSError as e:
+            if e.code != hs.HS_ENOMEM:
+                raise
+            for f in facs:
+                f.close(stream=s)
+            self.n_alloc_failures += 1
+            return None
+
+    def _launch_on(self, group, s, states, facs):
+        torch = self.torch
         with torch.cuda.stream(s):
             for r in group:
+                r.attempts += 1
+                if self.fault is not None:
+                    self.fault("build", r)
                 if r.psi0 is not None:
                     st = torch.from_numpy(np.ascontiguousarray(r.psi0)).to("cuda", self.tdt, non_blocking=True)
                 else:
@@ -147,6 +180,12 @@ class Server:
             ev.record(s)
         return _Group(group, facs, states, b, s, ev, 0, out, host)
 
+    def _runnable(self, r: Request) -> bool:
+        if r.rid in self._cancel:
+            r.cancelled = True
+            return False
+        return True
+
     def run(self, requests: Sequence[Request], realtime: bool = True, poll_s: float = 5e-5):
         """Serve the requests (sorted by arrival).  realtime: wait for arrival times;
         otherwise every request is available at once.  Returns a stats dict."""
@@ -163,7 +202,9 @@ class Server:
         while pending or waiting or inflight:
             now = time.perf_counter() - t0
             while pending and (not realtime or pending[0].arrival <= now):
-                waiting.append(pending.popleft())
+                r = pending.popleft()
+                if self._runnable(r):
+                    waiting.append(r)
             # retire finished groups
             keep = []
             for g in inflight:
@@ -171,6 +212,9 @@ class Server:
                     t_done = t0_event.elapsed_time(g.event) / 1000.0
                     norms = g.out[:, 2].cpu().numpy()
                     for k, r in enumerate(g.reqs):
+                        if r.rid in self._cancel:
+                            r.cancelled = True
+                            continue
                         r.done = t_done
                         r.norm2 = float(norms[k])
                         if self.keep_results:
@@ -180,13 +224,18 @@ class Server:
                         f.close(stream=g.stream)
                     self.used -= g.bytes
                     n_inflight -= len(g.reqs)
+                    self._paused = False
                 else:
                     keep.append(g)
             inflight = keep
             # admit
             group, gbytes = [], 0
-            while waiting and n_inflight + len(group) < self.max_inflight and len(group) < self.max_group:
+            while (waiting and not self._paused and n_inflight + len(group) < self.max_inflight
+                   and len(group) < self.max_group):
                 r = waiting[0]
+                if not self._runnable(r):
+                    waiting.popleft()
+                    continue
                 need = self._bytes(r)
                 if self.used + gbytes + need > self.budget:
                     if not inflight and not group and self.used == 0:
@@ -198,6 +247,18 @@ class Server:
                 gbytes += need
             if group:
                 g = self._launch(group, t0_event)
+                if g is None:
+                    # out of device memory: requests that failed three times are
+                    # reported failed, the rest wait (at the head of the queue)
+                    # until an in-flight group returns its memory
+                    for r in reversed(group):
+                        if r.attempts >= 3:
+                            r.error = "device memory exhausted"
+                            r.done = time.perf_counter() - t0
+                        else:
+                            waiting.appendleft(r)
+                    self._paused = bool(inflight)
+                    continue
                 g.bytes = gbytes
                 self.used += gbytes
                 self.peak_used = max(self.peak_used, self.used)
@@ -210,11 +271,14 @@ class Server:
                 wait = min(1e-3, max(0.0, pending[0].arrival - (time.perf_counter() - t0)))
             time.sleep(wait)
         torch.cuda.synchronize()
-        lat = np.array([r.done - r.arrival for r in requests])
+        served = [r for r in requests if not r.cancelled and r.error is None]
+        lat = np.array([r.done - r.arrival for r in served]) if served else np.zeros(1)
         t_first = min(r.arrival for r in requests)
-        t_last = max(r.done for r in requests)
-        updates = sum(r.updates for r in requests)
-        return dict(n=len(requests), p50_ms=float(np.percentile(lat, 50) * 1e3), p99_ms=float(np.percentile(lat, 99) * 1e3),
+        t_last = max((r.done for r in served), default=t_first)
+        updates = sum(r.updates for r in served)
+        return dict(n=len(served), n_cancelled=sum(r.cancelled for r in requests),
+                    n_failed=sum(r.error is not None for r in requests),
+                    p50_ms=float(np.percentile(lat, 50) * 1e3), p99_ms=float(np.percentile(lat, 99) * 1e3),
                     mean_ms=float(lat.mean() * 1e3), makespan_s=t_last - t_first, updates=updates,
                     throughput=updates / max(t_last - t_first, 1e-9), peak_bytes=self.peak_used,
-                    launches=hs.hs_kernel_launches() - l0)
+                    alloc_failures=self.n_alloc_failures, launches=hs.hs_kernel_launches() - l0)

@@ -108,3 +108,27 @@ def test_batch_and_serve_generators_plan(oracle, lib):
     for job in W.batch256(n_jobs=24, n_hi=14):
         x, z, n = oracle.parse_terms(job.ham.labels)
         _compare(oracle, x, z, n, job.budget)
+
+
+def test_parse_terms_matches_oracle(oracle, lib):
+    """Term canonicalisation in the library (hs_parse_terms) equals the oracle's parser bit for bit."""
+    rng = np.random.default_rng(78)
+    for trial in range(100):
+        n = int(rng.integers(1, 31))
+        labels = ["".join(rng.choice(list("IXYZ"), size=n)) for _ in range(int(rng.integers(1, 20)))]
+        x, z, nq = hs.hs_parse_terms(labels)
+        ox, oz, on = oracle.parse_terms(labels)
+        assert nq == on and np.array_equal(x, np.asarray(ox, np.uint64)) and np.array_equal(z, np.asarray(oz, np.uint64))
+    for bad in (["XQ"], ["XX", "X"], [], ["I" * 31]):
+        with pytest.raises(hs.HSError) as e:
+            hs.hs_parse_terms(bad)
+        assert e.value.code == hs.HS_EINVAL
+
+
+def test_no_pauli_parsing_in_python_package():
+    """Labels are parsed only by the library: the Python package marshals them."""
+    pkg = os.path.join(ROOT, "paper_2606_16959_gb300")
+    for name in os.listdir(pkg):
+        if name.endswith(".py"):
+            src = open(os.path.join(pkg, name)).read()
+            assert 'in "XY"' not in src and 'in "ZY"' not in src, name

@@ -88,3 +88,66 @@ def test_poisson_stream_latency():
     assert stats["n"] == 40 and 0 < stats["p50_ms"] <= stats["p99_ms"]
     assert stats["throughput"] > 0
     assert all(abs(r.norm2 - 1.0) < 1e-4 for r in reqs)
+
+
+def _alone(r):
+    a = serve.Request(r.labels, r.coeffs, r.n_qubits, r.t, r.n_steps, r.budget, psi0=r.psi0, rid=r.rid)
+    serve.Server(keep_results=True).run([a], realtime=False)
+    return a.result
+
+
+def test_allocation_failure_is_retried_and_the_rest_unchanged():
+    """A build that runs out of device memory (injected on the host as HS_ENOMEM
+    on request 3's first attempt) puts its group back in the queue; every
+    request completes with the bits it has when served alone."""
+    mix = _requests(11, 9, 9, 12)
+    srv = serve.Server(keep_results=True, max_group=2, n_streams=2)
+
+    def fault(stage, r):
+        if stage == "build" and r.rid == 3 and r.attempts == 1:
+            raise hs.HSError(hs.HS_ENOMEM, "injected allocation failure")
+    srv.fault = fault
+    stats = srv.run(mix, realtime=False)
+    assert stats["n"] == 9 and stats["alloc_failures"] == 1 and stats["n_failed"] == 0
+    assert mix[3].attempts == 2
+    for r in mix:
+        assert np.array_equal(r.result, _alone(r)), r.rid
+
+
+def test_persistent_allocation_failure_fails_one_request_only():
+    mix = _requests(12, 6, 9, 11)
+    srv = serve.Server(keep_results=True, max_group=1)
+    srv.fault = lambda stage, r: (_ for _ in ()).throw(hs.HSError(hs.HS_ENOMEM, "injected")) if r.rid == 2 else None
+    stats = srv.run(mix, realtime=False)
+    assert stats["n"] == 5 and stats["n_failed"] == 1 and mix[2].error and mix[2].result is None
+    for r in mix:
+        if r.rid != 2:
+            assert np.array_equal(r.result, _alone(r)), r.rid
+
+
+def test_cancelled_request_never_runs_and_the_rest_unchanged():
+    mix = _requests(13, 8, 9, 12)
+    srv = serve.Server(keep_results=True, max_group=2)
+    srv.cancel(5)
+    stats = srv.run(mix, realtime=False)
+    assert stats["n"] == 7 and stats["n_cancelled"] == 1
+    assert mix[5].cancelled and mix[5].result is None and mix[5].updates == 0
+    for r in mix:
+        if r.rid != 5:
+            assert np.array_equal(r.result, _alone(r)), r.rid
+
+
+def test_slow_job_does_not_hold_back_the_others():
+    """A 22-qubit, 100-step request admitted first runs on its own stream; the
+    small requests admitted after it finish before it and keep their bits."""
+    rng = np.random.default_rng(14)
+    big_h = W.heisenberg_chain(22, rng.uniform(0.5, 1.5, 22))
+    big = serve.Request(list(big_h.labels), big_h.coeffs, 22, 1.0, 100, 8, psi0=W.gaussian_state(22, rng), rid=100)
+    small = _requests(15, 6, 9, 11)
+    srv = serve.Server(keep_results=True, max_group=1, n_streams=8)  # the big request's stream takes no other
+    stats = srv.run([big] + small, realtime=False)
+    assert stats["n"] == 7
+    assert max(r.done for r in small) < big.done
+    for r in small:
+        assert np.array_equal(r.result, _alone(r)), r.rid
+    assert abs(big.norm2 - 1.0) < 1e-4
