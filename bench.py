@@ -182,17 +182,21 @@ def max_over_ranks(v, world):
 
 
 TUNE_CACHE = os.path.join(ROOT, "paper_2606_16959_gb300", "_build", "autotune_bench.json")
-# Committed ncu summary per workload, and the kernel it covers.
-PROFILE_SUMMARY = {"heis16": ("sweep_kernel_heis16.md", "sweep_kernel"),
-                   "maxcut24": ("sweep_kernel_maxcut24.md", "sweep_kernel"),
-                   "batch256": ("batch_level_kernel_batch256.md", "batch_level_kernel"),
-                   "taylor16": ("spmv_kernel_taylor16.md", "spmv_kernel"),
-                   "anneal24": ("sweep_kernel_anneal24.md", "sweep_kernel")}
+# Committed ncu summaries are named <kernel>_<workload>.md (profiles/).
 # Device-code sources of each kernel: a summary's DRAM figures count only while
 # these are unchanged since the capture.
 KERNEL_SOURCES = {"sweep_kernel": ("apply.cu", "sweep_core.cuh", "hs_internal.h"),
+                  "qsweep_kernel": ("qsweep.cu", "qsweep.h", "sweep_core.cuh", "hs_internal.h"),
                   "batch_level_kernel": ("batch.cu", "sweep_core.cuh", "hs_internal.h"),
+                  "batch_qsweep_kernel": ("qsweep.cu", "qsweep.h", "batch.cu", "sweep_core.cuh", "hs_internal.h"),
                   "spmv_kernel": ("dia.cu",)}
+
+
+def sweep_kernel_name(opts, n_sweeps):
+    """The kernel an evolution's fused launches run under these options."""
+    if not n_sweeps:
+        return "apply_plain_kernel"
+    return "qsweep_kernel" if opts.get("method") == 3 else "sweep_kernel"
 
 
 def kernel_source_hash(kernel):
@@ -204,13 +208,12 @@ def kernel_source_hash(kernel):
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload):
+def profiled_traffic(workload, kernel):
     """DRAM bytes per launch of the dominant kernel from the committed ncu
     summary, or None if there is none or the kernel's sources changed since."""
-    if workload not in PROFILE_SUMMARY:
+    if kernel not in KERNEL_SOURCES:
         return None
-    fname, kernel = PROFILE_SUMMARY[workload]
-    path = os.path.join(ROOT, "profiles", fname)
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
     if not os.path.exists(path):
         return None
     vals = {}
@@ -725,13 +728,14 @@ def run_ours(args):
     avg_launch_s = statistics.mean(res["evolve_ms"]) / 1000.0 / max(1, launches_evolve)
     per_launch_bytes = res["alg_bytes"] / max(1, launches_evolve)
     achieved = per_launch_bytes / avg_launch_s / 1e9
-    traffic = profiled_traffic(args.workload) if not args.qubits else None
+    kernel = sweep_kernel_name(args.tuned_opts, res["n_sweeps"])
+    traffic = profiled_traffic(args.workload, kernel) if not args.qubits else None
     line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": K, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": dtype, "data": "synthetic", "config": config_of(args, job, desc, res),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                          "traffic": traffic, "peak_source": peak_kind,
-                         "kernel": "sweep_kernel" if res["n_sweeps"] else "apply_plain_kernel",
+                         "kernel": kernel,
                          "algorithmic_bytes_per_launch": per_launch_bytes,
                          "avg_launch_us": avg_launch_s * 1e6, **dram_fields(traffic, avg_launch_s, hbm),
                          **({"note": "evolution time per sweep launch, including the per-step rebuild "
@@ -765,7 +769,7 @@ def run_batch(args, rank, world):
     launch_s = statistics.mean(res["launch_ms"]) / 1000.0
     per_launch_bytes = res["alg_bytes"] / max(1, res["levels"])
     achieved = res["alg_bytes"] / launch_s / 1e9
-    traffic = profiled_traffic("batch256") if args.batch_jobs == 256 else None
+    traffic = profiled_traffic("batch256", res.get("kernel", "batch_level_kernel")) if args.batch_jobs == 256 else None
     cfg = {"workload": "batch256", "description": desc, "n_jobs": len(jobs), "levels_per_step": res["levels"],
            "ctas_per_step": res["ctas"], "separate_jobs": res["separate"], "tile_bits": 10, "smem_kb_per_cta": 24,
            "l2": "flushed (512 MiB write) before every timed step"}
@@ -898,7 +902,7 @@ def run_taylor(args, rank, world):
     launch_s = statistics.mean(res["evolve_ms"]) / 1000.0 / max(1, info["r"])
     per_launch = 8 * info["S"] + 2 * 8 * res["N"]
     achieved = per_launch / launch_s / 1e9
-    traffic = profiled_traffic("taylor16") if not args.qubits else None
+    traffic = profiled_traffic("taylor16", "spmv_kernel") if not args.qubits else None
     cfg = {"workload": "taylor16", "description": desc, "n_qubits": job.ham.n_qubits, "n_terms": len(job.ham.labels),
            "diag_budget": job.budget, "t": job.t, "n_rhs": 1, "H_diags": info["H_diags"], "n_steps": info["r"],
            "U_diags": info["D"], "taylor_terms": info["K"], "l2": "flushed (512 MiB write) before every timed step"}

@@ -82,7 +82,10 @@ bool plan_qsweep(const hs_factors* f, const std::vector<int>& factors, uint32_t 
   for (int g : factors) {
     const Group& G = p.groups[g];
     if ((G.span & ~uint64_t(local_mask)) != 0) return fail("factor flips outside the tile");
-    if (G.vt0 >= 0 && G.nslot >= 1 && G.nslot <= 2 && G.vt_n <= kMaxVt) {
+    // A factor of several terms with a value table of at most two slots (a
+    // Heisenberg bond) is read from its table; a single term is cheaper as
+    // its rotation.
+    if (G.last - G.first > 1 && G.vt0 >= 0 && G.nslot >= 1 && G.nslot <= 2 && G.vt_n <= kMaxVt) {
       const uint32_t u = G.nslot == 2 ? p.slot_u[G.slot0 + 1] : 0u;
       if (__builtin_popcount(loc(u)) <= 2) {
         ops.push_back(HOp{OP_TAB, g, -1, {}, loc(u)});
@@ -142,12 +145,43 @@ bool plan_qsweep(const hs_factors* f, const std::vector<int>& factors, uint32_t 
     for (size_t i = 0; i < ops.size(); ++i) lay_of[i] = cur;
   }
 
-  // 3. Emit the descriptor.
-  std::map<uint32_t, int> lay_id;
+  // 3. Emit the descriptor.  Thread positions of a layout: five lane bits,
+  // then the warp bits (thread index bits 5 and up).  A layout keeps the
+  // previous layout's warp bits when they are still thread bits, so that the
+  // change is a warp-local exchange (each warp writes and reads back the same
+  // rows, with no CTA-wide barrier); otherwise it prefers warp bits that the
+  // next layout can keep.
+  std::vector<uint32_t> seq;  // distinct consecutive layouts
+  for (size_t i = 0; i < ops.size(); ++i)
+    if (seq.empty() || seq.back() != lay_of[i]) seq.push_back(lay_of[i]);
+  const int n_warp_bits = std::max(0, (T - B) - 5);
+  std::vector<std::vector<int>> warp_pos(seq.size());
+  for (size_t li = 0; li < seq.size(); ++li) {
+    const uint32_t thr_mask = tile_all & ~seq[li];
+    std::vector<int> w;
+    if (li > 0) {
+      bool keep = true;
+      for (int b : warp_pos[li - 1]) keep = keep && ((thr_mask >> b) & 1u);
+      if (keep) w = warp_pos[li - 1];
+    }
+    if (w.empty() && n_warp_bits > 0) {
+      const uint32_t next = li + 1 < seq.size() ? (tile_all & ~seq[li + 1]) : 0u;
+      // highest thread bits first, those the next layout also has as thread bits before the others
+      for (int pass = 0; pass < 2 && int(w.size()) < n_warp_bits; ++pass)
+        for (int b = T - 1; b >= 0 && int(w.size()) < n_warp_bits; --b)
+          if (((thr_mask >> b) & 1u) && (pass == 1 || ((next >> b) & 1u)) &&
+              std::find(w.begin(), w.end(), b) == w.end())
+            w.push_back(b);
+      std::sort(w.begin(), w.end());
+    }
+    warp_pos[li] = w;
+  }
+  std::map<std::pair<uint32_t, std::vector<int>>, int> lay_id;
   std::map<int, int> rot_id, tab_id;
   std::map<std::tuple<int, int, uint32_t>, int> phase_id;  // (factor, first term of the run, layout)
-  auto add_layout = [&](uint32_t R) -> int {
-    auto it = lay_id.find(R);
+  auto add_layout = [&](uint32_t R, const std::vector<int>& wpos) -> int {
+    const auto key = std::make_pair(R, wpos);
+    auto it = lay_id.find(key);
     if (it != lay_id.end()) return it->second;
     if (a.n_lay >= kMaxLayouts) return -1;
     Layout& L = a.lay[a.n_lay];
@@ -160,15 +194,15 @@ bool plan_qsweep(const hs_factors* f, const std::vector<int>& factors, uint32_t 
       L.qoff[i] = (c64 && rp == 0) ? 0u : swz(c64 ? (bit >> 1) : bit);
       L.goff[i] = glob(bit);
     }
-    // Thread positions: three lanes whose chunk bits differ mod 3 first (the
-    // eight threads of a quarter-warp then hit distinct 16-byte bank groups),
-    // then the rest in ascending order.
-    std::vector<int> thr;
+    // Lanes: the thread bits that are not warp bits, three whose chunk bits
+    // differ mod 3 first (the eight threads of a quarter-warp then hit
+    // distinct 16-byte bank groups).
+    std::vector<int> lanes;
     for (int b = 0; b < T; ++b)
-      if (!((R >> b) & 1u)) thr.push_back(b);
+      if (!((R >> b) & 1u) && std::find(wpos.begin(), wpos.end(), b) == wpos.end()) lanes.push_back(b);
     std::vector<int> order, restp;
     bool used_res[3] = {false, false, false};
-    for (int b : thr) {
+    for (int b : lanes) {
       const int res = (c64 ? b - 1 : b) % 3;
       if (order.size() < 3 && res >= 0 && !used_res[res]) {
         used_res[res] = true;
@@ -178,27 +212,48 @@ bool plan_qsweep(const hs_factors* f, const std::vector<int>& factors, uint32_t 
       }
     }
     order.insert(order.end(), restp.begin(), restp.end());
+    order.insert(order.end(), wpos.begin(), wpos.end());
     L.n_thr = int(order.size());
     for (size_t k = 0; k < order.size(); ++k) L.thr[k] = int8_t(order[k]);
-    lay_id[R] = a.n_lay;
+    // The warp's chunk bits W (register and lane bits; chunk bit = local bit
+    // - 1 for complex64, whose bit 0 stays inside a chunk), in address order.
+    std::vector<int> W;
+    for (int b = c64 ? 1 : 0; b < T; ++b)
+      if (std::find(wpos.begin(), wpos.end(), b) == wpos.end()) W.push_back(c64 ? b - 1 : b);
+    if (W.size() < 5) return -1;
+    for (int k = 0; k < 5; ++k) L.wlo[k] = int8_t(W[k]);
+    const int nj = 1 << (B - (c64 ? 1 : 0));
+    if (int(W.size()) != 5 + (B - (c64 ? 1 : 0))) return -1;
+    for (int mm = 0; mm < nj; ++mm) {
+      uint32_t c = 0;
+      for (int k = 0; k < B - (c64 ? 1 : 0); ++k)
+        if ((mm >> k) & 1) c |= 1u << W[5 + k];
+      L.mswz[mm] = swz(c);
+      L.mglob[mm] = glob(c64 ? (c << 1) : c);
+    }
+    lay_id[key] = a.n_lay;
     return a.n_lay++;
   };
   auto reg_coords = [&](uint32_t lmask, uint32_t R) { return pext32(lmask & R, R); };
 
   uint32_t emitted = 0xffffffffu;  // no layout yet
+  int seq_i = -1;
   std::vector<PClass> cls;
   std::vector<PTerm> pts;
   for (size_t i = 0; i < ops.size(); ++i) {
     const HOp& h = ops[i];
     const uint32_t R = lay_of[i];
     if (R != emitted) {
-      const int li = add_layout(R);
+      ++seq_i;
+      const int li = add_layout(R, warp_pos[seq_i]);
       if (li < 0) return fail("too many register layouts");
       if (a.n_ops >= kMaxOps) return fail("too many ops");
       Op& o = a.ops[a.n_ops++];
       o = Op();
       o.type = OP_LAYOUT;
       o.idx = int16_t(li);
+      // bit 0: the warp bits are those of the previous layout (warp-local exchange)
+      o.flags = uint8_t(seq_i > 0 && warp_pos[seq_i] == warp_pos[seq_i - 1] ? 1 : 0);
       emitted = R;
     }
     if (a.n_ops >= kMaxOps) return fail("too many ops");
@@ -211,10 +266,11 @@ bool plan_qsweep(const hs_factors* f, const std::vector<int>& factors, uint32_t 
       if (it != tab_id.end()) {
         ti = it->second;
       } else {
-        if (a.n_tab >= kMaxTab || a.n_vt + G.vt_n > kMaxVt) return fail("value tables exceed the sweep's limits");
+        if (a.n_tab >= kMaxTab || a.n_vt + 1 + G.vt_n > kMaxVt) return fail("value tables exceed the sweep's limits");
         ti = a.n_tab++;
         Tab& t = a.tab[ti];
         t.vt0 = G.vt0;
+        a.n_vt += a.n_vt & 1;  // every table starts on a 16-byte boundary (two complex64 entries)
         t.s0 = a.n_vt;
         t.n = G.vt_n;
         t.sm = G.smask;
@@ -235,6 +291,7 @@ bool plan_qsweep(const hs_factors* f, const std::vector<int>& factors, uint32_t 
         if (a.n_rot >= kMaxRot) return fail("too many rotations");
         ri = a.n_rot++;
         a.rot[ri].cs = key;
+        a.rot[ri].fast = p.z[h.term] == 0 ? 1 : 0;
         rot_id[key] = ri;
       }
       const uint64_t x = p.x[h.term], z = p.z[h.term];
@@ -272,6 +329,7 @@ bool plan_qsweep(const hs_factors* f, const std::vector<int>& factors, uint32_t 
           c.thr = lpart & ~R & tile_all;
           c.t0 = int16_t(pts.size());
           c.c0p = int16_t(c0p);
+          c.mu = int16_t(reg_coords(lpart, R));
           for (int j : by_local[lpart]) pts.push_back(PTerm{G.kind * m + j, uint32_t(p.z[j] & ~uint64_t(local_mask))});
           c.nt = int16_t(int(pts.size()) - c.t0);
           cls.push_back(c);
@@ -299,6 +357,7 @@ bool plan_qsweep(const hs_factors* f, const std::vector<int>& factors, uint32_t 
     a.ops[a.n_ops++] = o;
   }
   if (a.n_ops == 0) return fail("empty sweep");
+  a.n_vt += a.n_vt & 1;
   a.n_cls = int(cls.size());
   a.n_pterm = int(pts.size());
   std::copy(cls.begin(), cls.end(), a.cls);

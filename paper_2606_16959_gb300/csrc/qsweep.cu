@@ -75,14 +75,28 @@ __device__ __forceinline__ void rot_ku(typename C2<R>::T (&x)[NR], R c, R s, boo
   using T2 = typename C2<R>::T;
   constexpr int HB = highest_bit(KU);
   if (fast) {
-    // y = 0, z = 0: coefficient -i sin on every row.
+    // y = 0, z = 0: cos I - i sin X_u = m (u I - i v X_u) with the larger of
+    // |cos|, |sin| factored out as m (applied once per sweep, see the
+    // prologue): here c holds the ratio and s the form, 0: (u, v) = (c, 1)...
+    // i.e. form 0 is I - i tan X (m = cos), form 1 is cot I - i X (m = sin).
+    if (s == R(0)) {
 #pragma unroll
-    for (int k = 0; k < NR; ++k) {
-      if (k & HB) continue;
-      const int k2 = k ^ KU;
-      const T2 b1 = x[k], b2 = x[k2];
-      x[k] = T2{fma(s, b2.y, c * b1.x), fma(-s, b2.x, c * b1.y)};
-      x[k2] = T2{fma(s, b1.y, c * b2.x), fma(-s, b1.x, c * b2.y)};
+      for (int k = 0; k < NR; ++k) {
+        if (k & HB) continue;
+        const int k2 = k ^ KU;
+        const T2 b1 = x[k], b2 = x[k2];
+        x[k] = T2{fma(c, b2.y, b1.x), fma(-c, b2.x, b1.y)};
+        x[k2] = T2{fma(c, b1.y, b2.x), fma(-c, b1.x, b2.y)};
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < NR; ++k) {
+        if (k & HB) continue;
+        const int k2 = k ^ KU;
+        const T2 b1 = x[k], b2 = x[k2];
+        x[k] = T2{fma(c, b1.x, b2.y), fma(c, b1.y, -b2.x)};
+        x[k2] = T2{fma(c, b2.x, b1.y), fma(c, b2.y, -b1.x)};
+      }
     }
     return;
   }
@@ -112,34 +126,52 @@ __device__ __forceinline__ void tab_ku(typename C2<R>::T (&x)[NR], const typenam
                                        uint32_t pt, const uint32_t (&pr)[B]) {
   using T2 = typename C2<R>::T;
   constexpr int HB = KU ? highest_bit(KU) : 0;
-#pragma unroll
-  for (int k = 0; k < NR; ++k) {
-    if (KU && (k & HB)) continue;
+  // Pattern of register row k: pt ^ XOR of pr[i] over the set bits i of k.
+  auto pat = [&](int k) {
     uint32_t p = pt;
 #pragma unroll
     for (int i = 0; i < B; ++i)
       if ((k >> i) & 1) p ^= pr[i];
-    const T2* v = tb + p * uint32_t(ns);
-    if (KU == 0) {
-      const T2 v0 = v[0];
-      x[k] = T2{fma(v0.x, x[k].x, -v0.y * x[k].y), fma(v0.x, x[k].y, v0.y * x[k].x)};
-    } else {
-      const int k2 = k ^ KU;
-      uint32_t p2 = pt;
+    return p;
+  };
+  if constexpr (KU == 0) {
 #pragma unroll
-      for (int i = 0; i < B; ++i)
-        if ((k2 >> i) & 1) p2 ^= pr[i];
-      const T2* w = tb + p2 * uint32_t(ns);
-      const T2 a0 = v[0], a1 = v[1], c0 = w[0], c1 = w[1];
-      const T2 b1 = x[k], b2 = x[k2];
-      T2 r1, r2;
-      r1.x = fma(a0.x, b1.x, fma(-a0.y, b1.y, fma(a1.x, b2.x, -a1.y * b2.y)));
-      r1.y = fma(a0.x, b1.y, fma(a0.y, b1.x, fma(a1.x, b2.y, a1.y * b2.x)));
-      r2.x = fma(c0.x, b2.x, fma(-c0.y, b2.y, fma(c1.x, b1.x, -c1.y * b1.y)));
-      r2.y = fma(c0.x, b2.y, fma(c0.y, b2.x, fma(c1.x, b1.y, c1.y * b1.x)));
-      x[k] = r1;
-      x[k2] = r2;
+    for (int k = 0; k < NR; ++k) {
+      const T2 v0 = tb[pat(k) * uint32_t(ns)];
+      x[k] = T2{fma(v0.x, x[k].x, -v0.y * x[k].y), fma(v0.x, x[k].y, v0.y * x[k].x)};
     }
+  } else {
+  // Two slots: a row's entries (r, r) and (r, r ^ u) sit side by side in the
+  // table, one 2 * sizeof(T2)-byte load.
+#pragma unroll
+  for (int k = 0; k < NR; ++k) {
+    if (k & HB) continue;
+    const int k2 = k ^ KU;
+    T2 a0, a1, c0, c1;
+    if constexpr (sizeof(T2) == 8) {
+      const float4 va = *reinterpret_cast<const float4*>(tb + pat(k) * 2u);
+      const float4 vc = *reinterpret_cast<const float4*>(tb + pat(k2) * 2u);
+      a0 = T2{va.x, va.y};
+      a1 = T2{va.z, va.w};
+      c0 = T2{vc.x, vc.y};
+      c1 = T2{vc.z, vc.w};
+    } else {
+      const T2* va = tb + pat(k) * 2u;
+      const T2* vc = tb + pat(k2) * 2u;
+      a0 = va[0];
+      a1 = va[1];
+      c0 = vc[0];
+      c1 = vc[1];
+    }
+    const T2 b1 = x[k], b2 = x[k2];
+    T2 r1, r2;
+    r1.x = fma(a0.x, b1.x, fma(-a0.y, b1.y, fma(a1.x, b2.x, -a1.y * b2.y)));
+    r1.y = fma(a0.x, b1.y, fma(a0.y, b1.x, fma(a1.x, b2.y, a1.y * b2.x)));
+    r2.x = fma(c0.x, b2.x, fma(-c0.y, b2.y, fma(c1.x, b1.x, -c1.y * b1.y)));
+    r2.y = fma(c0.x, b2.y, fma(c0.y, b2.x, fma(c1.x, b1.y, c1.y * b1.x)));
+    x[k] = r1;
+    x[k2] = r2;
+  }
   }
 }
 
@@ -177,42 +209,95 @@ __device__ __forceinline__ void tab_dispatch(typename C2<R>::T (&x)[NR], int ku,
 }
 
 // ---------------------------------------------------------------------------
-// PHASE: x[k] <- e0 exp(-i pi phi_k) x[k], phi = WHT(E) over the register bits.
+// PHASE: x[k] <- exp(-i phi(r_k)) x[k].  With the tile's fixed bits folded
+// into the per-tile class constants (units of pi) and the thread's bits into
+// E[mu] = sum over the classes with register part mu of +-C_c, the phase of
+// register row k is e0 * prod_mu exp(-i pi E[mu] chi_mu(k)), chi_mu(k) =
+// (-1)^popcount(mu & k).  The factors of mu = 0 and of the single register
+// bits are multiplied out in two small groups of bits (all rows' values from
+// a few products); every other mu present multiplies each row by
+// cos(pi E) -+ i sin(pi E).  One sincospi per present mu, not per row.
 // ---------------------------------------------------------------------------
-template <typename R, int NR>
-__device__ __forceinline__ void phase_apply(typename C2<R>::T (&x)[NR], const Args& a, int pi, const R* Cs,
-                                         typename C2<R>::T e0, uint32_t lt) {
-  using T2 = typename C2<R>::T;
-  const Phase& P = a.ph[pi];
-  R E[NR];
-#pragma unroll
-  for (int mu = 0; mu < NR; ++mu) {
-    R e = R(0);
-    if ((P.mu_mask >> mu) & 1u) {
-      const int c1 = P.cls0 + P.mu_beg[mu + 1];
-      for (int cc = P.cls0 + P.mu_beg[mu]; cc < c1; ++cc) {
-        const R v = Cs[cc];
-        e += parity(a.cls[cc].thr & lt) ? -v : v;
-      }
-    }
-    E[mu] = e;
+template <typename R>
+__device__ __forceinline__ R class_sum(const PClass* cls, const R* Cs, int c0, int c1, uint32_t lt) {
+  R e = R(0);
+  for (int cc = c0; cc < c1; ++cc) {
+    const R v = Cs[cc];
+    e += parity(cls[cc].thr & lt) ? -v : v;
   }
+  return e;
+}
+
+template <typename R, int NR, int B>
+__device__ __forceinline__ void phase_apply(typename C2<R>::T (&x)[NR], const Phase& P, const PClass* cls,
+                                            const R* Cs, typename C2<R>::T e0, uint32_t lt) {
+  using T2 = typename C2<R>::T;
+  constexpr int B1 = (B + 1) / 2, B2 = B - B1;  // the single-bit factors in two groups
+  const int base = P.cls0;
+  // mu = 0 (thread-dependent part of the constant) folded into e0.
+  T2 g0 = e0;
+  {
+    const R e = class_sum<R>(cls, Cs, base + P.mu_beg[0], base + P.mu_beg[1], lt);
+    R sn, cn;
+    sincospi_r(e, &sn, &cn);
+    g0 = T2{fma(g0.x, cn, g0.y * sn), fma(g0.y, cn, -g0.x * sn)};
+  }
+  // Single register bits: (cos, sin) of pi E[2^i].
+  R cb[B], sb[B];
 #pragma unroll
-  for (int h = 1; h < NR; h <<= 1)
+  for (int i = 0; i < B; ++i) {
+    const int mu = 1 << i;
+    const R e = class_sum<R>(cls, Cs, base + P.mu_beg[mu], base + P.mu_beg[mu + 1], lt);
+    sincospi_r(e, &sb[i], &cb[i]);
+  }
+  // Group values, applied one group at a time (fewer live registers):
+  // A[a] = g0 prod_{i < B1} f_i(bit i of a), then Bv[b] = prod_{i < B2}
+  // f_{B1+i}(bit i of b); f_i(0) = cos - i sin, f_i(1) = cos + i sin.
+  {
+    T2 A[1 << B1];
+    A[0] = g0;
 #pragma unroll
-    for (int k = 0; k < NR; ++k)
-      if (!(k & h)) {
-        const R u = E[k], v = E[k | h];
-        E[k] = u + v;
-        E[k | h] = u - v;
+    for (int i = 0; i < B1; ++i)
+#pragma unroll
+      for (int k = 0; k < (1 << i); ++k) {
+        const T2 p = A[k];
+        const R ac = p.x * cb[i], bs = p.y * sb[i], bc = p.y * cb[i], as = p.x * sb[i];
+        A[k] = T2{ac + bs, bc - as};
+        A[k + (1 << i)] = T2{ac - bs, bc + as};
       }
 #pragma unroll
-  for (int k = 0; k < NR; ++k) {
+    for (int k = 0; k < NR; ++k) x[k] = cmul<T2, R>(x[k], A[k & ((1 << B1) - 1)].x, A[k & ((1 << B1) - 1)].y);
+  }
+  {
+    T2 Bv[1 << B2];
+    Bv[0] = T2{R(1), R(0)};
+#pragma unroll
+    for (int i = 0; i < B2; ++i)
+#pragma unroll
+      for (int k = 0; k < (1 << i); ++k) {
+        const T2 p = Bv[k];
+        const R c = cb[B1 + i], sn = sb[B1 + i];
+        const R ac = p.x * c, bs = p.y * sn, bc = p.y * c, as = p.x * sn;
+        Bv[k] = T2{ac + bs, bc - as};
+        Bv[k + (1 << i)] = T2{ac - bs, bc + as};
+      }
+#pragma unroll
+    for (int k = 0; k < NR; ++k) x[k] = cmul<T2, R>(x[k], Bv[k >> B1].x, Bv[k >> B1].y);
+  }
+  // Every other register pattern present (two or more register bits).
+  uint32_t rest = P.mu_mask;
+#pragma unroll
+  for (int i = 0; i <= B; ++i) rest &= ~(i == 0 ? 1u : (1u << (1 << (i - 1))));
+  for (; rest; rest &= rest - 1u) {
+    const int mu = __ffs(rest) - 1;
+    const R e = class_sum<R>(cls, Cs, base + P.mu_beg[mu], base + P.mu_beg[mu + 1], lt);
     R sn, cn;
-    sincospi_r(E[k], &sn, &cn);
-    // e0 * (cn - i sn)
-    const R px = fma(e0.x, cn, e0.y * sn), py = fma(e0.y, cn, -e0.x * sn);
-    x[k] = cmul<T2, R>(x[k], px, py);
+    sincospi_r(e, &sn, &cn);
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+      const R ss = parity(uint32_t(mu) & uint32_t(k)) ? sn : -sn;
+      x[k] = cmul<T2, R>(x[k], cn, ss);
+    }
   }
 }
 
@@ -225,145 +310,266 @@ __global__ void __launch_bounds__(B == 5 ? 256 : 512, B == 5 ? 2 : 1) qsweep_ker
   constexpr int NR = 1 << B;
   constexpr int V = 16 / int(sizeof(T2));  // rows per 16-byte chunk (2 for complex64)
   constexpr int VB = V == 2 ? 1 : 0;       // register bits inside a chunk
-  constexpr int NJ = NR / V;               // chunks per thread
+  constexpr int NJ = NR / V;               // chunks per thread (also chunks of the tile / NT)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int NT = blockDim.x;
+  const int lg_nt = __ffs(NT) - 1;
   const uint32_t tid = threadIdx.x;
   const uint32_t TS = 1u << a.tile_bits;
-  const uint32_t n_chunks = TS / V;
   const uint32_t m0 = a.m0, m1 = a.m1;
   const int sh = a.sh;
 
-  // Shared memory: [tile][rotation (cos, sin)][value tables][e0 per phase][class constants]
+  // Shared memory: [tile][value tables][rotations][e0 per phase][scale]
+  // [class constants][ops][layouts][phase headers][classes][phase terms]
+  const int n_warps = NT >> 5;
+  const int warp = tid >> 5, lane = tid & 31;
   T2* tile = reinterpret_cast<T2*>(smem_raw);
-  T2* rcs = tile + TS;
-  T2* vts = rcs + a.n_rot;
-  T2* e0s = vts + a.n_vt;
-  R* Cs = reinterpret_cast<R*>(e0s + a.n_phase);
+  T2* vts = tile + TS;  // 16-byte aligned (the planner keeps n_vt and every table start even)
+  T2* rcs = vts + a.n_vt;
+  // Per-warp copies of the per-tile phase constants (each warp computes its
+  // own, so no CTA barrier is needed for them).
+  T2* e0s = rcs + a.n_rot + warp * a.n_phase;
+  R* Cs = reinterpret_cast<R*>(rcs + a.n_rot + n_warps * a.n_phase) + warp * a.n_cls;
+  unsigned char* meta = reinterpret_cast<unsigned char*>(
+      reinterpret_cast<R*>(rcs + a.n_rot + n_warps * a.n_phase) + n_warps * a.n_cls);
+  meta += (16 - reinterpret_cast<uintptr_t>(meta) % 16) % 16;
+  Op* sops = reinterpret_cast<Op*>(meta);
+  Layout* slay = reinterpret_cast<Layout*>(sops + a.n_ops);
+  Phase* sph = reinterpret_cast<Phase*>(slay + a.n_lay);
+  PClass* scls = reinterpret_cast<PClass*>(sph + a.n_phase);
+  PTerm* spt = reinterpret_cast<PTerm*>(scls + a.n_cls);
+  // per phase term: theta / pi reduced to [-1, 1]; then the warps' partial
+  // products of the rotation scale (both 16-byte aligned: the structures
+  // before them are 4-byte aligned only)
+  auto align16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) + 15) & ~uintptr_t(15); };
+  R* thpi = reinterpret_cast<R*>(align16(spt + a.n_pterm));
+  double* mpart = reinterpret_cast<double*>(align16(thpi + a.n_pterm));
 
   // Per-CTA tables (written by launches that completed before this grid began).
+  {
+    auto copy_words = [&](void* dst, const void* src, size_t bytes) {
+      const uint32_t* s4 = static_cast<const uint32_t*>(src);
+      uint32_t* d4 = static_cast<uint32_t*>(dst);
+      for (uint32_t w = tid; w < bytes / 4; w += NT) d4[w] = s4[w];
+    };
+    copy_words(sops, a.ops, sizeof(Op) * a.n_ops);
+    copy_words(slay, a.lay, sizeof(Layout) * a.n_lay);
+    copy_words(sph, a.ph, sizeof(Phase) * a.n_phase);
+    copy_words(scls, a.cls, sizeof(PClass) * a.n_cls);
+    copy_words(spt, a.pt, sizeof(PTerm) * a.n_pterm);
+  }
+  // Rotations: (cos, sin) of the term's angle; a rotation on the fast path
+  // (y = 0, z = 0) is kept as the ratio of the smaller to the larger of
+  // |cos|, |sin| and its form (see rot_ku), and the larger factor goes into
+  // the sweep's scale, applied to the rows before they are stored.  Each
+  // thread takes one rotation slot, one op and one phase term (all loads
+  // independent), and the scale's factors are multiplied in FP64 across the
+  // warp and then across the warps' partial products.
   for (int i = tid; i < a.n_rot; i += NT) {
     const double* p = a.cs + 2 * int64_t(a.rot[i].cs);
-    rcs[i] = T2{R(p[0]), R(p[1])};
+    const double c = p[0], sn = p[1];
+    if (a.rot[i].fast)
+      rcs[i] = fabs(sn) <= fabs(c) ? T2{R(sn / c), R(0)} : T2{R(c / sn), R(1)};
+    else
+      rcs[i] = T2{R(c), R(sn)};
+  }
+  {
+    double m = 1.0;
+    for (int oi = tid; oi < a.n_ops; oi += NT) {
+      const Op& op = a.ops[oi];
+      if (op.type == OP_ROT && (op.flags & 1)) {
+        const double* p = a.cs + 2 * int64_t(a.rot[op.idx].cs);
+        const double c = p[0], sn = p[1];
+        m *= fabs(sn) <= fabs(c) ? c : sn;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m *= __shfl_xor_sync(0xffffffffu, m, o);
+    if (lane == 0) mpart[warp] = m;
+  }
+  for (int t = tid; t < a.n_pterm; t += NT) {
+    const double u = a.th[a.pt[t].th] * 0.318309886183790671537767526745;
+    thpi[t] = R(u - 2.0 * rint(0.5 * u));
   }
   for (int t = 0; t < a.n_tab; ++t) {
-    const Tab& tb = a.tab[t];
-    const T2* g = reinterpret_cast<const T2*>(a.vt) + tb.vt0;
-    for (int e = tid; e < tb.n; e += NT) vts[tb.s0 + e] = g[e];
+    const T2* g = reinterpret_cast<const T2*>(a.vt) + a.tab[t].vt0;
+    const int s0 = a.tab[t].s0, n = a.tab[t].n;
+    for (int e = tid; e < n; e += NT) vts[s0 + e] = g[e];
   }
-
+  const int n_ops = a.n_ops, n_cls = a.n_cls;
   const uint32_t u0 = blockIdx.x * uint32_t(a.units_per_cta);
   const uint32_t u1 = min(uint32_t(a.n_units), u0 + uint32_t(a.units_per_cta));
+  __syncthreads();  // the tables are in shared memory
   for (uint32_t unit = u0; unit < u1; ++unit) {
     const uint32_t tile_id = unit & ((1u << a.n_tiles_log2) - 1u);
     const int rhs = int(unit >> a.n_tiles_log2);
     const uint32_t base = deposit_runs(tile_id, a.rest);
     const T2* src = reinterpret_cast<const T2*>(a.src) + int64_t(rhs) * a.N;
     T2* dst = reinterpret_cast<T2*>(a.dst) + int64_t(rhs) * a.N;
-    __syncthreads();  // the previous unit is done with the tile and the per-tile constants
+    if (unit != u0) __syncthreads();  // every warp is done with the previous unit's tile
+    // Per-tile phase constants, in this warp's copy: class sums of +-theta_j
+    // (units of pi, each term reduced mod 2 in FP64 once per CTA) with the
+    // signs of the tile's fixed bits, reduced mod 2 again; a constant class
+    // becomes its phase op's e0.
+    for (int cc = lane; cc < n_cls; cc += 32) {
+      const PClass C = scls[cc];
+      R acc = R(0);
+      for (int t = C.t0; t < C.t0 + C.nt; ++t) {
+        const R v = thpi[t];
+        acc += parity(spt[t].rest & base) ? -v : v;
+      }
+      const R ur = acc - R(2) * rint(R(0.5) * acc);  // the class angle in units of pi, reduced to [-1, 1]
+      if (C.c0p >= 0) {
+        R sn, cn;
+        sincospi_r(ur, &sn, &cn);
+        e0s[C.c0p] = T2{cn, -sn};
+        Cs[cc] = R(0);
+      } else {
+        Cs[cc] = ur;
+      }
+    }
     if (unit == u0) {
       // The state written by the previous launch is visible only after this;
       // the next sweep may start its table loads meanwhile.
       grid_dependency_wait();
       grid_launch_dependents();
     }
-    for (uint32_t c = tid; c < n_chunks; c += NT)
-      cp_async16(tile + swz(c) * V, src + (global_of(c * V, m0, m1, sh) | base));
-    cp_async_commit();
-    // Per-tile phase constants: class sums of +-theta_j in FP64 with the signs
-    // of the tile's fixed bits; a constant class becomes its phase op's e0.
-    for (int cc = tid; cc < a.n_cls; cc += NT) {
-      const PClass& C = a.cls[cc];
-      double acc = 0.0;
-      for (int t = C.t0; t < C.t0 + C.nt; ++t) {
-        const PTerm& pt = a.pt[t];
-        const double th = a.th[pt.th];
-        acc += parity(pt.rest & base) ? -th : th;
-      }
-      if (C.c0p >= 0) {
-        double sn, cn;
-        sincos(acc, &sn, &cn);
-        e0s[C.c0p] = T2{R(cn), R(-sn)};
-      }
-      Cs[cc] = R(acc * 0.318309886183790671537767526745);  // in units of pi
-    }
-    cp_async_wait(0);
 
     T2 x[NR];
-    int cur = -1;
     uint32_t lt = 0, st = 0, gt = 0;  // row of register index 0: local, swizzled chunk, global
-    auto chunk_of = [&](int j) -> uint32_t {
-      const Layout& L = a.lay[cur];
-      uint32_t pc = st;
-#pragma unroll
-      for (int i = 0; i < B - VB; ++i)
-        if ((j >> i) & 1) pc ^= L.qoff[i + VB];
-      return pc;
-    };
-    auto load_rows = [&]() {
-#pragma unroll
-      for (int j = 0; j < NJ; ++j) {
-        const uint32_t pc = chunk_of(j);
-        if constexpr (V == 2) {
-          const float4 w = *reinterpret_cast<const float4*>(tile + pc * 2);
-          x[2 * j] = T2{w.x, w.y};
-          x[2 * j + 1] = T2{w.z, w.w};
-        } else {
-          x[j] = tile[pc];
-        }
-      }
-    };
-    auto store_rows = [&]() {
-#pragma unroll
-      for (int j = 0; j < NJ; ++j) {
-        const uint32_t pc = chunk_of(j);
-        if constexpr (V == 2) {
-          *reinterpret_cast<float4*>(tile + pc * 2) = make_float4(x[2 * j].x, x[2 * j].y, x[2 * j + 1].x,
-                                                                  x[2 * j + 1].y);
-        } else {
-          tile[pc] = x[j];
-        }
-      }
-    };
+    const Layout* cur = nullptr;      // the register layout in effect
 
-    for (int oi = 0; oi < a.n_ops; ++oi) {
-      const Op op = a.ops[oi];
+    for (int oi = 0; oi < n_ops; ++oi) {
+      const Op op = sops[oi];
       if (op.type == OP_LAYOUT) {
-        __syncthreads();  // every thread is done reading the previous layout (or the copies have landed)
-        if (cur >= 0) {
-          store_rows();
-          __syncthreads();
+        // A thread writes back only rows of its own warp (each warp owns the
+        // rows with its warp-bit values), so a warp barrier orders those writes
+        // after the warp's reads of the previous layout; the new layout reads
+        // other warps' rows unless its warp bits are the previous ones (flag).
+        if (cur) {
+          __syncwarp();
+          uint32_t q[B];
+#pragma unroll
+          for (int i = 0; i < B; ++i) q[i] = cur->qoff[i];
+#pragma unroll
+          for (int j = 0; j < NJ; ++j) {
+            uint32_t pc = st;
+#pragma unroll
+            for (int i = 0; i < B - VB; ++i)
+              if ((j >> i) & 1) pc ^= q[i + VB];
+            if constexpr (V == 2) {
+              *reinterpret_cast<float4*>(tile + pc * 2) =
+                  make_float4(x[2 * j].x, x[2 * j].y, x[2 * j + 1].x, x[2 * j + 1].y);
+            } else {
+              tile[pc] = x[j];
+            }
+          }
+          if (op.flags & 1)
+            __syncwarp();
+          else
+            __syncthreads();
         }
-        const Layout& L = a.lay[op.idx];
+        const Layout* L = slay + op.idx;
         uint32_t l = 0;
-        for (int i = 0; i < L.n_thr; ++i) l |= ((tid >> i) & 1u) << L.thr[i];
+        const int n_thr = L->n_thr;
+        for (int i = 0; i < n_thr; ++i) l |= ((tid >> i) & 1u) << L->thr[i];
+        if (!cur) {
+          // First layout: the warp copies its own rows from HBM in address
+          // order (coalesced), then each thread reads its rows; a warp barrier
+          // suffices since no other warp reads them.
+          uint32_t lc = 0;
+#pragma unroll
+          for (int k = 0; k < 5; ++k) lc |= uint32_t((lane >> k) & 1) << L->wlo[k];
+          // the warp's fixed chunk bits: the warp bits of this thread's row
+          uint32_t wb = 0;
+          for (int i = 5; i < n_thr; ++i) wb |= ((tid >> i) & 1u) << L->thr[i];
+          const uint32_t c0 = lc | (wb >> VB);
+          const uint32_t s0 = swz(c0), g0 = global_of(c0 * V, m0, m1, sh) | base;
+#pragma unroll 4
+          for (int mm = 0; mm < NJ; ++mm)
+            cp_async16(tile + (s0 ^ L->mswz[mm]) * V, src + (g0 ^ L->mglob[mm]));
+          cp_async_commit();
+          cp_async_wait(0);
+          __syncwarp();
+        }
+        uint32_t q[B];
+#pragma unroll
+        for (int i = 0; i < B; ++i) q[i] = L->qoff[i];
         lt = l;
         st = swz(l >> VB);
         gt = global_of(l, m0, m1, sh) | base;
-        cur = op.idx;
-        load_rows();
+        cur = L;
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+          uint32_t pc = st;
+#pragma unroll
+          for (int i = 0; i < B - VB; ++i)
+            if ((j >> i) & 1) pc ^= q[i + VB];
+          if constexpr (V == 2) {
+            const float4 w = *reinterpret_cast<const float4*>(tile + pc * 2);
+            x[2 * j] = T2{w.x, w.y};
+            x[2 * j + 1] = T2{w.z, w.w};
+          } else {
+            x[j] = tile[pc];
+          }
+        }
       } else if (op.type == OP_ROT) {
         const T2 cs = rcs[op.idx];
         const bool fast = op.flags & 1;
-        const int sb = fast ? 0 : (parity(op.zrest & base) ^ parity(op.zthr & lt));
-        rot_dispatch<R, NR>(x, op.ku, cs.x, cs.y, fast, (op.flags >> 1) & 3, op.zk, sb);
+        const int sbit = fast ? 0 : (parity(op.zrest & base) ^ parity(op.zthr & lt));
+        rot_dispatch<R, NR>(x, op.ku, cs.x, cs.y, fast, (op.flags >> 1) & 3, op.zk, sbit);
       } else if (op.type == OP_TAB) {
         const Tab& tb = a.tab[op.idx];
-        const Layout& L = a.lay[cur];
+        const uint32_t sm = tb.sm;
+        const int tsh = tb.sh;
         uint32_t pr[B];
 #pragma unroll
-        for (int i = 0; i < B; ++i) pr[i] = pattern_fast(L.goff[i], tb.sm, tb.sh);
-        tab_dispatch<R, NR, B>(x, op.ku, vts + tb.s0, tb.ns, pattern_fast(gt, tb.sm, tb.sh), pr);
+        for (int i = 0; i < B; ++i) pr[i] = pattern_fast(cur->goff[i], sm, tsh);
+        tab_dispatch<R, NR, B>(x, op.ku, vts + tb.s0, tb.ns, pattern_fast(gt, sm, tsh), pr);
       } else {
-        phase_apply<R, NR>(x, a, op.idx, Cs, e0s[op.idx], lt);
+        phase_apply<R, NR, B>(x, sph[op.idx], scls, Cs, e0s[op.idx], lt);
       }
     }
-    __syncthreads();
-    store_rows();
-    __syncthreads();
-    for (uint32_t c = tid; c < n_chunks; c += NT)
-      *reinterpret_cast<uint4*>(dst + (global_of(c * V, m0, m1, sh) | base)) =
-          *reinterpret_cast<const uint4*>(tile + swz(c) * V);
+    __syncwarp();  // the warp's reads of the last layout are done (it writes back its own rows)
+    {
+      double md = 1.0;
+      for (int w = 0; w < n_warps; ++w) md *= mpart[w];
+      const R m = R(md);
+#pragma unroll
+      for (int k = 0; k < NR; ++k) x[k] = T2{x[k].x * m, x[k].y * m};
+    }
+    uint32_t q[B];
+#pragma unroll
+    for (int i = 0; i < B; ++i) q[i] = cur->qoff[i];
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+      uint32_t pc = st;
+#pragma unroll
+      for (int i = 0; i < B - VB; ++i)
+        if ((j >> i) & 1) pc ^= q[i + VB];
+      if constexpr (V == 2) {
+        *reinterpret_cast<float4*>(tile + pc * 2) = make_float4(x[2 * j].x, x[2 * j].y, x[2 * j + 1].x, x[2 * j + 1].y);
+      } else {
+        tile[pc] = x[j];
+      }
+    }
+    __syncwarp();
+    {
+      // The warp's rows back to HBM in address order (coalesced).
+      const Layout* L = cur;
+      const int n_thr = L->n_thr;
+      uint32_t lc = 0;
+#pragma unroll
+      for (int k = 0; k < 5; ++k) lc |= uint32_t((lane >> k) & 1) << L->wlo[k];
+      uint32_t wb = 0;
+      for (int i = 5; i < n_thr; ++i) wb |= ((tid >> i) & 1u) << L->thr[i];
+      const uint32_t c0 = lc | (wb >> VB);
+      const uint32_t s0 = swz(c0), g0 = global_of(c0 * V, m0, m1, sh) | base;
+#pragma unroll 4
+      for (int mm = 0; mm < NJ; ++mm)
+        *reinterpret_cast<uint4*>(dst + (g0 ^ L->mglob[mm])) =
+            *reinterpret_cast<const uint4*>(tile + (s0 ^ L->mswz[mm]) * V);
+    }
   }
 }
 
@@ -393,9 +599,13 @@ cudaError_t prepare_qsweep() {
   return cudaSuccess;
 }
 
-size_t qsweep_smem_bytes(const Args& a, hs_dtype dt) {
+size_t qsweep_smem_bytes(const Args& a, hs_dtype dt, int B) {
   const size_t e = elem_bytes(dt), r = e / 2;
-  return ((size_t(1) << a.tile_bits) + a.n_rot + a.n_vt + a.n_phase) * e + size_t(a.n_cls) * r;
+  const size_t warps = size_t(1) << (a.tile_bits - B - 5);
+  const size_t head =
+      ((size_t(1) << a.tile_bits) + a.n_rot + a.n_vt + warps * a.n_phase) * e + warps * size_t(a.n_cls) * r;
+  return (head + 15) / 16 * 16 + sizeof(Op) * a.n_ops + sizeof(Layout) * a.n_lay + sizeof(Phase) * a.n_phase +
+         sizeof(PClass) * a.n_cls + sizeof(PTerm) * a.n_pterm + 16 + r * a.n_pterm + 16 + 8 * warps;
 }
 
 cudaError_t launch_qsweep(const hs_factors* f, Args& a, const void* src, void* dst, int n_rhs, int B, bool pdl,
@@ -413,7 +623,7 @@ cudaError_t launch_qsweep(const hs_factors* f, Args& a, const void* src, void* d
   a.n_tiles_log2 = p.n_qubits - a.tile_bits;
   a.n_units = (1 << a.n_tiles_log2) * n_rhs;
   if (a.units_per_cta < 1) a.units_per_cta = 1;
-  const size_t smem = qsweep_smem_bytes(a, f->dtype);
+  const size_t smem = qsweep_smem_bytes(a, f->dtype, B);
   if (smem > kSweepSmemMax) return cudaErrorInvalidValue;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(unsigned((a.n_units + a.units_per_cta - 1) / a.units_per_cta), 1u, 1u);

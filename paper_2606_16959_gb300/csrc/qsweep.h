@@ -61,10 +61,20 @@ struct Layout {
   uint32_t goff[kMaxB];  // per register bit: global row offset (global image of the local bit)
   int8_t thr[28];      // local positions of the thread-index bits, thread bit 0 first
   int32_t n_thr;
+  // A warp's rows (fixed warp bits, all register and lane bits) copied in
+  // address order: chunk e = lane + 32 m of the warp's set lies at chunk
+  // pdep(lane, wlo) ^ pdep(32 m, W) ^ (the warp's fixed chunk bits), W the
+  // warp's chunk bits; mswz / mglob hold the swizzled chunk and global row
+  // of pdep(32 m, W).
+  int8_t wlo[5];       // the five lowest chunk bits of W
+  int8_t pad[3];
+  uint32_t mswz[1 << (kMaxB - 1)];
+  uint32_t mglob[1 << (kMaxB - 1)];
 };
 
 struct Rot {
-  int32_t cs;  // index of the term's (cos, sin) pair in the factor set's angle table
+  int32_t cs;    // index of the term's (cos, sin) pair in the factor set's angle table
+  int32_t fast;  // y = 0 and z = 0: kept as a ratio with its larger factor in the sweep's scale
 };
 
 struct Tab {
@@ -88,7 +98,7 @@ struct PClass {
   uint32_t thr;   // local part on thread positions (local-index mask)
   int16_t t0, nt; // terms [t0, t0 + nt) of the phase term list
   int16_t c0p;    // the phase op whose constant class (empty local part) this is, else -1
-  int16_t pad;
+  int16_t mu;     // register part (register coordinates)
 };
 
 struct PTerm {
@@ -134,7 +144,7 @@ __host__ __device__ __forceinline__ uint32_t swz(uint32_t c) {
 bool plan_qsweep(const hs_factors* f, const std::vector<int>& factors, uint32_t local_mask, int T, int B,
                  Args& a, std::string* why);
 
-size_t qsweep_smem_bytes(const Args& a, hs_dtype dt);
+size_t qsweep_smem_bytes(const Args& a, hs_dtype dt, int B);
 cudaError_t launch_qsweep(const hs_factors* f, Args& a, const void* src, void* dst, int n_rhs, int B,
                           bool pdl, cudaStream_t s);
 cudaError_t prepare_qsweep();
