@@ -430,6 +430,24 @@ def batch_jobs(args, dtype="c64"):
     return jobs, desc
 
 
+def batch_options(jobs, views, args, dtype):
+    """Batch options from the batch autotuner (kept in the autotune cache so that
+    a later run, e.g. under a profiler, replays the same configuration)."""
+    from paper_2606_16959_gb300 import hs
+    import torch
+    if not args.autotune:
+        return {}
+    key = f"batch{len(jobs)}:{dtype}:{torch.cuda.get_device_name()}"
+    cache = load_tune_cache()
+    if key not in cache:
+        facs = [hs.hs_build_factors(j.ham.labels, j.ham.coeffs, j.t, j.n_steps, j.budget, dtype) for j in jobs]
+        cache[key] = hs.hs_batch_autotune([(f, v, j.n_steps) for f, v, j in zip(facs, views, jobs)])
+        for f in facs:
+            f.close()
+        save_tune_cache(cache)
+    return cache[key]
+
+
 def time_batch(jobs, args, world, rank, dtype):
     """Device-timed batch steps: build every job's factors, plan the batch, one
     batched launch sequence, and each job's FP64 norm; states resident."""
@@ -446,11 +464,12 @@ def time_batch(jobs, args, world, rank, dtype):
     outs = torch.zeros(len(jobs), 4, dtype=torch.float64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     E = torch.cuda.Event
+    bopts = batch_options(jobs, views, args, dtype)
 
     def step():
         work.copy_(init)
         facs = [hs.hs_build_factors(j.ham.labels, j.ham.coeffs, j.t, j.n_steps, j.budget, dtype) for j in jobs]
-        b = hs.hs_batch_create([(f, v, j.n_steps) for f, v, j in zip(facs, views, jobs)], use_graph=False)
+        b = hs.hs_batch_create([(f, v, j.n_steps) for f, v, j in zip(facs, views, jobs)], use_graph=False, **bopts)
         e0, e1 = E(enable_timing=True), E(enable_timing=True)
         e0.record()
         hs.hs_batch_launch(b)
@@ -492,10 +511,11 @@ def time_batch(jobs, args, world, rank, dtype):
     total_ms = max_over_ranks(sum(step_ms), world)
     return dict(units=info[2], levels=info[0], ctas=info[1], separate=info[3], step_ms=step_ms, launch_ms=launch_ms,
                 total_ms=total_ms, alg_bytes=alg, clocks=clocks, max_norm_drift=float(np.max(np.abs(norms - 1.0))),
-                launches=hs.hs_kernel_launches() - l0)
+                launches=hs.hs_kernel_launches() - l0, bopts=bopts,
+                kernel="batch_qsweep_kernel" if bopts.get("method") == 3 else "batch_level_kernel")
 
 
-def time_batch_e2e(jobs, args, dtype):
+def time_batch_e2e(jobs, args, dtype, bopts):
     import torch
     from paper_2606_16959_gb300 import hs
     dev = torch.device("cuda", torch.cuda.current_device())
@@ -515,7 +535,7 @@ def time_batch_e2e(jobs, args, dtype):
         s0.record()
         work.copy_(host_in, non_blocking=True)
         facs = [hs.hs_build_factors(j.ham.labels, j.ham.coeffs, j.t, j.n_steps, j.budget, dtype) for j in jobs]
-        b = hs.hs_batch_create([(f, v, j.n_steps) for f, v, j in zip(facs, views, jobs)], use_graph=False)
+        b = hs.hs_batch_create([(f, v, j.n_steps) for f, v, j in zip(facs, views, jobs)], use_graph=False, **bopts)
         hs.hs_batch_launch(b)
         for k, v in enumerate(views):
             hs.hs_inner_device(v, v, outs[k])
@@ -764,20 +784,20 @@ def run_batch(args, rank, world):
     res = time_batch(jobs, args, world, rank, dtype)
     K = args.steps
     value = res["units"] * K * world / (res["total_ms"] / 1000.0)
-    e2e = time_batch_e2e(jobs, args, dtype)
+    e2e = time_batch_e2e(jobs, args, dtype, res["bopts"])
     hbm, peak_kind = peaks()
     launch_s = statistics.mean(res["launch_ms"]) / 1000.0
     per_launch_bytes = res["alg_bytes"] / max(1, res["levels"])
     achieved = res["alg_bytes"] / launch_s / 1e9
     traffic = profiled_traffic("batch256", res.get("kernel", "batch_level_kernel")) if args.batch_jobs == 256 else None
     cfg = {"workload": "batch256", "description": desc, "n_jobs": len(jobs), "levels_per_step": res["levels"],
-           "ctas_per_step": res["ctas"], "separate_jobs": res["separate"], "tile_bits": 10, "smem_kb_per_cta": 24,
+           "ctas_per_step": res["ctas"], "separate_jobs": res["separate"], "batch_options": res["bopts"],
            "l2": "flushed (512 MiB write) before every timed step"}
     line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": K, "warmup": args.warmup,
             "ms_per_step": res["total_ms"] / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": dtype, "data": "synthetic", "config": cfg,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                         "traffic": traffic, "peak_source": peak_kind, "kernel": "batch_level_kernel",
+                         "traffic": traffic, "peak_source": peak_kind, "kernel": res["kernel"],
                          "algorithmic_bytes_per_launch": per_launch_bytes,
                          "avg_launch_us": launch_s * 1e6 / max(1, res["levels"]),
                          **dram_fields(traffic, launch_s / max(1, res["levels"]), hbm)},

@@ -261,6 +261,12 @@ typedef struct {
   int no_tables; /* as in hs_evolve_opts: 1 stages every factor from its diagonals */
   int tiles_per_cta; /* tiles one CTA evolves back to back, loading its sweep's tables once
                         (0 = library choice, at most 64) */
+  int method;        /* HS_METHOD_REG: register-blocked sweeps (as hs_evolve_ex's REG; tile_bits
+                        0 = 13 for complex64, 12 for complex128, at most 13; a job below tile_bits
+                        qubits gets tiles of its own size, one below reg_bits + 5 qubits or whose
+                        sweeps cannot be expressed as register ops runs with its own launches);
+                        any other value: the staged tile sweeps described above */
+  int reg_bits;      /* REG: rows per thread 2^reg_bits, 4 or 5 (0 = 5 for complex64, 4 for complex128) */
 } hs_batch_opts;
 
 /* Plan a batch (host only; device tables are uploaded on the first launch's
@@ -284,6 +290,16 @@ int hs_batch_info(const hs_batch* b, int* n_levels, int64_t* n_ctas, int64_t* n_
 
 /* Free a batch (NULL is a no-op).  Synchronises the device first. */
 void hs_batch_free(hs_batch* b);
+
+/* Measure candidate batch options (staged sweeps over several tile sizes,
+ * shared-memory budgets and tiles per CTA; register-blocked sweeps over tile
+ * sizes, contiguous low bits and register widths) for these jobs, each timed
+ * on a scratch copy of every job's states (the jobs' own states are not
+ * modified), and return the fastest in *best (use_graph as given in
+ * best->use_graph on entry, 0 if best holds garbage).  Allocates one scratch
+ * buffer of all the jobs' states, synchronises cuda_stream; do not call
+ * during stream capture.  Errors as hs_batch_create, HS_ENOMEM, HS_ECUDA. */
+int hs_batch_autotune(const hs_batch_job* jobs, size_t n_jobs, void* cuda_stream, hs_batch_opts* best);
 
 /* One call over job arrays (the batched form of hs_evolve): job k evolves
  * psi[k] (n_rhs[k] states, device buffer of the factors' dtype) in place by

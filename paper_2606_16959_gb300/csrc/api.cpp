@@ -120,7 +120,8 @@ bool has_plain(const std::vector<hs::Sweep>& sw) {
 // distinct sweep is planned once; a sweep that cannot be expressed as register
 // ops is replaced by plain launches of its factors.
 void plan_reg(const hs_factors* f, std::vector<hs::Sweep>& sw, int tile_bits, int reg_bits, QPlans& qp) {
-  std::map<std::pair<uint32_t, std::vector<int>>, std::shared_ptr<hs::q::Args>> memo;
+  using Pieces = std::vector<std::pair<std::vector<int>, std::shared_ptr<hs::q::Args>>>;
+  std::map<std::pair<uint32_t, std::vector<int>>, std::pair<bool, Pieces>> memo;
   std::vector<hs::Sweep> out;
   QPlans plans;
   for (hs::Sweep& w : sw) {
@@ -131,18 +132,21 @@ void plan_reg(const hs_factors* f, std::vector<hs::Sweep>& sw, int tile_bits, in
     }
     const auto key = std::make_pair(w.local_mask, w.factors);
     auto it = memo.find(key);
-    std::shared_ptr<hs::q::Args> a;
-    if (it != memo.end()) {
-      a = it->second;
-    } else {
-      a = std::make_shared<hs::q::Args>();
+    if (it == memo.end()) {
+      Pieces pieces;
       std::string why;
-      if (!hs::q::plan_qsweep(f, w.factors, w.local_mask, tile_bits, reg_bits, *a, &why)) a = nullptr;
-      memo[key] = a;
+      const bool ok = hs::q::plan_qsweep_runs(f, w.factors, w.local_mask, tile_bits, reg_bits, pieces, &why);
+      it = memo.emplace(key, std::make_pair(ok, std::move(pieces))).first;
     }
-    if (a) {
-      out.push_back(std::move(w));
-      plans.push_back(a);
+    if (it->second.first) {
+      for (const auto& pc : it->second.second) {
+        hs::Sweep s2;
+        s2.fused = true;
+        s2.local_mask = w.local_mask;
+        s2.factors = pc.first;
+        out.push_back(std::move(s2));
+        plans.push_back(pc.second);
+      }
     } else {
       for (int g : w.factors) {
         hs::Sweep pl;
@@ -450,6 +454,7 @@ int build_impl(const uint64_t* x, const uint64_t* z, const double* coeffs, const
   const size_t o_fv = put(nullptr, 8);                   // drive value of hs_factors_set_drive
   const size_t o_cs = put(nullptr, m * 16 * hk.size());  // (cos, sin) per term and angle kind, written on the device
   const size_t o_th = put(nullptr, m * 8 * hk.size());   // the angles themselves
+  const size_t o_rq = put(nullptr, m * 32 * hk.size());  // register-sweep record per term and angle kind
   unsigned char* d_blob = nullptr;
   if ((rc = guard(hs::pool_malloc((void**)&d_blob, blob.size(), s), "cudaMallocAsync(tables)"))) {
     release(f.release(), s);
@@ -481,6 +486,7 @@ int build_impl(const uint64_t* x, const uint64_t* z, const double* coeffs, const
   bi.h = reinterpret_cast<const double*>(d_blob + o_h);
   bi.cs = reinterpret_cast<double*>(d_blob + o_cs);
   bi.th = reinterpret_cast<double*>(d_blob + o_th);
+  bi.rq = reinterpret_cast<double*>(d_blob + o_rq);
   bi.fval = reinterpret_cast<double*>(d_blob + o_fv);
   bi.n_kinds = int(hk.size());
   bi.dep_all = reinterpret_cast<const int*>(d_blob + o_da);

@@ -22,6 +22,7 @@
 
 #include "counters.h"
 #include "hs_internal.h"
+#include "qsweep.h"
 #include "sweep_core.cuh"
 
 namespace hs {
@@ -192,6 +193,21 @@ struct hs_batch {
   int64_t updates = 0;
   int64_t ctas = 0;
   int64_t n_batched = 0;
+  // Register-blocked batches: one descriptor per distinct sweep of every
+  // batched job, and per tile size a sequence of levels over them.
+  bool reg = false;
+  int reg_bits = 0;
+  struct QGroup {
+    int tile_bits = 0;
+    size_t smem = 0, prefix_smem = 0;
+    std::vector<Level> levels;
+    std::vector<int> lvl_desc, lvl_prefix;
+    int* d_lvl_desc = nullptr;
+    int* d_lvl_prefix = nullptr;
+  };
+  std::vector<hs::q::Args> qdescs;
+  hs::q::Args* d_qdescs = nullptr;
+  std::vector<QGroup> qgroups;
 };
 
 namespace {
@@ -199,9 +215,13 @@ namespace {
 void batch_release(hs_batch* b, cudaStream_t s) {
   if (!b) return;
   if (b->graph) cudaGraphExecDestroy(b->graph);
-  void* bufs[] = {b->d_jobs, b->d_sweeps, b->d_facs, b->d_lvl_sweep, b->d_lvl_prefix};
+  void* bufs[] = {b->d_jobs, b->d_sweeps, b->d_facs, b->d_lvl_sweep, b->d_lvl_prefix, b->d_qdescs};
   for (void* p : bufs)
     if (p) cudaFreeAsync(p, s);
+  for (auto& g : b->qgroups) {
+    if (g.d_lvl_desc) cudaFreeAsync(g.d_lvl_desc, s);
+    if (g.d_lvl_prefix) cudaFreeAsync(g.d_lvl_prefix, s);
+  }
   delete b;
 }
 
@@ -216,6 +236,17 @@ cudaError_t upload(T** dptr, const std::vector<T>& v, cudaStream_t s) {
 int upload_tables(hs_batch* b, cudaStream_t s) {
   if (b->uploaded) return HS_OK;
   cudaError_t e;
+  if (b->reg) {
+    e = upload(&b->d_qdescs, b->qdescs, s);
+    for (auto& g : b->qgroups)
+      if (e == cudaSuccess && (e = upload(&g.d_lvl_desc, g.lvl_desc, s)) == cudaSuccess)
+        e = upload(&g.d_lvl_prefix, g.lvl_prefix, s);
+    if (e != cudaSuccess)
+      return hs::report_error(e == cudaErrorMemoryAllocation ? HS_ENOMEM : HS_ECUDA,
+                              std::string("batch tables: ") + cudaGetErrorString(e));
+    b->uploaded = true;
+    return HS_OK;
+  }
   if ((e = upload(&b->d_jobs, b->hjobs, s)) != cudaSuccess || (e = upload(&b->d_sweeps, b->hsweeps, s)) != cudaSuccess ||
       (e = upload(&b->d_facs, b->hfacs, s)) != cudaSuccess || (e = upload(&b->d_lvl_sweep, b->hlvl_sweep, s)) != cudaSuccess ||
       (e = upload(&b->d_lvl_prefix, b->hlvl_prefix, s)) != cudaSuccess)
@@ -230,6 +261,16 @@ int enqueue_batch(hs_batch* b, cudaStream_t s) {
     hs_evolve_opts o{HS_METHOD_AUTO, 0, 0, 0, 0, 0, 0, 0};
     int rc = hs_evolve_ex(j.f, j.psi, j.n_rhs, j.n_steps, &o, s);
     if (rc != HS_OK) return rc;
+  }
+  if (b->reg) {
+    for (const hs_batch::QGroup& g : b->qgroups)
+      for (const hs_batch::Level& L : g.levels) {
+        hs::q::LevelArgs a{b->d_qdescs, g.d_lvl_desc, g.d_lvl_prefix, L.off, L.count, uint32_t(g.prefix_smem)};
+        cudaError_t e = hs::q::launch_qlevel(b->dtype, b->reg_bits, g.tile_bits, a, L.ctas, g.smem, s);
+        if (e != cudaSuccess)
+          return hs::report_error(HS_ECUDA, std::string("batch level launch: ") + cudaGetErrorString(e));
+      }
+    return HS_OK;
   }
   LevelFn fn = b->dtype == HS_C64 ? level_fn<float>(b->rows) : level_fn<double>(b->rows);
   if (!fn) return hs::report_error(HS_EINVAL, "internal: no batch kernel for this tile size");
@@ -255,12 +296,124 @@ int enqueue_batch(hs_batch* b, cudaStream_t s) {
 
 }  // namespace
 
+namespace {
+
+// Plan a batch of register-blocked sweeps: every job is scheduled as
+// hs_evolve_ex's REG method schedules it (same sweeps, same ops, so results
+// are bitwise those of evolving each job alone with the same options), with
+// tiles of min(tile_bits, n) qubits; jobs are grouped by tile size, and level
+// k of a group runs the k-th sweep of each of its jobs.
+int create_reg_batch(const hs_batch_job* jobs, size_t n_jobs, const hs_batch_opts& o, hs_batch** out) {
+  std::unique_ptr<hs_batch> b(new hs_batch());
+  b->reg = true;
+  b->dtype = jobs[0].factors ? jobs[0].factors->dtype : HS_C64;
+  const hs_dtype dt = b->dtype;
+  const bool c64 = dt == HS_C64;
+  const int B = o.reg_bits > 0 ? o.reg_bits : (c64 ? 5 : 4);
+  if (B != 4 && B != 5) return hs::report_error(HS_EINVAL, "reg_bits must be 0, 4 or 5");
+  if (!c64 && B != 4) return hs::report_error(HS_EINVAL, "complex128 register sweeps use reg_bits 4");
+  const int T = o.tile_bits > 0 ? o.tile_bits : (c64 ? 13 : 12);
+  if (T < B + 5 || T > 13) return hs::report_error(HS_EINVAL, "register batches take tile_bits reg_bits + 5 .. 13");
+  b->reg_bits = B;
+  b->tile_bits = T;
+  b->low_bits = o.low_bits > 0 ? o.low_bits : (c64 ? 2 : 1);
+  b->use_graph = o.use_graph != 0;
+  struct GJob { std::vector<int> descs; int64_t units; };
+  std::map<int, std::vector<GJob>> by_tile;
+  for (size_t j = 0; j < n_jobs; ++j) {
+    const hs_batch_job& J = jobs[j];
+    if (!J.factors || !J.psi) return hs::report_error(HS_EINVAL, "job " + std::to_string(j) + ": null factors or psi");
+    if (J.factors->dtype != dt) return hs::report_error(HS_EDTYPE, "jobs differ in dtype");
+    if (J.n_rhs < 1 || J.n_steps < 0) return hs::report_error(HS_EINVAL, "job " + std::to_string(j) + ": bad n_rhs/n_steps");
+    if (reinterpret_cast<uintptr_t>(J.psi) % 16) return hs::report_error(HS_EINVAL, "psi must be 16-byte aligned");
+    const hs::Plan& p = J.factors->plan;
+    b->updates += int64_t(J.n_steps) * int64_t(p.step_seq.size()) * p.N * J.n_rhs;
+    if (J.n_steps == 0) continue;
+    const int n = p.n_qubits;
+    const int Tj = std::min(T, n);
+    bool ok = n >= B + 5;
+    std::vector<hs::Sweep> sw;
+    if (ok) sw = hs::plan_sweeps(p, J.n_steps, Tj, b->low_bits, true);
+    for (const hs::Sweep& w : sw) ok = ok && w.fused;
+    const size_t keep = b->qdescs.size();
+    GJob gj;
+    std::map<std::pair<uint32_t, std::vector<int>>, std::vector<int>> memo;  // sweep -> its pieces' descriptors
+    for (size_t k = 0; ok && k < sw.size(); ++k) {
+      const auto key = std::make_pair(sw[k].local_mask, sw[k].factors);
+      auto it = memo.find(key);
+      if (it != memo.end()) {
+        gj.descs.insert(gj.descs.end(), it->second.begin(), it->second.end());
+        continue;
+      }
+      std::vector<std::pair<std::vector<int>, std::shared_ptr<hs::q::Args>>> pieces;
+      std::string why;
+      if (!hs::q::plan_qsweep_runs(J.factors, sw[k].factors, sw[k].local_mask, Tj, B, pieces, &why)) {
+        ok = false;
+        break;
+      }
+      std::vector<int> ids;
+      for (auto& pc : pieces) {
+        hs::q::Args& a = *pc.second;
+        hs::q::fill_job(J.factors, a, J.psi, J.n_rhs);
+        a.units_per_cta = 1;
+        ids.push_back(int(b->qdescs.size()));
+        b->qdescs.push_back(a);
+      }
+      gj.descs.insert(gj.descs.end(), ids.begin(), ids.end());
+      memo[key] = std::move(ids);
+    }
+    if (!ok) {
+      b->qdescs.resize(keep);
+      b->separate.push_back(hs_batch::Sep{J.factors, J.psi, J.n_rhs, J.n_steps});
+      continue;
+    }
+    gj.units = int64_t(1) << (n - Tj);
+    gj.units *= J.n_rhs;
+    by_tile[Tj].push_back(std::move(gj));
+    ++b->n_batched;
+  }
+  for (auto& kv : by_tile) {
+    hs_batch::QGroup g;
+    g.tile_bits = kv.first;
+    size_t smem = 0, max_levels = 0;
+    for (const GJob& gj : kv.second) {
+      max_levels = std::max(max_levels, gj.descs.size());
+      for (int d : gj.descs) smem = std::max(smem, hs::q::qsweep_smem_bytes(b->qdescs[d], dt, B));
+    }
+    int max_count = 0;
+    for (size_t k = 0; k < max_levels; ++k) {
+      hs_batch::Level L{int(g.lvl_desc.size()), 0, 0};
+      for (const GJob& gj : kv.second) {
+        if (k >= gj.descs.size()) continue;
+        g.lvl_desc.push_back(gj.descs[k]);
+        g.lvl_prefix.push_back(int(L.ctas));
+        L.ctas += gj.units;
+        ++L.count;
+      }
+      if (L.ctas >= (int64_t(1) << 31)) return hs::report_error(HS_EINVAL, "batch level exceeds 2^31 CTAs");
+      max_count = std::max(max_count, L.count);
+      b->ctas += L.ctas;
+      g.levels.push_back(L);
+    }
+    g.prefix_smem = (smem + 15) / 16 * 16;
+    g.smem = g.prefix_smem + size_t(max_count) * sizeof(int);
+    if (g.smem > hs::kSweepSmemMax) return hs::report_error(HS_EINVAL, "batch needs more shared memory than a CTA has");
+    b->levels.insert(b->levels.end(), g.levels.begin(), g.levels.end());  // for hs_batch_info
+    b->qgroups.push_back(std::move(g));
+  }
+  *out = b.release();
+  return HS_OK;
+}
+
+}  // namespace
+
 extern "C" int hs_batch_create(const hs_batch_job* jobs, size_t n_jobs, const hs_batch_opts* opts, hs_batch** out) {
   if (!out) return hs::report_error(HS_EINVAL, "out is NULL");
   *out = nullptr;
   if (!jobs || n_jobs == 0) return hs::report_error(HS_EINVAL, "no jobs");
-  hs_batch_opts o{0, 0, 1, 0, 0, 0};
+  hs_batch_opts o{0, 0, 1, 0, 0, 0, 0, 0};
   if (opts) o = *opts;
+  if (o.method == HS_METHOD_REG) return create_reg_batch(jobs, n_jobs, o, out);
   std::unique_ptr<hs_batch> b(new hs_batch());
   b->dtype = jobs[0].factors ? jobs[0].factors->dtype : HS_C64;
   int min_n = 64;
@@ -419,9 +572,13 @@ extern "C" int hs_batch_launch(hs_batch* b, void* cuda_stream) {
   cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
   cudaError_t e = hs::prepare_kernels();
   if (e != cudaSuccess) return hs::report_error(HS_ECUDA, std::string("kernel attributes: ") + cudaGetErrorString(e));
+  if (b->reg) {
+    e = hs::q::prepare_qsweep();
+    if (e != cudaSuccess) return hs::report_error(HS_ECUDA, std::string("kernel attributes: ") + cudaGetErrorString(e));
+  }
   static std::mutex attr_mu;
   static bool attr_done[2][9] = {};
-  {
+  if (!b->reg) {
     std::lock_guard<std::mutex> lk(attr_mu);
     bool& done = attr_done[b->dtype == HS_C64 ? 0 : 1][b->rows];
     if (!done) {
@@ -487,7 +644,7 @@ extern "C" int hs_evolve_batch(const hs_factors* const* f, void* const* psi, con
   if (!f || !psi || !n_rhs || !n_steps || n_jobs == 0) return hs::report_error(HS_EINVAL, "null job arrays or no jobs");
   std::vector<hs_batch_job> jobs(n_jobs);
   for (size_t k = 0; k < n_jobs; ++k) jobs[k] = hs_batch_job{f[k], psi[k], n_rhs[k], n_steps[k]};
-  hs_batch_opts o{0, 0, 0, 0, 0, 0};
+  hs_batch_opts o{0, 0, 0, 0, 0, 0, 0, 0};
   hs_batch* b = nullptr;
   int rc = hs_batch_create(jobs.data(), n_jobs, &o, &b);
   if (rc != HS_OK) return rc;

@@ -334,8 +334,12 @@ __global__ void __launch_bounds__(256) value_table_kernel(BuildArgs a, const uin
 // cs[2 (k n + j) + {0, 1}] = (cos, sin)(c_j * h[k]) for kind k, with c_j =
 // coeff[j], or coeff[j] + f coeff1[j] (f = *fval, the product rounded before
 // the sum, no fused multiply-add) for a time-dependent set.
+// rq[4 (k n + j) + {0..3}]: what a register sweep needs of the rotation: the
+// ratio of the smaller to the larger of |cos|, |sin| (tan or cot), its form
+// (0: tan, 1: cot), the larger factor (cos or sin, signed) and theta / pi
+// reduced to [-1, 1].
 __global__ void sincos_kernel(const double* coeff, const double* coeff1, const double* fval, const double* h,
-                              int n_kinds, double* cs, double* th, int n) {
+                              int n_kinds, double* cs, double* th, double* rq, int n) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e < n * n_kinds) {
     const int k = e / n, j = e - k * n;
@@ -347,6 +351,12 @@ __global__ void sincos_kernel(const double* coeff, const double* coeff1, const d
     sincos(theta, &s, &co);
     cs[2 * e] = co;
     cs[2 * e + 1] = s;
+    const bool tan_form = fabs(s) <= fabs(co);
+    rq[4 * e] = tan_form ? s / co : co / s;
+    rq[4 * e + 1] = tan_form ? 0.0 : 1.0;
+    rq[4 * e + 2] = tan_form ? co : s;
+    const double u = theta * 0.318309886183790671537767526745;
+    rq[4 * e + 3] = u - 2.0 * rint(0.5 * u);
   }
 }
 
@@ -363,7 +373,7 @@ cudaError_t launch_sincos(const hs_factors* f, const double* d_fval, cudaStream_
   const hs_build_inputs& b = f->bin;
   const int n = int(f->plan.x.size());
   sincos_kernel<<<(n * b.n_kinds + 127) / 128, 128, 0, s>>>(b.coeff, b.coeff1, d_fval, b.h, b.n_kinds, b.cs, b.th,
-                                                            n);
+                                                            b.rq, n);
   note_launches();
   return cudaGetLastError();
 }

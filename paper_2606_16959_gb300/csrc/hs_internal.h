@@ -145,6 +145,7 @@ struct hs_build_inputs {
   const double* h = nullptr;       // angle multiple of each kind
   double* cs = nullptr;            // (cos, sin) per kind and term, written on the device
   double* th = nullptr;            // the angle per kind and term, written on the device
+  double* rq = nullptr;            // register-sweep record per kind and term (4 doubles), written on the device
   double* fval = nullptr;          // one drive value (hs_factors_set_drive)
   int n_kinds = 1;
   // Groups holding a term with b_j != 0: all of them, those without a value

@@ -281,8 +281,10 @@ bool plan_qsweep(const hs_factors* f, const std::vector<int>& factors, uint32_t 
       }
       o.idx = int16_t(ti);
       o.ku = uint8_t(reg_coords(h.need, R));
-    } else if (h.type == OP_ROT) {
-      const int key = G.kind * m + h.term;
+    } else if (h.type == OP_ROT || (h.type == OP_PHASE && h.terms.size() == 1)) {
+      // (a run of one diagonal term is a diagonal rotation, DROT)
+      const int term = h.type == OP_ROT ? h.term : h.terms[0];
+      const int key = G.kind * m + term;
       auto it = rot_id.find(key);
       int ri;
       if (it != rot_id.end()) {
@@ -291,18 +293,19 @@ bool plan_qsweep(const hs_factors* f, const std::vector<int>& factors, uint32_t 
         if (a.n_rot >= kMaxRot) return fail("too many rotations");
         ri = a.n_rot++;
         a.rot[ri].cs = key;
-        a.rot[ri].fast = p.z[h.term] == 0 ? 1 : 0;
+        a.rot[ri].fast = (p.x[term] != 0 && p.z[term] == 0) ? 1 : 0;
         rot_id[key] = ri;
       }
-      const uint64_t x = p.x[h.term], z = p.z[h.term];
+      const uint64_t x = p.x[term], z = p.z[term];
       const int y = __builtin_popcountll(x & z);
+      o.type = x ? OP_ROT : OP_DROT;
       o.idx = int16_t(ri);
       o.ku = uint8_t(reg_coords(h.need, R));
       const uint32_t zl = loc(z);
       o.zk = uint8_t(reg_coords(zl, R));
       o.zthr = zl & ~R & tile_all;
       o.zrest = uint32_t(z & ~uint64_t(local_mask));
-      o.flags = uint8_t((z == 0 ? 1 : 0) | (((y + 3) & 3) << 1));
+      o.flags = uint8_t((x != 0 && z == 0 ? 1 : 0) | (((y + 3) & 3) << 1));
     } else {
       const auto key = std::make_tuple(h.g, h.terms.front(), R);
       auto it = phase_id.find(key);
@@ -358,11 +361,53 @@ bool plan_qsweep(const hs_factors* f, const std::vector<int>& factors, uint32_t 
   }
   if (a.n_ops == 0) return fail("empty sweep");
   a.n_vt += a.n_vt & 1;
+  // Runs of consecutive fast rotations (y = 0, z = 0: X-type terms, which all
+  // commute) on distinct single register bits become one ROTN op.
+  {
+    int w = 0;
+    for (int r = 0; r < a.n_ops;) {
+      const Op& o = a.ops[r];
+      const bool single = o.type == OP_ROT && (o.flags & 1) && __builtin_popcount(o.ku) == 1;
+      if (!single) {
+        a.ops[w++] = a.ops[r++];
+        continue;
+      }
+      Op n = Op();
+      n.type = OP_ROTN;
+      int k = r;
+      while (k < a.n_ops) {
+        const Op& q = a.ops[k];
+        if (!(q.type == OP_ROT && (q.flags & 1) && __builtin_popcount(q.ku) == 1) || (n.ku & q.ku)) break;
+        const int bit = __builtin_ctz(q.ku);
+        if (q.idx > 255) break;
+        n.ku |= q.ku;
+        if (bit < 4) n.zthr |= uint32_t(q.idx) << (8 * bit);
+        else n.zrest |= uint32_t(q.idx) << (8 * (bit - 4));
+        ++k;
+      }
+      a.ops[w++] = n;
+      r = k;
+    }
+    a.n_ops = w;
+  }
   a.n_cls = int(cls.size());
   a.n_pterm = int(pts.size());
   std::copy(cls.begin(), cls.end(), a.cls);
   std::copy(pts.begin(), pts.end(), a.pt);
   return true;
+}
+
+bool plan_qsweep_runs(const hs_factors* f, const std::vector<int>& factors, uint32_t local_mask, int T, int B,
+                      std::vector<std::pair<std::vector<int>, std::shared_ptr<Args>>>& out, std::string* why) {
+  auto a = std::make_shared<Args>();
+  if (plan_qsweep(f, factors, local_mask, T, B, *a, why)) {
+    out.emplace_back(factors, std::move(a));
+    return true;
+  }
+  if (factors.size() < 2) return false;
+  const size_t h = factors.size() / 2;
+  const std::vector<int> lo(factors.begin(), factors.begin() + h), hi(factors.begin() + h, factors.end());
+  return plan_qsweep_runs(f, lo, local_mask, T, B, out, why) && plan_qsweep_runs(f, hi, local_mask, T, B, out, why);
 }
 
 }  // namespace q

@@ -24,6 +24,7 @@
 // the bulk precision, with exp(-i C0) from an FP64 sincos per tile).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <mutex>
 
@@ -175,6 +176,33 @@ __device__ __forceinline__ void tab_ku(typename C2<R>::T (&x)[NR], const typenam
   }
 }
 
+// ROTN: commuting X rotations on distinct single register bits, one
+// compile-time body per bit (no dispatch on the flip).
+template <typename R, int NR, int I, int B>
+__device__ __forceinline__ void rot_run(typename C2<R>::T (&x)[NR], const Op& op, const typename C2<R>::T* rcs) {
+  if constexpr (I < B) {
+    if ((op.ku >> I) & 1) {
+      const int slot = int((I < 4 ? (op.zthr >> (8 * I)) : (op.zrest >> (8 * (I - 4)))) & 0xffu);
+      const typename C2<R>::T cs = rcs[slot];
+      rot_ku<R, NR, (1 << I)>(x, cs.x, cs.y, true, 0, 0u, 0);
+    }
+    rot_run<R, NR, I + 1, B>(x, op, rcs);
+  }
+}
+
+// DROT: x[k] <- (cos - i sin (-1)^popcount(z & r_k)) x[k], the rotation of one
+// diagonal term; sb is the parity of z over the row's fixed bits.
+template <typename R, int NR>
+__device__ __forceinline__ void diag_rot(typename C2<R>::T (&x)[NR], R c, R s, uint32_t zk, int sb) {
+  using T2 = typename C2<R>::T;
+#pragma unroll
+  for (int k = 0; k < NR; ++k) {
+    const R ss = (sb ^ parity(zk & uint32_t(k))) ? -s : s;
+    const T2 v = x[k];
+    x[k] = T2{fma(ss, v.y, c * v.x), fma(-ss, v.x, c * v.y)};
+  }
+}
+
 // Register flips the planner may emit: one or two register bits.
 #define HS_Q_KU_LIST(X) \
   X(1) X(2) X(4) X(8) X(16) X(3) X(5) X(6) X(9) X(10) X(12) X(17) X(18) X(20) X(24)
@@ -252,7 +280,17 @@ __device__ __forceinline__ void phase_apply(typename C2<R>::T (&x)[NR], const Ph
   }
   // Group values, applied one group at a time (fewer live registers):
   // A[a] = g0 prod_{i < B1} f_i(bit i of a), then Bv[b] = prod_{i < B2}
-  // f_{B1+i}(bit i of b); f_i(0) = cos - i sin, f_i(1) = cos + i sin.
+  // f_{B1+i}(bit i of b); f_i(0) = cos - i sin, f_i(1) = cos + i sin.  A
+  // pattern mu of two or more register bits within one group multiplies that
+  // group's values; one that spans both groups multiplies every row.
+  uint32_t rest = P.mu_mask;
+#pragma unroll
+  for (int i = 0; i <= B; ++i) rest &= ~(i == 0 ? 1u : (1u << (1 << (i - 1))));
+  constexpr uint32_t GA = (1u << B1) - 1u;
+  auto mu_factor = [&](int mu, R& cn, R& sn) {
+    const R e = class_sum<R>(cls, Cs, base + P.mu_beg[mu], base + P.mu_beg[mu + 1], lt);
+    sincospi_r(e, &sn, &cn);
+  };
   {
     T2 A[1 << B1];
     A[0] = g0;
@@ -265,8 +303,15 @@ __device__ __forceinline__ void phase_apply(typename C2<R>::T (&x)[NR], const Ph
         A[k] = T2{ac + bs, bc - as};
         A[k + (1 << i)] = T2{ac - bs, bc + as};
       }
+    for (uint32_t r = rest & ((1u << (1u << B1)) - 1u); r; r &= r - 1u) {  // mu inside group A
+      const int mu = __ffs(r) - 1;
+      R cn, sn;
+      mu_factor(mu, cn, sn);
 #pragma unroll
-    for (int k = 0; k < NR; ++k) x[k] = cmul<T2, R>(x[k], A[k & ((1 << B1) - 1)].x, A[k & ((1 << B1) - 1)].y);
+      for (int k = 0; k < (1 << B1); ++k) A[k] = cmul<T2, R>(A[k], cn, parity(uint32_t(mu) & uint32_t(k)) ? sn : -sn);
+    }
+#pragma unroll
+    for (int k = 0; k < NR; ++k) x[k] = cmul<T2, R>(x[k], A[k & GA].x, A[k & GA].y);
   }
   {
     T2 Bv[1 << B2];
@@ -281,18 +326,23 @@ __device__ __forceinline__ void phase_apply(typename C2<R>::T (&x)[NR], const Ph
         Bv[k] = T2{ac + bs, bc - as};
         Bv[k + (1 << i)] = T2{ac - bs, bc + as};
       }
+    for (uint32_t r = rest; r; r &= r - 1u) {  // mu inside group B
+      const int mu = __ffs(r) - 1;
+      if (uint32_t(mu) & GA) continue;
+      R cn, sn;
+      mu_factor(mu, cn, sn);
+#pragma unroll
+      for (int k = 0; k < (1 << B2); ++k)
+        Bv[k] = cmul<T2, R>(Bv[k], cn, parity(uint32_t(mu >> B1) & uint32_t(k)) ? sn : -sn);
+    }
 #pragma unroll
     for (int k = 0; k < NR; ++k) x[k] = cmul<T2, R>(x[k], Bv[k >> B1].x, Bv[k >> B1].y);
   }
-  // Every other register pattern present (two or more register bits).
-  uint32_t rest = P.mu_mask;
-#pragma unroll
-  for (int i = 0; i <= B; ++i) rest &= ~(i == 0 ? 1u : (1u << (1 << (i - 1))));
-  for (; rest; rest &= rest - 1u) {
-    const int mu = __ffs(rest) - 1;
-    const R e = class_sum<R>(cls, Cs, base + P.mu_beg[mu], base + P.mu_beg[mu + 1], lt);
-    R sn, cn;
-    sincospi_r(e, &sn, &cn);
+  for (uint32_t r = rest; r; r &= r - 1u) {  // mu across the two groups
+    const int mu = __ffs(r) - 1;
+    if (!(uint32_t(mu) & GA) || uint32_t(mu) <= GA) continue;
+    R cn, sn;
+    mu_factor(mu, cn, sn);
 #pragma unroll
     for (int k = 0; k < NR; ++k) {
       const R ss = parity(uint32_t(mu) & uint32_t(k)) ? sn : -sn;
@@ -302,32 +352,40 @@ __device__ __forceinline__ void phase_apply(typename C2<R>::T (&x)[NR], const Ph
 }
 
 // ---------------------------------------------------------------------------
-// The kernel.  NT = 2^(T - B) threads; NR = 2^B rows per thread.
+// The sweep of units [u0, u1) of one descriptor (single launch: the kernel
+// parameter; batched launch: a descriptor in global memory).  NT = 2^(T - B)
+// threads; NR = 2^B rows per thread.
+//
+// A unit's tile moves HBM -> shared memory -> registers by warp-cooperative
+// copies (each warp copies exactly the rows its threads hold in the first
+// layout, in address order), so the first read needs only a warp barrier.
+// Once a unit has read its last layout, the tile buffer is free: after one CTA
+// barrier every warp starts copying its rows of the CTA's next unit, which
+// land while the current unit finishes in registers and writes its rows
+// straight back to HBM.
 // ---------------------------------------------------------------------------
 template <typename R, int B>
-__global__ void __launch_bounds__(B == 5 ? 256 : 512, B == 5 ? 2 : 1) qsweep_kernel(const __grid_constant__ Args a) {
+__device__ __forceinline__ void qsweep_core(const Args& a, uint32_t u0, uint32_t u1, unsigned char* smem_raw,
+                                            bool pdl) {
   using T2 = typename C2<R>::T;
   constexpr int NR = 1 << B;
   constexpr int V = 16 / int(sizeof(T2));  // rows per 16-byte chunk (2 for complex64)
   constexpr int VB = V == 2 ? 1 : 0;       // register bits inside a chunk
-  constexpr int NJ = NR / V;               // chunks per thread (also chunks of the tile / NT)
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int NJ = NR / V;               // chunks per thread
   const int NT = blockDim.x;
-  const int lg_nt = __ffs(NT) - 1;
   const uint32_t tid = threadIdx.x;
   const uint32_t TS = 1u << a.tile_bits;
   const uint32_t m0 = a.m0, m1 = a.m1;
   const int sh = a.sh;
-
-  // Shared memory: [tile][value tables][rotations][e0 per phase][scale]
-  // [class constants][ops][layouts][phase headers][classes][phase terms]
   const int n_warps = NT >> 5;
   const int warp = tid >> 5, lane = tid & 31;
+
+  // Shared memory: [tile][value tables][rotations][per-warp e0 per phase]
+  // [per-warp class constants][ops][layouts][phase headers][classes][terms]
+  // [term angles][scale partials]
   T2* tile = reinterpret_cast<T2*>(smem_raw);
   T2* vts = tile + TS;  // 16-byte aligned (the planner keeps n_vt and every table start even)
   T2* rcs = vts + a.n_vt;
-  // Per-warp copies of the per-tile phase constants (each warp computes its
-  // own, so no CTA barrier is needed for them).
   T2* e0s = rcs + a.n_rot + warp * a.n_phase;
   R* Cs = reinterpret_cast<R*>(rcs + a.n_rot + n_warps * a.n_phase) + warp * a.n_cls;
   unsigned char* meta = reinterpret_cast<unsigned char*>(
@@ -338,9 +396,6 @@ __global__ void __launch_bounds__(B == 5 ? 256 : 512, B == 5 ? 2 : 1) qsweep_ker
   Phase* sph = reinterpret_cast<Phase*>(slay + a.n_lay);
   PClass* scls = reinterpret_cast<PClass*>(sph + a.n_phase);
   PTerm* spt = reinterpret_cast<PTerm*>(scls + a.n_cls);
-  // per phase term: theta / pi reduced to [-1, 1]; then the warps' partial
-  // products of the rotation scale (both 16-byte aligned: the structures
-  // before them are 4-byte aligned only)
   auto align16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) + 15) & ~uintptr_t(15); };
   R* thpi = reinterpret_cast<R*>(align16(spt + a.n_pterm));
   double* mpart = reinterpret_cast<double*>(align16(thpi + a.n_pterm));
@@ -358,59 +413,87 @@ __global__ void __launch_bounds__(B == 5 ? 256 : 512, B == 5 ? 2 : 1) qsweep_ker
     copy_words(scls, a.cls, sizeof(PClass) * a.n_cls);
     copy_words(spt, a.pt, sizeof(PTerm) * a.n_pterm);
   }
-  // Rotations: (cos, sin) of the term's angle; a rotation on the fast path
-  // (y = 0, z = 0) is kept as the ratio of the smaller to the larger of
-  // |cos|, |sin| and its form (see rot_ku), and the larger factor goes into
-  // the sweep's scale, applied to the rows before they are stored.  Each
-  // thread takes one rotation slot, one op and one phase term (all loads
-  // independent), and the scale's factors are multiplied in FP64 across the
-  // warp and then across the warps' partial products.
+  // Rotations: a fast rotation (y = 0, z = 0) as the ratio and form of the
+  // factor build's record, its larger factor in the sweep's scale (the warps'
+  // partial products, multiplied together where the scale is applied); any
+  // other rotation as (cos, sin).
   for (int i = tid; i < a.n_rot; i += NT) {
-    const double* p = a.cs + 2 * int64_t(a.rot[i].cs);
-    const double c = p[0], sn = p[1];
-    if (a.rot[i].fast)
-      rcs[i] = fabs(sn) <= fabs(c) ? T2{R(sn / c), R(0)} : T2{R(c / sn), R(1)};
-    else
-      rcs[i] = T2{R(c), R(sn)};
+    const int e = a.rot[i].cs;
+    if (a.rot[i].fast) {
+      const double* q = a.rq + 4 * int64_t(e);
+      rcs[i] = T2{R(q[0]), R(q[1])};
+    } else {
+      const double* p = a.cs + 2 * int64_t(e);
+      rcs[i] = T2{R(p[0]), R(p[1])};
+    }
   }
   {
     double m = 1.0;
     for (int oi = tid; oi < a.n_ops; oi += NT) {
       const Op& op = a.ops[oi];
       if (op.type == OP_ROT && (op.flags & 1)) {
-        const double* p = a.cs + 2 * int64_t(a.rot[op.idx].cs);
-        const double c = p[0], sn = p[1];
-        m *= fabs(sn) <= fabs(c) ? c : sn;
+        m *= a.rq[4 * int64_t(a.rot[op.idx].cs) + 2];
+      } else if (op.type == OP_ROTN) {
+#pragma unroll
+        for (int i = 0; i < B; ++i)
+          if ((op.ku >> i) & 1) {
+            const int slot = int((i < 4 ? (op.zthr >> (8 * i)) : (op.zrest >> (8 * (i - 4)))) & 0xffu);
+            m *= a.rq[4 * int64_t(a.rot[slot].cs) + 2];
+          }
       }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m *= __shfl_xor_sync(0xffffffffu, m, o);
     if (lane == 0) mpart[warp] = m;
   }
-  for (int t = tid; t < a.n_pterm; t += NT) {
-    const double u = a.th[a.pt[t].th] * 0.318309886183790671537767526745;
-    thpi[t] = R(u - 2.0 * rint(0.5 * u));
-  }
+  for (int t = tid; t < a.n_pterm; t += NT) thpi[t] = R(a.rq[4 * int64_t(a.pt[t].th) + 3]);
   for (int t = 0; t < a.n_tab; ++t) {
     const T2* g = reinterpret_cast<const T2*>(a.vt) + a.tab[t].vt0;
     const int s0 = a.tab[t].s0, n = a.tab[t].n;
     for (int e = tid; e < n; e += NT) vts[s0 + e] = g[e];
   }
   const int n_ops = a.n_ops, n_cls = a.n_cls;
-  const uint32_t u0 = blockIdx.x * uint32_t(a.units_per_cta);
-  const uint32_t u1 = min(uint32_t(a.n_units), u0 + uint32_t(a.units_per_cta));
-  __syncthreads();  // the tables are in shared memory
+
+  // Index of the last layout op (the tile buffer is free after its reads).
+  int last_lay = 0;
+  for (int oi = 0; oi < n_ops; ++oi)
+    if (a.ops[oi].type == OP_LAYOUT) last_lay = oi;
+
+  // Warp-cooperative copy of this warp's rows of a unit in layout L (the
+  // first layout of the sweep) into the tile buffer.
+  auto unit_base = [&](uint32_t unit) { return deposit_runs(unit & ((1u << a.n_tiles_log2) - 1u), a.rest); };
+  auto unit_src = [&](uint32_t unit) {
+    return reinterpret_cast<const T2*>(a.src) + int64_t(unit >> a.n_tiles_log2) * a.N;
+  };
+  auto copy_in = [&](const Layout* L, uint32_t base, const T2* src) {
+    const int n_thr = L->n_thr;
+    uint32_t lc = 0;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) lc |= uint32_t((lane >> k) & 1) << L->wlo[k];
+    uint32_t wb = 0;
+    for (int i = 5; i < n_thr; ++i) wb |= ((tid >> i) & 1u) << L->thr[i];
+    const uint32_t c0 = lc | (wb >> VB);
+    const uint32_t s0 = swz(c0), g0 = global_of(c0 * V, m0, m1, sh) | base;
+#pragma unroll 4
+    for (int mm = 0; mm < NJ; ++mm) cp_async16(tile + (s0 ^ L->mswz[mm]) * V, src + (g0 ^ L->mglob[mm]));
+    cp_async_commit();
+  };
+  const Layout* L0 = slay + a.ops[0].idx;  // the first op is always a layout
+
+  if (pdl) grid_dependency_wait();  // the state written by the previous launch is visible after this
+  __syncthreads();                  // the tables are in shared memory
+  if (u0 < u1) copy_in(L0, unit_base(u0), unit_src(u0));
+  if (pdl) grid_launch_dependents();  // the next sweep may load its tables meanwhile
+
   for (uint32_t unit = u0; unit < u1; ++unit) {
-    const uint32_t tile_id = unit & ((1u << a.n_tiles_log2) - 1u);
-    const int rhs = int(unit >> a.n_tiles_log2);
-    const uint32_t base = deposit_runs(tile_id, a.rest);
-    const T2* src = reinterpret_cast<const T2*>(a.src) + int64_t(rhs) * a.N;
-    T2* dst = reinterpret_cast<T2*>(a.dst) + int64_t(rhs) * a.N;
-    if (unit != u0) __syncthreads();  // every warp is done with the previous unit's tile
+    const uint32_t base = unit_base(unit);
+    T2* dst = reinterpret_cast<T2*>(a.dst) + int64_t(unit >> a.n_tiles_log2) * a.N;
     // Per-tile phase constants, in this warp's copy: class sums of +-theta_j
-    // (units of pi, each term reduced mod 2 in FP64 once per CTA) with the
-    // signs of the tile's fixed bits, reduced mod 2 again; a constant class
-    // becomes its phase op's e0.
+    // (units of pi, each term reduced mod 2 in FP64 by the factor build) with
+    // the signs of the tile's fixed bits, reduced mod 2 again; a constant class
+    // becomes its phase op's e0.  (The warp barrier keeps a lane from writing
+    // them while another lane still reads the previous unit's.)
+    __syncwarp();
     for (int cc = lane; cc < n_cls; cc += 32) {
       const PClass C = scls[cc];
       R acc = R(0);
@@ -418,7 +501,7 @@ __global__ void __launch_bounds__(B == 5 ? 256 : 512, B == 5 ? 2 : 1) qsweep_ker
         const R v = thpi[t];
         acc += parity(spt[t].rest & base) ? -v : v;
       }
-      const R ur = acc - R(2) * rint(R(0.5) * acc);  // the class angle in units of pi, reduced to [-1, 1]
+      const R ur = acc - R(2) * rint(R(0.5) * acc);
       if (C.c0p >= 0) {
         R sn, cn;
         sincospi_r(ur, &sn, &cn);
@@ -428,13 +511,8 @@ __global__ void __launch_bounds__(B == 5 ? 256 : 512, B == 5 ? 2 : 1) qsweep_ker
         Cs[cc] = ur;
       }
     }
-    if (unit == u0) {
-      // The state written by the previous launch is visible only after this;
-      // the next sweep may start its table loads meanwhile.
-      grid_dependency_wait();
-      grid_launch_dependents();
-    }
 
+    __syncwarp();
     T2 x[NR];
     uint32_t lt = 0, st = 0, gt = 0;  // row of register index 0: local, swizzled chunk, global
     const Layout* cur = nullptr;      // the register layout in effect
@@ -468,30 +546,14 @@ __global__ void __launch_bounds__(B == 5 ? 256 : 512, B == 5 ? 2 : 1) qsweep_ker
             __syncwarp();
           else
             __syncthreads();
+        } else {
+          cp_async_wait(0);  // this unit's rows, copied by this warp
+          __syncwarp();
         }
         const Layout* L = slay + op.idx;
         uint32_t l = 0;
         const int n_thr = L->n_thr;
         for (int i = 0; i < n_thr; ++i) l |= ((tid >> i) & 1u) << L->thr[i];
-        if (!cur) {
-          // First layout: the warp copies its own rows from HBM in address
-          // order (coalesced), then each thread reads its rows; a warp barrier
-          // suffices since no other warp reads them.
-          uint32_t lc = 0;
-#pragma unroll
-          for (int k = 0; k < 5; ++k) lc |= uint32_t((lane >> k) & 1) << L->wlo[k];
-          // the warp's fixed chunk bits: the warp bits of this thread's row
-          uint32_t wb = 0;
-          for (int i = 5; i < n_thr; ++i) wb |= ((tid >> i) & 1u) << L->thr[i];
-          const uint32_t c0 = lc | (wb >> VB);
-          const uint32_t s0 = swz(c0), g0 = global_of(c0 * V, m0, m1, sh) | base;
-#pragma unroll 4
-          for (int mm = 0; mm < NJ; ++mm)
-            cp_async16(tile + (s0 ^ L->mswz[mm]) * V, src + (g0 ^ L->mglob[mm]));
-          cp_async_commit();
-          cp_async_wait(0);
-          __syncwarp();
-        }
         uint32_t q[B];
 #pragma unroll
         for (int i = 0; i < B; ++i) q[i] = L->qoff[i];
@@ -513,11 +575,22 @@ __global__ void __launch_bounds__(B == 5 ? 256 : 512, B == 5 ? 2 : 1) qsweep_ker
             x[j] = tile[pc];
           }
         }
+        if (oi == last_lay && unit + 1 < u1) {
+          // The tile buffer is free once every warp has read its rows: start
+          // copying the next unit's rows.
+          __syncthreads();
+          copy_in(L0, unit_base(unit + 1), unit_src(unit + 1));
+        }
+      } else if (op.type == OP_ROTN) {
+        rot_run<R, NR, 0, B>(x, op, rcs);
       } else if (op.type == OP_ROT) {
         const T2 cs = rcs[op.idx];
         const bool fast = op.flags & 1;
         const int sbit = fast ? 0 : (parity(op.zrest & base) ^ parity(op.zthr & lt));
         rot_dispatch<R, NR>(x, op.ku, cs.x, cs.y, fast, (op.flags >> 1) & 3, op.zk, sbit);
+      } else if (op.type == OP_DROT) {
+        const T2 cs = rcs[op.idx];
+        diag_rot<R, NR>(x, cs.x, cs.y, op.zk, parity(op.zrest & base) ^ parity(op.zthr & lt));
       } else if (op.type == OP_TAB) {
         const Tab& tb = a.tab[op.idx];
         const uint32_t sm = tb.sm;
@@ -530,7 +603,9 @@ __global__ void __launch_bounds__(B == 5 ? 256 : 512, B == 5 ? 2 : 1) qsweep_ker
         phase_apply<R, NR, B>(x, sph[op.idx], scls, Cs, e0s[op.idx], lt);
       }
     }
-    __syncwarp();  // the warp's reads of the last layout are done (it writes back its own rows)
+    // The sweep's rotation scale, then the rows straight to HBM: register row
+    // 2j (and 2j + 1 in the same 16 bytes for complex64) sits at global row
+    // gt ^ XOR of the layout's global offsets of the set bits of 2j.
     {
       double md = 1.0;
       for (int w = 0; w < n_warps; ++w) md *= mpart[w];
@@ -538,40 +613,49 @@ __global__ void __launch_bounds__(B == 5 ? 256 : 512, B == 5 ? 2 : 1) qsweep_ker
 #pragma unroll
       for (int k = 0; k < NR; ++k) x[k] = T2{x[k].x * m, x[k].y * m};
     }
-    uint32_t q[B];
+    uint32_t go[B];
 #pragma unroll
-    for (int i = 0; i < B; ++i) q[i] = cur->qoff[i];
+    for (int i = 0; i < B; ++i) go[i] = cur->goff[i];
 #pragma unroll
     for (int j = 0; j < NJ; ++j) {
-      uint32_t pc = st;
+      uint32_t g = gt;
 #pragma unroll
       for (int i = 0; i < B - VB; ++i)
-        if ((j >> i) & 1) pc ^= q[i + VB];
+        if ((j >> i) & 1) g ^= go[i + VB];
       if constexpr (V == 2) {
-        *reinterpret_cast<float4*>(tile + pc * 2) = make_float4(x[2 * j].x, x[2 * j].y, x[2 * j + 1].x, x[2 * j + 1].y);
+        *reinterpret_cast<float4*>(dst + g) = make_float4(x[2 * j].x, x[2 * j].y, x[2 * j + 1].x, x[2 * j + 1].y);
       } else {
-        tile[pc] = x[j];
+        dst[g] = x[j];
       }
-    }
-    __syncwarp();
-    {
-      // The warp's rows back to HBM in address order (coalesced).
-      const Layout* L = cur;
-      const int n_thr = L->n_thr;
-      uint32_t lc = 0;
-#pragma unroll
-      for (int k = 0; k < 5; ++k) lc |= uint32_t((lane >> k) & 1) << L->wlo[k];
-      uint32_t wb = 0;
-      for (int i = 5; i < n_thr; ++i) wb |= ((tid >> i) & 1u) << L->thr[i];
-      const uint32_t c0 = lc | (wb >> VB);
-      const uint32_t s0 = swz(c0), g0 = global_of(c0 * V, m0, m1, sh) | base;
-#pragma unroll 4
-      for (int mm = 0; mm < NJ; ++mm)
-        *reinterpret_cast<uint4*>(dst + (g0 ^ L->mglob[mm])) =
-            *reinterpret_cast<const uint4*>(tile + (s0 ^ L->mswz[mm]) * V);
     }
   }
 }
+
+template <typename R, int B>
+__global__ void __launch_bounds__(B == 5 ? 256 : 512, B == 5 ? 2 : 1) qsweep_kernel(const __grid_constant__ Args a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const uint32_t u0 = blockIdx.x * uint32_t(a.units_per_cta);
+  const uint32_t u1 = min(uint32_t(a.n_units), u0 + uint32_t(a.units_per_cta));
+  qsweep_core<R, B>(a, u0, u1, smem_raw, true);
+}
+
+template <typename R, int B>
+__global__ void __launch_bounds__(B == 5 ? 256 : 512, B == 5 ? 2 : 1) qlevel_kernel(const __grid_constant__ LevelArgs p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  int* pref = reinterpret_cast<int*>(smem_raw + p.prefix_smem);
+  for (int i = threadIdx.x; i < p.count; i += blockDim.x) pref[i] = p.lvl_prefix[p.off + i];
+  __syncthreads();
+  int lo = 0, hi = p.count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (pref[mid] <= int(blockIdx.x)) lo = mid; else hi = mid - 1;
+  }
+  const Args& a = p.descs[p.lvl_desc[p.off + lo]];
+  const uint32_t u = blockIdx.x - uint32_t(pref[lo]);
+  qsweep_core<R, B>(a, u, u + 1, smem_raw, true);
+}
+
+using LFn = void (*)(LevelArgs);
 
 using QFn = void (*)(Args);
 
@@ -595,6 +679,11 @@ cudaError_t prepare_qsweep() {
     e = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSweepSmemMax));
     if (e != cudaSuccess) return e;
   }
+  const LFn lfns[3] = {qlevel_kernel<float, 5>, qlevel_kernel<float, 4>, qlevel_kernel<double, 4>};
+  for (LFn fn : lfns) {
+    e = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSweepSmemMax));
+    if (e != cudaSuccess) return e;
+  }
   if (dev < 64) done[dev] = true;
   return cudaSuccess;
 }
@@ -608,21 +697,51 @@ size_t qsweep_smem_bytes(const Args& a, hs_dtype dt, int B) {
          sizeof(PClass) * a.n_cls + sizeof(PTerm) * a.n_pterm + 16 + r * a.n_pterm + 16 + 8 * warps;
 }
 
-cudaError_t launch_qsweep(const hs_factors* f, Args& a, const void* src, void* dst, int n_rhs, int B, bool pdl,
-                          cudaStream_t s) {
+void fill_job(const hs_factors* f, Args& a, void* psi, int n_rhs) {
   const Plan& p = f->plan;
-  QFn fn = qsweep_fn(f->dtype, B);
-  if (!fn || a.tile_bits - B < 5 || a.tile_bits > p.n_qubits) return cudaErrorInvalidValue;
-  a.src = src;
-  a.dst = dst;
+  a.src = psi;
+  a.dst = psi;
   a.cs = f->bin.cs;
   a.th = f->bin.th;
+  a.rq = f->bin.rq;
   a.vt = f->d_vt;
   a.N = p.N;
   a.n_rhs = n_rhs;
   a.n_tiles_log2 = p.n_qubits - a.tile_bits;
   a.n_units = (1 << a.n_tiles_log2) * n_rhs;
-  if (a.units_per_cta < 1) a.units_per_cta = 1;
+}
+
+cudaError_t launch_qlevel(hs_dtype dt, int B, int tile_bits, const LevelArgs& L, int64_t ctas, size_t smem,
+                          cudaStream_t s) {
+  LFn fn = dt == HS_C64 ? (B == 5 ? qlevel_kernel<float, 5> : (B == 4 ? qlevel_kernel<float, 4> : nullptr))
+                        : (B == 4 ? qlevel_kernel<double, 4> : nullptr);
+  if (!fn || tile_bits - B < 5 || smem > kSweepSmemMax || ctas <= 0 || ctas >= (int64_t(1) << 31))
+    return cudaErrorInvalidValue;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(unsigned(ctas), 1u, 1u);
+  cfg.blockDim = dim3(unsigned(1u << (tile_bits - B)), 1u, 1u);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, fn, L);
+  if (e == cudaSuccess) note_launches();
+  return e;
+}
+
+cudaError_t launch_qsweep(const hs_factors* f, Args& a, const void* src, void* dst, int n_rhs, int B, bool pdl,
+                          cudaStream_t s) {
+  const Plan& p = f->plan;
+  QFn fn = qsweep_fn(f->dtype, B);
+  if (!fn || a.tile_bits - B < 5 || a.tile_bits > p.n_qubits) return cudaErrorInvalidValue;
+  fill_job(f, a, const_cast<void*>(src), n_rhs);
+  a.dst = dst;
+  // Several tiles per CTA once the grid is large (the per-CTA tables are then
+  // loaded once for them), keeping about eight waves of two CTAs per SM.
+  if (a.units_per_cta < 1) a.units_per_cta = std::max(1, std::min(4, a.n_units / (152 * 2 * 8)));
   const size_t smem = qsweep_smem_bytes(a, f->dtype, B);
   if (smem > kSweepSmemMax) return cudaErrorInvalidValue;
   cudaLaunchConfig_t cfg = {};

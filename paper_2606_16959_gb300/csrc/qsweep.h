@@ -17,6 +17,8 @@
 //   ROT    one non-diagonal term of a factor without such a table: its exact
 //          rotation cos(theta) I - i sin(theta) P_j, from the FP64 (cos, sin)
 //          of the factor build;
+//   DROT   a single diagonal term between non-diagonal ones: its rotation
+//          exp(-i theta (-1)^popcount(z & r)) from the build's FP64 (cos, sin);
 //   PHASE  a run of consecutive diagonal terms (x = 0) of such a factor: the
 //          phase exp(-i sum_j theta_j (-1)^popcount(z_j & r)) computed for
 //          each row from (z_j, theta_j) -- the factor values are generated
@@ -26,6 +28,8 @@
 #pragma once
 
 #include <cstdint>
+#include <memory>
+#include <utility>
 
 #include "hs_internal.h"
 
@@ -42,7 +46,7 @@ constexpr int kMaxClasses = 256;
 constexpr int kMaxVt = 2048;   // value-table entries held in shared memory
 constexpr int kMaxB = 5;       // register bits per thread
 
-enum : uint8_t { OP_ROT = 0, OP_TAB = 1, OP_PHASE = 2, OP_LAYOUT = 3 };
+enum : uint8_t { OP_ROT = 0, OP_TAB = 1, OP_PHASE = 2, OP_LAYOUT = 3, OP_ROTN = 4, OP_DROT = 5 };
 
 struct Op {
   uint8_t type;
@@ -53,6 +57,9 @@ struct Op {
   int16_t pad;
   uint32_t zthr;  // ROT: z's bits in the tile on thread positions (local-index mask)
   uint32_t zrest; // ROT: z's bits outside the tile (global mask)
+  // ROTN (a run of consecutive rotations exp(-i theta X_q) on distinct single
+  // register bits, which commute): ku is the mask of those register bits and
+  // byte i of (zthr, zrest) the rotation slot of register bit i.
 };
 
 struct Layout {
@@ -111,6 +118,7 @@ struct Args {
   void* dst;
   const double* cs;  // (cos, sin) per kind and term (FP64)
   const double* th;  // theta per kind and term (FP64)
+  const double* rq;  // register-sweep record per kind and term (FP64, see the factor build)
   const void* vt;    // value tables (storage type)
   int64_t N;
   int n_rhs;
@@ -144,7 +152,30 @@ __host__ __device__ __forceinline__ uint32_t swz(uint32_t c) {
 bool plan_qsweep(const hs_factors* f, const std::vector<int>& factors, uint32_t local_mask, int T, int B,
                  Args& a, std::string* why);
 
+// The same for a run of factors that may exceed a descriptor's limits: the
+// run is split into consecutive shorter runs (same local mask) until each
+// fits.  Returns false if a single factor cannot be expressed.
+bool plan_qsweep_runs(const hs_factors* f, const std::vector<int>& factors, uint32_t local_mask, int T, int B,
+                      std::vector<std::pair<std::vector<int>, std::shared_ptr<Args>>>& out, std::string* why);
+
 size_t qsweep_smem_bytes(const Args& a, hs_dtype dt, int B);
+
+// The job-dependent fields of a descriptor: state (evolved in place), the
+// factor set's angle records and value tables, and the unit count (tiles of
+// the planned local mask times n_rhs states).
+void fill_job(const hs_factors* f, Args& a, void* psi, int n_rhs);
+
+// One level of a batch of register sweeps: CTA c runs unit c - prefix[e] of
+// descriptor lvl_desc[off + e], e the last entry with prefix[off + e] <= c.
+struct LevelArgs {
+  const Args* descs;
+  const int* lvl_desc;
+  const int* lvl_prefix;
+  int off, count;
+  uint32_t prefix_smem;  // byte offset of the level's prefix table in shared memory
+};
+cudaError_t launch_qlevel(hs_dtype dt, int B, int tile_bits, const LevelArgs& L, int64_t ctas, size_t smem,
+                          cudaStream_t s);
 cudaError_t launch_qsweep(const hs_factors* f, Args& a, const void* src, void* dst, int n_rhs, int B,
                           bool pdl, cudaStream_t s);
 cudaError_t prepare_qsweep();

@@ -133,3 +133,71 @@ extern "C" int hs_autotune(const hs_factors* f, const void* psi, int n_rhs, int 
   *best = best_o;
   return HS_OK;
 }
+
+extern "C" int hs_batch_autotune(const hs_batch_job* jobs, size_t n_jobs, void* cuda_stream, hs_batch_opts* best) {
+  if (!jobs || n_jobs == 0 || !best) return hs::report_error(HS_EINVAL, "null argument or no jobs");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+  const hs_dtype dt = jobs[0].factors ? jobs[0].factors->dtype : HS_C64;
+  // Scratch copies of every job's states (16-byte aligned each).
+  std::vector<size_t> off(n_jobs + 1, 0);
+  for (size_t j = 0; j < n_jobs; ++j) {
+    if (!jobs[j].factors || !jobs[j].psi || jobs[j].n_rhs < 1)
+      return hs::report_error(HS_EINVAL, "job " + std::to_string(j) + ": null factors or psi");
+    const size_t bytes = size_t(jobs[j].n_rhs) * size_t(jobs[j].factors->plan.N) * hs::elem_bytes(jobs[j].factors->dtype);
+    off[j + 1] = off[j] + (bytes + 255) / 256 * 256;
+  }
+  unsigned char* work = nullptr;
+  cudaError_t e = hs::pool_malloc(reinterpret_cast<void**>(&work), off[n_jobs], s);
+  if (e != cudaSuccess) return hs::report_error(e == cudaErrorMemoryAllocation ? HS_ENOMEM : HS_ECUDA,
+                                                std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
+  std::vector<hs_batch_job> wj(jobs, jobs + n_jobs);
+  for (size_t j = 0; j < n_jobs; ++j) wj[j].psi = work + off[j];
+  std::vector<hs_batch_opts> cand;
+  for (int tb : {9, 10, 11})
+    for (int kb : {24, 48})
+      for (int tpc : {4, 8}) cand.push_back(hs_batch_opts{tb, 0, 0, kb, 0, tpc, 0, 0});
+  for (int B : {5, 4}) {
+    if (dt == HS_C128 && B != 4) continue;
+    for (int tb : {13, 12})
+      for (int lb : {2, 3}) cand.push_back(hs_batch_opts{tb, lb, 0, 0, 0, 0, HS_METHOD_REG, B});
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best_ms = 1e30f;
+  hs_batch_opts best_o = cand[0];
+  int rc = HS_OK;
+  for (const hs_batch_opts& o : cand) {
+    hs_batch* b = nullptr;
+    if (hs_batch_create(wj.data(), n_jobs, &o, &b) != HS_OK) continue;  // options that do not apply
+    float t_min = 1e30f;
+    bool ok = true;
+    for (int rep = 0; rep < 2 && ok; ++rep) {
+      for (size_t j = 0; j < n_jobs; ++j)
+        cudaMemcpyAsync(wj[j].psi, jobs[j].psi,
+                        size_t(jobs[j].n_rhs) * size_t(jobs[j].factors->plan.N) * hs::elem_bytes(dt),
+                        cudaMemcpyDeviceToDevice, s);
+      cudaEventRecord(e0, s);
+      if (hs_batch_launch(b, cuda_stream) != HS_OK) ok = false;
+      cudaEventRecord(e1, s);
+      if (cudaEventSynchronize(e1) != cudaSuccess) { ok = false; rc = HS_ECUDA; }
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      t_min = std::min(t_min, ms);
+    }
+    hs_batch_free_async(b, cuda_stream);
+    if (rc != HS_OK) break;
+    if (ok && t_min < best_ms) {
+      best_ms = t_min;
+      best_o = o;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFreeAsync(work, s);
+  cudaStreamSynchronize(s);
+  if (rc != HS_OK) return hs::report_error(rc, "batch autotune: a CUDA call failed");
+  best_o.use_graph = best->use_graph == 1 ? 1 : 0;
+  *best = best_o;
+  return HS_OK;
+}

@@ -31,7 +31,7 @@ EXPORTS = (
     "hs_spmv", "hs_dia_evolve", "hs_dia_convert", "hs_dia_info", "hs_dia_get", "hs_dia_free",
     "hs_kernel_launches", "hs_expectation", "hs_build_factors_ex", "hs_factors_sequence",
     "hs_build_factors_td", "hs_evolve_td", "hs_factors_set_drive", "hs_dia_evolve_td",
-    "hs_parse_terms", "hs_evolve_batch",
+    "hs_parse_terms", "hs_evolve_batch", "hs_batch_autotune",
 )
 
 
@@ -48,7 +48,8 @@ class BatchJob(ctypes.Structure):
 
 class BatchOpts(ctypes.Structure):
     _fields_ = [("tile_bits", ctypes.c_int), ("low_bits", ctypes.c_int), ("use_graph", ctypes.c_int),
-                ("smem_kb", ctypes.c_int), ("no_tables", ctypes.c_int), ("tiles_per_cta", ctypes.c_int)]
+                ("smem_kb", ctypes.c_int), ("no_tables", ctypes.c_int), ("tiles_per_cta", ctypes.c_int),
+                ("method", ctypes.c_int), ("reg_bits", ctypes.c_int)]
 
 
 class EvolveOpts(ctypes.Structure):
@@ -127,6 +128,7 @@ def lib() -> ctypes.CDLL:
                                      ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(i)]
         L.hs_evolve_batch.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(i), ctypes.POINTER(i), sz,
                                       vp]
+        L.hs_batch_autotune.argtypes = [ctypes.POINTER(BatchJob), sz, vp, ctypes.POINTER(BatchOpts)]
         L.hs_kernel_launches.argtypes = []
         L.hs_kernel_launches.restype = ctypes.c_uint64
         for name in EXPORTS:
@@ -471,7 +473,7 @@ class Batch:
 
 
 def hs_batch_create(jobs, tile_bits: int = 0, low_bits: int = 0, use_graph: bool = True, smem_kb: int = 0,
-                    no_tables: bool = False, tiles_per_cta: int = 0) -> Batch:
+                    no_tables: bool = False, tiles_per_cta: int = 0, method: int = 0, reg_bits: int = 0) -> Batch:
     """jobs: sequence of (Factors, state tensor, n_steps)."""
     arr = (BatchJob * len(jobs))()
     keep = []
@@ -480,10 +482,31 @@ def hs_batch_create(jobs, tile_bits: int = 0, low_bits: int = 0, use_graph: bool
         arr[k] = BatchJob(f.handle.value, ptr, n_rhs, int(n_steps))
         keep.append((f, psi))
     o = BatchOpts(int(tile_bits), int(low_bits), int(bool(use_graph)), int(smem_kb), int(bool(no_tables)),
-                  int(tiles_per_cta))
+                  int(tiles_per_cta), int(method), int(reg_bits))
     out = ctypes.c_void_p()
     _check(lib().hs_batch_create(arr, len(jobs), ctypes.byref(o), ctypes.byref(out)))
     return Batch(out.value, keep)
+
+
+def _batch_jobs(jobs):
+    arr = (BatchJob * len(jobs))()
+    keep = []
+    for k, (f, psi, n_steps) in enumerate(jobs):
+        ptr, n_rhs = _check_state(f, psi)
+        arr[k] = BatchJob(f.handle.value, ptr, n_rhs, int(n_steps))
+        keep.append((f, psi))
+    return arr, keep
+
+
+def hs_batch_autotune(jobs, use_graph: bool = False, stream=None) -> dict:
+    """Time candidate batch options on scratch copies of the jobs' states; the
+    fastest as keyword arguments for hs_batch_create."""
+    arr, _ = _batch_jobs(jobs)
+    o = BatchOpts()
+    o.use_graph = int(bool(use_graph))
+    _check(lib().hs_batch_autotune(arr, len(jobs), _stream(stream), ctypes.byref(o)))
+    return dict(tile_bits=o.tile_bits, low_bits=o.low_bits, smem_kb=o.smem_kb, no_tables=bool(o.no_tables),
+                tiles_per_cta=o.tiles_per_cta, method=o.method, reg_bits=o.reg_bits)
 
 
 def hs_batch_launch(b: Batch, stream=None) -> None:

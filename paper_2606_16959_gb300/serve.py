@@ -89,7 +89,8 @@ class _Group:
 
 class Server:
     def __init__(self, dtype: str = "c64", hbm_bytes: Optional[int] = None, max_inflight: int = 64,
-                 max_group: int = 32, n_streams: int = 4, tile_bits: int = 0, keep_results: bool = False):
+                 max_group: int = 32, n_streams: int = 4, tile_bits: int = 0, keep_results: bool = False,
+                 batch_opts: Optional[dict] = None):
         import torch
         self.torch = torch
         self.dtype = dtype
@@ -100,7 +101,11 @@ class Server:
         self.max_inflight = max_inflight
         self.max_group = max_group
         self.streams = [torch.cuda.Stream() for _ in range(n_streams)]
-        self.tile_bits = tile_bits
+        # options of every batch (hs_batch_create keywords, e.g. from
+        # hs.hs_batch_autotune on a representative group)
+        self.batch_opts = dict(batch_opts or {})
+        if tile_bits:
+            self.batch_opts["tile_bits"] = tile_bits
         self.keep_results = keep_results
         self.used = 0
         self.peak_used = 0
@@ -167,8 +172,8 @@ class Server:
                 states.append(st)
                 facs.append(hs.hs_build_factors(r.labels, r.coeffs, r.t, r.n_steps, r.budget, self.dtype, stream=s))
                 r.updates = r.n_steps * facs[-1].n_factors * (1 << r.n_qubits)
-            b = hs.hs_batch_create([(f, st, r.n_steps) for f, st, r in zip(facs, states, group)],
-                                   tile_bits=self.tile_bits, use_graph=False)
+            b = hs.hs_batch_create([(f, st, r.n_steps) for f, st, r in zip(facs, states, group)], use_graph=False,
+                                   **self.batch_opts)
             hs.hs_batch_launch(b, stream=s)
             out = torch.zeros(len(group), 4, dtype=torch.float64, device="cuda")
             for k, st in enumerate(states):

@@ -219,3 +219,47 @@ def test_reg_maxcut24_against_fused_path():
     x, z, _ = O.parse_terms(job.ham.labels)
     want0 = O.evolve_direct(x, z, job.ham.coeffs, job.t / 25, 2, job.psi0[0])
     _check(got0, want0, "c64", "maxcut24 state 0")
+
+
+@pytest.mark.parametrize("dt", ["c64", "c128"])
+def test_reg_batch_equals_jobs_alone_bitwise_and_oracle(dt):
+    """A register-sweep batch (one level launch per sweep index and tile size)
+    reproduces every job evolved alone with the same options bit for bit: jobs
+    above and below the batch's tile size, one too small for a register tile
+    (its own launches), several states per job; small jobs against the oracle."""
+    rng = np.random.default_rng(4200)
+    tdt = _tdt(dt)
+    B = 5 if dt == "c64" else 4
+    hams = [(W.tfim_chain(14, 1.0, 0.7), 8), (W.heisenberg_chain(13, rng.uniform(0.5, 1.5, 13)), 8),
+            (W.maxcut_3regular(12, 3), 4), (W.tfim_chain(11, 0.9, 1.2), 4), (W.heisenberg_chain(12, rng.uniform(0.5, 1.5, 12)), 4),
+            (W.tfim_chain(8, 1.0, 0.5), 4), (_random_ham(rng, 12, 10), 8)]
+    jobs = []
+    for k, (ham, budget) in enumerate(hams):
+        steps = int(rng.integers(2, 7))
+        R = 1 + (k % 3 == 0)
+        psi0 = np.stack([W.gaussian_state(ham.n_qubits, rng) for _ in range(R)])
+        f = hs.hs_build_factors(ham.labels, ham.coeffs, 0.8, steps, budget, dt)
+        jobs.append((ham, f, psi0, steps))
+    states = [torch.from_numpy(p).to("cuda", tdt) for _, _, p, _ in jobs]
+    b = hs.hs_batch_create([(f, s, st) for (_, f, _, st), s in zip(jobs, states)], method=REG, tile_bits=13 if dt == "c64" else 12,
+                           low_bits=3 if dt == "c64" else 1)
+    assert b.n_separate >= 1  # the 8-qubit job
+    hs.hs_batch_launch(b)
+    torch.cuda.synchronize()
+    for (ham, f, p0, steps), got in zip(jobs, states):
+        ref = torch.from_numpy(p0).to("cuda", tdt)
+        if ham.n_qubits >= B + 5:
+            hs.hs_evolve_ex(f, ref, steps, method=REG, tile_bits=13 if dt == "c64" else 12, low_bits=3 if dt == "c64" else 1,
+                            reg_bits=B)
+        else:
+            hs.hs_evolve(f, ref, steps)
+        assert torch.equal(got, ref), (ham.family, ham.n_qubits)
+        _check(got.cpu().numpy(), _oracle(ham, 0.8, steps, p0), dt, f"{ham.family} n={ham.n_qubits}")
+    # a second launch (graph replay) evolves by the same steps again
+    hs.hs_batch_launch(b)
+    torch.cuda.synchronize()
+    ham, f, p0, steps = jobs[0]
+    _check(states[0].cpu().numpy(), _oracle(ham, 1.6, 2 * steps, p0), dt, "relaunch")  # two launches: 2 steps of 0.8 / steps each
+    b.close()
+    for _, f, _, _ in jobs:
+        f.close()
