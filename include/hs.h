@@ -387,6 +387,19 @@ const char* hs_last_error(void);
  * the paper's method. */
 uint64_t hs_kernel_launches(void);
 
+/* Index checks (not part of the paper's method).  A library compiled with
+ * -DHS_DEBUG_BOUNDS tests every state row, diagonal element, slot and
+ * row-base table entry, value-table entry and per-term record a kernel
+ * addresses against its array's extent; a failed test counts, records the
+ * first failure and redirects the access to element 0 (no trap, the context
+ * stays usable, the launch's results are void).  out4 (host, 4 words)
+ * receives the number of failures, then the first failure's site, index and
+ * extent (sites are listed in csrc/bounds.cuh); reset != 0 clears the counts.
+ * Call it after the checked work has completed (e.g. after a device
+ * synchronise).  Returns 1 in a checking build, 0 in the ordinary build (out4
+ * zeroed), HS_EINVAL for a null out4, HS_ECUDA if a read fails. */
+int hs_debug_bounds(uint64_t* out4, int reset);
+
 #ifdef __cplusplus
 }
 #endif

@@ -273,6 +273,14 @@ uint64_t end_capture_count() {
   return t_captured;
 }
 
+// Readers of the translation units' bounds words (HS_DEBUG_BOUNDS build).
+using BoundsReader = int (*)(uint64_t* out4, bool reset);
+static std::vector<BoundsReader>& bounds_readers() {
+  static std::vector<BoundsReader> r;
+  return r;
+}
+void register_bounds_reader(BoundsReader r) { bounds_readers().push_back(r); }
+
 // The library's stream-ordered memory pool on the current device: memory freed
 // by hs_free_factors_async / hs_batch_free_async stays in the pool (release
 // threshold unlimited) so that the next factor build reuses it without mapping
@@ -519,6 +527,23 @@ extern "C" {
 const char* hs_last_error(void) { return g_err.c_str(); }
 
 uint64_t hs_kernel_launches(void) { return hs::g_launches.load(std::memory_order_relaxed); }
+
+int hs_debug_bounds(uint64_t* out4, int reset) {
+  if (!out4) return hs::report_error(HS_EINVAL, "null argument");
+  out4[0] = out4[1] = out4[2] = out4[3] = 0;
+#ifdef HS_DEBUG_BOUNDS
+  for (hs::BoundsReader r : hs::bounds_readers()) {
+    uint64_t w[4];
+    if (r(w, reset != 0) != 0) return hs::report_error(HS_ECUDA, "reading a bounds word failed");
+    if (w[0] && !out4[0]) { out4[1] = w[1]; out4[2] = w[2]; out4[3] = w[3]; }
+    out4[0] += w[0];
+  }
+  return 1;
+#else
+  (void)reset;
+  return 0;
+#endif
+}
 
 int hs_build_factors_ex(const uint64_t* x, const uint64_t* z, const double* coeffs, size_t n_terms, int n_qubits,
                         double t, int n_steps, int diag_budget, int order, hs_dtype dtype, void* cuda_stream,

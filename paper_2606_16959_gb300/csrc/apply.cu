@@ -52,7 +52,8 @@ __global__ void __launch_bounds__(256) apply_plain_kernel(const typename C2<R>::
                                                           const int64_t* __restrict__ offs,
                                                           const int64_t* __restrict__ rowbase, int D,
                                                           const typename C2<R>::T* __restrict__ x,
-                                                          typename C2<R>::T* __restrict__ y, int64_t N, int n_rhs) {
+                                                          typename C2<R>::T* __restrict__ y, int64_t N, int n_rhs,
+                                                          int64_t n_vals) {
   using T2 = typename C2<R>::T;
   for (int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; r < N; r += int64_t(gridDim.x) * blockDim.x) {
     for (int q0 = 0; q0 < n_rhs; q0 += RB) {
@@ -62,10 +63,10 @@ __global__ void __launch_bounds__(256) apply_plain_kernel(const typename C2<R>::
       for (int k = 0; k < D; ++k) {
         const int64_t c = r + offs[k];
         if (c < 0 || c >= N) continue;
-        const T2 v = vals[rowbase[k] + r];
+        const T2 v = vals[HS_BCHK(rowbase[k] + r, n_vals, BS_PLAIN_VAL)];
 #pragma unroll
         for (int q = 0; q < RB; ++q)
-          if (q0 + q < n_rhs) cfma(acc[q], v, x[int64_t(q0 + q) * N + c]);
+          if (q0 + q < n_rhs) cfma(acc[q], v, x[HS_BCHK(int64_t(q0 + q) * N + c, int64_t(n_rhs) * N, BS_PLAIN_X)]);
       }
 #pragma unroll
       for (int q = 0; q < RB; ++q)
@@ -169,23 +170,23 @@ cudaError_t launch_apply_plain(const hs_factors* f, int g, const void* x, void* 
     auto xs = static_cast<const float2*>(x);
     auto ys = static_cast<float2*>(y);
     if (n_rhs >= 16)
-      apply_plain_kernel<float, 16><<<blocks, threads, 0, s>>>(v, offs, rb, G.D, xs, ys, p.N, n_rhs);
+      apply_plain_kernel<float, 16><<<blocks, threads, 0, s>>>(v, offs, rb, G.D, xs, ys, p.N, n_rhs, p.total_elems);
     else if (n_rhs >= 8)
-      apply_plain_kernel<float, 8><<<blocks, threads, 0, s>>>(v, offs, rb, G.D, xs, ys, p.N, n_rhs);
+      apply_plain_kernel<float, 8><<<blocks, threads, 0, s>>>(v, offs, rb, G.D, xs, ys, p.N, n_rhs, p.total_elems);
     else if (n_rhs >= 4)
-      apply_plain_kernel<float, 4><<<blocks, threads, 0, s>>>(v, offs, rb, G.D, xs, ys, p.N, n_rhs);
+      apply_plain_kernel<float, 4><<<blocks, threads, 0, s>>>(v, offs, rb, G.D, xs, ys, p.N, n_rhs, p.total_elems);
     else
-      apply_plain_kernel<float, 1><<<blocks, threads, 0, s>>>(v, offs, rb, G.D, xs, ys, p.N, n_rhs);
+      apply_plain_kernel<float, 1><<<blocks, threads, 0, s>>>(v, offs, rb, G.D, xs, ys, p.N, n_rhs, p.total_elems);
   } else {
     auto v = reinterpret_cast<const double2*>(f->d_vals);
     auto xs = static_cast<const double2*>(x);
     auto ys = static_cast<double2*>(y);
     if (n_rhs >= 8)
-      apply_plain_kernel<double, 8><<<blocks, threads, 0, s>>>(v, offs, rb, G.D, xs, ys, p.N, n_rhs);
+      apply_plain_kernel<double, 8><<<blocks, threads, 0, s>>>(v, offs, rb, G.D, xs, ys, p.N, n_rhs, p.total_elems);
     else if (n_rhs >= 4)
-      apply_plain_kernel<double, 4><<<blocks, threads, 0, s>>>(v, offs, rb, G.D, xs, ys, p.N, n_rhs);
+      apply_plain_kernel<double, 4><<<blocks, threads, 0, s>>>(v, offs, rb, G.D, xs, ys, p.N, n_rhs, p.total_elems);
     else
-      apply_plain_kernel<double, 1><<<blocks, threads, 0, s>>>(v, offs, rb, G.D, xs, ys, p.N, n_rhs);
+      apply_plain_kernel<double, 1><<<blocks, threads, 0, s>>>(v, offs, rb, G.D, xs, ys, p.N, n_rhs, p.total_elems);
   }
   note_launches();
   return cudaGetLastError();
@@ -202,6 +203,10 @@ cudaError_t launch_sweep(const hs_factors* f, const SweepLaunch& L, cudaStream_t
   a.slot_tab = f->d_slot_tab;
   a.tab_rb = f->d_tab_rb;
   a.N = p.N;
+  a.n_vals = p.total_elems;
+  a.n_vt_g = p.total_vt;
+  a.n_slot_g = int(p.slot_u.size());
+  a.n_tab_g = int(p.tab_rb.size());
   a.n_rhs = L.n_rhs;
   a.rhs_block = L.rhs_block;
   a.tile_bits = L.tile_bits;

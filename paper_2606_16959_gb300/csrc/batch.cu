@@ -41,6 +41,8 @@ struct BJob {
   const int32_t* slot_tab;
   const int64_t* tab_rb;
   int64_t N;
+  int64_t n_vals, n_vt_g;  // extents (index checks only)
+  int n_slot_g, n_tab_g;
   int n_qubits;
   int n_rhs;
 };
@@ -104,6 +106,10 @@ __global__ void __launch_bounds__(kBatchThreads) batch_level_kernel(const __grid
     sa->slot_tab = bj.slot_tab;
     sa->tab_rb = bj.tab_rb;
     sa->N = bj.N;
+    sa->n_vals = bj.n_vals;
+    sa->n_vt_g = bj.n_vt_g;
+    sa->n_slot_g = bj.n_slot_g;
+    sa->n_tab_g = bj.n_tab_g;
     sa->n_rhs = bj.n_rhs;
     sa->rhs_block = 1;
     sa->tile_bits = p.tile_bits;
@@ -467,7 +473,8 @@ extern "C" int hs_batch_create(const hs_batch_job* jobs, size_t n_jobs, const hs
     }
     const int jid = int(hjobs.size());
     const hs_factors* f = J.factors;
-    hjobs.push_back(BJob{J.psi, f->d_vals, f->d_vt, f->d_slot_u, f->d_slot_tab, f->d_tab_rb, p.N, p.n_qubits, J.n_rhs});
+    hjobs.push_back(BJob{J.psi, f->d_vals, f->d_vt, f->d_slot_u, f->d_slot_tab, f->d_tab_rb, p.N, p.total_elems,
+                         p.total_vt, int(p.slot_u.size()), int(p.tab_rb.size()), p.n_qubits, J.n_rhs});
     const int64_t units = (int64_t(1) << (p.n_qubits - T)) * J.n_rhs;
     job_ctas.push_back((units + b->tiles_per_cta - 1) / b->tiles_per_cta);
     std::map<std::pair<uint32_t, std::vector<int>>, int> uniq;

@@ -15,6 +15,7 @@
 #include <cstdint>
 
 #include "counters.h"
+#include "bounds.cuh"
 #include "hs_internal.h"
 
 namespace hs {
@@ -44,6 +45,7 @@ struct BuildArgs {
   const int* dir;         // per group: +1 terms first..last act in order, -1 reversed
   int m;                  // number of terms
   const int* glist;       // groups of grid row blockIdx.y (NULL: group blockIdx.y)
+  int64_t n_vals, n_vt;   // extents of vals and vt (index checks only)
 };
 
 __device__ __forceinline__ int group_of(const BuildArgs& a) {
@@ -258,7 +260,7 @@ __device__ __forceinline__ void write_row(const BuildArgs& a, const GroupRows<MA
       for (int s = 0; s < NS; ++s)
         if (s == cc) v = make_double2(w[s].x, -w[s].y);
     }
-    store_val(a.vals, a.rowbase[d0 + k] + r, v, c64);
+    store_val(a.vals, HS_BCHK(a.rowbase[d0 + k] + r, a.n_vals, BS_BUILD_VAL), v, c64);
   }
 }
 
@@ -296,7 +298,7 @@ __global__ void __launch_bounds__(256) build_kernel(BuildArgs a, bool c64) {
 #pragma unroll
       for (int s = 0; s < MAXS; ++s)
         if (s < G.S) {
-          const double2 v = load_val(a.vt, int64_t(vt0) + int64_t(pat) * G.S + s, c64);
+          const double2 v = load_val(a.vt, HS_BCHK(int64_t(vt0) + int64_t(pat) * G.S + s, a.n_vt, BS_BUILD_VT), c64);
           w[s] = make_double2(v.x, -v.y);  // the table holds conj(w)
         }
     } else {
@@ -328,7 +330,9 @@ __global__ void __launch_bounds__(256) value_table_kernel(BuildArgs a, const uin
   G.row(a, r, w);
 #pragma unroll
   for (int s = 0; s < MAXS; ++s)
-    if (s < G.S) store_val(vt, int64_t(vt0[g]) + int64_t(p) * G.S + s, make_double2(w[s].x, -w[s].y), c64);
+    if (s < G.S)
+      store_val(vt, HS_BCHK(int64_t(vt0[g]) + int64_t(p) * G.S + s, a.n_vt, BS_BUILD_VT), make_double2(w[s].x, -w[s].y),
+                c64);
 }
 
 // cs[2 (k n + j) + {0, 1}] = (cos, sin)(c_j * h[k]) for kind k, with c_j =
@@ -364,7 +368,7 @@ BuildArgs build_args(const hs_factors* f, const int* glist) {
   const hs_build_inputs& b = f->bin;
   return BuildArgs{f->d_vals, f->d_offs, f->d_rowbase, f->d_fac_D, f->d_fac_diag0, b.cs, b.th, b.x, b.z, b.cx,
                    b.gfirst, b.glast, b.basis, b.xdim, b.pivot, f->plan.N, b.smask, b.vt0, f->d_vt, b.kind,
-                   b.dir, int(f->plan.x.size()), glist};
+                   b.dir, int(f->plan.x.size()), glist, f->plan.total_elems, f->plan.total_vt};
 }
 
 }  // namespace

@@ -30,6 +30,7 @@
 #include <vector>
 
 #include "../../include/hs_dia.h"
+#include "bounds.cuh"
 #include "counters.h"
 #include "hs_internal.h"
 
@@ -354,7 +355,8 @@ template <typename R, int RB, int W, int RPT>
 __global__ void __launch_bounds__(32 * W) spmv_kernel(const typename CT<R>::T2* __restrict__ vals,
                                                       const int64_t* __restrict__ meta, int D,
                                                       const typename CT<R>::T2* __restrict__ x,
-                                                      typename CT<R>::T2* __restrict__ y, int64_t N, int n_rhs) {
+                                                      typename CT<R>::T2* __restrict__ y, int64_t N, int n_rhs,
+                                                      int64_t n_vals) {
   using T2 = typename CT<R>::T2;
   constexpr int TILE = 32 * RPT;
   __shared__ R part[W > 1 ? W - 1 : 1][RB][2][TILE];
@@ -380,13 +382,13 @@ __global__ void __launch_bounds__(32 * W) spmv_kernel(const typename CT<R>::T2* 
           const int64_t i = i0 + 32 * e;
           const int64_t c = i + d;
           const bool ok = (uint64_t(c) < uint64_t(N)) && (i < N);
-          const T2 v0 = vals[ok ? base + i : 0];
+          const T2 v0 = vals[HS_BCHK(ok ? base + i : 0, n_vals, hs::BS_DIA_VAL)];
           const R vx = ok ? v0.x : R(0), vy = ok ? v0.y : R(0);
           const int64_t cc = ok ? c : 0;
 #pragma unroll
           for (int q = 0; q < RB; ++q) {
             if (r0 + q < n_rhs) {
-              const T2 u = x[int64_t(r0 + q) * N + cc];
+              const T2 u = x[HS_BCHK(int64_t(r0 + q) * N + cc, int64_t(n_rhs) * N, hs::BS_DIA_X)];
               ax[e][q] = fma(vx, u.x, fma(-vy, u.y, ax[e][q]));
               ay[e][q] = fma(vx, u.y, fma(vy, u.x, ay[e][q]));
             }
@@ -967,7 +969,7 @@ cudaError_t launch_spmv_k(const hs_dia* a, const void* x, void* y, int n_rhs, cu
   cfg.blockDim = dim3(32 * W, 1u, 1u);
   const cudaError_t e = cudaLaunchKernelEx(&cfg, spmv_kernel<R, RB, W, kSpmvRPT>, (const T2*)a->d_vals,
                                            (const int64_t*)a->d_meta, int(a->offs.size()), (const T2*)x, (T2*)y,
-                                           a->N, n_rhs);
+                                           a->N, n_rhs, a->total);
   if (e == cudaSuccess) hs::note_launches();
   return e;
 }

@@ -420,10 +420,10 @@ __device__ __forceinline__ void qsweep_core(const Args& a, uint32_t u0, uint32_t
   for (int i = tid; i < a.n_rot; i += NT) {
     const int e = a.rot[i].cs;
     if (a.rot[i].fast) {
-      const double* q = a.rq + 4 * int64_t(e);
+      const double* q = a.rq + 4 * HS_BCHK(e, a.n_terms_g, BS_REG_TERM);
       rcs[i] = T2{R(q[0]), R(q[1])};
     } else {
-      const double* p = a.cs + 2 * int64_t(e);
+      const double* p = a.cs + 2 * HS_BCHK(e, a.n_terms_g, BS_REG_TERM);
       rcs[i] = T2{R(p[0]), R(p[1])};
     }
   }
@@ -432,13 +432,13 @@ __device__ __forceinline__ void qsweep_core(const Args& a, uint32_t u0, uint32_t
     for (int oi = tid; oi < a.n_ops; oi += NT) {
       const Op& op = a.ops[oi];
       if (op.type == OP_ROT && (op.flags & 1)) {
-        m *= a.rq[4 * int64_t(a.rot[op.idx].cs) + 2];
+        m *= a.rq[4 * HS_BCHK(a.rot[op.idx].cs, a.n_terms_g, BS_REG_TERM) + 2];
       } else if (op.type == OP_ROTN) {
 #pragma unroll
         for (int i = 0; i < B; ++i)
           if ((op.ku >> i) & 1) {
             const int slot = int((i < 4 ? (op.zthr >> (8 * i)) : (op.zrest >> (8 * (i - 4)))) & 0xffu);
-            m *= a.rq[4 * int64_t(a.rot[slot].cs) + 2];
+            m *= a.rq[4 * HS_BCHK(a.rot[slot].cs, a.n_terms_g, BS_REG_TERM) + 2];
           }
       }
     }
@@ -446,11 +446,11 @@ __device__ __forceinline__ void qsweep_core(const Args& a, uint32_t u0, uint32_t
     for (int o = 16; o > 0; o >>= 1) m *= __shfl_xor_sync(0xffffffffu, m, o);
     if (lane == 0) mpart[warp] = m;
   }
-  for (int t = tid; t < a.n_pterm; t += NT) thpi[t] = R(a.rq[4 * int64_t(a.pt[t].th) + 3]);
+  for (int t = tid; t < a.n_pterm; t += NT) thpi[t] = R(a.rq[4 * HS_BCHK(a.pt[t].th, a.n_terms_g, BS_REG_TERM) + 3]);
   for (int t = 0; t < a.n_tab; ++t) {
     const T2* g = reinterpret_cast<const T2*>(a.vt) + a.tab[t].vt0;
     const int s0 = a.tab[t].s0, n = a.tab[t].n;
-    for (int e = tid; e < n; e += NT) vts[s0 + e] = g[e];
+    for (int e = tid; e < n; e += NT) vts[s0 + e] = g[HS_BCHK(a.tab[t].vt0 + e, a.n_vt_g, BS_REG_VT) - a.tab[t].vt0];
   }
   const int n_ops = a.n_ops, n_cls = a.n_cls;
 
@@ -463,7 +463,7 @@ __device__ __forceinline__ void qsweep_core(const Args& a, uint32_t u0, uint32_t
   // first layout of the sweep) into the tile buffer.
   auto unit_base = [&](uint32_t unit) { return deposit_runs(unit & ((1u << a.n_tiles_log2) - 1u), a.rest); };
   auto unit_src = [&](uint32_t unit) {
-    return reinterpret_cast<const T2*>(a.src) + int64_t(unit >> a.n_tiles_log2) * a.N;
+    return reinterpret_cast<const T2*>(a.src) + HS_BCHK(unit >> a.n_tiles_log2, a.n_rhs, BS_REG_STATE) * a.N;
   };
   auto copy_in = [&](const Layout* L, uint32_t base, const T2* src) {
     const int n_thr = L->n_thr;
@@ -475,7 +475,8 @@ __device__ __forceinline__ void qsweep_core(const Args& a, uint32_t u0, uint32_t
     const uint32_t c0 = lc | (wb >> VB);
     const uint32_t s0 = swz(c0), g0 = global_of(c0 * V, m0, m1, sh) | base;
 #pragma unroll 4
-    for (int mm = 0; mm < NJ; ++mm) cp_async16(tile + (s0 ^ L->mswz[mm]) * V, src + (g0 ^ L->mglob[mm]));
+    for (int mm = 0; mm < NJ; ++mm)
+      cp_async16(tile + (s0 ^ L->mswz[mm]) * V, src + HS_BCHK(g0 ^ L->mglob[mm], a.N - (V - 1), BS_REG_STATE));
     cp_async_commit();
   };
   const Layout* L0 = slay + a.ops[0].idx;  // the first op is always a layout
@@ -487,7 +488,7 @@ __device__ __forceinline__ void qsweep_core(const Args& a, uint32_t u0, uint32_t
 
   for (uint32_t unit = u0; unit < u1; ++unit) {
     const uint32_t base = unit_base(unit);
-    T2* dst = reinterpret_cast<T2*>(a.dst) + int64_t(unit >> a.n_tiles_log2) * a.N;
+    T2* dst = reinterpret_cast<T2*>(a.dst) + HS_BCHK(unit >> a.n_tiles_log2, a.n_rhs, BS_REG_STATE) * a.N;
     // Per-tile phase constants, in this warp's copy: class sums of +-theta_j
     // (units of pi, each term reduced mod 2 in FP64 by the factor build) with
     // the signs of the tile's fixed bits, reduced mod 2 again; a constant class
@@ -623,9 +624,10 @@ __device__ __forceinline__ void qsweep_core(const Args& a, uint32_t u0, uint32_t
       for (int i = 0; i < B - VB; ++i)
         if ((j >> i) & 1) g ^= go[i + VB];
       if constexpr (V == 2) {
-        *reinterpret_cast<float4*>(dst + g) = make_float4(x[2 * j].x, x[2 * j].y, x[2 * j + 1].x, x[2 * j + 1].y);
+        *reinterpret_cast<float4*>(dst + HS_BCHK(g, a.N - 1, BS_REG_STATE)) =
+            make_float4(x[2 * j].x, x[2 * j].y, x[2 * j + 1].x, x[2 * j + 1].y);
       } else {
-        dst[g] = x[j];
+        dst[HS_BCHK(g, a.N, BS_REG_STATE)] = x[j];
       }
     }
   }
@@ -651,7 +653,7 @@ __global__ void __launch_bounds__(B == 5 ? 256 : 512, B == 5 ? 2 : 1) qlevel_ker
     if (pref[mid] <= int(blockIdx.x)) lo = mid; else hi = mid - 1;
   }
   const Args& a = p.descs[p.lvl_desc[p.off + lo]];
-  const uint32_t u = blockIdx.x - uint32_t(pref[lo]);
+  const uint32_t u = uint32_t(HS_BCHK(blockIdx.x - uint32_t(pref[lo]), a.n_units, BS_BATCH_JOB));
   qsweep_core<R, B>(a, u, u + 1, smem_raw, true);
 }
 
@@ -706,6 +708,8 @@ void fill_job(const hs_factors* f, Args& a, void* psi, int n_rhs) {
   a.rq = f->bin.rq;
   a.vt = f->d_vt;
   a.N = p.N;
+  a.n_vt_g = p.total_vt;
+  a.n_terms_g = int(p.x.size()) * p.n_kinds;
   a.n_rhs = n_rhs;
   a.n_tiles_log2 = p.n_qubits - a.tile_bits;
   a.n_units = (1 << a.n_tiles_log2) * n_rhs;

@@ -121,6 +121,8 @@ struct Args {
   const double* rq;  // register-sweep record per kind and term (FP64, see the factor build)
   const void* vt;    // value tables (storage type)
   int64_t N;
+  int64_t n_vt_g;    // extents of vt and of the per-term records (index checks only)
+  int n_terms_g;
   int n_rhs;
   int tile_bits;
   int n_tiles_log2;

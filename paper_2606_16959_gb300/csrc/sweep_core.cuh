@@ -6,6 +6,7 @@
 
 #include <cstdint>
 
+#include "bounds.cuh"
 #include "hs_internal.h"
 
 namespace hs {
@@ -35,6 +36,9 @@ struct SweepArgs {
   const int32_t* slot_tab;
   const int64_t* tab_rb;
   int64_t N;
+  // Extents of vals, vt, slot_u / slot_tab and tab_rb (index checks only).
+  int64_t n_vals, n_vt_g;
+  int n_slot_g, n_tab_g;
   int n_rhs;
   int rhs_block;
   int tile_bits;
@@ -277,7 +281,7 @@ __device__ __forceinline__ void sweep_reg(const SweepArgs& a, T2* tile, T2* othe
     for (int i = 0; i < ROWS; ++i) xr[i] = acc[i];
   }
 #pragma unroll
-  for (int i = 0; i < ROWS; ++i) dst_state[grow[i]] = xr[i];
+  for (int i = 0; i < ROWS; ++i) dst_state[HS_BCHK(grow[i], a.N, BS_SWEEP_STATE)] = xr[i];
 }
 
 // Block of TS / ROWS threads; thread t owns local rows t + i * blockDim.x.
@@ -327,7 +331,7 @@ __device__ __forceinline__ void sweep_tiles(const SweepArgs& a, uint32_t u0, uin
       const int mid = (lo + hi + 1) >> 1;
       if (a.fmslot[mid] <= t) lo = mid; else hi = mid - 1;
     }
-    const int gs = a.fslot0[lo] + (t - a.fmslot[lo]);
+    const int gs = int(HS_BCHK(a.fslot0[lo] + (t - a.fmslot[lo]), a.n_slot_g, BS_SWEEP_SLOT));
     const uint32_t u = a.slot_u[gs];
     mslot[t] = SlotMeta{u, local_of(u, m0, m1, sh), a.ftab_s[lo] + (a.slot_tab[gs] - a.ftab_g[lo]),
                         a.fvt[lo] >= 0 ? -1 : lo * a.stage_planes + (t - a.fmslot[lo])};
@@ -338,7 +342,7 @@ __device__ __forceinline__ void sweep_tiles(const SweepArgs& a, uint32_t u0, uin
       const int mid = (lo + hi + 1) >> 1;
       if (a.ftab_s[mid] <= e) lo = mid; else hi = mid - 1;
     }
-    mtab[e] = a.tab_rb[a.ftab_g[lo] + (e - a.ftab_s[lo])];
+    mtab[e] = a.tab_rb[HS_BCHK(a.ftab_g[lo] + (e - a.ftab_s[lo]), a.n_tab_g, BS_SWEEP_TAB)];
   }
   // Value tables: entry e belongs to the last factor whose shared start is <= e
   // (factors without a table have empty ranges, so that factor owns it).
@@ -350,7 +354,7 @@ __device__ __forceinline__ void sweep_tiles(const SweepArgs& a, uint32_t u0, uin
         const int mid = (lo + hi + 1) >> 1;
         if (a.fvts[mid] <= e) lo = mid; else hi = mid - 1;
       }
-      vts[e] = gvt[a.fvt[lo] + (e - a.fvts[lo])];
+      vts[e] = gvt[HS_BCHK(a.fvt[lo] + (e - a.fvts[lo]), a.n_vt_g, BS_SWEEP_VT)];
     }
   }
   __syncthreads();
@@ -385,12 +389,15 @@ __device__ __forceinline__ void sweep_tiles(const SweepArgs& a, uint32_t u0, uin
       const uint32_t r = global_of(c * V, m0, m1, sh) | base;
       const int64_t* tab = mtab + m.tab;
       const uint32_t pat = pattern_of(r, m.u);
+#ifdef HS_DEBUG_BOUNDS
+      HS_BCHK(m.tab + ((m.u & 1u) ? (pat | 1u) : pat), a.n_mtab, BS_SWEEP_TAB);
+#endif
       if (V == 1 || !(m.u & 1u)) {
-        cp_async16(dst_s, vals + tab[pat] + r);
+        cp_async16(dst_s, vals + HS_BCHK(tab[pat] + r, a.n_vals - (V - 1), BS_SWEEP_VAL));
       } else {
         // u flips bit 0: the two rows of a 16-byte chunk lie on different diagonals.
-        cp_async8(dst_s, vals + tab[pat] + r);
-        cp_async8(dst_s + 1, vals + tab[pat | 1u] + r + 1);
+        cp_async8(dst_s, vals + HS_BCHK(tab[pat] + r, a.n_vals, BS_SWEEP_VAL));
+        cp_async8(dst_s + 1, vals + HS_BCHK(tab[pat | 1u] + r + 1, a.n_vals, BS_SWEEP_VAL));
       }
     }
   };
@@ -412,7 +419,7 @@ __device__ __forceinline__ void sweep_tiles(const SweepArgs& a, uint32_t u0, uin
   }
   for (uint32_t c = threadIdx.x; c < n_chunks; c += NT) {
     const uint32_t l = c * V;
-    const T2* sp = src + int64_t(rhs0) * a.N + (global_of(l, m0, m1, sh) | base);
+    const T2* sp = src + int64_t(rhs0) * a.N + HS_BCHK(global_of(l, m0, m1, sh) | base, a.N - (V - 1), BS_SWEEP_STATE);
     T2* tp = tile + l;
     for (int q = 0; q < nrb; ++q, sp += a.N, tp += TS) cp_async16(tp, sp);
   }
@@ -435,7 +442,7 @@ __device__ __forceinline__ void sweep_tiles(const SweepArgs& a, uint32_t u0, uin
   // Store the tile.
   for (uint32_t c = threadIdx.x; c < n_chunks; c += NT) {
     const uint32_t l = c * V;
-    T2* dp = dst + int64_t(rhs0) * a.N + (global_of(l, m0, m1, sh) | base);
+    T2* dp = dst + int64_t(rhs0) * a.N + HS_BCHK(global_of(l, m0, m1, sh) | base, a.N - (V - 1), BS_SWEEP_STATE);
     const T2* tp = tile + l;
     for (int q = 0; q < nrb; ++q, dp += a.N, tp += TS)
       *reinterpret_cast<uint4*>(dp) = *reinterpret_cast<const uint4*>(tp);

@@ -18,7 +18,10 @@ HS_METHOD_AUTO, HS_METHOD_PLAIN, HS_METHOD_FUSED, HS_METHOD_REG = 0, 1, 2, 3
 HS_MAX_QUBITS = 30
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libhs.so")
+# HS_DEBUG_BOUNDS=1 in the environment selects the index-checking build
+# (_build.build(debug=True)); otherwise the ordinary one.
+DEBUG_BOUNDS = os.environ.get("HS_DEBUG_BOUNDS", "") not in ("", "0")
+LIB_PATH = os.path.join(_HERE, "_build_debug" if DEBUG_BOUNDS else "_build", "libhs.so")
 
 # Every symbol declared in include/hs.h and include/hs_dia.h.
 EXPORTS = (
@@ -29,7 +32,7 @@ EXPORTS = (
     "hs_batch_free_async",
     "hs_dia_from_terms", "hs_dia_from_masks", "hs_dia_create", "hs_spgemm", "hs_spme", "hs_estimate_timesteps",
     "hs_spmv", "hs_dia_evolve", "hs_dia_convert", "hs_dia_info", "hs_dia_get", "hs_dia_free",
-    "hs_kernel_launches", "hs_expectation", "hs_build_factors_ex", "hs_factors_sequence",
+    "hs_kernel_launches", "hs_debug_bounds", "hs_expectation", "hs_build_factors_ex", "hs_factors_sequence",
     "hs_build_factors_td", "hs_evolve_td", "hs_factors_set_drive", "hs_dia_evolve_td",
     "hs_parse_terms", "hs_evolve_batch", "hs_batch_autotune",
 )
@@ -131,11 +134,22 @@ def lib() -> ctypes.CDLL:
         L.hs_batch_autotune.argtypes = [ctypes.POINTER(BatchJob), sz, vp, ctypes.POINTER(BatchOpts)]
         L.hs_kernel_launches.argtypes = []
         L.hs_kernel_launches.restype = ctypes.c_uint64
+        L.hs_debug_bounds.argtypes = [ctypes.POINTER(ctypes.c_uint64), i]
         for name in EXPORTS:
             if name not in ("hs_free_factors", "hs_last_error", "hs_batch_free", "hs_dia_free", "hs_kernel_launches"):
                 getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
+
+
+def hs_debug_bounds(reset: bool = False):
+    """Index-check record of the library: None for the ordinary build, else
+    (failures, site, index, extent) of the first failure (zeros when none)."""
+    w = (ctypes.c_uint64 * 4)()
+    rc = lib().hs_debug_bounds(w, int(bool(reset)))
+    if rc < 0:
+        _check(rc)
+    return None if rc == 0 else tuple(int(v) for v in w)
 
 
 def hs_kernel_launches() -> int:

@@ -41,3 +41,18 @@ def oracle():
     import oracle as o
     o.build()
     return o
+
+
+@pytest.fixture(autouse=True)
+def _bounds_word(request):
+    """In the index-checking build (HS_DEBUG_BOUNDS=1), every GPU test must
+    leave the library's bounds words at zero."""
+    yield
+    if request.node.get_closest_marker("gpu") is None or os.environ.get("HS_DEBUG_BOUNDS", "") in ("", "0"):
+        return
+    import torch
+    from paper_2606_16959_gb300 import hs
+    torch.cuda.synchronize()
+    w = hs.hs_debug_bounds(reset=True)
+    assert w is not None, "HS_DEBUG_BOUNDS=1 but the loaded library has no index checks"
+    assert w[0] == 0, f"{w[0]} out-of-range indices; first at site {w[1]}: index {w[2]}, extent {w[3]}"

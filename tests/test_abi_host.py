@@ -38,6 +38,27 @@ def test_exports_every_declared_symbol(lib):
     assert sorted(hs.EXPORTS) == decl
 
 
+def test_debug_bounds_word_of_ordinary_build(lib):
+    """The ordinary build has no index checks: hs_debug_bounds says so without
+    touching a device, and rejects a null output."""
+    if hs.DEBUG_BOUNDS:
+        pytest.skip("the index-checking build is loaded")
+    assert hs.hs_debug_bounds() is None
+    assert lib.hs_debug_bounds(None, 0) == hs.HS_EINVAL
+
+
+def test_debug_bounds_sources():
+    """Every kernel translation unit that addresses factor values, tables or
+    states goes through the index check of the HS_DEBUG_BOUNDS build."""
+    csrc = os.path.join(ROOT, "paper_2606_16959_gb300", "csrc")
+    sites = {}
+    for name in ("sweep_core.cuh", "apply.cu", "qsweep.cu", "build.cu", "dia.cu"):
+        sites[name] = set(re.findall(r"BS_[A-Z_]+", open(os.path.join(csrc, name)).read()))
+    used = set().union(*sites.values())
+    declared = set(re.findall(r"^\s*(BS_[A-Z_]+)\s*=", open(os.path.join(csrc, "bounds.cuh")).read(), flags=re.M))
+    assert declared and used == declared, (declared - used, used - declared)
+
+
 def test_plan_rejects_bad_input(lib):
     with pytest.raises(hs.HSError) as e:
         hs.hs_plan_factors([1], [0], 0, 4)
