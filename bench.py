@@ -48,6 +48,9 @@ def parse_args():
                     choices=["heis16", "maxcut24", "tfim10", "batch256", "serve", "taylor16", "anneal24"])
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--serve-rate", type=float, default=500.0)
+    ap.add_argument("--serve-find-rate", action="store_true",
+                    help="serve: search the highest Poisson rate whose queue stays bounded over 20 s and report "
+                         "p50/p99 there, at half of it and at --serve-rate")
     ap.add_argument("--autotune", type=int, default=1)
     ap.add_argument("--batch-jobs", type=int, default=256)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
@@ -186,9 +189,9 @@ TUNE_CACHE = os.path.join(ROOT, "paper_2606_16959_gb300", "_build", "autotune_be
 # Device-code sources of each kernel: a summary's DRAM figures count only while
 # these are unchanged since the capture.
 KERNEL_SOURCES = {"sweep_kernel": ("apply.cu", "sweep_core.cuh", "hs_internal.h"),
-                  "qsweep_kernel": ("qsweep.cu", "qsweep.h", "sweep_core.cuh", "hs_internal.h"),
+                  "qsweep_kernel": ("qsweep.cu", "qsweep.h", "sweep_core.cuh", "bounds.cuh", "hs_internal.h"),
                   "batch_level_kernel": ("batch.cu", "sweep_core.cuh", "hs_internal.h"),
-                  "batch_qsweep_kernel": ("qsweep.cu", "qsweep.h", "batch.cu", "sweep_core.cuh", "hs_internal.h"),
+                  "qlevel_kernel": ("qsweep.cu", "qsweep.h", "batch.cu", "sweep_core.cuh", "bounds.cuh", "hs_internal.h"),
                   "spmv_kernel": ("dia.cu",)}
 
 
@@ -512,7 +515,7 @@ def time_batch(jobs, args, world, rank, dtype):
     return dict(units=info[2], levels=info[0], ctas=info[1], separate=info[3], step_ms=step_ms, launch_ms=launch_ms,
                 total_ms=total_ms, alg_bytes=alg, clocks=clocks, max_norm_drift=float(np.max(np.abs(norms - 1.0))),
                 launches=hs.hs_kernel_launches() - l0, bopts=bopts,
-                kernel="batch_qsweep_kernel" if bopts.get("method") == 3 else "batch_level_kernel")
+                kernel="qlevel_kernel" if bopts.get("method") == 3 else "batch_level_kernel")
 
 
 def time_batch_e2e(jobs, args, dtype, bopts):
@@ -946,6 +949,71 @@ def run_taylor(args, rank, world):
         dist.destroy_process_group()
 
 
+def serve_batch_opts(jobs, n=16):
+    """Batch options for served groups: hs_batch_autotune on a group of the
+    stream's first requests (factors and seeded states built on the device)."""
+    import torch
+    from paper_2606_16959_gb300 import hs
+    sel = jobs[:n]
+    facs, states = [], []
+    for j in sel:
+        facs.append(hs.hs_build_factors(j.ham.labels, j.ham.coeffs, j.t, j.n_steps, j.budget, "c64"))
+        g = torch.Generator(device="cuda")
+        g.manual_seed(int(j.seed))
+        st = torch.complex(torch.randn(1 << j.ham.n_qubits, generator=g, device="cuda"),
+                           torch.randn(1 << j.ham.n_qubits, generator=g, device="cuda"))
+        states.append(st / torch.linalg.vector_norm(st))
+    opts = hs.hs_batch_autotune([(f, st, j.n_steps) for f, st, j in zip(facs, states, sel)])
+    for f in facs:
+        f.close()
+    torch.cuda.synchronize()
+    return opts
+
+
+def serve_trial(rate, seconds, opts, seed=1005):
+    """One realtime Poisson stream through a fresh server; its stats with the
+    offered rate and whether the queue stayed bounded (the median latency of
+    the last quarter of the requests within 1.5x that of the second quarter
+    plus 25 ms)."""
+    from paper_2606_16959_gb300 import serve, workloads as W
+    reqs = serve.requests_from_jobs(W.serve_stream(rate=rate, duration=seconds, seed=seed))
+    st = serve.Server(batch_opts=opts).run(reqs, realtime=True)
+    st.update(rate=rate, seconds=seconds, bounded=bool(st["p50_q4_ms"] <= 1.5 * st["p50_q2_ms"] + 25.0))
+    return st
+
+
+def find_serve_rate(args, opts):
+    """Highest bounded rate over 20-s streams: start from the capacity of an
+    all-at-once run, step by 1.25x until the boundary, then report p50/p99 at
+    that rate, at half of it and at --serve-rate."""
+    from paper_2606_16959_gb300 import serve, workloads as W
+    probe = serve.requests_from_jobs(W.serve_stream(rate=args.serve_rate, duration=2.0, seed=1005))
+    for r in probe:
+        r.arrival = 0.0
+    cap = serve.Server(batch_opts=opts).run(probe, realtime=False)
+    capacity = cap["n"] / max(cap["makespan_s"], 1e-9)
+    trials = []
+    rate = 0.8 * capacity
+    st = serve_trial(rate, 20.0, opts)
+    trials.append(st)
+    step = 1.25 if st["bounded"] else 1 / 1.25
+    for _ in range(6):
+        nxt = serve_trial(rate * step, 20.0, opts)
+        trials.append(nxt)
+        if nxt["bounded"] != st["bounded"]:
+            break
+        rate, st = rate * step, nxt
+    good = [t for t in trials if t["bounded"]]
+    best = max(good, key=lambda t: t["rate"]) if good else None
+    half = serve_trial(best["rate"] / 2, 20.0, opts) if best else None
+    conf = serve_trial(args.serve_rate, 20.0, opts)
+    keys = ("rate", "n", "p50_ms", "p99_ms", "mean_ms", "bounded", "backlog_at_last_arrival", "drain_s",
+            "p50_q2_ms", "p50_q4_ms", "throughput", "peak_bytes")
+    pick = lambda t: None if t is None else {k: t[k] for k in keys}
+    return dict(capacity_req_s=capacity, capacity_run={"n": cap["n"], "makespan_s": cap["makespan_s"]},
+                sustainable=pick(best), half=pick(half), configured=pick(conf), trials=[pick(t) for t in trials])
+
+
 def run_serve(args, rank, world):
     """A step = serving one Poisson request stream (arrivals over --serve-seconds,
     then the drain).  Value = amplitude updates of all requests / (last
@@ -957,11 +1025,19 @@ def run_serve(args, rank, world):
     desc = (f"Poisson stream {args.serve_rate:g} req/s for {args.serve_seconds:g} s (seed 1005): TFIM, Heisenberg, "
             "MaxCut (n~U{12..24}) and one-hot TSP (16 qubits), t~U[0.5,2], steps~U{10..100}, complex64, "
             "per-family budgets; HBM admission")
+    bopts = serve_batch_opts(jobs)
     for _ in range(args.warmup):
         warm = serve.requests_from_jobs(jobs[:8])
         for r in warm:
             r.arrival = 0.0
-        serve.Server().run(warm, realtime=False)
+        serve.Server(batch_opts=bopts).run(warm, realtime=False)
+    if args.serve_find_rate:
+        if rank == 0:
+            res = find_serve_rate(args, bopts)
+            print(json.dumps({"workload": "serve", "search": "sustainable Poisson rate", "batch_options": bopts,
+                              "description": desc.replace(f" {args.serve_rate:g} req/s for {args.serve_seconds:g} s",
+                                                          ""), **res}))
+        return
     runs = []
     barrier(world)
     sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
@@ -971,7 +1047,7 @@ def run_serve(args, rank, world):
     l0 = hs.hs_kernel_launches()
     for _ in range(args.steps):
         reqs = serve.requests_from_jobs(jobs)
-        runs.append(serve.Server().run(reqs, realtime=True))
+        runs.append(serve.Server(batch_opts=bopts).run(reqs, realtime=True))
     served_launches = hs.hs_kernel_launches() - l0
     clocks = sampler.stop() if sampler else None
     barrier(world)
@@ -984,8 +1060,12 @@ def run_serve(args, rank, world):
             "warmup": args.warmup, "ms_per_step": 1000 * span / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
             "config": {"workload": "serve", "description": desc, "requests_per_step": len(jobs),
-                       "l2": "inputs larger than L2 (factor sets up to 16 GB)"},
+                       "l2": "inputs larger than L2 (factor sets up to 16 GB)", "batch_options": bopts},
             "latency_ms": {"p50": p50, "p99": p99, "mean": statistics.mean([r["mean_ms"] for r in runs])},
+            "queue": {"backlog_at_last_arrival": max(r["backlog_at_last_arrival"] for r in runs),
+                      "drain_s": max(r["drain_s"] for r in runs),
+                      "p50_q2_ms": statistics.median([r["p50_q2_ms"] for r in runs]),
+                      "p50_q4_ms": statistics.median([r["p50_q4_ms"] for r in runs])},
             "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 32 * len(jobs)},
             "gpu_launches": served_launches, "clocks": clocks, "peak_admitted_bytes": max(r["peak_bytes"] for r in runs)}
     if rank == 0:

@@ -52,7 +52,9 @@ enum {
   HS_EINVAL = -1,   /* bad argument: label, length, n_qubits, t, steps, budget, coefficient */
   HS_ENOMEM = -2,   /* device allocation failed */
   HS_ECUDA = -3,    /* a CUDA runtime call or kernel launch failed */
-  HS_ETIMEOUT = -4, /* a bounded device-side wait ran out */
+  HS_ETIMEOUT = -4, /* reserved for a bounded device-side wait that ran out; no kernel of this
+                       library waits on a flag, a peer or an mbarrier (dependent launches
+                       are ordered by the stream), so no call returns it */
   HS_EDTYPE = -5    /* dtype mismatch between arguments */
 };
 

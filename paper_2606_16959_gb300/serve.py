@@ -281,9 +281,20 @@ class Server:
         t_first = min(r.arrival for r in requests)
         t_last = max((r.done for r in served), default=t_first)
         updates = sum(r.updates for r in served)
+        # Queue growth: requests still in the system when the last one arrived,
+        # the drain after it, and the median latency of the second and the last
+        # quarter of the requests by arrival (equal when the queue is bounded).
+        t_arr = max(r.arrival for r in requests)
+        by_arr = sorted(served, key=lambda r: r.arrival)
+        q = max(1, len(by_arr) // 4)
+
+        def _p50(rs):
+            return float(np.median([r.done - r.arrival for r in rs]) * 1e3) if rs else 0.0
+        growth = dict(backlog_at_last_arrival=sum(r.done > t_arr for r in served), drain_s=max(0.0, t_last - t_arr),
+                      p50_q2_ms=_p50(by_arr[q:2 * q]), p50_q4_ms=_p50(by_arr[-q:]))
         return dict(n=len(served), n_cancelled=sum(r.cancelled for r in requests),
                     n_failed=sum(r.error is not None for r in requests),
                     p50_ms=float(np.percentile(lat, 50) * 1e3), p99_ms=float(np.percentile(lat, 99) * 1e3),
                     mean_ms=float(lat.mean() * 1e3), makespan_s=t_last - t_first, updates=updates,
                     throughput=updates / max(t_last - t_first, 1e-9), peak_bytes=self.peak_used,
-                    alloc_failures=self.n_alloc_failures, launches=hs.hs_kernel_launches() - l0)
+                    alloc_failures=self.n_alloc_failures, launches=hs.hs_kernel_launches() - l0, **growth)
