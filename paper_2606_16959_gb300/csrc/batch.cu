@@ -181,6 +181,7 @@ struct hs_batch {
   struct Level {
     int off, count;
     int64_t ctas;
+    bool full = false;  // register sweeps: some descriptor of the level needs the full kernel
   };
   std::vector<Level> levels;
   int max_count = 0;
@@ -272,7 +273,7 @@ int enqueue_batch(hs_batch* b, cudaStream_t s) {
     for (const hs_batch::QGroup& g : b->qgroups)
       for (const hs_batch::Level& L : g.levels) {
         hs::q::LevelArgs a{b->d_qdescs, g.d_lvl_desc, g.d_lvl_prefix, L.off, L.count, uint32_t(g.prefix_smem)};
-        cudaError_t e = hs::q::launch_qlevel(b->dtype, b->reg_bits, g.tile_bits, a, L.ctas, g.smem, s);
+        cudaError_t e = hs::q::launch_qlevel(b->dtype, b->reg_bits, L.full, g.tile_bits, a, L.ctas, g.smem, s);
         if (e != cudaSuccess)
           return hs::report_error(HS_ECUDA, std::string("batch level launch: ") + cudaGetErrorString(e));
       }
@@ -393,6 +394,7 @@ int create_reg_batch(const hs_batch_job* jobs, size_t n_jobs, const hs_batch_opt
         if (k >= gj.descs.size()) continue;
         g.lvl_desc.push_back(gj.descs[k]);
         g.lvl_prefix.push_back(int(L.ctas));
+        L.full = L.full || b->qdescs[gj.descs[k]].full != 0;
         L.ctas += gj.units;
         ++L.count;
       }

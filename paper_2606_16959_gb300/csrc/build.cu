@@ -338,10 +338,10 @@ __global__ void __launch_bounds__(256) value_table_kernel(BuildArgs a, const uin
 // cs[2 (k n + j) + {0, 1}] = (cos, sin)(c_j * h[k]) for kind k, with c_j =
 // coeff[j], or coeff[j] + f coeff1[j] (f = *fval, the product rounded before
 // the sum, no fused multiply-add) for a time-dependent set.
-// rq[4 (k n + j) + {0..3}]: what a register sweep needs of the rotation: the
-// ratio of the smaller to the larger of |cos|, |sin| (tan or cot), its form
-// (0: tan, 1: cot), the larger factor (cos or sin, signed) and theta / pi
-// reduced to [-1, 1].
+// rq[4 (k n + j) + {0..3}]: what a register sweep needs of the rotation
+// exp(-i theta P) = cos(theta') (I - i tan(theta') P) (-i P)^k, theta = theta'
+// + k pi / 2 with |theta'| <= pi / 4: tan(theta'), k mod 4, cos(theta') and
+// theta / pi reduced to [-1, 1].
 __global__ void sincos_kernel(const double* coeff, const double* coeff1, const double* fval, const double* h,
                               int n_kinds, double* cs, double* th, double* rq, int n) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -355,12 +355,19 @@ __global__ void sincos_kernel(const double* coeff, const double* coeff1, const d
     sincos(theta, &s, &co);
     cs[2 * e] = co;
     cs[2 * e + 1] = s;
-    const bool tan_form = fabs(s) <= fabs(co);
-    rq[4 * e] = tan_form ? s / co : co / s;
-    rq[4 * e + 1] = tan_form ? 0.0 : 1.0;
-    rq[4 * e + 2] = tan_form ? co : s;
-    const double u = theta * 0.318309886183790671537767526745;
-    rq[4 * e + 3] = u - 2.0 * rint(0.5 * u);
+    // theta = pi u (mod 2 pi), u in [-1, 1]; u = v + k / 2 with k = rint(2 u)
+    // and |v| <= 1/4 (an exact subtraction), so that
+    // exp(-i theta P) = cos(pi v) (I - i tan(pi v) P) (-i P)^k.
+    const double u0 = theta * 0.318309886183790671537767526745;
+    const double u = u0 - 2.0 * rint(0.5 * u0);
+    const double kh = rint(2.0 * u);
+    const double v = u - 0.5 * kh;
+    double sv, cv;
+    sincospi(v, &sv, &cv);
+    rq[4 * e] = sv / cv;
+    rq[4 * e + 1] = double(int(kh) & 3);
+    rq[4 * e + 2] = cv;
+    rq[4 * e + 3] = u;
   }
 }
 

@@ -394,6 +394,9 @@ bool plan_qsweep(const hs_factors* f, const std::vector<int>& factors, uint32_t 
   a.n_pterm = int(pts.size());
   std::copy(cls.begin(), cls.end(), a.cls);
   std::copy(pts.begin(), pts.end(), a.pt);
+  a.full = 0;
+  for (int i = 0; i < a.n_ops; ++i)
+    if (a.ops[i].type == OP_TAB || (a.ops[i].type == OP_ROT && !(a.ops[i].flags & 1))) a.full = 1;
   return true;
 }
 

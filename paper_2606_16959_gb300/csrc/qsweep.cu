@@ -69,36 +69,49 @@ __device__ __forceinline__ T2 cmul(T2 a, R bx, R by) {
 // ROT: x <- (cos I - i sin P_j) x for one term whose flips are the register
 // coordinates KU.  Row k's partner is k ^ KU; the off-diagonal coefficient of
 // row k is sin * i^q * (-1)^popcount(z & r_{k ^ KU}), r_k the global row.
+//
+// A term with y = 0 and z = 0 (P = X on the flipped qubits) takes the factor
+// build's split exp(-i theta P) = cos(theta') (I - i t P) (-i P)^k, t =
+// tan(theta'), |theta'| <= pi / 4: rot_tan applies I - i t P with two fused
+// multiply-adds per amplitude, cos(theta') and (-i)^k go into the sweep's
+// scale, and an odd k swaps the partner rows (flip_pairs) at the end of the
+// op, so the rotation itself has no data-dependent branch.
 // ---------------------------------------------------------------------------
 template <typename R, int NR, int KU>
+__device__ __forceinline__ void rot_tan(typename C2<R>::T (&x)[NR], R t) {
+  using T2 = typename C2<R>::T;
+  constexpr int HB = highest_bit(KU);
+#pragma unroll
+  for (int k = 0; k < NR; ++k) {
+    if (k & HB) continue;
+    const int k2 = k ^ KU;
+    const T2 b1 = x[k], b2 = x[k2];
+    x[k] = T2{fma(t, b2.y, b1.x), fma(-t, b2.x, b1.y)};
+    x[k2] = T2{fma(t, b1.y, b2.x), fma(-t, b1.x, b2.y)};
+  }
+}
+
+template <typename R, int NR, int KU>
+__device__ __forceinline__ void flip_pairs(typename C2<R>::T (&x)[NR]) {
+  using T2 = typename C2<R>::T;
+  constexpr int HB = highest_bit(KU);
+#pragma unroll
+  for (int k = 0; k < NR; ++k) {
+    if (k & HB) continue;
+    const T2 b = x[k];
+    x[k] = x[k ^ KU];
+    x[k ^ KU] = b;
+  }
+}
+
+template <typename R, int NR, int KU>
 __device__ __forceinline__ void rot_ku(typename C2<R>::T (&x)[NR], R c, R s, bool fast, int q, uint32_t zk,
-                                       int sb) {
+                                       int sb, bool flip) {
   using T2 = typename C2<R>::T;
   constexpr int HB = highest_bit(KU);
   if (fast) {
-    // y = 0, z = 0: cos I - i sin X_u = m (u I - i v X_u) with the larger of
-    // |cos|, |sin| factored out as m (applied once per sweep, see the
-    // prologue): here c holds the ratio and s the form, 0: (u, v) = (c, 1)...
-    // i.e. form 0 is I - i tan X (m = cos), form 1 is cot I - i X (m = sin).
-    if (s == R(0)) {
-#pragma unroll
-      for (int k = 0; k < NR; ++k) {
-        if (k & HB) continue;
-        const int k2 = k ^ KU;
-        const T2 b1 = x[k], b2 = x[k2];
-        x[k] = T2{fma(c, b2.y, b1.x), fma(-c, b2.x, b1.y)};
-        x[k2] = T2{fma(c, b1.y, b2.x), fma(-c, b1.x, b2.y)};
-      }
-    } else {
-#pragma unroll
-      for (int k = 0; k < NR; ++k) {
-        if (k & HB) continue;
-        const int k2 = k ^ KU;
-        const T2 b1 = x[k], b2 = x[k2];
-        x[k] = T2{fma(c, b1.x, b2.y), fma(c, b1.y, -b2.x)};
-        x[k2] = T2{fma(c, b2.x, b1.y), fma(c, b2.y, -b1.x)};
-      }
-    }
+    rot_tan<R, NR, KU>(x, c);
+    if (flip) flip_pairs<R, NR, KU>(x);
     return;
   }
   const R qx = (q == 0) ? s : (q == 2 ? -s : R(0));
@@ -176,18 +189,50 @@ __device__ __forceinline__ void tab_ku(typename C2<R>::T (&x)[NR], const typenam
   }
 }
 
-// ROTN: commuting X rotations on distinct single register bits, one
-// compile-time body per bit (no dispatch on the flip).
-template <typename R, int NR, int I, int B>
-__device__ __forceinline__ void rot_run(typename C2<R>::T (&x)[NR], const Op& op, const typename C2<R>::T* rcs) {
+// ROTN: commuting X rotations on distinct single register bits (tan form,
+// see ROT), the slot of register bit i in byte i of (zthr, zrest).  The full
+// run and the run without bit 0 are straight-line bodies; any other run tests
+// its bits.  The odd-k swaps follow the whole run (every factor of the run is
+// a function of its own X, so they commute).
+__device__ __forceinline__ int rotn_slot(const Op& op, int i) {
+  return int((i < 4 ? (op.zthr >> (8 * i)) : (op.zrest >> (8 * (i - 4)))) & 0xffu);
+}
+
+template <typename R, int NR, int B, int MASK, int I>
+__device__ __forceinline__ void rotn_fixed(typename C2<R>::T (&x)[NR], const Op& op, const typename C2<R>::T* rcs) {
   if constexpr (I < B) {
-    if ((op.ku >> I) & 1) {
-      const int slot = int((I < 4 ? (op.zthr >> (8 * I)) : (op.zrest >> (8 * (I - 4)))) & 0xffu);
-      const typename C2<R>::T cs = rcs[slot];
-      rot_ku<R, NR, (1 << I)>(x, cs.x, cs.y, true, 0, 0u, 0);
-    }
-    rot_run<R, NR, I + 1, B>(x, op, rcs);
+    if constexpr (((MASK >> I) & 1) != 0) rot_tan<R, NR, (1 << I)>(x, rcs[rotn_slot(op, I)].x);
+    rotn_fixed<R, NR, B, MASK, I + 1>(x, op, rcs);
   }
+}
+
+template <typename R, int NR, int B, int I>
+__device__ __forceinline__ void rotn_any(typename C2<R>::T (&x)[NR], const Op& op, const typename C2<R>::T* rcs) {
+  if constexpr (I < B) {
+    if ((op.ku >> I) & 1) rot_tan<R, NR, (1 << I)>(x, rcs[rotn_slot(op, I)].x);
+    rotn_any<R, NR, B, I + 1>(x, op, rcs);
+  }
+}
+
+template <typename R, int NR, int B, int I>
+__device__ __forceinline__ void flip_run(typename C2<R>::T (&x)[NR], uint32_t fl) {
+  if constexpr (I < B) {
+    if ((fl >> I) & 1) flip_pairs<R, NR, (1 << I)>(x);
+    flip_run<R, NR, B, I + 1>(x, fl);
+  }
+}
+
+template <typename R, int NR, int B>
+__device__ __forceinline__ void rot_run(typename C2<R>::T (&x)[NR], const Op& op, const typename C2<R>::T* rcs,
+                                        uint32_t fl) {
+  constexpr int FULL = (1 << B) - 1;
+  if (op.ku == FULL)
+    rotn_fixed<R, NR, B, FULL, 0>(x, op, rcs);
+  else if (op.ku == (FULL & ~1))
+    rotn_fixed<R, NR, B, (FULL & ~1), 0>(x, op, rcs);
+  else
+    rotn_any<R, NR, B, 0>(x, op, rcs);
+  if (fl) flip_run<R, NR, B, 0>(x, fl);
 }
 
 // DROT: x[k] <- (cos - i sin (-1)^popcount(z & r_k)) x[k], the rotation of one
@@ -209,14 +254,30 @@ __device__ __forceinline__ void diag_rot(typename C2<R>::T (&x)[NR], R c, R s, u
 
 template <typename R, int NR>
 __device__ __forceinline__ void rot_dispatch(typename C2<R>::T (&x)[NR], int ku, R c, R s, bool fast, int q,
-                                          uint32_t zk, int sb) {
+                                          uint32_t zk, int sb, bool flip) {
   switch (ku) {
 #define HS_Q_ROT_CASE(K) \
   case K:                \
-    if constexpr (K < NR) rot_ku<R, NR, K>(x, c, s, fast, q, zk, sb); \
+    if constexpr (K < NR) rot_ku<R, NR, K>(x, c, s, fast, q, zk, sb, flip); \
     break;
     HS_Q_KU_LIST(HS_Q_ROT_CASE)
 #undef HS_Q_ROT_CASE
+    default: break;
+  }
+}
+
+template <typename R, int NR>
+__device__ __forceinline__ void tan_dispatch(typename C2<R>::T (&x)[NR], int ku, R t, bool flip) {
+  switch (ku) {
+#define HS_Q_TAN_CASE(K)                  \
+  case K:                                 \
+    if constexpr (K < NR) {               \
+      rot_tan<R, NR, K>(x, t);            \
+      if (flip) flip_pairs<R, NR, K>(x);  \
+    }                                     \
+    break;
+    HS_Q_KU_LIST(HS_Q_TAN_CASE)
+#undef HS_Q_TAN_CASE
     default: break;
   }
 }
@@ -364,7 +425,7 @@ __device__ __forceinline__ void phase_apply(typename C2<R>::T (&x)[NR], const Ph
 // land while the current unit finishes in registers and writes its rows
 // straight back to HBM.
 // ---------------------------------------------------------------------------
-template <typename R, int B>
+template <typename R, int B, bool FULL>
 __device__ __forceinline__ void qsweep_core(const Args& a, uint32_t u0, uint32_t u1, unsigned char* smem_raw,
                                             bool pdl) {
   using T2 = typename C2<R>::T;
@@ -399,6 +460,13 @@ __device__ __forceinline__ void qsweep_core(const Args& a, uint32_t u0, uint32_t
   auto align16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) + 15) & ~uintptr_t(15); };
   R* thpi = reinterpret_cast<R*>(align16(spt + a.n_pterm));
   double* mpart = reinterpret_cast<double*>(align16(thpi + a.n_pterm));
+  int* kpart = reinterpret_cast<int*>(mpart + n_warps);
+  uint8_t* flips = reinterpret_cast<uint8_t*>(kpart + n_warps);  // per op: register bits whose partners swap
+
+  auto unit_base = [&](uint32_t unit) { return deposit_runs(unit & ((1u << a.n_tiles_log2) - 1u), a.rest); };
+  auto unit_src = [&](uint32_t unit) {
+    return reinterpret_cast<const T2*>(a.src) + HS_BCHK(unit >> a.n_tiles_log2, a.n_rhs, BS_REG_STATE) * a.N;
+  };
 
   // Per-CTA tables (written by launches that completed before this grid began).
   {
@@ -413,15 +481,16 @@ __device__ __forceinline__ void qsweep_core(const Args& a, uint32_t u0, uint32_t
     copy_words(scls, a.cls, sizeof(PClass) * a.n_cls);
     copy_words(spt, a.pt, sizeof(PTerm) * a.n_pterm);
   }
-  // Rotations: a fast rotation (y = 0, z = 0) as the ratio and form of the
-  // factor build's record, its larger factor in the sweep's scale (the warps'
-  // partial products, multiplied together where the scale is applied); any
-  // other rotation as (cos, sin).
+  // Rotations: a fast rotation (y = 0, z = 0) as tan(theta') of the factor
+  // build's record, with cos(theta') and its quarter turns k in the sweep's
+  // scale (the warps' partial products and sums, combined where the scale is
+  // applied) and an odd k as a swap of partners in its op; any other rotation
+  // as (cos, sin).
   for (int i = tid; i < a.n_rot; i += NT) {
     const int e = a.rot[i].cs;
     if (a.rot[i].fast) {
       const double* q = a.rq + 4 * HS_BCHK(e, a.n_terms_g, BS_REG_TERM);
-      rcs[i] = T2{R(q[0]), R(q[1])};
+      rcs[i] = T2{R(q[0]), R(0)};
     } else {
       const double* p = a.cs + 2 * HS_BCHK(e, a.n_terms_g, BS_REG_TERM);
       rcs[i] = T2{R(p[0]), R(p[1])};
@@ -429,22 +498,35 @@ __device__ __forceinline__ void qsweep_core(const Args& a, uint32_t u0, uint32_t
   }
   {
     double m = 1.0;
+    int kq = 0;
+    auto take = [&](int rot) {
+      const double* q = a.rq + 4 * HS_BCHK(a.rot[rot].cs, a.n_terms_g, BS_REG_TERM);
+      m *= q[2];
+      const int k = int(q[1]);
+      kq += k;
+      return k & 1;
+    };
     for (int oi = tid; oi < a.n_ops; oi += NT) {
       const Op& op = a.ops[oi];
+      uint32_t fl = 0;
       if (op.type == OP_ROT && (op.flags & 1)) {
-        m *= a.rq[4 * HS_BCHK(a.rot[op.idx].cs, a.n_terms_g, BS_REG_TERM) + 2];
+        fl = uint32_t(take(op.idx));
       } else if (op.type == OP_ROTN) {
 #pragma unroll
         for (int i = 0; i < B; ++i)
-          if ((op.ku >> i) & 1) {
-            const int slot = int((i < 4 ? (op.zthr >> (8 * i)) : (op.zrest >> (8 * (i - 4)))) & 0xffu);
-            m *= a.rq[4 * HS_BCHK(a.rot[slot].cs, a.n_terms_g, BS_REG_TERM) + 2];
-          }
+          if ((op.ku >> i) & 1) fl |= uint32_t(take(rotn_slot(op, i))) << i;
       }
+      flips[oi] = uint8_t(fl);
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m *= __shfl_xor_sync(0xffffffffu, m, o);
-    if (lane == 0) mpart[warp] = m;
+    for (int o = 16; o > 0; o >>= 1) {
+      m *= __shfl_xor_sync(0xffffffffu, m, o);
+      kq += __shfl_xor_sync(0xffffffffu, kq, o);
+    }
+    if (lane == 0) {
+      mpart[warp] = m;
+      kpart[warp] = kq;
+    }
   }
   for (int t = tid; t < a.n_pterm; t += NT) thpi[t] = R(a.rq[4 * HS_BCHK(a.pt[t].th, a.n_terms_g, BS_REG_TERM) + 3]);
   for (int t = 0; t < a.n_tab; ++t) {
@@ -461,10 +543,6 @@ __device__ __forceinline__ void qsweep_core(const Args& a, uint32_t u0, uint32_t
 
   // Warp-cooperative copy of this warp's rows of a unit in layout L (the
   // first layout of the sweep) into the tile buffer.
-  auto unit_base = [&](uint32_t unit) { return deposit_runs(unit & ((1u << a.n_tiles_log2) - 1u), a.rest); };
-  auto unit_src = [&](uint32_t unit) {
-    return reinterpret_cast<const T2*>(a.src) + HS_BCHK(unit >> a.n_tiles_log2, a.n_rhs, BS_REG_STATE) * a.N;
-  };
   auto copy_in = [&](const Layout* L, uint32_t base, const T2* src) {
     const int n_thr = L->n_thr;
     uint32_t lc = 0;
@@ -480,6 +558,7 @@ __device__ __forceinline__ void qsweep_core(const Args& a, uint32_t u0, uint32_t
     cp_async_commit();
   };
   const Layout* L0 = slay + a.ops[0].idx;  // the first op is always a layout
+
 
   if (pdl) grid_dependency_wait();  // the state written by the previous launch is visible after this
   __syncthreads();                  // the tables are in shared memory
@@ -583,65 +662,83 @@ __device__ __forceinline__ void qsweep_core(const Args& a, uint32_t u0, uint32_t
           copy_in(L0, unit_base(unit + 1), unit_src(unit + 1));
         }
       } else if (op.type == OP_ROTN) {
-        rot_run<R, NR, 0, B>(x, op, rcs);
+        rot_run<R, NR, B>(x, op, rcs, flips[oi]);
       } else if (op.type == OP_ROT) {
         const T2 cs = rcs[op.idx];
-        const bool fast = op.flags & 1;
-        const int sbit = fast ? 0 : (parity(op.zrest & base) ^ parity(op.zthr & lt));
-        rot_dispatch<R, NR>(x, op.ku, cs.x, cs.y, fast, (op.flags >> 1) & 3, op.zk, sbit);
+        if constexpr (FULL) {
+          const bool fast = op.flags & 1;
+          const int sbit = fast ? 0 : (parity(op.zrest & base) ^ parity(op.zthr & lt));
+          rot_dispatch<R, NR>(x, op.ku, cs.x, cs.y, fast, (op.flags >> 1) & 3, op.zk, sbit, flips[oi] != 0);
+        } else {
+          tan_dispatch<R, NR>(x, op.ku, cs.x, flips[oi] != 0);  // the planner sends only tan-form rotations here
+        }
       } else if (op.type == OP_DROT) {
         const T2 cs = rcs[op.idx];
         diag_rot<R, NR>(x, cs.x, cs.y, op.zk, parity(op.zrest & base) ^ parity(op.zthr & lt));
       } else if (op.type == OP_TAB) {
-        const Tab& tb = a.tab[op.idx];
-        const uint32_t sm = tb.sm;
-        const int tsh = tb.sh;
-        uint32_t pr[B];
+        if constexpr (FULL) {
+          const Tab& tb = a.tab[op.idx];
+          const uint32_t sm = tb.sm;
+          const int tsh = tb.sh;
+          uint32_t pr[B];
 #pragma unroll
-        for (int i = 0; i < B; ++i) pr[i] = pattern_fast(cur->goff[i], sm, tsh);
-        tab_dispatch<R, NR, B>(x, op.ku, vts + tb.s0, tb.ns, pattern_fast(gt, sm, tsh), pr);
+          for (int i = 0; i < B; ++i) pr[i] = pattern_fast(cur->goff[i], sm, tsh);
+          tab_dispatch<R, NR, B>(x, op.ku, vts + tb.s0, tb.ns, pattern_fast(gt, sm, tsh), pr);
+        }
       } else {
         phase_apply<R, NR, B>(x, sph[op.idx], scls, Cs, e0s[op.idx], lt);
       }
     }
-    // The sweep's rotation scale, then the rows straight to HBM: register row
-    // 2j (and 2j + 1 in the same 16 bytes for complex64) sits at global row
-    // gt ^ XOR of the layout's global offsets of the set bits of 2j.
-    {
-      double md = 1.0;
-      for (int w = 0; w < n_warps; ++w) md *= mpart[w];
-      const R m = R(md);
-#pragma unroll
-      for (int k = 0; k < NR; ++k) x[k] = T2{x[k].x * m, x[k].y * m};
+    // The sweep's rotation scale m (-i)^K, then the rows straight to HBM:
+    // register row 2j (and 2j + 1 in the same 16 bytes for complex64) sits at
+    // global row gt ^ XOR of the layout's global offsets of the set bits of 2j.
+    // (One store body per form of the scale, so no join follows it.)
+    double md = 1.0;
+    int kq = 0;
+    for (int w = 0; w < n_warps; ++w) {
+      md *= mpart[w];
+      kq += kpart[w];
     }
+    const R m = R(md);
+    const int K = kq & 3;
     uint32_t go[B];
 #pragma unroll
     for (int i = 0; i < B; ++i) go[i] = cur->goff[i];
+    auto store_rows = [&](auto scale) {
 #pragma unroll
-    for (int j = 0; j < NJ; ++j) {
-      uint32_t g = gt;
+      for (int j = 0; j < NJ; ++j) {
+        uint32_t g = gt;
 #pragma unroll
-      for (int i = 0; i < B - VB; ++i)
-        if ((j >> i) & 1) g ^= go[i + VB];
-      if constexpr (V == 2) {
-        *reinterpret_cast<float4*>(dst + HS_BCHK(g, a.N - 1, BS_REG_STATE)) =
-            make_float4(x[2 * j].x, x[2 * j].y, x[2 * j + 1].x, x[2 * j + 1].y);
-      } else {
-        dst[HS_BCHK(g, a.N, BS_REG_STATE)] = x[j];
+        for (int i = 0; i < B - VB; ++i)
+          if ((j >> i) & 1) g ^= go[i + VB];
+        if constexpr (V == 2) {
+          const T2 v0 = scale(x[2 * j]), v1 = scale(x[2 * j + 1]);
+          *reinterpret_cast<float4*>(dst + HS_BCHK(g, a.N - 1, BS_REG_STATE)) = make_float4(v0.x, v0.y, v1.x, v1.y);
+        } else {
+          dst[HS_BCHK(g, a.N, BS_REG_STATE)] = scale(x[j]);
+        }
       }
+    };
+    if (K == 0) {
+      store_rows([&](T2 v) { return T2{v.x * m, v.y * m}; });
+    } else {
+      const R cr = K == 2 ? -m : R(0), ci = K == 1 ? -m : (K == 3 ? m : R(0));
+      store_rows([&](T2 v) { return T2{fma(v.x, cr, -v.y * ci), fma(v.x, ci, v.y * cr)}; });
     }
   }
 }
 
-template <typename R, int B>
+// FULL: the kernel with the TAB and general-rotation paths; sweeps without
+// them run the lighter instantiation (fewer live registers, no spills).
+template <typename R, int B, bool FULL>
 __global__ void __launch_bounds__(B == 5 ? 256 : 512, B == 5 ? 2 : 1) qsweep_kernel(const __grid_constant__ Args a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const uint32_t u0 = blockIdx.x * uint32_t(a.units_per_cta);
   const uint32_t u1 = min(uint32_t(a.n_units), u0 + uint32_t(a.units_per_cta));
-  qsweep_core<R, B>(a, u0, u1, smem_raw, true);
+  qsweep_core<R, B, FULL>(a, u0, u1, smem_raw, true);
 }
 
-template <typename R, int B>
+template <typename R, int B, bool FULL>
 __global__ void __launch_bounds__(B == 5 ? 256 : 512, B == 5 ? 2 : 1) qlevel_kernel(const __grid_constant__ LevelArgs p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   int* pref = reinterpret_cast<int*>(smem_raw + p.prefix_smem);
@@ -654,17 +751,28 @@ __global__ void __launch_bounds__(B == 5 ? 256 : 512, B == 5 ? 2 : 1) qlevel_ker
   }
   const Args& a = p.descs[p.lvl_desc[p.off + lo]];
   const uint32_t u = uint32_t(HS_BCHK(blockIdx.x - uint32_t(pref[lo]), a.n_units, BS_BATCH_JOB));
-  qsweep_core<R, B>(a, u, u + 1, smem_raw, true);
+  qsweep_core<R, B, FULL>(a, u, u + 1, smem_raw, true);
 }
 
 using LFn = void (*)(LevelArgs);
 
 using QFn = void (*)(Args);
 
-QFn qsweep_fn(hs_dtype dt, int B) {
-  if (dt == HS_C64) return B == 5 ? qsweep_kernel<float, 5> : (B == 4 ? qsweep_kernel<float, 4> : nullptr);
-  return B == 4 ? qsweep_kernel<double, 4> : nullptr;
+template <bool FULL>
+QFn qsweep_fn_t(hs_dtype dt, int B) {
+  if (dt == HS_C64)
+    return B == 5 ? qsweep_kernel<float, 5, FULL> : (B == 4 ? qsweep_kernel<float, 4, FULL> : nullptr);
+  return B == 4 ? qsweep_kernel<double, 4, FULL> : nullptr;
 }
+QFn qsweep_fn(hs_dtype dt, int B, bool full) { return full ? qsweep_fn_t<true>(dt, B) : qsweep_fn_t<false>(dt, B); }
+
+template <bool FULL>
+LFn qlevel_fn_t(hs_dtype dt, int B) {
+  if (dt == HS_C64)
+    return B == 5 ? qlevel_kernel<float, 5, FULL> : (B == 4 ? qlevel_kernel<float, 4, FULL> : nullptr);
+  return B == 4 ? qlevel_kernel<double, 4, FULL> : nullptr;
+}
+LFn qlevel_fn(hs_dtype dt, int B, bool full) { return full ? qlevel_fn_t<true>(dt, B) : qlevel_fn_t<false>(dt, B); }
 
 }  // namespace
 
@@ -676,16 +784,17 @@ cudaError_t prepare_qsweep() {
   if (e != cudaSuccess) return e;
   std::lock_guard<std::mutex> lk(mu);
   if (dev < 64 && done[dev]) return cudaSuccess;
-  const QFn fns[3] = {qsweep_kernel<float, 5>, qsweep_kernel<float, 4>, qsweep_kernel<double, 4>};
-  for (QFn fn : fns) {
-    e = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSweepSmemMax));
-    if (e != cudaSuccess) return e;
-  }
-  const LFn lfns[3] = {qlevel_kernel<float, 5>, qlevel_kernel<float, 4>, qlevel_kernel<double, 4>};
-  for (LFn fn : lfns) {
-    e = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSweepSmemMax));
-    if (e != cudaSuccess) return e;
-  }
+  const hs_dtype dts[3] = {HS_C64, HS_C64, HS_C128};
+  const int Bs[3] = {5, 4, 4};
+  for (int v = 0; v < 3; ++v)
+    for (bool full : {false, true}) {
+      e = cudaFuncSetAttribute((const void*)qsweep_fn(dts[v], Bs[v], full), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               int(kSweepSmemMax));
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute((const void*)qlevel_fn(dts[v], Bs[v], full),
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSweepSmemMax));
+      if (e != cudaSuccess) return e;
+    }
   if (dev < 64) done[dev] = true;
   return cudaSuccess;
 }
@@ -696,7 +805,7 @@ size_t qsweep_smem_bytes(const Args& a, hs_dtype dt, int B) {
   const size_t head =
       ((size_t(1) << a.tile_bits) + a.n_rot + a.n_vt + warps * a.n_phase) * e + warps * size_t(a.n_cls) * r;
   return (head + 15) / 16 * 16 + sizeof(Op) * a.n_ops + sizeof(Layout) * a.n_lay + sizeof(Phase) * a.n_phase +
-         sizeof(PClass) * a.n_cls + sizeof(PTerm) * a.n_pterm + 16 + r * a.n_pterm + 16 + 8 * warps;
+         sizeof(PClass) * a.n_cls + sizeof(PTerm) * a.n_pterm + 16 + r * a.n_pterm + 16 + 12 * warps + a.n_ops;
 }
 
 void fill_job(const hs_factors* f, Args& a, void* psi, int n_rhs) {
@@ -715,10 +824,9 @@ void fill_job(const hs_factors* f, Args& a, void* psi, int n_rhs) {
   a.n_units = (1 << a.n_tiles_log2) * n_rhs;
 }
 
-cudaError_t launch_qlevel(hs_dtype dt, int B, int tile_bits, const LevelArgs& L, int64_t ctas, size_t smem,
+cudaError_t launch_qlevel(hs_dtype dt, int B, bool full, int tile_bits, const LevelArgs& L, int64_t ctas, size_t smem,
                           cudaStream_t s) {
-  LFn fn = dt == HS_C64 ? (B == 5 ? qlevel_kernel<float, 5> : (B == 4 ? qlevel_kernel<float, 4> : nullptr))
-                        : (B == 4 ? qlevel_kernel<double, 4> : nullptr);
+  LFn fn = qlevel_fn(dt, B, full);
   if (!fn || tile_bits - B < 5 || smem > kSweepSmemMax || ctas <= 0 || ctas >= (int64_t(1) << 31))
     return cudaErrorInvalidValue;
   cudaLaunchConfig_t cfg = {};
@@ -739,7 +847,7 @@ cudaError_t launch_qlevel(hs_dtype dt, int B, int tile_bits, const LevelArgs& L,
 cudaError_t launch_qsweep(const hs_factors* f, Args& a, const void* src, void* dst, int n_rhs, int B, bool pdl,
                           cudaStream_t s) {
   const Plan& p = f->plan;
-  QFn fn = qsweep_fn(f->dtype, B);
+  QFn fn = qsweep_fn(f->dtype, B, a.full != 0);
   if (!fn || a.tile_bits - B < 5 || a.tile_bits > p.n_qubits) return cudaErrorInvalidValue;
   fill_job(f, a, const_cast<void*>(src), n_rhs);
   a.dst = dst;

@@ -132,6 +132,7 @@ struct Args {
   int sh;
   Runs rest;
   int n_ops, n_lay, n_rot, n_tab, n_phase, n_cls, n_pterm, n_vt;
+  int full;          // 1 if a TAB op or a rotation other than tan form occurs (the larger kernel)
   Op ops[kMaxOps];
   Layout lay[kMaxLayouts];
   Rot rot[kMaxRot];
@@ -176,7 +177,7 @@ struct LevelArgs {
   int off, count;
   uint32_t prefix_smem;  // byte offset of the level's prefix table in shared memory
 };
-cudaError_t launch_qlevel(hs_dtype dt, int B, int tile_bits, const LevelArgs& L, int64_t ctas, size_t smem,
+cudaError_t launch_qlevel(hs_dtype dt, int B, bool full, int tile_bits, const LevelArgs& L, int64_t ctas, size_t smem,
                           cudaStream_t s);
 cudaError_t launch_qsweep(const hs_factors* f, Args& a, const void* src, void* dst, int n_rhs, int B,
                           bool pdl, cudaStream_t s);

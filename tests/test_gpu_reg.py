@@ -113,6 +113,34 @@ def test_reg_chains_tiles_and_low_bits(dt):
             _check(got, want, dt, f"{ham.family} budget={budget} tb={tb} lb={lb}")
 
 
+@pytest.mark.parametrize("dt", ["c128", "c64"])
+def test_reg_large_angles_every_quarter_turn(dt):
+    """X-type rotations with angles over [-pi, pi] (every k = rint(2 theta / pi)
+    mod 4 of the tan-form split, including the swapped-partner cases), single
+    and two-qubit flips, between diagonal terms, against the oracle."""
+    rng = np.random.default_rng(4103)
+    n = 14
+    labels, coeffs = [], []
+    for q in range(n):
+        labels.append(W.label_of(n, {q: "X"}))
+        labels.append(W.label_of(n, {q: "Z", (q + 3) % n: "Z"}))
+    for q in (0, 2, 5, 9, 12):
+        labels.append(W.label_of(n, {q: "X", (q + 1) % n: "X"}))
+    labels.append(W.label_of(n, {1: "X", 11: "X"}))
+    coeffs = rng.uniform(-6.0, 6.0, len(labels))
+    ham = W.Hamiltonian("random", n, labels, coeffs)
+    t, steps = 1.0, 2  # theta = c * 0.5 spans about [-3, 3]
+    thetas = np.asarray(coeffs) * t / steps
+    ks = {int(np.rint(2 * th / np.pi)) % 4 for th in thetas}
+    assert ks == {0, 1, 2, 3}
+    psi0 = np.stack([W.gaussian_state(n, rng) for _ in range(2)])
+    want = _oracle(ham, t, steps, psi0)
+    for budget in (1, 4):
+        for B in ((4, 5) if dt == "c64" else (4,)):
+            got = _evolve(ham, t, steps, budget, dt, psi0, method=REG, reg_bits=B)
+            _check(got, want, dt, f"budget={budget} B={B}")
+
+
 def test_reg_maxcut_sixteen_states_and_tsp():
     job = W.maxcut24(n=16, n_rhs=16, n_steps=6)
     want = _oracle(job.ham, job.t, job.n_steps, job.psi0)
