@@ -433,17 +433,35 @@ def batch_jobs(args, dtype="c64"):
     return jobs, desc
 
 
+_BUILD_POOL = None
+
+
+def build_all(jobs, dtype):
+    """Factor sets of independent jobs, built from host threads (the library's
+    host planning of each job is independent; the calls release the GIL and
+    enqueue their device work on the same stream)."""
+    global _BUILD_POOL
+    from concurrent.futures import ThreadPoolExecutor
+    from paper_2606_16959_gb300 import hs
+    if _BUILD_POOL is None:
+        _BUILD_POOL = ThreadPoolExecutor(max_workers=max(1, min(16, os.cpu_count() or 1)))
+    return list(_BUILD_POOL.map(
+        lambda j: hs.hs_build_factors(j.ham.labels, j.ham.coeffs, j.t, j.n_steps, j.budget, dtype), jobs))
+
+
 def batch_options(jobs, views, args, dtype):
     """Batch options from the batch autotuner (kept in the autotune cache so that
     a later run, e.g. under a profiler, replays the same configuration)."""
     from paper_2606_16959_gb300 import hs
     import torch
+    if args.method or args.tile_bits:  # given on the command line (profiling cases)
+        return {k: v for k, v in (("method", args.method), ("tile_bits", args.tile_bits)) if v}
     if not args.autotune:
         return {}
     key = f"batch{len(jobs)}:{dtype}:{torch.cuda.get_device_name()}"
     cache = load_tune_cache()
     if key not in cache:
-        facs = [hs.hs_build_factors(j.ham.labels, j.ham.coeffs, j.t, j.n_steps, j.budget, dtype) for j in jobs]
+        facs = build_all(jobs, dtype)
         cache[key] = hs.hs_batch_autotune([(f, v, j.n_steps) for f, v, j in zip(facs, views, jobs)])
         for f in facs:
             f.close()
@@ -471,7 +489,7 @@ def time_batch(jobs, args, world, rank, dtype):
 
     def step():
         work.copy_(init)
-        facs = [hs.hs_build_factors(j.ham.labels, j.ham.coeffs, j.t, j.n_steps, j.budget, dtype) for j in jobs]
+        facs = build_all(jobs, dtype)
         b = hs.hs_batch_create([(f, v, j.n_steps) for f, v, j in zip(facs, views, jobs)], use_graph=False, **bopts)
         e0, e1 = E(enable_timing=True), E(enable_timing=True)
         e0.record()
@@ -537,7 +555,7 @@ def time_batch_e2e(jobs, args, dtype, bopts):
         s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s0.record()
         work.copy_(host_in, non_blocking=True)
-        facs = [hs.hs_build_factors(j.ham.labels, j.ham.coeffs, j.t, j.n_steps, j.budget, dtype) for j in jobs]
+        facs = build_all(jobs, dtype)
         b = hs.hs_batch_create([(f, v, j.n_steps) for f, v, j in zip(facs, views, jobs)], use_graph=False, **bopts)
         hs.hs_batch_launch(b)
         for k, v in enumerate(views):

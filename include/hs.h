@@ -305,8 +305,9 @@ int hs_batch_autotune(const hs_batch_job* jobs, size_t n_jobs, void* cuda_stream
 
 /* One call over job arrays (the batched form of hs_evolve): job k evolves
  * psi[k] (n_rhs[k] states, device buffer of the factors' dtype) in place by
- * n_steps[k] steps of f[k].  Plans a batch with the default options,
- * enqueues its launches on cuda_stream (directly, no graph) and frees the
+ * n_steps[k] steps of f[k].  Plans a batch of register-blocked sweeps
+ * (hs_batch_opts method HS_METHOD_REG, every other option the library's
+ * choice), enqueues its launches on cuda_stream (directly, no graph) and frees the
  * batch's tables in stream order; the same work as hs_batch_create +
  * hs_batch_launch + hs_batch_free_async.  All arrays are host arrays of
  * n_jobs entries.  Errors as hs_batch_create and hs_batch_launch. */

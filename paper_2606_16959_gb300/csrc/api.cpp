@@ -412,7 +412,7 @@ int build_impl(const uint64_t* x, const uint64_t* z, const double* coeffs, const
   fp->d_vt = static_cast<unsigned char*>(fp->d_vals) + size_t(p.total_elems) * hs::elem_bytes(dtype);
   const size_t m = n_terms;
   std::vector<int> fD(G), fd0(G), gfirst(G), glast(G), xdim(G), pivot(G * hs::kMaxXDim, 0), vt0(G), gkind(G),
-      gdir(G), dep_all, dep_notab, dep_tab;
+      gdir(G), dep_all, dep_notab, dep_tab, tab_groups, row_groups;
   std::vector<uint32_t> smask(G);
   std::vector<uint64_t> basis(G * hs::kMaxXDim, 0);
   for (int g = 0; g < G; ++g) {
@@ -430,6 +430,7 @@ int build_impl(const uint64_t* x, const uint64_t* z, const double* coeffs, const
       basis[g * hs::kMaxXDim + i] = gr.basis[i];
       pivot[g * hs::kMaxXDim + i] = gr.pivot[i];
     }
+    (gr.vt0 >= 0 ? tab_groups : row_groups).push_back(g);
     bool dep = false;
     for (int j = gr.first; coeffs1 && j < gr.last; ++j) dep = dep || coeffs1[j] != 0.0;
     if (dep) {
@@ -457,6 +458,7 @@ int build_impl(const uint64_t* x, const uint64_t* z, const double* coeffs, const
   const size_t o_kind = put(gkind.data(), G * 4), o_dir = put(gdir.data(), G * 4);
   const size_t o_da = put(dep_all.data(), dep_all.size() * 4), o_dn = put(dep_notab.data(), dep_notab.size() * 4);
   const size_t o_dt = put(dep_tab.data(), dep_tab.size() * 4);
+  const size_t o_tg = put(tab_groups.data(), tab_groups.size() * 4), o_rg = put(row_groups.data(), row_groups.size() * 4);
   const std::vector<double> hk = hs::kind_steps(p.order, t / double(n_steps));
   const size_t o_h = put(hk.data(), hk.size() * 8);
   const size_t o_fv = put(nullptr, 8);                   // drive value of hs_factors_set_drive
@@ -503,6 +505,10 @@ int build_impl(const uint64_t* x, const uint64_t* z, const double* coeffs, const
   bi.n_dep_all = int(dep_all.size());
   bi.n_dep_notab = int(dep_notab.size());
   bi.n_dep_tab = int(dep_tab.size());
+  bi.tab_groups = reinterpret_cast<const int*>(d_blob + o_tg);
+  bi.row_groups = reinterpret_cast<const int*>(d_blob + o_rg);
+  bi.n_tab_groups = int(tab_groups.size());
+  bi.n_row_groups = int(row_groups.size());
   if ((rc = guard(cudaError_t(stage_upload(d_blob, blob.data(), o_fv, s)), "table upload"))) {
     cudaStreamSynchronize(s);
     release(f.release(), s);
@@ -510,7 +516,8 @@ int build_impl(const uint64_t* x, const uint64_t* z, const double* coeffs, const
   }
   e = hs::launch_sincos(fp, nullptr, s);
   if (e == cudaSuccess) e = hs::launch_value_tables(fp, nullptr, 0, s);
-  if (e == cudaSuccess) e = hs::launch_build(fp, nullptr, 0, s);
+  if (e == cudaSuccess)
+    e = hs::launch_build_split(fp, bi.tab_groups, bi.n_tab_groups, bi.row_groups, bi.n_row_groups, s);
   if (e != cudaSuccess) {
     cudaStreamSynchronize(s);
     release(f.release(), s);
@@ -797,7 +804,14 @@ cudaError_t enqueue_drive_rebuild(const hs_factors* f, const double* d_fval, con
   const hs_build_inputs& b = f->bin;
   cudaError_t e = hs::launch_sincos(f, d_fval, s);
   if (e == cudaSuccess && b.n_dep_tab > 0) e = hs::launch_value_tables(f, b.dep_tab, b.n_dep_tab, s);
-  if (e == cudaSuccess && n_diag > 0) e = hs::launch_build(f, diag_groups, n_diag, s);
+  if (e == cudaSuccess && n_diag > 0) {
+    if (diag_groups == b.dep_all)  // every driven factor: copy the tabled ones, build the others
+      e = hs::launch_build_split(f, b.dep_tab, b.n_dep_tab, b.dep_notab, b.n_dep_notab, s);
+    else if (diag_groups == b.dep_notab)
+      e = hs::launch_build_split(f, nullptr, 0, b.dep_notab, b.n_dep_notab, s);
+    else
+      e = hs::launch_build(f, diag_groups, n_diag, s);
+  }
   return e;
 }
 
@@ -892,10 +906,10 @@ int hs_evolve_td(hs_factors* f, void* psi, int n_rhs, const double* drive, int n
     }
     // Leave every stored value at the last step's drive.
     if (reg_only && b.n_dep_all > 0) {
-      cudaError_t e = hs::launch_build(f, b.dep_all, b.n_dep_all, cs);
+      cudaError_t e = hs::launch_build_split(f, b.dep_tab, b.n_dep_tab, b.dep_notab, b.n_dep_notab, cs);
       if (e != cudaSuccess) return cuda_fail(e, "factor build launch");
     } else if (!diag_all && b.n_dep_tab > 0) {
-      cudaError_t e = hs::launch_build(f, b.dep_tab, b.n_dep_tab, cs);
+      cudaError_t e = hs::launch_build_split(f, b.dep_tab, b.n_dep_tab, nullptr, 0, cs);
       if (e != cudaSuccess) return cuda_fail(e, "factor build launch");
     }
     return HS_OK;

@@ -12,11 +12,13 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <map>
 #include <mutex>
 #include <memory>
 #include <string>
+#include <thread>
 #include <tuple>
 #include <vector>
 
@@ -333,50 +335,84 @@ int create_reg_batch(const hs_batch_job* jobs, size_t n_jobs, const hs_batch_opt
     if (J.factors->dtype != dt) return hs::report_error(HS_EDTYPE, "jobs differ in dtype");
     if (J.n_rhs < 1 || J.n_steps < 0) return hs::report_error(HS_EINVAL, "job " + std::to_string(j) + ": bad n_rhs/n_steps");
     if (reinterpret_cast<uintptr_t>(J.psi) % 16) return hs::report_error(HS_EINVAL, "psi must be 16-byte aligned");
+  }
+  // Per job (independent, planned on host threads): its sweeps as descriptor
+  // pieces (a sweep seen before reuses its pieces), the order in which its
+  // levels use them, or "separate" when some sweep has no register form.
+  struct JobPlan {
+    bool ok = false;
+    int Tj = 0;
+    std::vector<std::shared_ptr<hs::q::Args>> pieces;
+    std::vector<int> order;  // indices into pieces, one per level
+  };
+  std::vector<JobPlan> plans(n_jobs);
+  const int lb = b->low_bits;
+  auto plan_job = [&](size_t j) {
+    const hs_batch_job& J = jobs[j];
+    JobPlan& P = plans[j];
     const hs::Plan& p = J.factors->plan;
-    b->updates += int64_t(J.n_steps) * int64_t(p.step_seq.size()) * p.N * J.n_rhs;
-    if (J.n_steps == 0) continue;
+    if (J.n_steps == 0) return;
     const int n = p.n_qubits;
-    const int Tj = std::min(T, n);
+    P.Tj = std::min(T, n);
     bool ok = n >= B + 5;
     std::vector<hs::Sweep> sw;
-    if (ok) sw = hs::plan_sweeps(p, J.n_steps, Tj, b->low_bits, true);
+    if (ok) sw = hs::plan_sweeps(p, J.n_steps, P.Tj, lb, true);
     for (const hs::Sweep& w : sw) ok = ok && w.fused;
-    const size_t keep = b->qdescs.size();
-    GJob gj;
-    std::map<std::pair<uint32_t, std::vector<int>>, std::vector<int>> memo;  // sweep -> its pieces' descriptors
+    std::map<std::pair<uint32_t, std::vector<int>>, std::vector<int>> memo;  // sweep -> its pieces
     for (size_t k = 0; ok && k < sw.size(); ++k) {
       const auto key = std::make_pair(sw[k].local_mask, sw[k].factors);
       auto it = memo.find(key);
       if (it != memo.end()) {
-        gj.descs.insert(gj.descs.end(), it->second.begin(), it->second.end());
+        P.order.insert(P.order.end(), it->second.begin(), it->second.end());
         continue;
       }
       std::vector<std::pair<std::vector<int>, std::shared_ptr<hs::q::Args>>> pieces;
       std::string why;
-      if (!hs::q::plan_qsweep_runs(J.factors, sw[k].factors, sw[k].local_mask, Tj, B, pieces, &why)) {
+      if (!hs::q::plan_qsweep_runs(J.factors, sw[k].factors, sw[k].local_mask, P.Tj, B, pieces, &why)) {
         ok = false;
         break;
       }
       std::vector<int> ids;
       for (auto& pc : pieces) {
-        hs::q::Args& a = *pc.second;
-        hs::q::fill_job(J.factors, a, J.psi, J.n_rhs);
-        a.units_per_cta = 1;
-        ids.push_back(int(b->qdescs.size()));
-        b->qdescs.push_back(a);
+        hs::q::fill_job(J.factors, *pc.second, J.psi, J.n_rhs);
+        pc.second->units_per_cta = 1;
+        ids.push_back(int(P.pieces.size()));
+        P.pieces.push_back(std::move(pc.second));
       }
-      gj.descs.insert(gj.descs.end(), ids.begin(), ids.end());
+      P.order.insert(P.order.end(), ids.begin(), ids.end());
       memo[key] = std::move(ids);
     }
-    if (!ok) {
-      b->qdescs.resize(keep);
+    P.ok = ok;
+  };
+  {
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const size_t n_thr = std::min<size_t>(std::min<size_t>(hw, 16), (n_jobs + 7) / 8);
+    std::atomic<size_t> next{0};
+    auto worker = [&]() {
+      for (size_t j; (j = next.fetch_add(1)) < n_jobs;) plan_job(j);
+    };
+    std::vector<std::thread> pool;
+    for (size_t t = 1; t < n_thr; ++t) pool.emplace_back(worker);
+    worker();
+    for (std::thread& t : pool) t.join();
+  }
+  for (size_t j = 0; j < n_jobs; ++j) {
+    const hs_batch_job& J = jobs[j];
+    const hs::Plan& p = J.factors->plan;
+    b->updates += int64_t(J.n_steps) * int64_t(p.step_seq.size()) * p.N * J.n_rhs;
+    if (J.n_steps == 0) continue;
+    JobPlan& P = plans[j];
+    if (!P.ok) {
       b->separate.push_back(hs_batch::Sep{J.factors, J.psi, J.n_rhs, J.n_steps});
       continue;
     }
-    gj.units = int64_t(1) << (n - Tj);
-    gj.units *= J.n_rhs;
-    by_tile[Tj].push_back(std::move(gj));
+    const int first = int(b->qdescs.size());
+    for (auto& a : P.pieces) b->qdescs.push_back(*a);
+    GJob gj;
+    gj.descs.reserve(P.order.size());
+    for (int i : P.order) gj.descs.push_back(first + i);
+    gj.units = (int64_t(1) << (p.n_qubits - P.Tj)) * J.n_rhs;
+    by_tile[P.Tj].push_back(std::move(gj));
     ++b->n_batched;
   }
   for (auto& kv : by_tile) {
@@ -653,7 +689,7 @@ extern "C" int hs_evolve_batch(const hs_factors* const* f, void* const* psi, con
   if (!f || !psi || !n_rhs || !n_steps || n_jobs == 0) return hs::report_error(HS_EINVAL, "null job arrays or no jobs");
   std::vector<hs_batch_job> jobs(n_jobs);
   for (size_t k = 0; k < n_jobs; ++k) jobs[k] = hs_batch_job{f[k], psi[k], n_rhs[k], n_steps[k]};
-  hs_batch_opts o{0, 0, 0, 0, 0, 0, 0, 0};
+  hs_batch_opts o{0, 0, 0, 0, 0, 0, HS_METHOD_REG, 0};  // register-blocked sweeps, other options the library's
   hs_batch* b = nullptr;
   int rc = hs_batch_create(jobs.data(), n_jobs, &o, &b);
   if (rc != HS_OK) return rc;

@@ -228,14 +228,6 @@ struct GroupRows {
   }
 };
 
-__device__ __forceinline__ double2 load_val(const void* vals, int64_t idx, bool c64) {
-  if (c64) {
-    const float2 v = reinterpret_cast<const float2*>(vals)[idx];
-    return make_double2(v.x, v.y);
-  }
-  return reinterpret_cast<const double2*>(vals)[idx];
-}
-
 // Row r of F on every structural diagonal: F[r, c] = conj(w[coord(r ^ c)])
 // when r ^ c lies in X, an exact zero otherwise.
 template <int NS, int MAXS>
@@ -264,6 +256,72 @@ __device__ __forceinline__ void write_row(const BuildArgs& a, const GroupRows<MA
   }
 }
 
+// Rows of a factor with a value table: the entry of row r on diagonal d_k is
+// table entry pattern(r) * S + cc, cc the coordinates of r ^ (r + d_k) in the
+// factor's basis (an exact zero when that mask is outside the x-mask set).
+// The table holds the stored values already rounded to the storage type, so
+// they are copied in that type with no FP64 arithmetic.
+template <typename T2, typename Grp>
+__device__ __forceinline__ void copy_rows(const BuildArgs& a, const Grp& G, int D, int d0, int vt0, uint32_t sm) {
+  const T2* __restrict__ vt = reinterpret_cast<const T2*>(a.vt);
+  T2* __restrict__ vals = reinterpret_cast<T2*>(a.vals);
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; r < a.N; r += stride) {
+    uint32_t pat = 0;
+    int q = 0;
+    for (uint32_t t = sm; t; t &= t - 1u, ++q) pat |= uint32_t((uint64_t(r) >> (__ffs(t) - 1)) & 1u) << q;
+    const int64_t e0 = int64_t(vt0) + int64_t(pat) * G.S;
+    for (int k = 0; k < D; ++k) {
+      const int64_t col = r + a.offs[d0 + k];
+      if (col < 0 || col >= a.N) continue;
+      const uint64_t uu = uint64_t(r) ^ uint64_t(col);
+      int cc = 0;
+      uint64_t rec = 0;
+#pragma unroll
+      for (int i = 0; i < kMaxXDim; ++i)
+        if (i < G.xd && ((uu >> G.piv[i]) & 1ull)) {
+          cc |= 1 << i;
+          rec ^= G.bas[i];
+        }
+      T2 v;
+      v.x = 0;
+      v.y = 0;
+      if (rec == uu) v = vt[HS_BCHK(e0 + cc, a.n_vt, BS_BUILD_VT)];
+      vals[HS_BCHK(a.rowbase[d0 + k] + r, a.n_vals, BS_BUILD_VAL)] = v;
+    }
+  }
+}
+
+// A factor's x-mask basis and pivots (all that copying from its value table needs).
+struct GroupBasis {
+  int xd, S;
+  uint64_t bas[kMaxXDim];
+  int piv[kMaxXDim];
+  __device__ __forceinline__ void load(const BuildArgs& a, int g) {
+    xd = a.xdim[g];
+    S = 1 << xd;
+#pragma unroll
+    for (int i = 0; i < kMaxXDim; ++i) {
+      bas[i] = (i < xd) ? a.basis[g * kMaxXDim + i] : 0;
+      piv[i] = (i < xd) ? a.pivot[g * kMaxXDim + i] : 0;
+    }
+  }
+};
+
+// The stored diagonals of factors with value tables (few registers, so the
+// copy runs at full occupancy whatever the widest factor of the set).
+__global__ void __launch_bounds__(256) copy_kernel(BuildArgs a, bool c64) {
+  const int g = group_of(a);
+  const int vt0 = a.vt0[g];
+  if (vt0 < 0) return;
+  GroupBasis G;
+  G.load(a, g);
+  if (c64)
+    copy_rows<float2>(a, G, a.fac_D[g], a.fac_diag0[g], vt0, a.smask[g]);
+  else
+    copy_rows<double2>(a, G, a.fac_D[g], a.fac_diag0[g], vt0, a.smask[g]);
+}
+
 template <int MAXS>
 __global__ void __launch_bounds__(256) build_kernel(BuildArgs a, bool c64) {
   const int g = group_of(a);
@@ -274,7 +332,14 @@ __global__ void __launch_bounds__(256) build_kernel(BuildArgs a, bool c64) {
   const uint32_t sm = a.smask[g];
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
 
-  if (MAXS >= 2 && vt0 < 0 && G.xd == 1) {
+  if (vt0 >= 0) {
+    if (c64)
+      copy_rows<float2>(a, G, D, d0, vt0, sm);
+    else
+      copy_rows<double2>(a, G, D, d0, vt0, sm);
+    return;
+  }
+  if (MAXS >= 2 && G.xd == 1) {
     // Two-element x-mask set: one thread per pair of rows (r, r ^ u_1).
     const int p = G.piv[0];
     const uint64_t lowm = (1ull << p) - 1ull;
@@ -289,21 +354,7 @@ __global__ void __launch_bounds__(256) build_kernel(BuildArgs a, bool c64) {
   }
   for (int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; r < a.N; r += stride) {
     double2 w[MAXS];
-    if (vt0 >= 0) {
-      // The row's values are those of its pattern at smask, already in the
-      // value table (rounded to the storage type, so copying them is exact).
-      uint32_t pat = 0;
-      int q = 0;
-      for (uint32_t t = sm; t; t &= t - 1u, ++q) pat |= uint32_t((uint64_t(r) >> (__ffs(t) - 1)) & 1u) << q;
-#pragma unroll
-      for (int s = 0; s < MAXS; ++s)
-        if (s < G.S) {
-          const double2 v = load_val(a.vt, HS_BCHK(int64_t(vt0) + int64_t(pat) * G.S + s, a.n_vt, BS_BUILD_VT), c64);
-          w[s] = make_double2(v.x, -v.y);  // the table holds conj(w)
-        }
-    } else {
-      G.row(a, uint64_t(r), w);
-    }
+    G.row(a, uint64_t(r), w);
     write_row(a, G, D, d0, r, w, c64);
   }
 }
@@ -389,12 +440,22 @@ cudaError_t launch_sincos(const hs_factors* f, const double* d_fval, cudaStream_
   return cudaGetLastError();
 }
 
+namespace {
+cudaError_t launch_rows(const hs_factors* f, const int* d_groups, int n_groups, int maxdim, cudaStream_t s);
+}
+
 cudaError_t launch_build(const hs_factors* f, const int* d_groups, int n_groups, cudaStream_t s) {
   const Plan& p = f->plan;
   const int G = d_groups ? n_groups : int(p.groups.size());
   if (G <= 0) return cudaSuccess;
   int maxdim = 0;
   for (const Group& g : p.groups) maxdim = g.xdim > maxdim ? g.xdim : maxdim;
+  return launch_rows(f, d_groups, G, maxdim, s);
+}
+
+namespace {
+cudaError_t launch_rows(const hs_factors* f, const int* d_groups, int G, int maxdim, cudaStream_t s) {
+  const Plan& p = f->plan;
   const BuildArgs a = build_args(f, d_groups);
   const bool c64 = f->dtype == HS_C64;
   const int threads = 256;
@@ -412,6 +473,30 @@ cudaError_t launch_build(const hs_factors* f, const int* d_groups, int n_groups,
   }
   note_launches();
   return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_build_split(const hs_factors* f, const int* d_vt_groups, int n_vt, const int* d_row_groups,
+                               int n_rows, cudaStream_t s) {
+  const Plan& p = f->plan;
+  const bool c64 = f->dtype == HS_C64;
+  const int threads = 256;
+  int64_t blocks_x = (p.N + threads - 1) / threads;
+  if (blocks_x > 4096) blocks_x = 4096;
+  if (n_vt > 0) {
+    const BuildArgs a = build_args(f, d_vt_groups);
+    copy_kernel<<<dim3{unsigned(blocks_x), unsigned(n_vt), 1u}, threads, 0, s>>>(a, c64);
+    note_launches();
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (n_rows > 0) {
+    int maxdim = 0;
+    for (const Group& g : p.groups)
+      if (g.vt0 < 0) maxdim = g.xdim > maxdim ? g.xdim : maxdim;
+    return launch_rows(f, d_row_groups, n_rows, maxdim, s);
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_value_tables(const hs_factors* f, const int* d_groups, int n_groups, cudaStream_t s) {

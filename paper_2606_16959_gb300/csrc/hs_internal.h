@@ -154,6 +154,10 @@ struct hs_build_inputs {
   const int* dep_notab = nullptr;
   const int* dep_tab = nullptr;
   int n_dep_all = 0, n_dep_notab = 0, n_dep_tab = 0;
+  // Every group with a value table, and every one without.
+  const int* tab_groups = nullptr;
+  const int* row_groups = nullptr;
+  int n_tab_groups = 0, n_row_groups = 0;
 };
 
 // Opaque object behind the C ABI.
@@ -200,6 +204,10 @@ cudaError_t launch_value_tables(const hs_factors* f, const int* d_groups, int n_
 // Factor values of the listed groups (d_groups NULL: all); groups with a value
 // table copy it, so their tables must be current (launch_value_tables first).
 cudaError_t launch_build(const hs_factors* f, const int* d_groups, int n_groups, cudaStream_t s);
+// The same with the groups split: those with value tables (copied from the
+// tables) and those without (built row by row in FP64).
+cudaError_t launch_build_split(const hs_factors* f, const int* d_vt_groups, int n_vt, const int* d_row_groups,
+                               int n_rows, cudaStream_t s);
 
 cudaError_t launch_apply_plain(const hs_factors* f, int g, const void* x, void* y, int n_rhs, cudaStream_t s);
 

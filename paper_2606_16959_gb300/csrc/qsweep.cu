@@ -462,6 +462,10 @@ __device__ __forceinline__ void qsweep_core(const Args& a, uint32_t u0, uint32_t
   double* mpart = reinterpret_cast<double*>(align16(thpi + a.n_pterm));
   int* kpart = reinterpret_cast<int*>(mpart + n_warps);
   uint8_t* flips = reinterpret_cast<uint8_t*>(kpart + n_warps);  // per op: register bits whose partners swap
+  // Per layout: the local-row bits a lane index and a warp index deposit
+  // (local row of a thread's register row 0 = dlane[lane] | dwarp[warp]).
+  uint32_t* dlane = reinterpret_cast<uint32_t*>(align16(flips + a.n_ops));
+  uint32_t* dwarp = dlane + 32 * a.n_lay;
 
   auto unit_base = [&](uint32_t unit) { return deposit_runs(unit & ((1u << a.n_tiles_log2) - 1u), a.rest); };
   auto unit_src = [&](uint32_t unit) {
@@ -480,6 +484,18 @@ __device__ __forceinline__ void qsweep_core(const Args& a, uint32_t u0, uint32_t
     copy_words(sph, a.ph, sizeof(Phase) * a.n_phase);
     copy_words(scls, a.cls, sizeof(PClass) * a.n_cls);
     copy_words(spt, a.pt, sizeof(PTerm) * a.n_pterm);
+  }
+  for (int e = tid; e < 48 * a.n_lay; e += NT) {
+    const int li = e / 48, j = e - 48 * li;
+    const Layout& L = a.lay[li];
+    uint32_t d = 0;
+    if (j < 32) {
+      for (int i = 0; i < 5 && i < L.n_thr; ++i) d |= uint32_t((j >> i) & 1) << L.thr[i];
+      dlane[32 * li + j] = d;
+    } else {
+      for (int i = 5; i < L.n_thr; ++i) d |= uint32_t(((j - 32) >> (i - 5)) & 1) << L.thr[i];
+      dwarp[16 * li + (j - 32)] = d;
+    }
   }
   // Rotations: a fast rotation (y = 0, z = 0) as tan(theta') of the factor
   // build's record, with cos(theta') and its quarter turns k in the sweep's
@@ -541,28 +557,62 @@ __device__ __forceinline__ void qsweep_core(const Args& a, uint32_t u0, uint32_t
   for (int oi = 0; oi < n_ops; ++oi)
     if (a.ops[oi].type == OP_LAYOUT) last_lay = oi;
 
-  // Warp-cooperative copy of this warp's rows of a unit in layout L (the
-  // first layout of the sweep) into the tile buffer.
-  auto copy_in = [&](const Layout* L, uint32_t base, const T2* src) {
-    const int n_thr = L->n_thr;
+  // Warp-cooperative copy of this warp's rows of a unit in the first layout of
+  // the sweep into the tile buffer: chunk mm of the thread lies at swizzled
+  // chunk s0 ^ mswz(mm) and global row g0 ^ mglob(mm), both maps linear over
+  // XOR, so four basis values each give all of them.
+  constexpr int NJB = B - VB;  // log2 NJ
+  uint32_t cin_s0, cin_g0;
+  {
+    const Layout& L = a.lay[a.ops[0].idx];
     uint32_t lc = 0;
 #pragma unroll
-    for (int k = 0; k < 5; ++k) lc |= uint32_t((lane >> k) & 1) << L->wlo[k];
+    for (int k = 0; k < 5; ++k) lc |= uint32_t((lane >> k) & 1) << L.wlo[k];
     uint32_t wb = 0;
-    for (int i = 5; i < n_thr; ++i) wb |= ((tid >> i) & 1u) << L->thr[i];
+    for (int i = 5; i < L.n_thr; ++i) wb |= ((tid >> i) & 1u) << L.thr[i];
     const uint32_t c0 = lc | (wb >> VB);
-    const uint32_t s0 = swz(c0), g0 = global_of(c0 * V, m0, m1, sh) | base;
-#pragma unroll 4
-    for (int mm = 0; mm < NJ; ++mm)
-      cp_async16(tile + (s0 ^ L->mswz[mm]) * V, src + HS_BCHK(g0 ^ L->mglob[mm], a.N - (V - 1), BS_REG_STATE));
+    cin_s0 = swz(c0);
+    cin_g0 = global_of(c0 * V, m0, m1, sh);
+  }
+  const Layout* L0 = slay + a.ops[0].idx;  // the first op is always a layout
+  auto copy_in = [&](uint32_t base, const T2* src) {
+    uint32_t ms[NJB], mg[NJB];
+#pragma unroll
+    for (int k = 0; k < NJB; ++k) {
+      ms[k] = L0->mswz[1 << k];
+      mg[k] = L0->mglob[1 << k];
+    }
+    const uint32_t g0 = cin_g0 | base;
+#pragma unroll
+    for (int mm = 0; mm < NJ; ++mm) {
+      uint32_t sx = cin_s0, gx = g0;
+#pragma unroll
+      for (int k = 0; k < NJB; ++k)
+        if ((mm >> k) & 1) {
+          sx ^= ms[k];
+          gx ^= mg[k];
+        }
+      cp_async16(tile + sx * V, src + HS_BCHK(gx, a.N - (V - 1), BS_REG_STATE));
+    }
     cp_async_commit();
   };
-  const Layout* L0 = slay + a.ops[0].idx;  // the first op is always a layout
-
 
   if (pdl) grid_dependency_wait();  // the state written by the previous launch is visible after this
   __syncthreads();                  // the tables are in shared memory
-  if (u0 < u1) copy_in(L0, unit_base(u0), unit_src(u0));
+  if (u0 < u1) copy_in(unit_base(u0), unit_src(u0));
+  // The sweep's rotation scale m (-i)^K (the same for every unit).
+  R m_sweep;
+  int k_sweep;
+  {
+    double md = 1.0;
+    int kq = 0;
+    for (int w = 0; w < n_warps; ++w) {
+      md *= mpart[w];
+      kq += kpart[w];
+    }
+    m_sweep = R(md);
+    k_sweep = kq & 3;
+  }
   if (pdl) grid_launch_dependents();  // the next sweep may load its tables meanwhile
 
   for (uint32_t unit = u0; unit < u1; ++unit) {
@@ -631,9 +681,7 @@ __device__ __forceinline__ void qsweep_core(const Args& a, uint32_t u0, uint32_t
           __syncwarp();
         }
         const Layout* L = slay + op.idx;
-        uint32_t l = 0;
-        const int n_thr = L->n_thr;
-        for (int i = 0; i < n_thr; ++i) l |= ((tid >> i) & 1u) << L->thr[i];
+        const uint32_t l = dlane[32 * op.idx + lane] | dwarp[16 * op.idx + warp];
         uint32_t q[B];
 #pragma unroll
         for (int i = 0; i < B; ++i) q[i] = L->qoff[i];
@@ -659,7 +707,7 @@ __device__ __forceinline__ void qsweep_core(const Args& a, uint32_t u0, uint32_t
           // The tile buffer is free once every warp has read its rows: start
           // copying the next unit's rows.
           __syncthreads();
-          copy_in(L0, unit_base(unit + 1), unit_src(unit + 1));
+          copy_in(unit_base(unit + 1), unit_src(unit + 1));
         }
       } else if (op.type == OP_ROTN) {
         rot_run<R, NR, B>(x, op, rcs, flips[oi]);
@@ -693,14 +741,8 @@ __device__ __forceinline__ void qsweep_core(const Args& a, uint32_t u0, uint32_t
     // register row 2j (and 2j + 1 in the same 16 bytes for complex64) sits at
     // global row gt ^ XOR of the layout's global offsets of the set bits of 2j.
     // (One store body per form of the scale, so no join follows it.)
-    double md = 1.0;
-    int kq = 0;
-    for (int w = 0; w < n_warps; ++w) {
-      md *= mpart[w];
-      kq += kpart[w];
-    }
-    const R m = R(md);
-    const int K = kq & 3;
+    const R m = m_sweep;
+    const int K = k_sweep;
     uint32_t go[B];
 #pragma unroll
     for (int i = 0; i < B; ++i) go[i] = cur->goff[i];
@@ -805,7 +847,8 @@ size_t qsweep_smem_bytes(const Args& a, hs_dtype dt, int B) {
   const size_t head =
       ((size_t(1) << a.tile_bits) + a.n_rot + a.n_vt + warps * a.n_phase) * e + warps * size_t(a.n_cls) * r;
   return (head + 15) / 16 * 16 + sizeof(Op) * a.n_ops + sizeof(Layout) * a.n_lay + sizeof(Phase) * a.n_phase +
-         sizeof(PClass) * a.n_cls + sizeof(PTerm) * a.n_pterm + 16 + r * a.n_pterm + 16 + 12 * warps + a.n_ops;
+         sizeof(PClass) * a.n_cls + sizeof(PTerm) * a.n_pterm + 16 + r * a.n_pterm + 16 + 12 * warps + a.n_ops + 16 +
+         192 * size_t(a.n_lay);
 }
 
 void fill_job(const hs_factors* f, Args& a, void* psi, int n_rhs) {

@@ -16,7 +16,13 @@
 //          table at the pattern of r's bits on the factor's support;
 //   ROT    one non-diagonal term of a factor without such a table: its exact
 //          rotation cos(theta) I - i sin(theta) P_j, from the FP64 (cos, sin)
-//          of the factor build;
+//          of the factor build; an X-type term (y = 0, z = 0) in the form
+//          cos(theta') (I - i tan(theta') P_j) (-i P_j)^k, theta = theta' +
+//          k pi / 2, |theta'| <= pi / 4: two fused multiply-adds per
+//          amplitude, cos(theta') and (-i)^k in one scale per sweep, an odd
+//          k a swap of partner rows;
+//   ROTN   a run of consecutive X-type single-qubit rotations on distinct
+//          register bits (they commute), applied back to back in that form;
 //   DROT   a single diagonal term between non-diagonal ones: its rotation
 //          exp(-i theta (-1)^popcount(z & r)) from the build's FP64 (cos, sin);
 //   PHASE  a run of consecutive diagonal terms (x = 0) of such a factor: the

@@ -291,3 +291,29 @@ def test_reg_batch_equals_jobs_alone_bitwise_and_oracle(dt):
     b.close()
     for _, f, _, _ in jobs:
         f.close()
+
+
+@pytest.mark.parametrize("dt", ["c64", "c128"])
+def test_evolve_batch_one_call(dt):
+    """hs_evolve_batch (one call over job arrays) is bitwise the register-sweep
+    batch with default options, and each job agrees with the oracle."""
+    rng = np.random.default_rng(4300)
+    tdt = _tdt(dt)
+    hams = [(W.tfim_chain(13, 1.0, 0.6), 4), (W.heisenberg_chain(12, rng.uniform(0.5, 1.5, 12)), 8),
+            (W.maxcut_3regular(14, 7), 4), (W.tfim_chain(9, 0.8, 1.1), 4)]
+    jobs = []
+    for ham, budget in hams:
+        steps = int(rng.integers(2, 6))
+        psi0 = np.stack([W.gaussian_state(ham.n_qubits, rng) for _ in range(2)])
+        jobs.append((ham, hs.hs_build_factors(ham.labels, ham.coeffs, 0.7, steps, budget, dt), psi0, steps))
+    one = [torch.from_numpy(p).to("cuda", tdt) for _, _, p, _ in jobs]
+    two = [s.clone() for s in one]
+    hs.hs_evolve_batch([(f, s, st) for (_, f, _, st), s in zip(jobs, one)])
+    b = hs.hs_batch_create([(f, s, st) for (_, f, _, st), s in zip(jobs, two)], method=REG, use_graph=False)
+    hs.hs_batch_launch(b)
+    torch.cuda.synchronize()
+    b.close()
+    for (ham, f, p0, steps), a, c in zip(jobs, one, two):
+        assert torch.equal(a, c), (ham.family, ham.n_qubits)
+        _check(a.cpu().numpy(), _oracle(ham, 0.7, steps, p0), dt, f"{ham.family} n={ham.n_qubits}")
+        f.close()
