@@ -436,17 +436,37 @@ def batch_jobs(args, dtype="c64"):
 _BUILD_POOL = None
 
 
+_BUILD_STREAMS = {}
+
+
 def build_all(jobs, dtype):
-    """Factor sets of independent jobs, built from host threads (the library's
-    host planning of each job is independent; the calls release the GIL and
-    enqueue their device work on the same stream)."""
+    """Factor sets of independent jobs, built from host threads, each thread on
+    a stream of its own (the jobs' host planning runs in parallel and their
+    small build kernels overlap on the device); the current stream then waits
+    for every build stream."""
     global _BUILD_POOL
+    import threading
+    import torch
     from concurrent.futures import ThreadPoolExecutor
     from paper_2606_16959_gb300 import hs
     if _BUILD_POOL is None:
         _BUILD_POOL = ThreadPoolExecutor(max_workers=max(1, min(16, os.cpu_count() or 1)))
-    return list(_BUILD_POOL.map(
-        lambda j: hs.hs_build_factors(j.ham.labels, j.ham.coeffs, j.t, j.n_steps, j.budget, dtype), jobs))
+    main = torch.cuda.current_stream()
+
+    def one(j):
+        tid = threading.get_ident()
+        st = _BUILD_STREAMS.get(tid)
+        if st is None:
+            st = _BUILD_STREAMS[tid] = torch.cuda.Stream()
+        st.wait_stream(main)  # inputs and freed memory of earlier work on the main stream
+        with torch.cuda.stream(st):
+            f = hs.hs_build_factors(j.ham.labels, j.ham.coeffs, j.t, j.n_steps, j.budget, dtype)
+        return f, st
+
+    out = list(_BUILD_POOL.map(one, jobs))
+    for st in {id(st): st for _, st in out}.values():
+        main.wait_stream(st)
+    return [f for f, _ in out]
 
 
 def batch_options(jobs, views, args, dtype):
@@ -991,12 +1011,12 @@ def serve_batch_opts(jobs, n=16):
 def serve_trial(rate, seconds, opts, seed=1005):
     """One realtime Poisson stream through a fresh server; its stats with the
     offered rate and whether the queue stayed bounded (the median latency of
-    the last quarter of the requests within 1.5x that of the second quarter
+    the last quarter of the requests within 1.2x that of the second quarter
     plus 25 ms)."""
     from paper_2606_16959_gb300 import serve, workloads as W
     reqs = serve.requests_from_jobs(W.serve_stream(rate=rate, duration=seconds, seed=seed))
     st = serve.Server(batch_opts=opts).run(reqs, realtime=True)
-    st.update(rate=rate, seconds=seconds, bounded=bool(st["p50_q4_ms"] <= 1.5 * st["p50_q2_ms"] + 25.0))
+    st.update(rate=rate, seconds=seconds, bounded=bool(st["p50_q4_ms"] <= 1.2 * st["p50_q2_ms"] + 25.0))
     return st
 
 
