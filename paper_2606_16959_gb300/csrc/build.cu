@@ -308,6 +308,67 @@ struct GroupBasis {
   }
 };
 
+// The stored diagonals of factors with value tables, one diagonal at a time
+// (its offset, row base and x-mask coordinates fixed for the whole pass), two
+// consecutive rows per thread and one 2 x sizeof(T2) store: a streaming write
+// with a few integer operations per element.  Row r's entry on diagonal d is
+// table entry pattern(r) * S + cc when r ^ (r + d) = u_cc lies in the x-mask
+// set, an exact zero otherwise.
+template <typename T2>
+__device__ __forceinline__ void copy_diagonals(const BuildArgs& a, const GroupBasis& G, int D, int d0, int vt0,
+                                               uint32_t sm) {
+  const T2* __restrict__ vt = reinterpret_cast<const T2*>(a.vt);
+  T2* __restrict__ vals = reinterpret_cast<T2*>(a.vals);
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int k = 0; k < D; ++k) {
+    const int64_t d = a.offs[d0 + k];
+    const int64_t rb = a.rowbase[d0 + k];
+    auto value = [&](int64_t r) -> T2 {
+      T2 v;
+      v.x = 0;
+      v.y = 0;
+      const int64_t col = r + d;
+      if (col < 0 || col >= a.N) return v;
+      const uint64_t uu = uint64_t(r) ^ uint64_t(col);
+      int cc = 0;
+      uint64_t rec = 0;
+#pragma unroll
+      for (int i = 0; i < kMaxXDim; ++i)
+        if (i < G.xd && ((uu >> G.piv[i]) & 1ull)) {
+          cc |= 1 << i;
+          rec ^= G.bas[i];
+        }
+      if (rec != uu) return v;
+      uint32_t pat = 0;
+      int q = 0;
+      for (uint32_t t = sm; t; t &= t - 1u, ++q) pat |= uint32_t((uint64_t(r) >> (__ffs(t) - 1)) & 1u) << q;
+      return vt[HS_BCHK(int64_t(vt0) + int64_t(pat) * G.S + cc, a.n_vt, BS_BUILD_VT)];
+    };
+    // Only the rows whose column is in range own an element of the diagonal
+    // (the others lie in neighbouring diagonals' storage). Rows r0, r0 + 1
+    // with r0 even: element rb + r0 is 16-byte aligned (the row base is a
+    // multiple of 32 bytes), so a pair inside the range is one vector store.
+    const int64_t lo = d < 0 ? -d : 0, hi = d > 0 ? a.N - d : a.N;
+    for (int64_t pr = (lo >> 1) + int64_t(blockIdx.x) * blockDim.x + threadIdx.x; pr < (hi + 1) >> 1; pr += stride) {
+      const int64_t r0 = 2 * pr;
+      const bool in0 = r0 >= lo && r0 < hi, in1 = r0 + 1 >= lo && r0 + 1 < hi;
+      if (in0 && in1) {
+        const T2 v0 = value(r0), v1 = value(r0 + 1);
+        if constexpr (sizeof(T2) == 8) {
+          *reinterpret_cast<float4*>(vals + HS_BCHK(rb + r0, a.n_vals - 1, BS_BUILD_VAL)) =
+              make_float4(v0.x, v0.y, v1.x, v1.y);
+        } else {
+          vals[HS_BCHK(rb + r0, a.n_vals, BS_BUILD_VAL)] = v0;
+          vals[HS_BCHK(rb + r0 + 1, a.n_vals, BS_BUILD_VAL)] = v1;
+        }
+      } else {
+        if (in0) vals[HS_BCHK(rb + r0, a.n_vals, BS_BUILD_VAL)] = value(r0);
+        if (in1) vals[HS_BCHK(rb + r0 + 1, a.n_vals, BS_BUILD_VAL)] = value(r0 + 1);
+      }
+    }
+  }
+}
+
 // The stored diagonals of factors with value tables (few registers, so the
 // copy runs at full occupancy whatever the widest factor of the set).
 __global__ void __launch_bounds__(256) copy_kernel(BuildArgs a, bool c64) {
@@ -317,9 +378,9 @@ __global__ void __launch_bounds__(256) copy_kernel(BuildArgs a, bool c64) {
   GroupBasis G;
   G.load(a, g);
   if (c64)
-    copy_rows<float2>(a, G, a.fac_D[g], a.fac_diag0[g], vt0, a.smask[g]);
+    copy_diagonals<float2>(a, G, a.fac_D[g], a.fac_diag0[g], vt0, a.smask[g]);
   else
-    copy_rows<double2>(a, G, a.fac_D[g], a.fac_diag0[g], vt0, a.smask[g]);
+    copy_diagonals<double2>(a, G, a.fac_D[g], a.fac_diag0[g], vt0, a.smask[g]);
 }
 
 template <int MAXS>
