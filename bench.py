@@ -524,6 +524,15 @@ def time_batch(jobs, args, world, rank, dtype):
         torch.cuda.synchronize()
         info = (b.n_levels, b.n_ctas, b.n_updates, b.n_separate)
         alg = sum(algorithmic_bytes(f, j, 1) for f, j in zip(facs, jobs))
+        state_bytes = 0
+        if bopts.get("method") == 3:  # levels each register-batched job takes part in x its state in and out
+            T, B = bopts.get("tile_bits") or 13, bopts.get("reg_bits") or 5
+            for f, j in zip(facs, jobs):
+                n = j.ham.n_qubits
+                if n >= B + 5:
+                    n_lv = hs.hs_evolve_plan(f, 1, j.n_steps, method=3, tile_bits=min(T, n),
+                                             low_bits=bopts.get("low_bits") or 2, reg_bits=B)[0]
+                    state_bytes += n_lv * 2 * 8 * (1 << n)
         b.close()
         for f in facs:
             f.close()
@@ -551,7 +560,8 @@ def time_batch(jobs, args, world, rank, dtype):
     norms = outs[:, 2].cpu().numpy()
     total_ms = max_over_ranks(sum(step_ms), world)
     return dict(units=info[2], levels=info[0], ctas=info[1], separate=info[3], step_ms=step_ms, launch_ms=launch_ms,
-                total_ms=total_ms, alg_bytes=alg, clocks=clocks, max_norm_drift=float(np.max(np.abs(norms - 1.0))),
+                total_ms=total_ms, alg_bytes=alg, state_bytes=state_bytes, clocks=clocks,
+                max_norm_drift=float(np.max(np.abs(norms - 1.0))),
                 launches=hs.hs_kernel_launches() - l0, bopts=bopts,
                 kernel="qlevel_kernel" if bopts.get("method") == 3 else "batch_level_kernel")
 
@@ -787,9 +797,14 @@ def run_ours(args):
     hbm, peak_kind = peaks()
     launches_evolve = res["n_sweeps"] + res["n_plain"]
     avg_launch_s = statistics.mean(res["evolve_ms"]) / 1000.0 / max(1, launches_evolve)
-    per_launch_bytes = res["alg_bytes"] / max(1, launches_evolve)
-    achieved = per_launch_bytes / avg_launch_s / 1e9
+    model_bytes = res["alg_bytes"] / max(1, launches_evolve)
     kernel = sweep_kernel_name(args.tuned_opts, res["n_sweeps"])
+    # A register sweep reads no stored factor value (it generates them), so its
+    # algorithmic bytes per launch are the state in and out once; the per
+    # factor-application figure of the staged paths stays beside it (model_*).
+    s_bytes = 8 if dtype == "c64" else 16
+    per_launch_bytes = 2 * s_bytes * res["N"] * res["R"] if kernel == "qsweep_kernel" else model_bytes
+    achieved = per_launch_bytes / avg_launch_s / 1e9
     traffic = profiled_traffic(args.workload, kernel) if not args.qubits else None
     line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": K, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -798,6 +813,7 @@ def run_ours(args):
                          "traffic": traffic, "peak_source": peak_kind,
                          "kernel": kernel,
                          "algorithmic_bytes_per_launch": per_launch_bytes,
+                         "model_bytes_per_launch": model_bytes, "model_frac": model_bytes / avg_launch_s / 1e9 / hbm,
                          "avg_launch_us": avg_launch_s * 1e6, **dram_fields(traffic, avg_launch_s, hbm),
                          **({"note": "evolution time per sweep launch, including the per-step rebuild "
                                      "launches of the driven factors"} if job.drive is not None else {})},
@@ -828,8 +844,11 @@ def run_batch(args, rank, world):
     e2e = time_batch_e2e(jobs, args, dtype, res["bopts"])
     hbm, peak_kind = peaks()
     launch_s = statistics.mean(res["launch_ms"]) / 1000.0
-    per_launch_bytes = res["alg_bytes"] / max(1, res["levels"])
-    achieved = res["alg_bytes"] / launch_s / 1e9
+    model_bytes = res["alg_bytes"] / max(1, res["levels"])
+    # register-sweep levels: the states of the level's jobs in and out (see run_ours)
+    total_bytes = res["state_bytes"] if res.get("kernel") == "qlevel_kernel" else res["alg_bytes"]
+    per_launch_bytes = total_bytes / max(1, res["levels"])
+    achieved = total_bytes / launch_s / 1e9
     traffic = profiled_traffic("batch256", res.get("kernel", "batch_level_kernel")) if args.batch_jobs == 256 else None
     cfg = {"workload": "batch256", "description": desc, "n_jobs": len(jobs), "levels_per_step": res["levels"],
            "ctas_per_step": res["ctas"], "separate_jobs": res["separate"], "batch_options": res["bopts"],
@@ -840,6 +859,8 @@ def run_batch(args, rank, world):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                          "traffic": traffic, "peak_source": peak_kind, "kernel": res["kernel"],
                          "algorithmic_bytes_per_launch": per_launch_bytes,
+                         "model_bytes_per_launch": model_bytes,
+                         "model_frac": res["alg_bytes"] / launch_s / 1e9 / hbm,
                          "avg_launch_us": launch_s * 1e6 / max(1, res["levels"]),
                          **dram_fields(traffic, launch_s / max(1, res["levels"]), hbm)},
             "e2e": {"value": res["units"] / (e2e["ms"] / 1000.0), "unit": METRIC,
