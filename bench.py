@@ -189,9 +189,9 @@ TUNE_CACHE = os.path.join(ROOT, "paper_2606_16959_gb300", "_build", "autotune_be
 # Device-code sources of each kernel: a summary's DRAM figures count only while
 # these are unchanged since the capture.
 KERNEL_SOURCES = {"sweep_kernel": ("apply.cu", "sweep_core.cuh", "hs_internal.h"),
-                  "qsweep_kernel": ("qsweep.cu", "qsweep.h", "sweep_core.cuh", "bounds.cuh", "hs_internal.h"),
+                  "qsweep_kernel": ("qsweep.cu", "qsweep.h", "qplan.cpp", "sweep_core.cuh", "bounds.cuh", "hs_internal.h"),
                   "batch_level_kernel": ("batch.cu", "sweep_core.cuh", "hs_internal.h"),
-                  "qlevel_kernel": ("qsweep.cu", "qsweep.h", "batch.cu", "sweep_core.cuh", "bounds.cuh", "hs_internal.h"),
+                  "qlevel_kernel": ("qsweep.cu", "qsweep.h", "qplan.cpp", "batch.cu", "sweep_core.cuh", "bounds.cuh", "hs_internal.h"),
                   "spmv_kernel": ("dia.cu",)}
 
 

@@ -116,8 +116,16 @@ bool plan_qsweep(const hs_factors* f, const std::vector<int>& factors, uint32_t 
   // bits; a new layout takes the needs of as many following ops as fit.
   const uint32_t pin = c64 ? 1u : 0u;
   const uint32_t tile_all = (T >= 32) ? 0xffffffffu : ((1u << T) - 1u);
+  // Spare register slots take bits above the five lowest chunk bits (local
+  // bits 1..5 for complex64, 0..4 for complex128) first, highest first, so
+  // that those bits stay thread bits: the lanes then span 32 consecutive
+  // 16-byte chunks and the direct stores of the last layout write whole
+  // 32-byte sectors.
+  const int lane_lo = c64 ? 1 : 0, lane_hi = lane_lo + 5;
   auto fill = [&](uint32_t R) {
-    for (int b = 0; b < T && __builtin_popcount(R) < B; ++b) R |= 1u << b;
+    for (int b = T - 1; b >= 0 && __builtin_popcount(R) < B; --b)
+      if (b >= lane_hi || b < lane_lo) R |= 1u << b;
+    for (int b = lane_lo; b < lane_hi && b < T && __builtin_popcount(R) < B; ++b) R |= 1u << b;
     return R;
   };
   std::vector<uint32_t> lay_of(ops.size(), 0);
