@@ -761,11 +761,41 @@ __device__ __forceinline__ void qsweep_core(const Args& a, uint32_t u0, uint32_t
         }
       }
     };
+    // When the two lowest register bits are local bits 0 and 1 (complex64;
+    // for complex128 register bit 0 is local bit 0) and the tile keeps those
+    // bits contiguous, a thread's registers 4q .. 4q + 3 (2q, 2q + 1) are 32
+    // consecutive bytes: one 32-byte store fills a whole sector.
+    constexpr int WB = V == 2 ? 2 : 1;  // register bits inside a 32-byte store
+    auto store_wide = [&](auto scale) {
+#pragma unroll
+      for (int q = 0; q < (NR >> WB); ++q) {
+        uint32_t g = gt;
+#pragma unroll
+        for (int i = WB; i < B; ++i)
+          if (((q << WB) >> i) & 1) g ^= go[i];
+        T2* p = dst + HS_BCHK(g, a.N - (1 << WB) + 1, BS_REG_STATE);
+        if constexpr (V == 2) {
+          const T2 v0 = scale(x[4 * q]), v1 = scale(x[4 * q + 1]), v2 = scale(x[4 * q + 2]), v3 = scale(x[4 * q + 3]);
+          asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};\n" ::"l"(p), "f"(v0.x), "f"(v0.y),
+                       "f"(v1.x), "f"(v1.y), "f"(v2.x), "f"(v2.y), "f"(v3.x), "f"(v3.y)
+                       : "memory");
+        } else {
+          const T2 v0 = scale(x[2 * q]), v1 = scale(x[2 * q + 1]);
+          asm volatile("st.global.v4.f64 [%0], {%1, %2, %3, %4};\n" ::"l"(p), "d"(v0.x), "d"(v0.y), "d"(v1.x), "d"(v1.y)
+                       : "memory");
+        }
+      }
+    };
+    const uint32_t wide_bits = (1u << WB) - 1u;  // local bits that must be the lowest register bits
+    const bool wide = (cur->reg & wide_bits) == wide_bits && (m0 & wide_bits) == wide_bits &&
+                      (reinterpret_cast<uintptr_t>(a.dst) & 31u) == 0;  // (states may be only 16-byte aligned)
     if (K == 0) {
-      store_rows([&](T2 v) { return T2{v.x * m, v.y * m}; });
+      auto sc = [&](T2 v) { return T2{v.x * m, v.y * m}; };
+      if (wide) store_wide(sc); else store_rows(sc);
     } else {
       const R cr = K == 2 ? -m : R(0), ci = K == 1 ? -m : (K == 3 ? m : R(0));
-      store_rows([&](T2 v) { return T2{fma(v.x, cr, -v.y * ci), fma(v.x, ci, v.y * cr)}; });
+      auto sc = [&](T2 v) { return T2{fma(v.x, cr, -v.y * ci), fma(v.x, ci, v.y * cr)}; };
+      if (wide) store_wide(sc); else store_rows(sc);
     }
   }
 }

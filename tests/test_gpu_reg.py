@@ -317,3 +317,23 @@ def test_evolve_batch_one_call(dt):
         assert torch.equal(a, c), (ham.family, ham.n_qubits)
         _check(a.cpu().numpy(), _oracle(ham, 0.7, steps, p0), dt, f"{ham.family} n={ham.n_qubits}")
         f.close()
+
+
+def test_reg_state_aligned_to_16_bytes_only():
+    """A state that is 16-byte but not 32-byte aligned (allowed by the C ABI)
+    takes the 16-byte store path and gives the same bits as an aligned one."""
+    rng = np.random.default_rng(4400)
+    ham = W.maxcut_3regular(14, 11)
+    psi0 = np.stack([W.gaussian_state(14, rng) for _ in range(2)])
+    f = hs.hs_build_factors(ham.labels, ham.coeffs, 0.9, 4, 4, "c64")
+    a = torch.from_numpy(psi0).to("cuda", torch.complex64)
+    buf = torch.zeros(2 * (1 << 14) + 2, dtype=torch.complex64, device="cuda")
+    b = buf[2:].view(2, 1 << 14)  # 16 bytes past a 256-byte boundary
+    assert b.data_ptr() % 32 == 16
+    b.copy_(a)
+    for psi in (a, b):
+        hs.hs_evolve_ex(f, psi, 4, method=REG, tile_bits=13, low_bits=3, reg_bits=5)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    _check(a.cpu().numpy(), _oracle(ham, 0.9, 4, psi0), "c64", "maxcut14")
+    f.close()
