@@ -177,8 +177,8 @@ typedef struct {
                      values as the stored diagonals); 1: every factor is staged from its diagonals */
   int reg_bits;   /* REG: rows per thread 2^reg_bits, 4 or 5 (complex128: 4); 0 = library choice
                      (5 for complex64, 4 for complex128).  REG tiles: tile_bits 0 = min(13, n_qubits)
-                     for complex64, min(12, n_qubits) for complex128; at most reg_bits + 8 (complex64)
-                     or 13 (complex128) */
+                     for complex64, min(12, n_qubits) for complex128; at least reg_bits + 5, at most
+                     13, or 14 for complex64 with reg_bits 5 (512 threads per CTA, one CTA per SM) */
 } hs_evolve_opts;
 
 /* hs_evolve with an explicit method and tiling (opts may be NULL = AUTO). */

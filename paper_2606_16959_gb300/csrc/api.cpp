@@ -668,7 +668,9 @@ int resolve_opts(const hs_factors* f, int n_rhs, const hs_evolve_opts* opts, hs_
       rb = 1;
       tb = o.tile_bits > 0 ? o.tile_bits : std::min(c64 ? 13 : 12, n);
       if (tb > n) tb = n;
-      if (tb < B + 5 || tb > 13) return fail(HS_EINVAL, "register sweeps take tile_bits reg_bits + 5 .. 13");
+      const int tb_max = (c64 && B == 5) ? 14 : 13;  // 2^(tile_bits - reg_bits) threads, at most 512
+      if (tb < B + 5 || tb > tb_max)
+        return fail(HS_EINVAL, "register sweeps take tile_bits reg_bits + 5 .. 13 (14 for complex64 with reg_bits 5)");
       return HS_OK;
     }
     // States too small for a register tile: fused sweeps with their defaults.

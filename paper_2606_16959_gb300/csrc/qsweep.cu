@@ -801,9 +801,11 @@ __device__ __forceinline__ void qsweep_core(const Args& a, uint32_t u0, uint32_t
 }
 
 // FULL: the kernel with the TAB and general-rotation paths; sweeps without
-// them run the lighter instantiation (fewer live registers, no spills).
-template <typename R, int B, bool FULL>
-__global__ void __launch_bounds__(B == 5 ? 256 : 512, B == 5 ? 2 : 1) qsweep_kernel(const __grid_constant__ Args a) {
+// them run the lighter instantiation (fewer live registers, no spills).  NT:
+// threads per CTA the instantiation is built for (2^(tile_bits - B); 512 for
+// 2^14-row complex64 tiles with five register bits, one CTA per SM).
+template <typename R, int B, bool FULL, int NT = (B == 5 ? 256 : 512)>
+__global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) qsweep_kernel(const __grid_constant__ Args a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const uint32_t u0 = blockIdx.x * uint32_t(a.units_per_cta);
   const uint32_t u1 = min(uint32_t(a.n_units), u0 + uint32_t(a.units_per_cta));
@@ -830,13 +832,21 @@ using LFn = void (*)(LevelArgs);
 
 using QFn = void (*)(Args);
 
+// The instantiation for (precision, register bits, tile bits): 2^(T - B)
+// threads, at most 256 for five register bits (512 with T = 14), at most 512
+// for four; nullptr otherwise.
 template <bool FULL>
-QFn qsweep_fn_t(hs_dtype dt, int B) {
-  if (dt == HS_C64)
-    return B == 5 ? qsweep_kernel<float, 5, FULL> : (B == 4 ? qsweep_kernel<float, 4, FULL> : nullptr);
-  return B == 4 ? qsweep_kernel<double, 4, FULL> : nullptr;
+QFn qsweep_fn_t(hs_dtype dt, int B, int tile_bits) {
+  const int tb = tile_bits - B;
+  if (tb < 5) return nullptr;
+  if (dt == HS_C64 && B == 5)
+    return tb <= 8 ? qsweep_kernel<float, 5, FULL> : (tb == 9 ? qsweep_kernel<float, 5, FULL, 512> : nullptr);
+  if (B == 4 && tb <= 9) return dt == HS_C64 ? qsweep_kernel<float, 4, FULL> : qsweep_kernel<double, 4, FULL>;
+  return nullptr;
 }
-QFn qsweep_fn(hs_dtype dt, int B, bool full) { return full ? qsweep_fn_t<true>(dt, B) : qsweep_fn_t<false>(dt, B); }
+QFn qsweep_fn(hs_dtype dt, int B, bool full, int tile_bits) {
+  return full ? qsweep_fn_t<true>(dt, B, tile_bits) : qsweep_fn_t<false>(dt, B, tile_bits);
+}
 
 template <bool FULL>
 LFn qlevel_fn_t(hs_dtype dt, int B) {
@@ -860,8 +870,11 @@ cudaError_t prepare_qsweep() {
   const int Bs[3] = {5, 4, 4};
   for (int v = 0; v < 3; ++v)
     for (bool full : {false, true}) {
-      e = cudaFuncSetAttribute((const void*)qsweep_fn(dts[v], Bs[v], full), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               int(kSweepSmemMax));
+      e = cudaFuncSetAttribute((const void*)qsweep_fn(dts[v], Bs[v], full, Bs[v] + 8),
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSweepSmemMax));
+      if (e == cudaSuccess && v == 0)
+        e = cudaFuncSetAttribute((const void*)qsweep_fn(dts[v], Bs[v], full, 14),
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSweepSmemMax));
       if (e == cudaSuccess)
         e = cudaFuncSetAttribute((const void*)qlevel_fn(dts[v], Bs[v], full),
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSweepSmemMax));
@@ -920,7 +933,7 @@ cudaError_t launch_qlevel(hs_dtype dt, int B, bool full, int tile_bits, const Le
 cudaError_t launch_qsweep(const hs_factors* f, Args& a, const void* src, void* dst, int n_rhs, int B, bool pdl,
                           cudaStream_t s) {
   const Plan& p = f->plan;
-  QFn fn = qsweep_fn(f->dtype, B, a.full != 0);
+  QFn fn = qsweep_fn(f->dtype, B, a.full != 0, a.tile_bits);
   if (!fn || a.tile_bits - B < 5 || a.tile_bits > p.n_qubits) return cudaErrorInvalidValue;
   fill_job(f, a, const_cast<void*>(src), n_rhs);
   a.dst = dst;

@@ -77,7 +77,8 @@ extern "C" int hs_autotune(const hs_factors* f, const void* psi, int n_rhs, int 
   const int n = f->plan.n_qubits;
   for (int B : {5, 4}) {
     if (dt == HS_C128 && B != 4) continue;
-    for (int tb = std::min(13, n); tb >= std::max(B + 5, std::min(13, n) - 2); --tb)
+    const int tmax = std::min((dt == HS_C64 && B == 5) ? 14 : 13, n);
+    for (int tb = tmax; tb >= std::max(B + 5, tmax - 2); --tb)
       for (int lb : {2, 3, 4}) {
         if (lb > tb) continue;
         hs_evolve_opts o{HS_METHOD_REG, tb, 1, 0, lb, 0, 0, 0};

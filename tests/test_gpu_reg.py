@@ -147,6 +147,11 @@ def test_reg_maxcut_sixteen_states_and_tsp():
     for B in (5, 4):
         got = _evolve(job.ham, job.t, job.n_steps, job.budget, "c64", job.psi0, method=REG, reg_bits=B)
         _check(got, want, "c64", f"maxcut16 B={B}")
+    # 2^14-row tiles (512 threads per CTA)
+    for lb in (2, 3, 4):
+        got = _evolve(job.ham, job.t, job.n_steps, job.budget, "c64", job.psi0, method=REG, reg_bits=5, tile_bits=14,
+                      low_bits=lb)
+        _check(got, want, "c64", f"maxcut16 T=14 lb={lb}")
     # one-hot TSP (16 qubits, every term diagonal): one phase run per step
     rng = np.random.default_rng(4102)
     tsp = W.tsp_onehot(4, 1234)
