@@ -116,6 +116,26 @@ int hs_build_factors_ex(const uint64_t* x, const uint64_t* z, const double* coef
                         int n_qubits, double t, int n_steps, int diag_budget, int order, hs_dtype dtype,
                         void* cuda_stream, hs_factors** out);
 
+/* Build options (flags of hs_build_factors_flags). */
+enum {
+  HS_BUILD_DEFER_DIAGONALS = 1 /* build the planned structure, the per-term records and the value
+                                  tables now, and the stored diagonals only when a call first needs
+                                  them (plain or staged evolution, hs_apply_factor, hs_factor_get,
+                                  a staged batch), on that call's stream; the register sweeps
+                                  generate the factors from the records and never need them.
+                                  Static sets only (time-dependent builds ignore the flag). */
+};
+
+/* hs_build_factors_ex with build options (flags: a combination of the
+ * HS_BUILD_* values above, 0 = hs_build_factors_ex).  The device memory of
+ * the diagonals is allocated at build time either way.  A deferred set's
+ * first use that needs the diagonals builds them on its own stream; uses on
+ * other streams must be ordered after it by the caller.  Errors as
+ * hs_build_factors_ex, and HS_EINVAL for an unknown flag. */
+int hs_build_factors_flags(const uint64_t* x, const uint64_t* z, const double* coeffs, size_t n_terms,
+                           int n_qubits, double t, int n_steps, int diag_budget, int order, hs_dtype dtype,
+                           int flags, void* cuda_stream, hs_factors** out);
+
 /* The product-formula order of a factor set and the factors one step applies
  * (indices for hs_factor_get, in application order).  seq may be NULL (then
  * only the length is returned); otherwise it holds capacity ints.  Errors:

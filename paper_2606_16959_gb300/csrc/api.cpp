@@ -309,6 +309,15 @@ cudaMemPool_t library_pool() {
   return pools[dev];
 }
 
+cudaError_t ensure_diagonals(const hs_factors* f, cudaStream_t s) {
+  std::lock_guard<std::mutex> lk(f->diag_mu);
+  if (!f->diag_pending) return cudaSuccess;
+  const hs_build_inputs& b = f->bin;
+  const cudaError_t e = launch_build_split(f, b.tab_groups, b.n_tab_groups, b.row_groups, b.n_row_groups, s);
+  if (e == cudaSuccess) f->diag_pending = false;
+  return e;
+}
+
 cudaError_t pool_malloc(void** ptr, size_t bytes, cudaStream_t s) {
   cudaMemPool_t p = library_pool();
   if (!p) return cudaMallocAsync(ptr, bytes, s);
@@ -372,7 +381,7 @@ namespace {
 // values built for f = 0).
 int build_impl(const uint64_t* x, const uint64_t* z, const double* coeffs, const double* coeffs1, size_t n_terms,
                int n_qubits, double t, int n_steps, int diag_budget, int order, hs_dtype dtype, void* cuda_stream,
-               hs_factors** out) {
+               hs_factors** out, int flags = 0) {
   if (!out) return fail(HS_EINVAL, "out is NULL");
   *out = nullptr;
   if (!x || !z || !coeffs) return fail(HS_EINVAL, "null term arrays");
@@ -516,7 +525,9 @@ int build_impl(const uint64_t* x, const uint64_t* z, const double* coeffs, const
   }
   e = hs::launch_sincos(fp, nullptr, s);
   if (e == cudaSuccess) e = hs::launch_value_tables(fp, nullptr, 0, s);
-  if (e == cudaSuccess)
+  if (e == cudaSuccess && (flags & HS_BUILD_DEFER_DIAGONALS) && !coeffs1)
+    fp->diag_pending = true;
+  else if (e == cudaSuccess)
     e = hs::launch_build_split(fp, bi.tab_groups, bi.n_tab_groups, bi.row_groups, bi.n_row_groups, s);
   if (e != cudaSuccess) {
     cudaStreamSynchronize(s);
@@ -557,6 +568,17 @@ int hs_build_factors_ex(const uint64_t* x, const uint64_t* z, const double* coef
                         hs_factors** out) {
   return build_impl(x, z, coeffs, nullptr, n_terms, n_qubits, t, n_steps, diag_budget, order, dtype, cuda_stream,
                     out);
+}
+
+int hs_build_factors_flags(const uint64_t* x, const uint64_t* z, const double* coeffs, size_t n_terms, int n_qubits,
+                           double t, int n_steps, int diag_budget, int order, hs_dtype dtype, int flags,
+                           void* cuda_stream, hs_factors** out) {
+  if (flags & ~int(HS_BUILD_DEFER_DIAGONALS)) {
+    if (out) *out = nullptr;
+    return fail(HS_EINVAL, "unknown build flag");
+  }
+  return build_impl(x, z, coeffs, nullptr, n_terms, n_qubits, t, n_steps, diag_budget, order, dtype, cuda_stream,
+                    out, flags);
 }
 
 int hs_build_factors_td(const uint64_t* x, const uint64_t* z, const double* coeffs0, const double* coeffs1,
@@ -741,6 +763,10 @@ int hs_evolve_ex(const hs_factors* f, void* psi, int n_rhs, int n_steps, const h
   const QPlans* qpp = qp.empty() ? nullptr : &qp;
   const bool scratch_needed = has_plain(sw);
   const size_t smem_budget = o.smem_kb > 0 ? size_t(o.smem_kb) * 1024 : hs::kSweepSmemDefault;
+  if (o.method != HS_METHOD_REG || scratch_needed) {  // the schedule reads stored diagonals
+    cudaError_t e = hs::ensure_diagonals(f, s);
+    if (e != cudaSuccess) return cuda_fail(e, "factor build launch");
+  }
 
   if (o.use_graph) {
     hs_factors::GraphKey key{psi, n_rhs, n_steps, int(o.method) * 128 + o.max_fuse + 16384 * o.reg_bits,
@@ -971,7 +997,9 @@ int hs_apply_factor(const hs_factors* f, int g, const void* x, void* y, int n_rh
   if (g < 0 || g >= int(f->plan.groups.size())) return fail(HS_EINVAL, "factor index out of range");
   if (!x || !y || x == y) return fail(HS_EINVAL, "x and y must be distinct non-NULL buffers");
   if (n_rhs < 1) return fail(HS_EINVAL, "n_rhs must be >= 1");
-  cudaError_t e = hs::launch_apply_plain(f, g, x, y, n_rhs, reinterpret_cast<cudaStream_t>(cuda_stream));
+  cudaError_t e = hs::ensure_diagonals(f, reinterpret_cast<cudaStream_t>(cuda_stream));
+  if (e != cudaSuccess) return cuda_fail(e, "factor build launch");
+  e = hs::launch_apply_plain(f, g, x, y, n_rhs, reinterpret_cast<cudaStream_t>(cuda_stream));
   return e == cudaSuccess ? HS_OK : cuda_fail(e, "apply launch");
 }
 
@@ -1030,7 +1058,9 @@ int hs_factor_get(const hs_factors* f, int g, int* term_first, int* term_last, i
   if (offsets)
     for (int k = 0; k < G.D; ++k) offsets[k] = f->plan.offs[G.diag0 + k];
   if (values) {
-    cudaError_t e = cudaDeviceSynchronize();
+    cudaError_t e = hs::ensure_diagonals(f, nullptr);  // (legacy stream; the synchronise below covers it)
+    if (e != cudaSuccess) return cuda_fail(e, "factor build launch");
+    e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
     const int64_t N = f->plan.N;
     const size_t es = hs::elem_bytes(f->dtype);

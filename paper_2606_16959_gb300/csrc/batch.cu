@@ -167,6 +167,7 @@ LevelFn level_fn(int rows) {
 }  // namespace
 
 struct hs_batch {
+  std::vector<const hs_factors*> diag_users;  // factor sets whose stored diagonals the batch reads
   uint64_t graph_kernels = 0;  // kernels one replay of the captured graph launches
   bool value_tables = true;    // read small-support factors from their value tables
   int tiles_per_cta = 1;       // units one CTA runs back to back (tables loaded once)
@@ -404,6 +405,7 @@ int create_reg_batch(const hs_batch_job* jobs, size_t n_jobs, const hs_batch_opt
     JobPlan& P = plans[j];
     if (!P.ok) {
       b->separate.push_back(hs_batch::Sep{J.factors, J.psi, J.n_rhs, J.n_steps});
+      b->diag_users.push_back(J.factors);  // its own (plain or staged) evolution reads the diagonals
       continue;
     }
     const int first = int(b->qdescs.size());
@@ -505,6 +507,7 @@ extern "C" int hs_batch_create(const hs_batch_job* jobs, size_t n_jobs, const hs
                                                 : std::vector<hs::Sweep>{};
     bool ok = !sw.empty();
     for (const hs::Sweep& w : sw) ok = ok && w.fused;
+    b->diag_users.push_back(J.factors);  // staged sweeps and separate evolutions read the diagonals
     if (!ok) {
       b->separate.push_back(hs_batch::Sep{J.factors, J.psi, J.n_rhs, J.n_steps});
       continue;
@@ -632,6 +635,12 @@ extern "C" int hs_batch_launch(hs_batch* b, void* cuda_stream) {
       if (e != cudaSuccess) return hs::report_error(HS_ECUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
       done = true;
     }
+  }
+  // Sets built with deferred diagonals: build them before any launch (and
+  // outside a capture) for the jobs that read them.
+  for (const hs_factors* f : b->diag_users) {
+    e = hs::ensure_diagonals(f, s);
+    if (e != cudaSuccess) return hs::report_error(HS_ECUDA, std::string("factor build: ") + cudaGetErrorString(e));
   }
   if (!b->uploaded) {
     int rc = upload_tables(b, s);

@@ -180,6 +180,10 @@ struct hs_factors {
   hs_build_inputs bin;           // build inputs (device pointers into d_tables)
   double* d_drive = nullptr;     // drive samples of hs_evolve_td (library-owned)
   int drive_cap = 0;
+  // HS_BUILD_DEFER_DIAGONALS: the stored diagonals are built by the first call
+  // that needs them (hs::ensure_diagonals).
+  mutable bool diag_pending = false;
+  mutable std::mutex diag_mu;
   // cached CUDA graphs of evolve launch sequences
   struct GraphKey {
     void* psi;
@@ -235,6 +239,10 @@ cudaError_t launch_inner(const void* a, const void* b, int64_t N, hs_dtype dt, d
 
 // Stream-ordered allocation from the library's memory pool (api.cpp).
 cudaError_t pool_malloc(void** ptr, size_t bytes, cudaStream_t s);
+
+// Build the stored diagonals of a set built with HS_BUILD_DEFER_DIAGONALS, on
+// stream s, if they are not built yet (api.cpp).
+cudaError_t ensure_diagonals(const hs_factors* f, cudaStream_t s);
 
 // Autotuner cache (tune.cpp).
 bool tuned_opts(const hs_factors* f, int n_rhs, hs_evolve_opts* out);

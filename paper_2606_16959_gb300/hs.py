@@ -15,6 +15,7 @@ import numpy as np
 HS_OK, HS_EINVAL, HS_ENOMEM, HS_ECUDA, HS_ETIMEOUT, HS_EDTYPE = 0, -1, -2, -3, -4, -5
 HS_C64, HS_C128 = 1, 2
 HS_METHOD_AUTO, HS_METHOD_PLAIN, HS_METHOD_FUSED, HS_METHOD_REG = 0, 1, 2, 3
+HS_BUILD_DEFER_DIAGONALS = 1
 HS_MAX_QUBITS = 30
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -32,7 +33,7 @@ EXPORTS = (
     "hs_batch_free_async",
     "hs_dia_from_terms", "hs_dia_from_masks", "hs_dia_create", "hs_spgemm", "hs_spme", "hs_estimate_timesteps",
     "hs_spmv", "hs_dia_evolve", "hs_dia_convert", "hs_dia_info", "hs_dia_get", "hs_dia_free",
-    "hs_kernel_launches", "hs_debug_bounds", "hs_expectation", "hs_build_factors_ex", "hs_factors_sequence",
+    "hs_kernel_launches", "hs_debug_bounds", "hs_expectation", "hs_build_factors_ex", "hs_build_factors_flags", "hs_factors_sequence",
     "hs_build_factors_td", "hs_evolve_td", "hs_factors_set_drive", "hs_dia_evolve_td",
     "hs_parse_terms", "hs_evolve_batch", "hs_batch_autotune",
 )
@@ -120,6 +121,8 @@ def lib() -> ctypes.CDLL:
         L.hs_expectation.argtypes = [vp, vp, i, vp, dp, dp]
         L.hs_build_factors_ex.argtypes = [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
                                           dp, sz, i, d, i, i, i, i, vp, ctypes.POINTER(vp)]
+        L.hs_build_factors_flags.argtypes = [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
+                                             dp, sz, i, d, i, i, i, i, i, vp, ctypes.POINTER(vp)]
         L.hs_factors_sequence.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), i, ctypes.POINTER(i)]
         L.hs_build_factors_td.argtypes = [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
                                           dp, dp, sz, i, d, i, i, i, i, vp, ctypes.POINTER(vp)]
@@ -263,10 +266,13 @@ def hs_parse_terms(labels: Sequence[str]):
 
 
 def hs_build_factors(labels: Sequence[str], coeffs, t: float, n_steps: int, diag_budget: int, dtype="c64",
-                     stream=None, order: int = 1) -> Factors:
-    if order != 1:
+                     stream=None, order: int = 1, defer_diagonals: bool = False) -> Factors:
+    """defer_diagonals: HS_BUILD_DEFER_DIAGONALS (the stored diagonals are built
+    by the first call that reads them; register sweeps never do)."""
+    if order != 1 or defer_diagonals:
         x, z, n = hs_parse_terms(labels)
-        return hs_build_factors_masks(x, z, coeffs, n, t, n_steps, diag_budget, dtype, stream, order)
+        return hs_build_factors_masks(x, z, coeffs, n, t, n_steps, diag_budget, dtype, stream, order,
+                                      defer_diagonals)
     arr = (ctypes.c_char_p * len(labels))(*[l.encode() for l in labels])
     c = np.ascontiguousarray(np.asarray(coeffs, dtype=np.float64))
     if c.size != len(labels):
@@ -279,18 +285,19 @@ def hs_build_factors(labels: Sequence[str], coeffs, t: float, n_steps: int, diag
 
 
 def hs_build_factors_masks(x, z, coeffs, n_qubits: int, t: float, n_steps: int, diag_budget: int, dtype="c64",
-                           stream=None, order: int = 1) -> Factors:
+                           stream=None, order: int = 1, defer_diagonals: bool = False) -> Factors:
     xa = np.ascontiguousarray(np.asarray(x, dtype=np.uint64))
     za = np.ascontiguousarray(np.asarray(z, dtype=np.uint64))
     c = np.ascontiguousarray(np.asarray(coeffs, dtype=np.float64))
     if not (xa.size == za.size == c.size):
         raise ValueError("x, z and coeffs differ in length")
     out = ctypes.c_void_p()
-    _check(lib().hs_build_factors_ex(xa.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
-                                     za.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
-                                     c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), xa.size, int(n_qubits),
-                                     float(t), int(n_steps), int(diag_budget), int(order), _dtype_code(dtype),
-                                     _stream(stream), ctypes.byref(out)))
+    _check(lib().hs_build_factors_flags(xa.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                        za.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                        c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), xa.size, int(n_qubits),
+                                        float(t), int(n_steps), int(diag_budget), int(order), _dtype_code(dtype),
+                                        HS_BUILD_DEFER_DIAGONALS if defer_diagonals else 0, _stream(stream),
+                                        ctypes.byref(out)))
     return Factors(out.value)
 
 

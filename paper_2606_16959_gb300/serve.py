@@ -10,7 +10,10 @@ states stay on the device; memory is returned in stream order when a group
 finishes.  Completion times come from CUDA events measured against a start
 event, so latency = GPU completion time - arrival time.
 
-A request's device bytes come from the structural dry run of its terms,
+Factor sets are built with their stored diagonals deferred
+(HS_BUILD_DEFER_DIAGONALS): the register-sweep batches generate every factor
+from its terms, so the diagonals are only built if a batch's own options need
+them.  A request's device bytes come from the structural dry run of its terms,
 cached per Hamiltonian structure (labels and budget), so admission does no
 planning work for a structure it has seen.  A build that fails for lack of
 device memory (HS_ENOMEM) puts its group back at the head of the queue and
@@ -170,7 +173,10 @@ class Server:
                     st = torch.complex(re, im).to(self.tdt)
                     st /= torch.linalg.vector_norm(st)
                 states.append(st)
-                facs.append(hs.hs_build_factors(r.labels, r.coeffs, r.t, r.n_steps, r.budget, self.dtype, stream=s))
+                # stored diagonals deferred: the register-sweep batches generate the
+                # factors from their terms (a staged batch would build them first)
+                facs.append(hs.hs_build_factors(r.labels, r.coeffs, r.t, r.n_steps, r.budget, self.dtype, stream=s,
+                                                defer_diagonals=True))
                 r.updates = r.n_steps * facs[-1].n_factors * (1 << r.n_qubits)
             b = hs.hs_batch_create([(f, st, r.n_steps) for f, st, r in zip(facs, states, group)], use_graph=False,
                                    **self.batch_opts)

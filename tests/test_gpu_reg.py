@@ -342,3 +342,55 @@ def test_reg_state_aligned_to_16_bytes_only():
     assert torch.equal(a, b)
     _check(a.cpu().numpy(), _oracle(ham, 0.9, 4, psi0), "c64", "maxcut14")
     f.close()
+
+
+def test_deferred_diagonals_every_consumer():
+    """HS_BUILD_DEFER_DIAGONALS: register sweeps never build the stored
+    diagonals; the first call that reads them (staged or plain evolution, a
+    graph capture, hs_apply_factor, hs_factor_get, a staged batch) builds them,
+    and every result is bitwise that of the eagerly built set."""
+    rng = np.random.default_rng(4500)
+    ham = W.tfim_chain(13, 1.0, 0.8)
+    psi0 = np.stack([W.gaussian_state(13, rng) for _ in range(2)])
+    t, steps, budget = 0.9, 4, 8
+
+    def run(defer, **kw):
+        f = hs.hs_build_factors(ham.labels, ham.coeffs, t, steps, budget, "c64", defer_diagonals=defer)
+        psi = torch.from_numpy(psi0).to("cuda", torch.complex64)
+        hs.hs_evolve_ex(f, psi, steps, **kw)
+        torch.cuda.synchronize()
+        return f, psi
+
+    for kw in (dict(method=REG), dict(method=hs.HS_METHOD_FUSED), dict(method=hs.HS_METHOD_PLAIN),
+               dict(method=hs.HS_METHOD_FUSED, use_graph=True)):
+        fe, a = run(False, **kw)
+        fd, b = run(True, **kw)
+        assert torch.equal(a, b), kw
+        if kw["method"] == REG:  # the deferred set still builds its diagonals when asked
+            for g in range(fe.n_factors):
+                assert np.array_equal(fe.factor(g)[3], fd.factor(g)[3])
+        fe.close()
+        fd.close()
+    _check(a.cpu().numpy(), _oracle(ham, t, steps, psi0), "c64", "deferred")
+    # hs_apply_factor and a staged batch on fresh deferred sets
+    fe = hs.hs_build_factors(ham.labels, ham.coeffs, t, steps, budget, "c64")
+    fd = hs.hs_build_factors(ham.labels, ham.coeffs, t, steps, budget, "c64", defer_diagonals=True)
+    x = torch.from_numpy(psi0).to("cuda", torch.complex64)
+    ye, yd = torch.empty_like(x), torch.empty_like(x)
+    hs.hs_apply_factor(fe, 0, x, ye)
+    hs.hs_apply_factor(fd, 0, x, yd)
+    torch.cuda.synchronize()
+    assert torch.equal(ye, yd)
+    fd.close()
+    fd = hs.hs_build_factors(ham.labels, ham.coeffs, t, steps, budget, "c64", defer_diagonals=True)
+    a, b = x.clone(), x.clone()
+    be = hs.hs_batch_create([(fe, a, steps)], use_graph=False)
+    bd = hs.hs_batch_create([(fd, b, steps)], use_graph=False)
+    hs.hs_batch_launch(be)
+    hs.hs_batch_launch(bd)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    be.close()
+    bd.close()
+    fe.close()
+    fd.close()
