@@ -314,46 +314,60 @@ struct GroupBasis {
 // with a few integer operations per element.  Row r's entry on diagonal d is
 // table entry pattern(r) * S + cc when r ^ (r + d) = u_cc lies in the x-mask
 // set, an exact zero otherwise.
+static_assert(HS_MAX_QUBITS <= 30, "copy_diagonals keeps row indices and offsets in 32 bits");
+
 template <typename T2>
 __device__ __forceinline__ void copy_diagonals(const BuildArgs& a, const GroupBasis& G, int D, int d0, int vt0,
                                                uint32_t sm) {
+  // Row and column indices fit in 32 bits (at most 2^30 rows), and so do the
+  // x-mask basis and the offsets.
   const T2* __restrict__ vt = reinterpret_cast<const T2*>(a.vt);
   T2* __restrict__ vals = reinterpret_cast<T2*>(a.vals);
-  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  const uint32_t stride = gridDim.x * blockDim.x;
+  const uint32_t N = uint32_t(a.N);
+  uint32_t bas[kMaxXDim];
+#pragma unroll
+  for (int i = 0; i < kMaxXDim; ++i) bas[i] = uint32_t(G.bas[i]);
+  // pattern(r): r's bits at smask, packed; a window of consecutive bits is a
+  // shift and a mask.
+  const int sm_lo = sm ? __ffs(sm) - 1 : 0;
+  const bool sm_window = ((sm >> sm_lo) & ((sm >> sm_lo) + 1u)) == 0u;
+  auto pattern = [&](uint32_t r) -> uint32_t {
+    if (sm_window) return (r & sm) >> sm_lo;
+    uint32_t p = 0;
+    int q = 0;
+    for (uint32_t t = sm; t; t &= t - 1u, ++q) p |= ((r >> (__ffs(t) - 1)) & 1u) << q;
+    return p;
+  };
   for (int k = 0; k < D; ++k) {
-    const int64_t d = a.offs[d0 + k];
+    const int32_t d = int32_t(a.offs[d0 + k]);
     const int64_t rb = a.rowbase[d0 + k];
-    auto value = [&](int64_t r) -> T2 {
+    auto value = [&](uint32_t r) -> T2 {
+      const uint32_t uu = r ^ uint32_t(int32_t(r) + d);
+      int cc = 0;
+      uint32_t rec = 0;
+#pragma unroll
+      for (int i = 0; i < kMaxXDim; ++i)
+        if (i < G.xd && ((uu >> G.piv[i]) & 1u)) {
+          cc |= 1 << i;
+          rec ^= bas[i];
+        }
       T2 v;
       v.x = 0;
       v.y = 0;
-      const int64_t col = r + d;
-      if (col < 0 || col >= a.N) return v;
-      const uint64_t uu = uint64_t(r) ^ uint64_t(col);
-      int cc = 0;
-      uint64_t rec = 0;
-#pragma unroll
-      for (int i = 0; i < kMaxXDim; ++i)
-        if (i < G.xd && ((uu >> G.piv[i]) & 1ull)) {
-          cc |= 1 << i;
-          rec ^= G.bas[i];
-        }
-      if (rec != uu) return v;
-      uint32_t pat = 0;
-      int q = 0;
-      for (uint32_t t = sm; t; t &= t - 1u, ++q) pat |= uint32_t((uint64_t(r) >> (__ffs(t) - 1)) & 1u) << q;
-      return vt[HS_BCHK(int64_t(vt0) + int64_t(pat) * G.S + cc, a.n_vt, BS_BUILD_VT)];
+      if (rec == uu) v = vt[HS_BCHK(int64_t(vt0) + int64_t(pattern(r)) * G.S + cc, a.n_vt, BS_BUILD_VT)];
+      return v;
     };
     // Only the rows whose column is in range own an element of the diagonal
     // (the others lie in neighbouring diagonals' storage). Rows r0, r0 + 1
     // with r0 even: element rb + r0 is 16-byte aligned (the row base is a
     // multiple of 32 bytes), so a pair inside the range is one vector store.
-    const int64_t lo = d < 0 ? -d : 0, hi = d > 0 ? a.N - d : a.N;
-    for (int64_t pr = (lo >> 1) + int64_t(blockIdx.x) * blockDim.x + threadIdx.x; pr < (hi + 1) >> 1; pr += stride) {
-      const int64_t r0 = 2 * pr;
-      const bool in0 = r0 >= lo && r0 < hi, in1 = r0 + 1 >= lo && r0 + 1 < hi;
+    const uint32_t lo = d < 0 ? uint32_t(-d) : 0u, hi = d > 0 ? N - uint32_t(d) : N;
+    for (uint32_t pr = (lo >> 1) + blockIdx.x * blockDim.x + threadIdx.x; pr < (hi + 1u) >> 1; pr += stride) {
+      const uint32_t r0 = 2u * pr;
+      const bool in0 = r0 >= lo && r0 < hi, in1 = r0 + 1u >= lo && r0 + 1u < hi;
       if (in0 && in1) {
-        const T2 v0 = value(r0), v1 = value(r0 + 1);
+        const T2 v0 = value(r0), v1 = value(r0 + 1u);
         if constexpr (sizeof(T2) == 8) {
           *reinterpret_cast<float4*>(vals + HS_BCHK(rb + r0, a.n_vals - 1, BS_BUILD_VAL)) =
               make_float4(v0.x, v0.y, v1.x, v1.y);
@@ -363,7 +377,7 @@ __device__ __forceinline__ void copy_diagonals(const BuildArgs& a, const GroupBa
         }
       } else {
         if (in0) vals[HS_BCHK(rb + r0, a.n_vals, BS_BUILD_VAL)] = value(r0);
-        if (in1) vals[HS_BCHK(rb + r0 + 1, a.n_vals, BS_BUILD_VAL)] = value(r0 + 1);
+        if (in1) vals[HS_BCHK(rb + r0 + 1, a.n_vals, BS_BUILD_VAL)] = value(r0 + 1u);
       }
     }
   }
