@@ -338,9 +338,8 @@ def time_ours(job, args, world, dtype, rank):
         step(keep)
     torch.cuda.synchronize()
     f0 = keep[0]
-    if job.drive is not None:  # one step's schedule, repeated (no sweep spans two steps)
-        n_sweeps, n_plain, tb, rb = hs.hs_evolve_plan(f0, R, 1, **opts)
-        n_sweeps, n_plain = n_sweeps * job.n_steps, n_plain * job.n_steps
+    if job.drive is not None:
+        n_sweeps, n_plain, tb, rb = hs.hs_evolve_td_plan(f0, R, job.n_steps, **opts)
     else:
         n_sweeps, n_plain, tb, rb = hs.hs_evolve_plan(f0, R, job.n_steps, **opts)
     alg = algorithmic_bytes(f0, job, R)
@@ -398,11 +397,11 @@ def time_e2e(job, args, dtype):
     # States are independent: with several states the step runs in chunks of
     # states, each chunk's upload overlapping the previous chunk's evolution
     # and each download the next one's (a copy stream beside the compute
-    # stream); one state, or a time-dependent job, runs as one piece.  Fewer,
-    # larger chunks keep the sweeps' grids full.
+    # stream); one state runs as one piece.  Fewer, larger chunks keep the
+    # sweeps' grids full.
     R = host_in.shape[0]
     n_chunks = args.e2e_chunks or 2  # (measured on maxcut24: 2 chunks 2.11e12, 4: 2.09e12, 8: 1.75e12)
-    if job.drive is not None or R % n_chunks or R < 2 * n_chunks:
+    if R % n_chunks or R < 2 * n_chunks:
         n_chunks = 1
     cs = R // n_chunks
     main = torch.cuda.current_stream()
@@ -854,8 +853,9 @@ def run_ours(args):
                          "algorithmic_bytes_per_launch": per_launch_bytes,
                          "model_bytes_per_launch": model_bytes, "model_frac": model_bytes / avg_launch_s / 1e9 / hbm,
                          "avg_launch_us": avg_launch_s * 1e6, **dram_fields(traffic, avg_launch_s, hbm),
-                         **({"note": "evolution time per sweep launch, including the per-step rebuild "
-                                     "launches of the driven factors"} if job.drive is not None else {})},
+                         **({"note": "evolution time per sweep launch, including the launches that "
+                                     "compute the driven factors' records and values"}
+                            if job.drive is not None else {})},
             "e2e": {"value": res["units"] / (e2e["ms"] / 1000.0), "unit": METRIC,
                     "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"]},
             "gpu_launches": res["launches"], "clocks": res["clocks"],

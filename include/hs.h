@@ -228,9 +228,16 @@ int hs_build_factors_td(const uint64_t* x, const uint64_t* z, const double* coef
  * FP64, the values of the factors that hold a term with coeffs1[j] != 0 (their
  * value tables, and the stored diagonals of factors that have no table or that
  * the chosen method reads from diagonals), then applies the step as
- * hs_evolve_ex would; sweeps never span two steps.  The factor values are
- * those of drive[n_steps - 1] afterwards, so calls on one factor set must be
- * ordered (one stream).  opts as hs_evolve_ex (NULL = AUTO); use_graph
+ * hs_evolve_ex would, with no sweep spanning two steps.  Exception: with
+ * HS_METHOD_REG, when every factor application of the n_steps (2 to 65535)
+ * steps fits a register sweep (no value-table factor, no plain launch), the
+ * term records of every step are computed first (one kernel, 48 bytes per
+ * term, angle kind and step, held by the factor set) and the register sweeps
+ * span steps as in hs_evolve_ex.  After an evolution of register sweeps alone
+ * the stored diagonals are rebuilt when something first reads them
+ * (hs_factor_get, hs_apply_factor, an evolution that reads them).  The factor
+ * values are those of drive[n_steps - 1] afterwards, so calls on one factor
+ * set must be ordered (one stream).  opts as hs_evolve_ex (NULL = AUTO); use_graph
  * captures the whole evolution once per (psi, n_rhs, n_steps, options) and
  * replays it with the new drive samples.  Errors: HS_EINVAL (static factor
  * set, NULL or non-finite drive, bad psi / n_rhs / options), HS_ENOMEM,
@@ -250,6 +257,14 @@ int hs_factors_set_drive(hs_factors* f, double drive, void* cuda_stream);
  * used.  Output pointers may be NULL.  Errors: HS_EINVAL. */
 int hs_evolve_plan(const hs_factors* f, int n_rhs, int n_steps, const hs_evolve_opts* opts, int* n_sweeps,
                    int* n_plain, int* tile_bits, int* rhs_block);
+
+/* Launch plan of hs_evolve_td for these arguments (a time-dependent set),
+ * as hs_evolve_plan: the sweep and plain launches of the whole n_steps-step
+ * evolution (register sweeps that span steps counted once; a per-step
+ * schedule n_steps times), without the per-step record and rebuild kernels.
+ * Errors: HS_EINVAL (also for a static factor set). */
+int hs_evolve_td_plan(const hs_factors* f, int n_rhs, int n_steps, const hs_evolve_opts* opts, int* n_sweeps,
+                      int* n_plain, int* tile_bits, int* rhs_block);
 
 /* Measure candidate launch parameters for evolving these n_rhs states by
  * n_steps steps (plain, and fused with several tile_bits / low_bits /

@@ -59,6 +59,7 @@ void release(hs_factors* f, cudaStream_t s) {
   if (f->d_vals) cudaFreeAsync(f->d_vals, s);
   if (f->d_tables) cudaFreeAsync(f->d_tables, s);
   if (f->d_drive) cudaFreeAsync(f->d_drive, s);
+  if (f->d_steprec) cudaFreeAsync(f->d_steprec, s);
   delete f;
 }
 
@@ -68,9 +69,18 @@ void release(hs_factors* f, cudaStream_t s) {
 using QPlans = std::vector<std::shared_ptr<hs::q::Args>>;
 
 // Enqueue the launches of one evolution on stream s.
+// StepRecords: per-step term records of a time-dependent set (register sweeps
+// that span steps address them from their first step).
+struct StepRecords {
+  const double* rq = nullptr;  // 4 doubles per record
+  const double* cs = nullptr;  // 2 doubles per record
+  int stride = 0;              // records per step
+  int n_steps = 0;
+};
+
 int enqueue_evolve(const hs_factors* f, const std::vector<hs::Sweep>& sw, void* psi, int n_rhs, int tile_bits,
                    int rhs_block, size_t smem_budget, bool value_tables, void* scratch, cudaStream_t s,
-                   const QPlans* qp = nullptr, int reg_bits = 0) {
+                   const QPlans* qp = nullptr, int reg_bits = 0, const StepRecords* rec = nullptr) {
   const hs::Plan& p = f->plan;
   void* cur = psi;
   void* other = scratch;
@@ -78,7 +88,11 @@ int enqueue_evolve(const hs_factors* f, const std::vector<hs::Sweep>& sw, void* 
   for (size_t wi = 0; wi < sw.size(); ++wi) {
     const hs::Sweep& w = sw[wi];
     cudaError_t e;
-    if (qp && (*qp)[wi]) {
+    if (qp && (*qp)[wi] && rec) {
+      const int st = w.steps.empty() ? 0 : w.steps[0];
+      e = hs::q::launch_qsweep(f, *(*qp)[wi], cur, cur, n_rhs, reg_bits, true, s, rec->rq + size_t(4) * st * rec->stride,
+                               rec->cs + size_t(2) * st * rec->stride, (rec->n_steps - st) * rec->stride);
+    } else if (qp && (*qp)[wi]) {
       e = hs::q::launch_qsweep(f, *(*qp)[wi], cur, cur, n_rhs, reg_bits, true, s);
     } else if (w.fused) {
       hs::SweepLaunch L;
@@ -119,9 +133,13 @@ bool has_plain(const std::vector<hs::Sweep>& sw) {
 // Register-blocked descriptors for the fused sweeps of sw (method REG): each
 // distinct sweep is planned once; a sweep that cannot be expressed as register
 // ops is replaced by plain launches of its factors.
-void plan_reg(const hs_factors* f, std::vector<hs::Sweep>& sw, int tile_bits, int reg_bits, QPlans& qp) {
+// step_stride > 0: the sweeps span steps of a time-dependent set whose term
+// records are kept per step (step_stride records each); a planned sweep's
+// steps become one entry, the step its records start at.
+void plan_reg(const hs_factors* f, std::vector<hs::Sweep>& sw, int tile_bits, int reg_bits, QPlans& qp,
+              int step_stride = 0) {
   using Pieces = std::vector<std::pair<std::vector<int>, std::shared_ptr<hs::q::Args>>>;
-  std::map<std::pair<uint32_t, std::vector<int>>, std::pair<bool, Pieces>> memo;
+  std::map<std::tuple<uint32_t, std::vector<int>, std::vector<int>>, std::pair<bool, Pieces>> memo;
   std::vector<hs::Sweep> out;
   QPlans plans;
   for (hs::Sweep& w : sw) {
@@ -130,28 +148,36 @@ void plan_reg(const hs_factors* f, std::vector<hs::Sweep>& sw, int tile_bits, in
       plans.push_back(nullptr);
       continue;
     }
-    const auto key = std::make_pair(w.local_mask, w.factors);
+    std::vector<int> rel;
+    if (step_stride > 0)
+      for (int st : w.steps) rel.push_back(st - w.steps[0]);
+    const auto key = std::make_tuple(w.local_mask, w.factors, rel);
     auto it = memo.find(key);
     if (it == memo.end()) {
       Pieces pieces;
       std::string why;
-      const bool ok = hs::q::plan_qsweep_runs(f, w.factors, w.local_mask, tile_bits, reg_bits, pieces, &why);
+      const bool ok = hs::q::plan_qsweep_runs(f, w.factors, w.local_mask, tile_bits, reg_bits, pieces, &why,
+                                               step_stride > 0 ? &rel : nullptr, step_stride);
       it = memo.emplace(key, std::make_pair(ok, std::move(pieces))).first;
     }
     if (it->second.first) {
+      size_t pos = 0;
       for (const auto& pc : it->second.second) {
         hs::Sweep s2;
         s2.fused = true;
         s2.local_mask = w.local_mask;
         s2.factors = pc.first;
+        s2.steps.assign(1, pos < w.steps.size() ? w.steps[pos] : 0);
+        pos += pc.first.size();
         out.push_back(std::move(s2));
         plans.push_back(pc.second);
       }
     } else {
-      for (int g : w.factors) {
+      for (size_t i = 0; i < w.factors.size(); ++i) {
         hs::Sweep pl;
         pl.fused = false;
-        pl.factors.push_back(g);
+        pl.factors.push_back(w.factors[i]);
+        if (i < w.steps.size()) pl.steps.push_back(w.steps[i]);
         out.push_back(std::move(pl));
         plans.push_back(nullptr);
       }
@@ -824,11 +850,54 @@ int hs_evolve(const hs_factors* f, void* psi, int n_rhs, int n_steps, void* cuda
   return hs_evolve_ex(f, psi, n_rhs, n_steps, nullptr, cuda_stream);
 }
 
+// The launches of a time-dependent evolution. Register sweeps generate their
+// factor values from per-term records, so with the records of every step
+// computed up front (one set per drive sample) a sweep may span steps as in
+// hs_evolve_ex; that holds when every sweep of the n_steps-step schedule is a
+// register sweep (returns true). Otherwise (stored factors, value tables,
+// plain launches) the values change from step to step and sw is one step's
+// launches, repeated.
+static bool plan_td(const hs_factors* f, int n_steps, const hs_evolve_opts& o, int tb, std::vector<hs::Sweep>& sw,
+                    QPlans& qp) {
+  if (o.method == HS_METHOD_REG && n_steps > 1 && n_steps <= 65535) {
+    sw = hs::plan_sweeps(f->plan, n_steps, tb, o.low_bits, true, hs::kMaxFusedDiags, o.max_fuse);
+    plan_reg(f, sw, tb, o.reg_bits, qp, int(f->plan.x.size()) * f->plan.n_kinds);
+    if (!has_plain(sw)) return true;
+  }
+  sw = hs::plan_sweeps(f->plan, 1, tb, o.low_bits, o.method != HS_METHOD_PLAIN, hs::kMaxFusedDiags, o.max_fuse);
+  qp.clear();
+  if (o.method == HS_METHOD_REG) plan_reg(f, sw, tb, o.reg_bits, qp);
+  return false;
+}
+
+int hs_evolve_td_plan(const hs_factors* f, int n_rhs, int n_steps, const hs_evolve_opts* opts, int* n_sweeps,
+                      int* n_plain, int* tile_bits, int* rhs_block) {
+  if (!f) return fail(HS_EINVAL, "factors is NULL");
+  if (!f->bin.coeff1) return fail(HS_EINVAL, "factors are not time-dependent (built without H1 coefficients)");
+  if (n_rhs < 1 || n_steps < 0) return fail(HS_EINVAL, "n_rhs must be >= 1 and n_steps >= 0");
+  hs_evolve_opts o;
+  int tb = 0, rb = 0;
+  int rc = resolve_opts(f, n_rhs, opts, o, tb, rb);
+  if (rc != HS_OK) return rc;
+  int ns = 0, np = 0;
+  if (n_steps > 0) {
+    std::vector<hs::Sweep> sw;
+    QPlans qp;
+    const int reps = plan_td(f, n_steps, o, tb, sw, qp) ? 1 : n_steps;
+    for (const hs::Sweep& w : sw) (w.fused ? ns : np) += reps;
+  }
+  if (n_sweeps) *n_sweeps = ns;
+  if (n_plain) *n_plain = np;
+  if (tile_bits) *tile_bits = tb;
+  if (rhs_block) *rhs_block = rb;
+  return HS_OK;
+}
+
 // Rebuild the values of the groups that depend on the drive for the drive
 // value at d_fval: angles, the value tables of those groups, then the stored
 // diagonals of the listed groups.
-cudaError_t enqueue_drive_rebuild(const hs_factors* f, const double* d_fval, const int* diag_groups, int n_diag,
-                                  cudaStream_t s) {
+static cudaError_t enqueue_drive_rebuild(const hs_factors* f, const double* d_fval, const int* diag_groups,
+                                         int n_diag, cudaStream_t s) {
   const hs_build_inputs& b = f->bin;
   cudaError_t e = hs::launch_sincos(f, d_fval, s);
   if (e == cudaSuccess && b.n_dep_tab > 0) e = hs::launch_value_tables(f, b.dep_tab, b.n_dep_tab, s);
@@ -874,16 +943,15 @@ int hs_evolve_td(hs_factors* f, void* psi, int n_rhs, const double* drive, int n
     if (e != cudaSuccess) return cuda_fail(e, "kernel attributes");
   }
   cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
-  // One step's launches: the values change from step to step, so no sweep
-  // spans a step boundary.
-  std::vector<hs::Sweep> sw = hs::plan_sweeps(f->plan, 1, tb, o.low_bits, o.method != HS_METHOD_PLAIN,
-                                              hs::kMaxFusedDiags, o.max_fuse);
-  QPlans qp;
+  const hs_build_inputs& b = f->bin;
   if (o.method == HS_METHOD_REG) {
     cudaError_t e = hs::q::prepare_qsweep();
     if (e != cudaSuccess) return cuda_fail(e, "kernel attributes");
-    plan_reg(f, sw, tb, o.reg_bits, qp);
   }
+  std::vector<hs::Sweep> sw;
+  QPlans qp;
+  const bool cross = plan_td(f, n_steps, o, tb, sw, qp);
+  const int stride = int(f->plan.x.size()) * f->plan.n_kinds;  // records per step
   const QPlans* qpp = qp.empty() ? nullptr : &qp;
   const bool scratch_needed = has_plain(sw);
   const size_t smem_budget = o.smem_kb > 0 ? size_t(o.smem_kb) * 1024 : hs::kSweepSmemDefault;
@@ -892,27 +960,31 @@ int hs_evolve_td(hs_factors* f, void* psi, int n_rhs, const double* drive, int n
   // rebuilt each step; plain launches and table-free sweeps read diagonals.
   // Register sweeps read value tables, the angles and their cos/sin (all
   // rebuilt each step) and no diagonals, so a schedule of register sweeps
-  // alone rebuilds no diagonals until the end.
-  const hs_build_inputs& b = f->bin;
+  // alone rebuilds no diagonals: they are left to be rebuilt when read.
   const bool reg_only = qpp && !scratch_needed;
   const bool diag_all = !tables || scratch_needed;
   const int* diag_groups = reg_only ? nullptr : (diag_all ? b.dep_all : b.dep_notab);
   const int n_diag = reg_only ? 0 : (diag_all ? b.n_dep_all : b.n_dep_notab);
 
-  // Drive samples in a library-owned device buffer (captured graphs read it).
-  if (f->drive_cap < n_steps) {
+  // Drive samples and per-step records in library-owned device buffers
+  // (captured graphs read them, so growing one drops those graphs).
+  auto drop_td_graphs = [&]() {
+    std::lock_guard<std::mutex> lk(f->graph_mu);
+    bool any = false;
+    for (const auto& kv : f->graphs) any = any || kv.first.variant == 1;
+    if (!any) return;
     cudaStreamSynchronize(s);
-    {
-      std::lock_guard<std::mutex> lk(f->graph_mu);
-      for (auto it = f->graphs.begin(); it != f->graphs.end();) {
-        if (it->first.variant == 1) {
-          cudaGraphExecDestroy(it->second);
-          it = f->graphs.erase(it);
-        } else {
-          ++it;
-        }
+    for (auto it = f->graphs.begin(); it != f->graphs.end();) {
+      if (it->first.variant == 1) {
+        cudaGraphExecDestroy(it->second);
+        it = f->graphs.erase(it);
+      } else {
+        ++it;
       }
     }
+  };
+  if (f->drive_cap < n_steps) {
+    drop_td_graphs();
     if (f->d_drive) cudaFreeAsync(f->d_drive, s);
     f->d_drive = nullptr;
     f->drive_cap = 0;
@@ -921,26 +993,63 @@ int hs_evolve_td(hs_factors* f, void* psi, int n_rhs, const double* drive, int n
     if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(drive)");
     f->drive_cap = cap;
   }
+  const size_t rec_doubles = size_t(6) * stride * n_steps;  // 4 (rq) + 2 (cos, sin) per record
+  if (cross && f->steprec_cap < rec_doubles) {
+    drop_td_graphs();
+    if (f->d_steprec) cudaFreeAsync(f->d_steprec, s);
+    f->d_steprec = nullptr;
+    f->steprec_cap = 0;
+    const size_t cap = std::max(rec_doubles, size_t(6) * stride * 64);
+    cudaError_t e = hs::pool_malloc((void**)&f->d_steprec, cap * sizeof(double), s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(step records)");
+    f->steprec_cap = cap;
+  }
   {
     cudaError_t e = cudaError_t(stage_upload(f->d_drive, drive, size_t(n_steps) * sizeof(double), s));
     if (e != cudaSuccess) return cuda_fail(e, "drive upload");
   }
   auto enqueue_all = [&](cudaStream_t cs, void* scratch) -> int {
+    if (cross) {
+      StepRecords rec;
+      rec.rq = f->d_steprec;
+      rec.cs = f->d_steprec + size_t(4) * stride * n_steps;
+      rec.stride = stride;
+      rec.n_steps = n_steps;
+      cudaError_t e = hs::launch_sincos_steps(f, f->d_drive, n_steps, const_cast<double*>(rec.cs),
+                                              const_cast<double*>(rec.rq), cs);
+      if (e != cudaSuccess) return cuda_fail(e, "step records launch");
+      int rc = enqueue_evolve(f, sw, psi, n_rhs, tb, rb, smem_budget, tables, nullptr, cs, qpp, o.reg_bits, &rec);
+      if (rc != HS_OK) return rc;
+      // The angles and value tables at the last step's drive; the stored
+      // diagonals follow when something reads them (diag_pending below).
+      e = enqueue_drive_rebuild(f, f->d_drive + (n_steps - 1), nullptr, 0, cs);
+      return e == cudaSuccess ? HS_OK : cuda_fail(e, "drive rebuild");
+    }
     for (int k = 0; k < n_steps; ++k) {
       cudaError_t e = enqueue_drive_rebuild(f, f->d_drive + k, diag_groups, n_diag, cs);
       if (e != cudaSuccess) return cuda_fail(e, "drive rebuild");
       int rc = enqueue_evolve(f, sw, psi, n_rhs, tb, rb, smem_budget, tables, scratch, cs, qpp, o.reg_bits);
       if (rc != HS_OK) return rc;
     }
-    // Leave every stored value at the last step's drive.
-    if (reg_only && b.n_dep_all > 0) {
-      cudaError_t e = hs::launch_build_split(f, b.dep_tab, b.n_dep_tab, b.dep_notab, b.n_dep_notab, cs);
-      if (e != cudaSuccess) return cuda_fail(e, "factor build launch");
-    } else if (!diag_all && b.n_dep_tab > 0) {
+    // Leave every stored value at the last step's drive (register sweeps
+    // alone: the angles and tables are; the diagonals follow when read).
+    if (!reg_only && !diag_all && b.n_dep_tab > 0) {
       cudaError_t e = hs::launch_build_split(f, b.dep_tab, b.n_dep_tab, nullptr, 0, cs);
       if (e != cudaSuccess) return cuda_fail(e, "factor build launch");
     }
     return HS_OK;
+  };
+  // Schedules that read stored diagonals need those of every factor current
+  // (a register-sweep evolution before leaves them to be rebuilt on first
+  // read); after one of register sweeps alone they are left that way.
+  if (!reg_only) {
+    cudaError_t e = hs::ensure_diagonals(f, s);
+    if (e != cudaSuccess) return cuda_fail(e, "factor build launch");
+  }
+  auto mark_pending = [&]() {
+    if (!reg_only) return;
+    std::lock_guard<std::mutex> lk(f->diag_mu);
+    f->diag_pending = true;
   };
 
   if (o.use_graph) {
@@ -977,6 +1086,7 @@ int hs_evolve_td(hs_factors* f, void* psi, int n_rhs, const double* drive, int n
     }
     cudaError_t e = cudaGraphLaunch(exec, s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+    mark_pending();
     std::lock_guard<std::mutex> lk2(g_graph_mu);
     hs::note_launches(g_graph_kernels[exec]);
     return HS_OK;
@@ -989,6 +1099,7 @@ int hs_evolve_td(hs_factors* f, void* psi, int n_rhs, const double* drive, int n
   }
   int rc = enqueue_all(s, scratch);
   if (scratch) cudaFreeAsync(scratch, s);
+  if (rc == HS_OK) mark_pending();
   return rc;
 }
 

@@ -468,32 +468,52 @@ __global__ void __launch_bounds__(256) value_table_kernel(BuildArgs a, const uin
 // exp(-i theta P) = cos(theta') (I - i tan(theta') P) (-i P)^k, theta = theta'
 // + k pi / 2 with |theta'| <= pi / 4: tan(theta'), k mod 4, cos(theta') and
 // theta / pi reduced to [-1, 1].
+// The records of term j at angle kind k: theta = c_j h_k with c_j = a_j, or
+// a_j + f b_j (the product rounded before the sum, no fused multiply-add).
+__device__ __forceinline__ void term_records(const double* coeff, const double* coeff1, double fv, const double* h,
+                                             int k, int j, double* th, double* cs, double* rq) {
+  double c = coeff[j];
+  if (coeff1) c = __dadd_rn(c, __dmul_rn(fv, coeff1[j]));
+  const double theta = c * h[k];
+  if (th) *th = theta;
+  double s, co;
+  sincos(theta, &s, &co);
+  cs[0] = co;
+  cs[1] = s;
+  // theta = pi u (mod 2 pi), u in [-1, 1]; u = v + k / 2 with k = rint(2 u)
+  // and |v| <= 1/4 (an exact subtraction), so that
+  // exp(-i theta P) = cos(pi v) (I - i tan(pi v) P) (-i P)^k.
+  const double u0 = theta * 0.318309886183790671537767526745;
+  const double u = u0 - 2.0 * rint(0.5 * u0);
+  const double kh = rint(2.0 * u);
+  const double v = u - 0.5 * kh;
+  double sv, cv;
+  sincospi(v, &sv, &cv);
+  rq[0] = sv / cv;
+  rq[1] = double(int(kh) & 3);
+  rq[2] = cv;
+  rq[3] = u;
+}
+
 __global__ void sincos_kernel(const double* coeff, const double* coeff1, const double* fval, const double* h,
                               int n_kinds, double* cs, double* th, double* rq, int n) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e < n * n_kinds) {
     const int k = e / n, j = e - k * n;
-    double c = coeff[j];
-    if (coeff1) c = __dadd_rn(c, __dmul_rn(fval ? *fval : 0.0, coeff1[j]));
-    const double theta = c * h[k];
-    th[e] = theta;
-    double s, co;
-    sincos(theta, &s, &co);
-    cs[2 * e] = co;
-    cs[2 * e + 1] = s;
-    // theta = pi u (mod 2 pi), u in [-1, 1]; u = v + k / 2 with k = rint(2 u)
-    // and |v| <= 1/4 (an exact subtraction), so that
-    // exp(-i theta P) = cos(pi v) (I - i tan(pi v) P) (-i P)^k.
-    const double u0 = theta * 0.318309886183790671537767526745;
-    const double u = u0 - 2.0 * rint(0.5 * u0);
-    const double kh = rint(2.0 * u);
-    const double v = u - 0.5 * kh;
-    double sv, cv;
-    sincospi(v, &sv, &cv);
-    rq[4 * e] = sv / cv;
-    rq[4 * e + 1] = double(int(kh) & 3);
-    rq[4 * e + 2] = cv;
-    rq[4 * e + 3] = u;
+    term_records(coeff, coeff1, fval ? *fval : 0.0, h, k, j, th + e, cs + 2 * e, rq + 4 * e);
+  }
+}
+
+// One set of records per drive sample: step blockIdx.y at offsets of
+// n * n_kinds records.
+__global__ void sincos_steps_kernel(const double* coeff, const double* coeff1, const double* fval, const double* h,
+                                    int n_kinds, double* cs, double* rq, int n) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int st = blockIdx.y;
+  if (e < n * n_kinds) {
+    const int k = e / n, j = e - k * n;
+    const size_t r = size_t(st) * n * n_kinds + e;
+    term_records(coeff, coeff1, fval[st], h, k, j, nullptr, cs + 2 * r, rq + 4 * r);
   }
 }
 
@@ -517,6 +537,17 @@ cudaError_t launch_sincos(const hs_factors* f, const double* d_fval, cudaStream_
 
 namespace {
 cudaError_t launch_rows(const hs_factors* f, const int* d_groups, int n_groups, int maxdim, cudaStream_t s);
+}
+
+cudaError_t launch_sincos_steps(const hs_factors* f, const double* d_fval, int n_steps, double* cs_out,
+                                double* rq_out, cudaStream_t s) {
+  const hs_build_inputs& b = f->bin;
+  const int n = int(f->plan.x.size());
+  if (n_steps <= 0 || n_steps > 65535) return cudaErrorInvalidValue;
+  sincos_steps_kernel<<<dim3((n * b.n_kinds + 127) / 128, n_steps), 128, 0, s>>>(b.coeff, b.coeff1, d_fval, b.h,
+                                                                                b.n_kinds, cs_out, rq_out, n);
+  note_launches();
+  return cudaGetLastError();
 }
 
 cudaError_t launch_build(const hs_factors* f, const int* d_groups, int n_groups, cudaStream_t s) {

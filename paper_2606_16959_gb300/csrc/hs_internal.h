@@ -107,6 +107,8 @@ struct Sweep {
   bool fused = true;         // tile sweep (true) or plain diagonal-times-vector (false)
   uint32_t local_mask = 0;   // fused: bits held by a tile
   std::vector<int> factors;  // fused: factor ids in order; plain: exactly one
+  std::vector<int> steps;    // the step of each factor application (for a planned register
+                             // sweep: one entry, the step its descriptor's term records start at)
 };
 
 // Plan the launches for n_steps steps with tiles of tile_bits local bits.
@@ -184,6 +186,8 @@ struct hs_factors {
   // that needs them (hs::ensure_diagonals).
   mutable bool diag_pending = false;
   mutable std::mutex diag_mu;
+  double* d_steprec = nullptr;   // per-step term records of register sweeps spanning steps (hs_evolve_td)
+  size_t steprec_cap = 0;        // doubles
   // cached CUDA graphs of evolve launch sequences
   struct GraphKey {
     void* psi;
@@ -203,6 +207,11 @@ namespace hs {
 // f->bin.cs; c_j = a_j, or a_j + f b_j with f read from d_fval when the set is
 // time-dependent (d_fval NULL: f = 0).
 cudaError_t launch_sincos(const hs_factors* f, const double* d_fval, cudaStream_t s);
+// The same per-term records for n_steps drive samples d_fval[0 .. n_steps),
+// step k's (cos, sin) at cs_out + 2 k r and register-sweep records at
+// rq_out + 4 k r, r = terms x angle kinds (one launch).
+cudaError_t launch_sincos_steps(const hs_factors* f, const double* d_fval, int n_steps, double* cs_out,
+                                double* rq_out, cudaStream_t s);
 // Value tables of the listed groups (d_groups NULL: every group with a table).
 cudaError_t launch_value_tables(const hs_factors* f, const int* d_groups, int n_groups, cudaStream_t s);
 // Factor values of the listed groups (d_groups NULL: all); groups with a value

@@ -350,6 +350,7 @@ std::vector<Sweep> plan_sweeps(const Plan& p, int n_steps, int tile_bits, int mi
         Sweep pl;
         pl.fused = false;
         pl.factors.push_back(g);
+        pl.steps.push_back(st);
         out.push_back(std::move(pl));
         continue;
       }
@@ -359,6 +360,7 @@ std::vector<Sweep> plan_sweeps(const Plan& p, int n_steps, int tile_bits, int mi
         used = 0;
       }
       cur.factors.push_back(g);
+      cur.steps.push_back(st);
       used |= span;
     }
   }

@@ -21,6 +21,7 @@ struct HOp {
   int term;               // ROT: term index
   std::vector<int> terms; // PHASE: term indices
   uint32_t need;          // ROT / TAB: local bits the op flips
+  int rs = 0;             // step of the factor application relative to the sweep's first
 };
 
 // Lowest bit of u when u's bits are consecutive (patterns are then a shift and
@@ -44,7 +45,7 @@ uint32_t pext32(uint32_t v, uint32_t m) {
 }  // namespace
 
 bool plan_qsweep(const hs_factors* f, const std::vector<int>& factors, uint32_t local_mask, int T, int B,
-                 Args& a, std::string* why) {
+                 Args& a, std::string* why, const std::vector<int>* steps, int step_stride) {
   const Plan& p = f->plan;
   const int n = p.n_qubits;
   const int m = int(p.x.size());
@@ -78,8 +79,12 @@ bool plan_qsweep(const hs_factors* f, const std::vector<int>& factors, uint32_t 
   auto glob = [&](uint32_t l) -> uint32_t { return (l & a.m0) | ((l & a.m1) << a.sh); };
 
   // 1. Ops of every factor, in application order.
+  if (steps && steps->size() != factors.size()) return fail("one step per factor application");
   std::vector<HOp> ops;
-  for (int g : factors) {
+  for (size_t fi = 0; fi < factors.size(); ++fi) {
+    const int g = factors[fi];
+    const int rs = steps ? (*steps)[fi] - (*steps)[0] : 0;
+    const size_t first_op = ops.size();
     const Group& G = p.groups[g];
     if ((G.span & ~uint64_t(local_mask)) != 0) return fail("factor flips outside the tile");
     // A factor of several terms with a value table of at most two slots (a
@@ -88,6 +93,8 @@ bool plan_qsweep(const hs_factors* f, const std::vector<int>& factors, uint32_t 
     if (G.last - G.first > 1 && G.vt0 >= 0 && G.nslot >= 1 && G.nslot <= 2 && G.vt_n <= kMaxVt) {
       const uint32_t u = G.nslot == 2 ? p.slot_u[G.slot0 + 1] : 0u;
       if (__builtin_popcount(loc(u)) <= 2) {
+        // (value tables hold one step's values: not in a sweep that spans steps)
+        if (steps) return fail("a value-table factor in a sweep over steps");
         ops.push_back(HOp{OP_TAB, g, -1, {}, loc(u)});
         continue;
       }
@@ -109,6 +116,7 @@ bool plan_qsweep(const hs_factors* f, const std::vector<int>& factors, uint32_t 
       ops.push_back(HOp{OP_ROT, g, j, {}, need});
     }
     if (!run.empty()) ops.push_back(HOp{OP_PHASE, g, -1, run, 0});
+    for (size_t k = first_op; k < ops.size(); ++k) ops[k].rs = rs;
   }
 
   // 2. Register layouts: a register op needs its flips (and, for complex64,
@@ -186,7 +194,7 @@ bool plan_qsweep(const hs_factors* f, const std::vector<int>& factors, uint32_t 
   }
   std::map<std::pair<uint32_t, std::vector<int>>, int> lay_id;
   std::map<int, int> rot_id, tab_id;
-  std::map<std::tuple<int, int, uint32_t>, int> phase_id;  // (factor, first term of the run, layout)
+  std::map<std::tuple<int, int, uint32_t, int>, int> phase_id;  // (factor, first term of the run, layout, relative step)
   auto add_layout = [&](uint32_t R, const std::vector<int>& wpos) -> int {
     const auto key = std::make_pair(R, wpos);
     auto it = lay_id.find(key);
@@ -292,7 +300,7 @@ bool plan_qsweep(const hs_factors* f, const std::vector<int>& factors, uint32_t 
     } else if (h.type == OP_ROT || (h.type == OP_PHASE && h.terms.size() == 1)) {
       // (a run of one diagonal term is a diagonal rotation, DROT)
       const int term = h.type == OP_ROT ? h.term : h.terms[0];
-      const int key = G.kind * m + term;
+      const int key = h.rs * step_stride + G.kind * m + term;
       auto it = rot_id.find(key);
       int ri;
       if (it != rot_id.end()) {
@@ -315,7 +323,7 @@ bool plan_qsweep(const hs_factors* f, const std::vector<int>& factors, uint32_t 
       o.zrest = uint32_t(z & ~uint64_t(local_mask));
       o.flags = uint8_t((x != 0 && z == 0 ? 1 : 0) | (((y + 3) & 3) << 1));
     } else {
-      const auto key = std::make_tuple(h.g, h.terms.front(), R);
+      const auto key = std::make_tuple(h.g, h.terms.front(), R, h.rs);
       auto it = phase_id.find(key);
       int pi;
       if (it != phase_id.end()) {
@@ -341,7 +349,8 @@ bool plan_qsweep(const hs_factors* f, const std::vector<int>& factors, uint32_t 
           c.t0 = int16_t(pts.size());
           c.c0p = int16_t(c0p);
           c.mu = int16_t(reg_coords(lpart, R));
-          for (int j : by_local[lpart]) pts.push_back(PTerm{G.kind * m + j, uint32_t(p.z[j] & ~uint64_t(local_mask))});
+          for (int j : by_local[lpart])
+            pts.push_back(PTerm{h.rs * step_stride + G.kind * m + j, uint32_t(p.z[j] & ~uint64_t(local_mask))});
           c.nt = int16_t(int(pts.size()) - c.t0);
           cls.push_back(c);
         };
@@ -409,16 +418,21 @@ bool plan_qsweep(const hs_factors* f, const std::vector<int>& factors, uint32_t 
 }
 
 bool plan_qsweep_runs(const hs_factors* f, const std::vector<int>& factors, uint32_t local_mask, int T, int B,
-                      std::vector<std::pair<std::vector<int>, std::shared_ptr<Args>>>& out, std::string* why) {
+                      std::vector<std::pair<std::vector<int>, std::shared_ptr<Args>>>& out, std::string* why,
+                      const std::vector<int>* steps, int step_stride) {
   auto a = std::make_shared<Args>();
-  if (plan_qsweep(f, factors, local_mask, T, B, *a, why)) {
+  if (plan_qsweep(f, factors, local_mask, T, B, *a, why, steps, step_stride)) {
     out.emplace_back(factors, std::move(a));
     return true;
   }
   if (factors.size() < 2) return false;
   const size_t h = factors.size() / 2;
   const std::vector<int> lo(factors.begin(), factors.begin() + h), hi(factors.begin() + h, factors.end());
-  return plan_qsweep_runs(f, lo, local_mask, T, B, out, why) && plan_qsweep_runs(f, hi, local_mask, T, B, out, why);
+  if (!steps) return plan_qsweep_runs(f, lo, local_mask, T, B, out, why) && plan_qsweep_runs(f, hi, local_mask, T, B, out, why);
+  // each piece addresses its records relative to its own first step
+  const std::vector<int> slo(steps->begin(), steps->begin() + h), shi(steps->begin() + h, steps->end());
+  return plan_qsweep_runs(f, lo, local_mask, T, B, out, why, &slo, step_stride) &&
+         plan_qsweep_runs(f, hi, local_mask, T, B, out, why, &shi, step_stride);
 }
 
 }  // namespace q

@@ -931,12 +931,17 @@ cudaError_t launch_qlevel(hs_dtype dt, int B, bool full, int tile_bits, const Le
 }
 
 cudaError_t launch_qsweep(const hs_factors* f, Args& a, const void* src, void* dst, int n_rhs, int B, bool pdl,
-                          cudaStream_t s) {
+                          cudaStream_t s, const double* rq, const double* cs, int n_terms) {
   const Plan& p = f->plan;
   QFn fn = qsweep_fn(f->dtype, B, a.full != 0, a.tile_bits);
   if (!fn || a.tile_bits - B < 5 || a.tile_bits > p.n_qubits) return cudaErrorInvalidValue;
   fill_job(f, a, const_cast<void*>(src), n_rhs);
   a.dst = dst;
+  if (rq) {
+    a.rq = rq;
+    a.cs = cs;
+    a.n_terms_g = n_terms;
+  }
   // Several tiles per CTA once the grid is large (the per-CTA tables are then
   // loaded once for them), up to eight, keeping at least four waves of two
   // CTAs per SM (eight units per CTA measured 2.7% faster than four on the

@@ -158,14 +158,19 @@ __host__ __device__ __forceinline__ uint32_t swz(uint32_t c) {
 // Host planner: the ops of a fused sweep (factors in order, two-run local mask)
 // for tiles of T bits and B register bits.  Returns false (with a reason) when
 // a factor cannot be expressed as register ops or a limit is exceeded.
+// steps (optional): the step of each factor application, for a sweep that
+// spans steps of a time-dependent set whose terms have one record per step:
+// a term record is then addressed (step - steps[0]) * step_stride + kind * m
+// + term, relative to the records of the sweep's first step.
 bool plan_qsweep(const hs_factors* f, const std::vector<int>& factors, uint32_t local_mask, int T, int B,
-                 Args& a, std::string* why);
+                 Args& a, std::string* why, const std::vector<int>* steps = nullptr, int step_stride = 0);
 
 // The same for a run of factors that may exceed a descriptor's limits: the
 // run is split into consecutive shorter runs (same local mask) until each
 // fits.  Returns false if a single factor cannot be expressed.
 bool plan_qsweep_runs(const hs_factors* f, const std::vector<int>& factors, uint32_t local_mask, int T, int B,
-                      std::vector<std::pair<std::vector<int>, std::shared_ptr<Args>>>& out, std::string* why);
+                      std::vector<std::pair<std::vector<int>, std::shared_ptr<Args>>>& out, std::string* why,
+                      const std::vector<int>* steps = nullptr, int step_stride = 0);
 
 size_t qsweep_smem_bytes(const Args& a, hs_dtype dt, int B);
 
@@ -185,8 +190,11 @@ struct LevelArgs {
 };
 cudaError_t launch_qlevel(hs_dtype dt, int B, bool full, int tile_bits, const LevelArgs& L, int64_t ctas, size_t smem,
                           cudaStream_t s);
+// rq, cs (optional): term records to use instead of the factor set's own
+// (n_terms of them), for a sweep over steps of a time-dependent set.
 cudaError_t launch_qsweep(const hs_factors* f, Args& a, const void* src, void* dst, int n_rhs, int B,
-                          bool pdl, cudaStream_t s);
+                          bool pdl, cudaStream_t s, const double* rq = nullptr, const double* cs = nullptr,
+                          int n_terms = 0);
 cudaError_t prepare_qsweep();
 
 }  // namespace q

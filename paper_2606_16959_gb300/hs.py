@@ -28,7 +28,7 @@ LIB_PATH = os.path.join(_HERE, "_build_debug" if DEBUG_BOUNDS else "_build", "li
 EXPORTS = (
     "hs_build_factors", "hs_build_factors_masks", "hs_evolve", "hs_evolve_ex", "hs_apply_factor",
     "hs_fidelity", "hs_inner_device", "hs_factors_info", "hs_factor_get", "hs_free_factors", "hs_last_error",
-    "hs_plan_factors", "hs_evolve_plan", "hs_inner_batch_noalloc", "hs_autotune",
+    "hs_plan_factors", "hs_evolve_plan", "hs_evolve_td_plan", "hs_inner_batch_noalloc", "hs_autotune",
     "hs_batch_create", "hs_batch_launch", "hs_batch_info", "hs_batch_free", "hs_free_factors_async",
     "hs_batch_free_async",
     "hs_dia_from_terms", "hs_dia_from_masks", "hs_dia_create", "hs_spgemm", "hs_spme", "hs_estimate_timesteps",
@@ -91,6 +91,7 @@ def lib() -> ctypes.CDLL:
         L.hs_plan_factors.argtypes = [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64), sz, i, i, i,
                                       ip, ip, ip, ip, ip, i64p, i64p, i, i]
         L.hs_evolve_plan.argtypes = [vp, i, i, ctypes.POINTER(EvolveOpts), ip, ip, ip, ip]
+        L.hs_evolve_td_plan.argtypes = [vp, i, i, ctypes.POINTER(EvolveOpts), ip, ip, ip, ip]
         L.hs_inner_batch_noalloc.argtypes = [vp, vp, i, i, i, vp, vp]
         L.hs_autotune.argtypes = [vp, vp, i, i, vp, ctypes.POINTER(EvolveOpts)]
         L.hs_batch_create.argtypes = [ctypes.POINTER(BatchJob), sz, ctypes.POINTER(BatchOpts), ctypes.POINTER(vp)]
@@ -371,6 +372,18 @@ def hs_evolve_plan(f: Factors, n_rhs: int, n_steps: int, method: int = HS_METHOD
     a, b, c, d = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     _check(lib().hs_evolve_plan(f.handle, int(n_rhs), int(n_steps), ctypes.byref(o), ctypes.byref(a), ctypes.byref(b),
                                 ctypes.byref(c), ctypes.byref(d)))
+    return a.value, b.value, c.value, d.value
+
+
+def hs_evolve_td_plan(f: Factors, n_rhs: int, n_steps: int, method: int = HS_METHOD_AUTO, tile_bits: int = 0,
+                      rhs_block: int = 0, use_graph: bool = False, low_bits: int = 0, max_fuse: int = 0,
+                      smem_kb: int = 0, no_tables: bool = False, reg_bits: int = 0):
+    """(n_sweep_launches, n_plain_launches, tile_bits, rhs_block) of a whole hs_evolve_td
+    of n_steps steps."""
+    o = _opts(method, tile_bits, rhs_block, use_graph, low_bits, max_fuse, smem_kb, no_tables, reg_bits)
+    a, b, c, d = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().hs_evolve_td_plan(f.handle, int(n_rhs), int(n_steps), ctypes.byref(o), ctypes.byref(a),
+                                   ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)))
     return a.value, b.value, c.value, d.value
 
 

@@ -212,6 +212,40 @@ def test_reg_time_dependent_and_graph():
                 f.close()
 
 
+def test_reg_time_dependent_sweeps_span_steps():
+    """Register sweeps of a time-dependent set read per-step term records, so
+    a sweep spans steps as in the time-independent schedule: the launches are
+    that schedule's sweeps plus the record and end-of-run rebuild kernels, and
+    the result matches the oracle at every step count (a sweep that starts
+    mid-run included)."""
+    rng = np.random.default_rng(4107)
+    ham = W.anneal_maxcut(16, seed=78)
+    x, z, n = O.parse_terms(ham.labels)
+    t = 1.1
+    for steps in (2, 7, 12):
+        fv = W.midpoint_samples(lambda s: 0.3 + np.sin(1.7 * s), t, steps)
+        psi0 = W.gaussian_state(n, rng)
+        want = O.evolve_direct_td(x, z, ham.a, ham.b, fv, t, psi0[None], 1)
+        f = hs.hs_build_factors_td(x, z, ham.a, ham.b, n, t, steps, 4, "c64")
+        n_sw, n_plain, _, _ = hs.hs_evolve_td_plan(f, 1, steps, method=REG)
+        assert n_plain == 0
+        if steps >= 7:  # fewer launches than one step's schedule repeated
+            assert n_sw < steps * hs.hs_evolve_td_plan(f, 1, 1, method=REG)[0]
+        psi = torch.from_numpy(psi0[None]).to("cuda", torch.complex64)
+        torch.cuda.synchronize()
+        before = hs.hs_kernel_launches()
+        hs.hs_evolve_td(f, psi, fv, method=REG)
+        torch.cuda.synchronize()
+        used = hs.hs_kernel_launches() - before
+        assert used <= n_sw + 5, (steps, used, n_sw)
+        _check(psi.cpu().numpy(), want, "c64", f"anneal16 td steps={steps}")
+        f.close()
+    g = hs.hs_build_factors(ham.labels, ham.a, t, 4, 4, "c64")
+    with pytest.raises(hs.HSError):
+        hs.hs_evolve_td_plan(g, 1, 4, method=REG)  # a static set
+    g.close()
+
+
 def test_reg_graph_replay_and_steps_compose():
     rng = np.random.default_rng(4106)
     ham = W.tfim_chain(15, 1.0, 0.8)

@@ -62,7 +62,10 @@ def test_td_matches_oracle(order, dt):
         psi = np.stack([W.gaussian_state(n, rng) for _ in range(2)])
         want = O.evolve_direct_td(x, z, ham.a, ham.b, fv, t, psi, order)
         f = hs.hs_build_factors_td(x, z, ham.a, ham.b, n, t, steps, budget, dt, order=order)
-        for kw in (dict(), dict(method=hs.HS_METHOD_PLAIN), dict(use_graph=True), dict(no_tables=True),
+        # register sweeps first: they leave the stored diagonals to be rebuilt
+        # on first read, which the schedules after them do
+        for kw in (dict(method=hs.HS_METHOD_REG), dict(method=hs.HS_METHOD_REG, use_graph=True),
+                   dict(), dict(method=hs.HS_METHOD_PLAIN), dict(use_graph=True), dict(no_tables=True),
                    dict(method=hs.HS_METHOD_FUSED, tile_bits=8, rhs_block=1, low_bits=1)):
             pd = torch.from_numpy(psi).to("cuda", tdt)
             hs.hs_evolve_td(f, pd, fv, **kw)
