@@ -156,6 +156,28 @@ int hs_plan_factors(const uint64_t* x, const uint64_t* z, size_t n_terms, int n_
                     hs_dtype dtype, int* n_factors, int* n_offsets, int* group_first, int* group_last, int* n_diags,
                     int64_t* offsets, int64_t* value_bytes, int capacity_factors, int capacity_offsets);
 
+/* Host-only launch schedule of n_steps steps (no GPU call): the factor
+ * applications in the order the sweeps apply them, with the factors grouped
+ * and stored as hs_build_factors_ex(order) would, tiles of tile_bits local
+ * qubits keeping the low_bits lowest ones, at most max_fuse (0 = 64)
+ * applications per sweep.  commuting = 0: the formula's order, each sweep a
+ * run of consecutive applications (the staged sweep's schedule); 1: the
+ * register sweep's schedule, in which a sweep may also take a later
+ * application that commutes with every application it passes over (each
+ * Pauli term of the one commutes with each term of the other), so that the
+ * product is the formula's up to the order of commuting factors (the
+ * product formula of Sec. 2 applies the same factors; only their rounding
+ * differs).  A factor that does not fit a tile is a sweep of its own.
+ * Outputs: *n_apps (= n_steps x step length) and *n_sweeps always; if the
+ * three arrays are non-NULL and capacity >= *n_apps, application k is factor
+ * app_factor[k] (an index for hs_factor_get; it holds the terms of group
+ * app_factor[k] mod G, G the count hs_plan_factors gives) of step
+ * app_step[k], applied by sweep sweep_of[k] (nondecreasing).  Errors:
+ * HS_EINVAL, HS_EDTYPE. */
+int hs_plan_schedule(const uint64_t* x, const uint64_t* z, size_t n_terms, int n_qubits, int diag_budget, int order,
+                     hs_dtype dtype, int n_steps, int tile_bits, int low_bits, int max_fuse, int commuting,
+                     int* n_apps, int* n_sweeps, int* app_factor, int* app_step, int* sweep_of, int capacity);
+
 /* Evolve psi in place by n_steps Trotter steps: for each step, apply the
  * factors F_0, ..., F_{G-1} in order (Alg. 3's loop, x <- U x, with U the
  * ordered product of the grouped factors).  psi: device buffer of n_rhs

@@ -124,6 +124,16 @@ int enqueue_evolve(const hs_factors* f, const std::vector<hs::Sweep>& sw, void* 
   return HS_OK;
 }
 
+// The launch schedule of n_steps steps: register sweeps may take commuting
+// factor applications out of order (hs::plan_sweeps_commuting); the other
+// methods apply the factors in the formula's order.
+std::vector<hs::Sweep> schedule(const hs_factors* f, int n_steps, const hs_evolve_opts& o, int tb) {
+  if (o.method == HS_METHOD_REG)
+    return hs::plan_sweeps_commuting(f->plan, n_steps, tb, o.low_bits, hs::kMaxFusedDiags, o.max_fuse);
+  return hs::plan_sweeps(f->plan, n_steps, tb, o.low_bits, o.method != HS_METHOD_PLAIN, hs::kMaxFusedDiags,
+                         o.max_fuse);
+}
+
 bool has_plain(const std::vector<hs::Sweep>& sw) {
   for (const hs::Sweep& w : sw)
     if (!w.fused) return true;
@@ -686,6 +696,36 @@ int hs_plan_factors(const uint64_t* x, const uint64_t* z, size_t n_terms, int n_
   return HS_OK;
 }
 
+int hs_plan_schedule(const uint64_t* x, const uint64_t* z, size_t n_terms, int n_qubits, int diag_budget, int order,
+                     hs_dtype dtype, int n_steps, int tile_bits, int low_bits, int max_fuse, int commuting,
+                     int* n_apps, int* n_sweeps, int* app_factor, int* app_step, int* sweep_of, int capacity) {
+  if (!x || !z || !n_apps || !n_sweeps) return fail(HS_EINVAL, "null argument");
+  if (!valid_dtype(dtype)) return fail(HS_EDTYPE, "dtype must be HS_C64 or HS_C128");
+  if (n_steps < 0 || n_steps > 65535) return fail(HS_EINVAL, "n_steps must be 0..65535");
+  if (tile_bits < 1 || low_bits < 0 || low_bits > tile_bits) return fail(HS_EINVAL, "tile_bits / low_bits out of range");
+  hs::Plan p;
+  std::string err;
+  int rc = hs::make_plan(x, z, nullptr, n_terms, n_qubits, diag_budget, dtype, p, &err, order);
+  if (rc != HS_OK) return fail(rc, err);
+  if (max_fuse <= 0 || max_fuse > hs::kMaxSweepFactors) max_fuse = hs::kMaxSweepFactors;
+  const std::vector<hs::Sweep> sw =
+      commuting ? hs::plan_sweeps_commuting(p, n_steps, tile_bits, low_bits, hs::kMaxFusedDiags, max_fuse)
+                : hs::plan_sweeps(p, n_steps, tile_bits, low_bits, true, hs::kMaxFusedDiags, max_fuse);
+  int k = 0;
+  const bool fill = app_factor && app_step && sweep_of &&
+                    int64_t(capacity) >= int64_t(n_steps) * int64_t(p.step_seq.size());
+  for (size_t w = 0; w < sw.size(); ++w)
+    for (size_t i = 0; i < sw[w].factors.size(); ++i, ++k)
+      if (fill) {
+        app_factor[k] = sw[w].factors[i];
+        app_step[k] = sw[w].steps[i];
+        sweep_of[k] = int(w);
+      }
+  *n_apps = k;
+  *n_sweeps = int(sw.size());
+  return HS_OK;
+}
+
 // Resolve evolve options: method, tile bits, rhs block, low bits.
 int resolve_opts(const hs_factors* f, int n_rhs, const hs_evolve_opts* opts, hs_evolve_opts& o, int& tb, int& rb) {
   o = hs_evolve_opts{HS_METHOD_AUTO, 0, 0, 0, 0, 0, 0, 0};
@@ -747,8 +787,7 @@ int hs_evolve_plan(const hs_factors* f, int n_rhs, int n_steps, const hs_evolve_
   int tb = 0, rb = 0;
   int rc = resolve_opts(f, n_rhs, opts, o, tb, rb);
   if (rc != HS_OK) return rc;
-  std::vector<hs::Sweep> sw = hs::plan_sweeps(f->plan, n_steps, tb, o.low_bits, o.method != HS_METHOD_PLAIN,
-                                              hs::kMaxFusedDiags, o.max_fuse);
+  std::vector<hs::Sweep> sw = schedule(f, n_steps, o, tb);
   QPlans qp;
   if (o.method == HS_METHOD_REG) plan_reg(f, sw, tb, o.reg_bits, qp);
   int ns = 0, np = 0;
@@ -778,8 +817,7 @@ int hs_evolve_ex(const hs_factors* f, void* psi, int n_rhs, int n_steps, const h
   }
   cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
   const size_t state_bytes = size_t(n_rhs) * size_t(f->plan.N) * hs::elem_bytes(f->dtype);
-  std::vector<hs::Sweep> sw = hs::plan_sweeps(f->plan, n_steps, tb, o.low_bits, o.method != HS_METHOD_PLAIN,
-                                              hs::kMaxFusedDiags, o.max_fuse);
+  std::vector<hs::Sweep> sw = schedule(f, n_steps, o, tb);
   QPlans qp;
   if (o.method == HS_METHOD_REG) {
     cudaError_t e = hs::q::prepare_qsweep();
@@ -860,11 +898,11 @@ int hs_evolve(const hs_factors* f, void* psi, int n_rhs, int n_steps, void* cuda
 static bool plan_td(const hs_factors* f, int n_steps, const hs_evolve_opts& o, int tb, std::vector<hs::Sweep>& sw,
                     QPlans& qp) {
   if (o.method == HS_METHOD_REG && n_steps > 1 && n_steps <= 65535) {
-    sw = hs::plan_sweeps(f->plan, n_steps, tb, o.low_bits, true, hs::kMaxFusedDiags, o.max_fuse);
+    sw = schedule(f, n_steps, o, tb);
     plan_reg(f, sw, tb, o.reg_bits, qp, int(f->plan.x.size()) * f->plan.n_kinds);
     if (!has_plain(sw)) return true;
   }
-  sw = hs::plan_sweeps(f->plan, 1, tb, o.low_bits, o.method != HS_METHOD_PLAIN, hs::kMaxFusedDiags, o.max_fuse);
+  sw = schedule(f, 1, o, tb);
   qp.clear();
   if (o.method == HS_METHOD_REG) plan_reg(f, sw, tb, o.reg_bits, qp);
   return false;

@@ -357,7 +357,7 @@ int create_reg_batch(const hs_batch_job* jobs, size_t n_jobs, const hs_batch_opt
     P.Tj = std::min(T, n);
     bool ok = n >= B + 5;
     std::vector<hs::Sweep> sw;
-    if (ok) sw = hs::plan_sweeps(p, J.n_steps, P.Tj, lb, true);
+    if (ok) sw = hs::plan_sweeps_commuting(p, J.n_steps, P.Tj, lb);
     for (const hs::Sweep& w : sw) ok = ok && w.fused;
     std::map<std::pair<uint32_t, std::vector<int>>, std::vector<int>> memo;  // sweep -> its pieces
     for (size_t k = 0; ok && k < sw.size(); ++k) {

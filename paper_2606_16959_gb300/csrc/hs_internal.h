@@ -116,6 +116,13 @@ struct Sweep {
 // fit a tile, get plain launches.
 std::vector<Sweep> plan_sweeps(const Plan& p, int n_steps, int tile_bits, int min_low_bits, bool fused,
                                int max_fused_diags = kMaxFusedDiags, int max_fuse = kMaxSweepFactors);
+// As plan_sweeps with fused = true, but a sweep may also take later factor
+// applications that commute with every application they pass over (up to two
+// steps past the last one it takes), so the product is the formula's up to the
+// order of commuting factors; the in-order schedule where that has no more
+// sweeps. The steps of a sweep's applications are nondecreasing.
+std::vector<Sweep> plan_sweeps_commuting(const Plan& p, int n_steps, int tile_bits, int min_low_bits,
+                                         int max_fused_diags = kMaxFusedDiags, int max_fuse = kMaxSweepFactors);
 
 // Decompose a bit mask into runs of consecutive set bits (low to high).
 Runs runs_of(uint64_t mask, int n_bits);

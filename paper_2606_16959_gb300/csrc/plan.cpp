@@ -325,6 +325,92 @@ uint64_t two_run_mask(uint64_t used, int n, int T, int low_bits) {
   return 0;
 }
 
+namespace {
+
+// Factors g and h commute when every term of one commutes with every term of
+// the other (Pauli strings (x1, z1) and (x2, z2) commute iff
+// |x1 & z2| + |z1 & x2| is even): then so do their exponentials.
+std::vector<char> commute_table(const Plan& p) {
+  const int G = int(p.groups.size());
+  std::vector<char> c(size_t(G) * G, 1);
+  for (int g = 0; g < G; ++g)
+    for (int h = g + 1; h < G; ++h) {
+      bool ok = true;
+      for (int i = p.groups[g].first; ok && i < p.groups[g].last; ++i)
+        for (int j = p.groups[h].first; ok && j < p.groups[h].last; ++j)
+          ok = (__builtin_popcountll((p.x[i] & p.z[j]) ^ (p.z[i] & p.x[j])) & 1) == 0;
+      c[size_t(g) * G + h] = c[size_t(h) * G + g] = ok;
+    }
+  for (int g = 0; g < G; ++g) {  // a factor and a later application of it: only if its own terms commute
+    bool ok = true;
+    for (int i = p.groups[g].first; ok && i < p.groups[g].last; ++i)
+      for (int j = i + 1; ok && j < p.groups[g].last; ++j)
+        ok = (__builtin_popcountll((p.x[i] & p.z[j]) ^ (p.z[i] & p.x[j])) & 1) == 0;
+    c[size_t(g) * G + g] = ok;
+  }
+  return c;
+}
+
+}  // namespace
+
+std::vector<Sweep> plan_sweeps_commuting(const Plan& p, int n_steps, int tile_bits, int min_low_bits,
+                                         int max_fused_diags, int max_fuse) {
+  if (max_fuse < 1 || max_fuse > kMaxSweepFactors) max_fuse = kMaxSweepFactors;
+  const int n = p.n_qubits;
+  tile_bits = std::min(tile_bits, n);
+  const int G = int(p.groups.size());
+  const std::vector<char> comm = commute_table(p);
+  const int per_step = int(p.step_seq.size());
+  const int L = n_steps * per_step;
+  auto fits_alone = [&](int g) {
+    return p.groups[g].D <= max_fused_diags && p.groups[g].nslot > 0 && min_low_bits <= tile_bits &&
+           two_run_mask(p.groups[g].span, n, tile_bits, min_low_bits) != 0;
+  };
+  // Applications in the formula's order; a sweep takes the first one not yet
+  // applied and then every later one that fits its tile and commutes with all
+  // the applications it passes over (those stay, in order, for later sweeps),
+  // looking at most two steps past the last one it took.
+  std::vector<char> done(size_t(L), 0);
+  std::vector<Sweep> out;
+  int head = 0;
+  while (head < L) {
+    const int g0 = p.step_seq[head % per_step];
+    if (!fits_alone(g0)) {
+      Sweep pl;
+      pl.fused = false;
+      pl.factors.push_back(g0);
+      pl.steps.push_back(head / per_step);
+      out.push_back(std::move(pl));
+      done[head] = 1;
+    } else {
+      Sweep cur;
+      uint64_t used = 0;
+      std::vector<int> passed;  // factor ids passed over
+      int last = head;
+      for (int i = head; i < L && i - last <= 2 * per_step && int(cur.factors.size()) < max_fuse; ++i) {
+        if (done[i]) continue;
+        const int g = p.step_seq[i % per_step];
+        bool take = fits_alone(g) && two_run_mask(used | p.groups[g].span, n, tile_bits, min_low_bits) != 0;
+        for (size_t k = 0; take && k < passed.size(); ++k) take = comm[size_t(g) * G + passed[k]] != 0;
+        if (take) {
+          cur.factors.push_back(g);
+          cur.steps.push_back(i / per_step);
+          used |= p.groups[g].span;
+          done[i] = 1;
+          last = i;
+        } else {
+          passed.push_back(g);
+        }
+      }
+      cur.local_mask = uint32_t(two_run_mask(used, n, tile_bits, min_low_bits));
+      out.push_back(std::move(cur));
+    }
+    while (head < L && done[head]) ++head;
+  }
+  std::vector<Sweep> in_order = plan_sweeps(p, n_steps, tile_bits, min_low_bits, true, max_fused_diags, max_fuse);
+  return in_order.size() <= out.size() ? in_order : out;
+}
+
 std::vector<Sweep> plan_sweeps(const Plan& p, int n_steps, int tile_bits, int min_low_bits, bool fused,
                                int max_fused_diags, int max_fuse) {
   if (max_fuse < 1 || max_fuse > kMaxSweepFactors) max_fuse = kMaxSweepFactors;

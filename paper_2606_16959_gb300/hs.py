@@ -28,7 +28,7 @@ LIB_PATH = os.path.join(_HERE, "_build_debug" if DEBUG_BOUNDS else "_build", "li
 EXPORTS = (
     "hs_build_factors", "hs_build_factors_masks", "hs_evolve", "hs_evolve_ex", "hs_apply_factor",
     "hs_fidelity", "hs_inner_device", "hs_factors_info", "hs_factor_get", "hs_free_factors", "hs_last_error",
-    "hs_plan_factors", "hs_evolve_plan", "hs_evolve_td_plan", "hs_inner_batch_noalloc", "hs_autotune",
+    "hs_plan_factors", "hs_plan_schedule", "hs_evolve_plan", "hs_evolve_td_plan", "hs_inner_batch_noalloc", "hs_autotune",
     "hs_batch_create", "hs_batch_launch", "hs_batch_info", "hs_batch_free", "hs_free_factors_async",
     "hs_batch_free_async",
     "hs_dia_from_terms", "hs_dia_from_masks", "hs_dia_create", "hs_spgemm", "hs_spme", "hs_estimate_timesteps",
@@ -90,6 +90,8 @@ def lib() -> ctypes.CDLL:
         ip, i64p = ctypes.POINTER(i), ctypes.POINTER(ctypes.c_int64)
         L.hs_plan_factors.argtypes = [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64), sz, i, i, i,
                                       ip, ip, ip, ip, ip, i64p, i64p, i, i]
+        L.hs_plan_schedule.argtypes = [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64), sz, i, i, i,
+                                       i, i, i, i, i, i, ip, ip, ip, ip, ip, i]
         L.hs_evolve_plan.argtypes = [vp, i, i, ctypes.POINTER(EvolveOpts), ip, ip, ip, ip]
         L.hs_evolve_td_plan.argtypes = [vp, i, i, ctypes.POINTER(EvolveOpts), ip, ip, ip, ip]
         L.hs_inner_batch_noalloc.argtypes = [vp, vp, i, i, i, vp, vp]
@@ -465,6 +467,24 @@ def hs_plan_factors(x, z, n_qubits: int, diag_budget: int, dtype="c64"):
         out.append((int(gf[g]), int(gl[g]), [int(o) for o in offs[k:k + nd[g]]]))
         k += int(nd[g])
     return out, int(vb.value)
+
+
+def hs_plan_schedule(x, z, n_qubits: int, diag_budget: int, n_steps: int, tile_bits: int, low_bits: int,
+                     order: int = 1, dtype="c64", max_fuse: int = 0, commuting: bool = True):
+    """Host-only launch schedule (no GPU): arrays (factor, step, sweep) per factor
+    application, in the order the sweeps apply them."""
+    xa = np.ascontiguousarray(np.asarray(x, dtype=np.uint64))
+    za = np.ascontiguousarray(np.asarray(z, dtype=np.uint64))
+    code = HS_C64 if dtype in ("c64", HS_C64) else HS_C128
+    na, ns = ctypes.c_int(), ctypes.c_int()
+    args = (xa.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), za.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+            xa.size, int(n_qubits), int(diag_budget), int(order), code, int(n_steps), int(tile_bits), int(low_bits),
+            int(max_fuse), int(bool(commuting)), ctypes.byref(na), ctypes.byref(ns))
+    _check(lib().hs_plan_schedule(*args, None, None, None, 0))
+    fac, st, sw = (np.zeros(na.value, dtype=np.int32) for _ in range(3))
+    ip = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    _check(lib().hs_plan_schedule(*args, ip(fac), ip(st), ip(sw), na.value))
+    return fac, st, sw
 
 
 def hs_inner_batch_noalloc(a, b, out, stream=None) -> None:
