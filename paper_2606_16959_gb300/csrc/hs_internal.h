@@ -80,7 +80,13 @@ struct Plan {
   std::vector<uint32_t> slot_u;   // per slot: its x-mask
   std::vector<int32_t> slot_tab;  // per slot: first entry in tab_rb (one sentinel at the end)
   std::vector<int64_t> tab_rb;    // per (slot, row pattern): row-indexed base of the diagonal
+  int g0 = 0;                     // groups of the first-order grouping (factor g holds group g mod g0)
+  std::vector<char> commute;      // g0 x g0: the groups' terms commute pairwise (empty above
+                                  // kMaxCommuteGroups groups)
 };
+
+// Largest grouping for which the plan records which groups commute.
+constexpr int kMaxCommuteGroups = 2048;
 
 // Parse labels into masks.  Returns HS_OK or HS_EINVAL (message in *err).
 int parse_labels(const char* const* labels, size_t n, std::vector<uint64_t>& x, std::vector<uint64_t>& z,

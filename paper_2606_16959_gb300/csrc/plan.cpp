@@ -290,6 +290,28 @@ int make_plan(const uint64_t* x, const uint64_t* z, const double* coeff, size_t 
   // the last diagonal stays inside the allocation.
   plan.total_elems = cursor + A;
   plan.slot_tab.push_back(int32_t(plan.tab_rb.size()));
+
+  // Which groups commute: g and h do when every term of one commutes with
+  // every term of the other (Pauli strings (x1, z1) and (x2, z2) commute iff
+  // |x1 & z2| + |z1 & x2| is even), and then so do their exponentials; the
+  // entry of g with itself says whether its own terms commute pairwise (then
+  // its factors at any angle and in either term order commute).
+  plan.g0 = G0;
+  if (G0 <= kMaxCommuteGroups) {
+    plan.commute.assign(size_t(G0) * G0, 1);
+    auto terms_commute = [&](int i, int j) {
+      return (__builtin_popcountll((x[i] & z[j]) ^ (z[i] & x[j])) & 1) == 0;
+    };
+    for (int g = 0; g < G0; ++g)
+      for (int h = g; h < G0; ++h) {
+        const Group& A = plan.groups[g];
+        const Group& B = plan.groups[h];
+        bool ok = true;
+        for (int i = A.first; ok && i < A.last; ++i)
+          for (int j = (g == h ? i + 1 : B.first); ok && j < B.last; ++j) ok = terms_commute(i, j);
+        plan.commute[size_t(g) * G0 + h] = plan.commute[size_t(h) * G0 + g] = ok;
+      }
+  }
   return HS_OK;
 }
 
@@ -325,42 +347,16 @@ uint64_t two_run_mask(uint64_t used, int n, int T, int low_bits) {
   return 0;
 }
 
-namespace {
-
-// Factors g and h commute when every term of one commutes with every term of
-// the other (Pauli strings (x1, z1) and (x2, z2) commute iff
-// |x1 & z2| + |z1 & x2| is even): then so do their exponentials.
-std::vector<char> commute_table(const Plan& p) {
-  const int G = int(p.groups.size());
-  std::vector<char> c(size_t(G) * G, 1);
-  for (int g = 0; g < G; ++g)
-    for (int h = g + 1; h < G; ++h) {
-      bool ok = true;
-      for (int i = p.groups[g].first; ok && i < p.groups[g].last; ++i)
-        for (int j = p.groups[h].first; ok && j < p.groups[h].last; ++j)
-          ok = (__builtin_popcountll((p.x[i] & p.z[j]) ^ (p.z[i] & p.x[j])) & 1) == 0;
-      c[size_t(g) * G + h] = c[size_t(h) * G + g] = ok;
-    }
-  for (int g = 0; g < G; ++g) {  // a factor and a later application of it: only if its own terms commute
-    bool ok = true;
-    for (int i = p.groups[g].first; ok && i < p.groups[g].last; ++i)
-      for (int j = i + 1; ok && j < p.groups[g].last; ++j)
-        ok = (__builtin_popcountll((p.x[i] & p.z[j]) ^ (p.z[i] & p.x[j])) & 1) == 0;
-    c[size_t(g) * G + g] = ok;
-  }
-  return c;
-}
-
-}  // namespace
 
 std::vector<Sweep> plan_sweeps_commuting(const Plan& p, int n_steps, int tile_bits, int min_low_bits,
                                          int max_fused_diags, int max_fuse) {
   if (max_fuse < 1 || max_fuse > kMaxSweepFactors) max_fuse = kMaxSweepFactors;
   const int n = p.n_qubits;
   tile_bits = std::min(tile_bits, n);
-  const int G = int(p.groups.size());
-  const std::vector<char> comm = commute_table(p);
+  const int G0 = p.g0;
   const int per_step = int(p.step_seq.size());
+  if (p.commute.empty() || int64_t(n_steps) * per_step > (int64_t(1) << 26))  // no table, or too long to mark
+    return plan_sweeps(p, n_steps, tile_bits, min_low_bits, true, max_fused_diags, max_fuse);
   const int L = n_steps * per_step;
   auto fits_alone = [&](int g) {
     return p.groups[g].D <= max_fused_diags && p.groups[g].nslot > 0 && min_low_bits <= tile_bits &&
@@ -391,7 +387,8 @@ std::vector<Sweep> plan_sweeps_commuting(const Plan& p, int n_steps, int tile_bi
         if (done[i]) continue;
         const int g = p.step_seq[i % per_step];
         bool take = fits_alone(g) && two_run_mask(used | p.groups[g].span, n, tile_bits, min_low_bits) != 0;
-        for (size_t k = 0; take && k < passed.size(); ++k) take = comm[size_t(g) * G + passed[k]] != 0;
+        for (size_t k = 0; take && k < passed.size(); ++k)
+          take = p.commute[size_t(g % G0) * G0 + passed[k] % G0] != 0;
         if (take) {
           cur.factors.push_back(g);
           cur.steps.push_back(i / per_step);
