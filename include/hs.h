@@ -198,8 +198,11 @@ typedef enum {
                           it, any other factor is applied term by term (exact rotations from the build's
                           FP64 cos/sin, runs of diagonal terms as phases generated from (z_j, theta_j) per
                           row, the future-work fusion of the factor values into the apply), so no stored
-                          diagonal is read.  A sweep with a term that flips more than two qubits falls back
-                          to PLAIN launches.  Needs n_qubits >= reg_bits + 5; smaller states use FUSED. */
+                          diagonal is read.  A sweep may apply a factor ahead of earlier ones whose terms
+                          all commute with its terms (hs_plan_schedule, commuting = 1): the same product
+                          up to rounding, with fewer sweeps.  A sweep with a term that flips more than two
+                          qubits falls back to PLAIN launches.  Needs n_qubits >= reg_bits + 5; smaller
+                          states use FUSED. */
 } hs_method;
 
 typedef struct {
