@@ -370,11 +370,11 @@ std::vector<Sweep> plan_sweeps_commuting(const Plan& p, int n_steps, int tile_bi
   std::vector<Sweep> out;
   int head = 0;
   while (head < L) {
-    const int g0 = p.step_seq[head % per_step];
-    if (!fits_alone(g0)) {
+    const int gh = p.step_seq[head % per_step];
+    if (!fits_alone(gh)) {
       Sweep pl;
       pl.fused = false;
-      pl.factors.push_back(g0);
+      pl.factors.push_back(gh);
       pl.steps.push_back(head / per_step);
       out.push_back(std::move(pl));
       done[head] = 1;
